@@ -1,0 +1,386 @@
+#!/usr/bin/env python3
+"""Throughput of QFactor-Sample instantiation on GB300: converged
+instantiations per second at cost <= 1e-8, and the sweep's HBM bandwidth
+against the measured peak.
+
+Workload (default): n = 12 qubits, brick wall of 17 two-qubit U(4) gates
+(three half-layers), target built from Haar-random gates in the same
+structure, M = 32 orthonormal training states, 32 multistarts, complex64
+sweeps with FP64 SVD, master gates, cost check and refinement, tol 1e-8,
+at most 500 sweeps.  One step = one full instantiation of one target (a new
+target per step).  Inputs are synthetic and seeded (the paper's benchmark
+circuits are not available); the B list (512 MiB) exceeds L2, so no flush
+is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank instantiates its own targets (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "converged instantiations/s at cost<=1e-8"
+UNIT = "instantiations/s"
+
+WORKLOADS = {
+    # name: (factory name, precision, description)
+    "brick_n12": ("brick_n12", 1, "n=12 brick wall 17 gates, M=32, 32 starts, complex64 sweeps + FP64 SVD/refine/check"),
+    "brick_n8": ("brick_n8", 0, "n=8 brick wall 28 gates, M=16, 16 starts, FP64"),
+    "chain_n3": ("chain_n3", 0, "n=3 chain of 4 gates, M=4, 1 start, FP64, tol 1e-10"),
+}
+HW_BAD = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown")
+
+
+def _problem(kind, seed):
+    from paper_2405_12866_gb300 import workloads as w
+    fac = getattr(w, WORKLOADS[kind][0])
+    return fac(target_seed=seed) if kind != "chain_n3" else w.chain_n3(target_seed=seed + 1)
+
+
+# ------------------------------------------------------------- env / ranks
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi clock and throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def traffic_record(kernel_src_hash):
+    """DRAM bytes per launch of the dominant kernel from a committed ncu summary,
+    used only while the kernel source is unchanged since the capture."""
+    path = os.path.join(ROOT, "profiles", "backward_traffic.json")
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    if d.get("source_sha256") != kernel_src_hash:
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("kernels_sweep.cu", "qfs_common.cuh", "qfs_kernels.h"):
+        h.update(open(os.path.join(ROOT, "paper_2405_12866_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+# --------------------------------------------------------- oracle baseline
+
+def _oracle_start_sweeps(args):
+    """Worker (spawned): `sweeps` oracle sweeps of one start; returns seconds."""
+    UPsi, Psi, G, pairs, n, sweeps = args
+    from oracle import qfs_oracle as o
+    t = time.perf_counter()
+    for _ in range(sweeps):
+        G = o.sweep(UPsi, Psi, G, pairs, n).gates
+    return time.perf_counter() - t
+
+
+def oracle_sample(kind, seed, sweeps_per_inst, converged_frac, sweeps=1, pool=None, cores=None):
+    """Time the oracle on a bounded sample of the workload: U Psi once and
+    `sweeps` sweeps of every start in parallel over host processes; scale to
+    instantiations/s with the given sweeps per instantiation."""
+    from oracle import qfs_oracle as o  # noqa: F401  (imported where it runs)
+    p = _problem(kind, seed)
+    Psi, G0 = p.samples(), p.init_gates()
+    t0 = time.perf_counter()
+    UPsi = p.U @ Psi
+    t_pre = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    pool.map(_oracle_start_sweeps, [(UPsi, Psi, G0[s], p.pairs, p.n, sweeps) for s in range(p.S)])
+    t_sw = (time.perf_counter() - t1) / sweeps
+    t_inst = t_pre + t_sw * sweeps_per_inst
+    return {"value": converged_frac / t_inst, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"{p.name}: U Psi once + {sweeps} sweep(s) of all {p.S} starts "
+                       f"({t_pre + t_sw * sweeps:.1f} s on {cores} processes), scaled to "
+                       f"{sweeps_per_inst:.1f} sweeps/instantiation x converged fraction {converged_frac:.2f}"),
+            "seconds_per_sweep_all_starts": t_sw, "seconds_precompute": t_pre}
+
+
+def golden_sweeps(kind):
+    path = os.path.join(ROOT, "tests", "golden", f"{kind}_oracle_runs.json")
+    try:
+        runs = json.load(open(path))
+        sw = [r["sweeps"] for r in runs.values()]
+        conv = [r["converged"] for r in runs.values()]
+        return float(np.mean(sw)), float(np.mean(conv)), len(sw)
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------- arms
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    cores = os.cpu_count()
+    g = golden_sweeps(args.workload)
+    sweeps_per_inst, conv_frac = (g[0], g[1]) if g else (100.0, 1.0)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        for i in range(args.warmup):
+            oracle_sample(args.workload, 1000 + i, sweeps_per_inst, conv_frac, pool=pool, cores=cores)
+        samples = [oracle_sample(args.workload, i, sweeps_per_inst, conv_frac, pool=pool, cores=cores)
+                   for i in range(args.steps)]
+    t_inst = float(np.mean([s["seconds_precompute"] + s["seconds_per_sweep_all_starts"] * sweeps_per_inst
+                            for s in samples]))
+    value = conv_frac / t_inst
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_inst,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOADS[args.workload][2],
+                                            "parallelism": "host processes over starts"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": samples[0]["sample"] + (
+                                 f"; sweeps/instantiation from the oracle's own full runs ({g[2]} targets)"
+                                 if g else "; sweeps/instantiation assumed 100 (no oracle runs recorded)")},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2405_12866_gb300 import build as qbuild
+    from paper_2405_12866_gb300 import qfs
+    if rank == 0 or world == 1:
+        qbuild.build()
+    if world > 1:
+        dist.barrier()
+    qfs.lib()
+    kind = args.workload
+    prec = WORKLOADS[kind][1]
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    ctx = qfs.Context(local, stream.cuda_stream)
+
+    # Inputs for every step, generated on the host and made resident before timing.
+    n_steps = args.warmup + args.steps
+    probs = [_problem(kind, rank * 100000 + i) for i in range(n_steps)]
+    first = probs[0]
+    L, S, M, n = first.L, first.S, first.M, first.n
+    dev_in = []
+    for p in probs:
+        dev_in.append((torch.from_numpy(p.U).to(dev), torch.from_numpy(p.samples()).to(dev),
+                       torch.from_numpy(np.ascontiguousarray(p.init_gates())).to(dev)))
+    out = torch.zeros((L, 4, 4), dtype=torch.complex128, device=dev)
+    prm = qfs.default_params(M=M, multistarts=S, max_sweeps=first.max_sweeps, dist_tol=first.tol,
+                             precision=prec)
+
+    def step(i):
+        U, Psi, G0 = dev_in[i]
+        return ctx.instantiate_dev(n, first.pairs, U, Psi, G0, prm, out)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    ctx.profile_reset()
+    ctx.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    results = [step(args.warmup + i) for i in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ctx.profile(False)
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    prof = {name: ctx.profile_read(k) for k, name in enumerate(qfs.PROF_NAMES)}
+    launches = ctx.profile_read(-1)["launches"]
+    conv = sum(r.converged for r in results)
+    sweeps = [r.sweeps for r in results]
+
+    if world > 1:
+        t = torch.tensor([ms, float(conv), float(launches)], device=dev, dtype=torch.float64)
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t.clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        ms_all, conv_all, launches_all = tmax[0].item(), tsum[1].item(), tsum[2].item()
+    else:
+        ms_all, conv_all, launches_all = ms, float(conv), float(launches)
+    value = conv_all / (ms_all / 1e3)
+
+    # End to end through the public host-pointer API: pinned host inputs,
+    # H2D of target, samples and initial gates inside the call, D2H of gates.
+    e2e = None
+    if args.e2e_steps > 0:
+        hin = []
+        for i in range(args.e2e_steps):
+            p = probs[(args.warmup + i) % n_steps]
+            U_h = torch.from_numpy(p.U).pin_memory().numpy()
+            Ps_h = torch.from_numpy(p.samples()).pin_memory().numpy()
+            G_h = torch.from_numpy(np.ascontiguousarray(p.init_gates())).pin_memory().numpy()
+            hin.append((U_h, Ps_h, G_h))
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        e2e_res = [ctx.instantiate(n, first.pairs, U_h, prm, Ps_h, G_h) for (U_h, Ps_h, G_h) in hin]
+        torch.cuda.synchronize(dev)
+        t_e2e = time.perf_counter() - t0
+        conv_e2e = sum(r.converged for r in e2e_res)
+        if world > 1:
+            t = torch.tensor([t_e2e, float(conv_e2e)], device=dev, dtype=torch.float64)
+            tm = t.clone()
+            dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+            ts = t.clone()
+            dist.all_reduce(ts, op=dist.ReduceOp.SUM)
+            t_e2e, conv_e2e = tm[0].item(), ts[1].item()
+        N = 1 << n
+        e2e = {"value": conv_e2e / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": 16 * (N * N + N * M + S * L * 16),
+               "d2h_bytes_per_step": 16 * L * 16 + 8 * S, "steps": args.e2e_steps}
+
+    peak, peak_src = peaks()
+    bwd = prof["backward"]
+    avg_ms = bwd["ms"] / max(bwd["timed"], 1)
+    bytes_per = bwd["bytes"] / max(bwd["timed"], 1)
+    achieved = bytes_per / (avg_ms / 1e3) / 1e9 if bwd["timed"] else None
+    h = kernel_source_hash()
+    tr = traffic_record(h)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64" if prec == 1 else "f64",
+        "data": "synthetic (seeded Haar-random targets of the stated structure)",
+        "config": {"workload": WORKLOADS[kind][2], "n": n, "gates": L, "M": M, "multistarts": S,
+                   "tol": first.tol, "max_sweeps": first.max_sweeps, "parallelism": f"{world} independent ranks",
+                   "l2": "inputs larger than L2 (B list 512 MiB per target), no flush"},
+        "converged": int(conv_all), "instantiations": args.steps * world,
+        "sweeps_per_instantiation": float(np.mean(sweeps)),
+        "roofline": {"bound": "hbm", "kernel": "k_backward (fused Phi update + environment)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None,
+                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback 6.8 TB/s",
+                     "traffic": tr, "avg_launch_us": avg_ms * 1e3, "algorithmic_bytes_per_launch": bytes_per,
+                     "launches_timed": bwd["timed"]},
+        "kernel_time_share": {k: round(v["ms"] / max(sum(x["ms"] for x in prof.values()), 1e-9), 4)
+                              for k, v in prof.items()},
+        "clocks": clk, "e2e": e2e, "gpu_launches": int(launches_all),
+    }
+    if rank == 0 and args.cpu_baseline:
+        ctx_mp = mp.get_context("spawn")
+        cores = os.cpu_count()
+        with ctx_mp.Pool(cores) as pool:
+            line["cpu_baseline"] = oracle_sample(kind, 0, float(np.mean(sweeps)),
+                                                 conv_all / (args.steps * world), pool=pool, cores=cores)
+        line["cpu_baseline"].pop("seconds_per_sweep_all_starts", None)
+        line["cpu_baseline"].pop("seconds_precompute", None)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=6)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="brick_n12")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

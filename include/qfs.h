@@ -1,0 +1,190 @@
+/* qfs.h -- C-ABI of libqfs: QFactor-Sample circuit instantiation on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * Method: Kukliansky et al., "Leveraging Quantum Machine Learning
+ * Generalization to Significantly Speed-up Quantum Compilation",
+ * arXiv 2405.12866.  Instantiation (Section 2.1): given a target unitary U on
+ * n qubits and a circuit structure C of 2-qubit gates, find gate unitaries
+ * minimising the sample cost (Section 3, Eq. qfactor_sample_cost_function)
+ *     c = (1/M) sum_j || U psi_j - C psi_j ||^2
+ *       = 2 - (2/M) Re sum_j <psi_j| U^dagger C |psi_j>
+ * over M orthonormal training states psi_j, by sweeps that replace each
+ * gate with Y X^dagger from the SVD E = X D Y^dagger of its environment
+ * (Eq. 2), right to left (Section 3), until c <= dist_tol or max_sweeps
+ * (Appendix A).
+ *
+ * Conventions used by every entry point:
+ *   - Complex numbers are interleaved (re, im) doubles, i.e. C99
+ *     double complex / numpy complex128.
+ *   - n qubits, N = 2^n.  Qubit q is bit (n-1-q) of a row index (qubit 0
+ *     is the most significant bit).
+ *   - pairs[2k], pairs[2k+1] = (a, b) are the qubits of gate k; the gate is
+ *     a row-major 4x4 matrix indexed by 2*bit_a + bit_b.  Gates act in list
+ *     order: gate 0 acts first, C = g_{L-1} ... g_1 g_0.
+ *   - A target is N x N row-major; samples are N x M row-major (column j is
+ *     psi_j); gates are L x 16 complex per start, starts contiguous.
+ *   - "host" pointers are ordinary CPU memory (pinned memory makes the
+ *     copies faster); "device" pointers are CUDA global memory on the
+ *     context's device, e.g. torch tensor data pointers.  The caller owns
+ *     every buffer passed in; the library never frees or keeps them.
+ *   - Every int-returning call returns QFS_OK (0) or a negative QFS_E*
+ *     code, and then qfs_last_error() describes the failure.  Reaching
+ *     max_sweeps without converging is not an error (converged = 0).
+ *   - A context is used by one host thread at a time.  Calls are
+ *     synchronous with respect to the host unless noted.
+ */
+#ifndef QFS_H
+#define QFS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QFS_OK 0
+#define QFS_EINVAL (-1)       /* bad argument (message says which) */
+#define QFS_ENOMEM (-2)       /* device workspace allocation failed */
+#define QFS_ECUDA (-3)        /* a CUDA call failed */
+#define QFS_ETIMEOUT (-4)     /* a bounded device wait ran out */
+#define QFS_EUNSUPPORTED (-5) /* valid but not supported (e.g. n > 14) */
+#define QFS_ENONFINITE (-6)   /* NaN or Inf in an input */
+
+#define QFS_FP64 0  /* every step in complex128 */
+#define QFS_MIXED 1 /* complex64 sweeps; FP64 SVD, master gates, refinement, cost check */
+
+#define QFS_MAX_QUBITS 14
+
+typedef struct qfs_ctx qfs_ctx;
+
+typedef struct {
+  int32_t n;             /* qubits, 2 <= n <= QFS_MAX_QUBITS */
+  int32_t L;             /* gates, >= 1 */
+  const int32_t* pairs;  /* host, 2*L qubit indices, a != b, both < n */
+} qfs_circuit;
+
+/* Hyperparameters (Appendix A of the paper).  qfs_default_params() fills
+ * the values of the paper's evaluation where they apply. */
+typedef struct {
+  int32_t M;                 /* training states, 1 <= M <= 2^n (number_of_training_states) */
+  int32_t multistarts;       /* independent random initial gate sets, >= 1 */
+  int32_t max_sweeps;        /* max_iter: sweeps per run, >= 1 */
+  int32_t min_sweeps;        /* min_iter before a plateau may stop a start */
+  int32_t plateau_window;    /* plateau_windows_size; 0 disables plateau detection */
+  int32_t precision;         /* QFS_FP64 or QFS_MIXED */
+  int32_t refine_sweeps_max; /* QFS_MIXED: FP64 refinement sweeps allowed per start */
+  int32_t reserved0;
+  uint64_t seed;             /* draws the training states and the initial gates */
+  double dist_tol;           /* stop when a start's cost <= dist_tol */
+  double diff_tol_r;         /* plateau: relative improvement threshold */
+  double beta;               /* update damping, 0 <= beta < 1 (0 = full update) */
+} qfs_params;
+
+typedef struct {
+  double cost;         /* sample cost of the returned gates (FP64) */
+  int32_t sweeps;      /* sweeps run (all starts in lock step) */
+  int32_t converged;   /* 1 if cost <= dist_tol */
+  int32_t best_start;  /* index of the returned start */
+  int32_t fp64_sweeps; /* QFS_MIXED: FP64 refinement sweeps run */
+} qfs_result;
+
+/* Fill *p with defaults: M = 2, multistarts = 16, max_sweeps = 10000,
+ * min_sweeps = 6, plateau_window = 0, precision = QFS_FP64,
+ * refine_sweeps_max = 50, seed = 0, dist_tol = 1e-8, diff_tol_r = 1e-5,
+ * beta = 0 (the paper's suggested values, with plateau detection off). */
+void qfs_default_params(qfs_params* p);
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a
+ * cudaStream_t to run on (e.g. torch.cuda.current_stream().cuda_stream), or
+ * NULL for a stream the context creates and owns.  The context owns its
+ * device workspace, grown on demand and freed by qfs_destroy. */
+int qfs_create(qfs_ctx** out, int device, void* cuda_stream);
+void qfs_destroy(qfs_ctx* ctx);
+
+/* Message of the last failed call on this host thread ("" if none).  The
+ * pointer stays valid until the thread's next qfs_* call. */
+const char* qfs_last_error(void);
+
+/* Number of SMs of the context's device (host query, no kernel). */
+int qfs_device_sms(const qfs_ctx* ctx);
+
+/* Kernel accounting.  Launches of every kind are always counted; with
+ * profiling enabled each launch is also bracketed by CUDA events on the
+ * context's stream, and qfs_profile_read returns, for one kind (or -1 for
+ * all), the launches, the timed launches, their total device time in ms and
+ * their total algorithmic traffic (bytes read + written by the definition
+ * of the step; FLOPs for QFS_PROF_GEMM).  The counters are per context. */
+#define QFS_PROF_BACKWARD 0 /* fused Phi update + environment partials */
+#define QFS_PROF_FORWARD 1  /* B_k = g_k B_{k-1} */
+#define QFS_PROF_UPDATE 2   /* warp SVD/polar update */
+#define QFS_PROF_GEMM 3     /* Phi_L = U Psi */
+#define QFS_PROF_RESIDUAL 4 /* complex64 residual cost pass */
+#define QFS_PROF_CHECK 5    /* FP64 cost check of a candidate start */
+#define QFS_PROF_OTHER 6    /* casts, input checks, finishing reductions */
+#define QFS_PROF_KINDS 7
+int qfs_profile_enable(qfs_ctx* ctx, int enable);
+int qfs_profile_reset(qfs_ctx* ctx);
+int qfs_profile_read(qfs_ctx* ctx, int32_t kind, int64_t* launches, int64_t* timed,
+                     double* total_ms, double* total_bytes);
+
+/* The method's own random draws (host only, no GPU): the M training states
+ * (Section 3 and Appendix A: columns of a Haar-random unitary, here the Q
+ * factor with positive R diagonal of a complex Gaussian N x M matrix) and
+ * S x L Haar-random initial gates, from Philox4x32-10 (Salmon et al. 2011)
+ * with key = seed, counter = (index, stream, 0); stream 1 = samples,
+ * stream 2 = initial gates.  samples_out: host N x M; gates_out: host
+ * S x L x 16 (either may be NULL). */
+int qfs_generate_inputs(uint64_t seed, int32_t n, int32_t M, int32_t S, int32_t L,
+                        double* samples_out, double* gates_out);
+
+/* Instantiate `target` (host, N x N) on `circuit`: draws samples and
+ * initial gates from p->seed, runs the multistart sweeps and writes the
+ * selected start's gates to gates_out (host, L x 16).  Multistarts run in
+ * lock step; the run stops at the first sweep after which some start has
+ * cost <= dist_tol and returns the start with the lowest cost then (lowest
+ * index on ties); otherwise the lowest final cost.  start_costs (host,
+ * multistarts doubles, may be NULL) receives every start's last cost. */
+int qfs_instantiate(qfs_ctx* ctx, const qfs_circuit* circuit, const double* target,
+                    const qfs_params* p, double* gates_out, qfs_result* result,
+                    double* start_costs);
+
+/* As qfs_instantiate, with the training states (host, N x M, orthonormal
+ * columns) and initial gates (host, multistarts x L x 16) given instead of
+ * drawn from the seed. */
+int qfs_instantiate_ex(qfs_ctx* ctx, const qfs_circuit* circuit, const double* target,
+                       const double* samples, const double* init_gates, const qfs_params* p,
+                       double* gates_out, qfs_result* result, double* start_costs);
+
+/* As qfs_instantiate_ex with every array in device memory (result stays a
+ * host struct).  Runs on the context's stream and returns when done. */
+int qfs_instantiate_dev(qfs_ctx* ctx, const qfs_circuit* circuit, const double* target_dev,
+                        const double* samples_dev, const double* init_gates_dev,
+                        const qfs_params* p, double* gates_out_dev, qfs_result* result,
+                        double* start_costs);
+
+/* Exactly one sweep (Section 3) for S starts, for parity checks: from
+ * gates_in (host, S x L x 16) with target (host N x N) and samples (host
+ * N x M), write the swept gates (host, S x L x 16), optionally every
+ * gate's environment as used (envs_out, host, S x L x 16, row-major
+ * E[x][y] = sum_{r,j} B_{k-1}[(x,r),j] conj(Phi_k[(y,r),j])) and each
+ * start's cost after the sweep (costs_out, host, S).  QFS_FP64 reports
+ * 2 - (2/M) Re Tr(g_1 E_1); QFS_MIXED runs the sweep in complex64 and
+ * reports the residual form (1/M) sum_j ||U psi_j - C psi_j||^2 of the
+ * swept gates accumulated from complex64 states. */
+int qfs_sweep_once(qfs_ctx* ctx, const qfs_circuit* circuit, const double* target,
+                   const double* samples, int32_t M, int32_t S, const double* gates_in,
+                   int32_t precision, double beta, double* gates_out, double* envs_out,
+                   double* costs_out);
+
+/* The update step alone (Eq. 2 with the damping of Appendix A) for `count`
+ * independent environments (host, count x 16): gates_out = polar factor of
+ * ((1-beta) E + beta g_old^dagger)^dagger.  gates_old may be NULL when
+ * beta = 0.  For a rank-deficient E any unitary completion is returned. */
+int qfs_gate_update(qfs_ctx* ctx, int32_t count, const double* envs, const double* gates_old,
+                    double beta, double* gates_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QFS_H */

@@ -1,0 +1,90 @@
+"""Write oracle reference runs of full-size workloads to tests/golden/.
+
+TEST INFRASTRUCTURE: calls only the oracle and the seeded input generator.
+For each target it runs the oracle's multistart instantiation (Appendix A
+stopping rule, lock step) with the starts spread over host processes in
+chunks of sweeps, which gives the same result as the sequential lock-step
+loop because the starts never interact before the stop.  Records, per
+target: converged, the stopping sweep, the selected start and its cost.
+
+    python -m oracle.make_golden brick_n12 0 1 2 3
+"""
+from __future__ import annotations
+
+import json
+import multiprocessing as mp
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from oracle import qfs_oracle as o  # noqa: E402
+
+
+def _chunk(args):
+    UPsi, Psi, G, pairs, n, sweeps = args
+    costs = []
+    for _ in range(sweeps):
+        r = o.sweep(UPsi, Psi, G, pairs, n)
+        G = r.gates
+        costs.append(r.cost)
+    return G, costs
+
+
+def lockstep_parallel(UPsi, Psi, G0, pairs, n, tol, max_sweeps, pool, chunk=10):
+    """The oracle's instantiate() with the starts on a process pool."""
+    S = G0.shape[0]
+    G = [G0[s] for s in range(S)]
+    trace = []
+    done = 0
+    while done < max_sweeps:
+        step = min(chunk, max_sweeps - done)
+        res = pool.map(_chunk, [(UPsi, Psi, G[s], pairs, n, step) for s in range(S)])
+        G = [r[0] for r in res]
+        block = np.array([r[1] for r in res]).T   # (step, S)
+        for i in range(step):
+            trace.append(block[i])
+            if np.any(block[i] <= tol):
+                # the sequential loop stops here; rerun the starts to this sweep
+                stop = done + i + 1
+                res = pool.map(_chunk, [(UPsi, Psi, G0[s], pairs, n, stop) for s in range(S)])
+                final = np.array([r[1][-1] for r in res])
+                best = int(np.argmin(final))
+                return dict(converged=True, sweeps=stop, best_start=best, cost=float(final[best]),
+                            start_costs=final.tolist())
+        done += step
+    final = np.array(trace[-1])
+    best = int(np.argmin(final))
+    return dict(converged=bool(final[best] <= tol), sweeps=done, best_start=best,
+                cost=float(final[best]), start_costs=final.tolist())
+
+
+def main(argv):
+    from paper_2405_12866_gb300 import workloads as w
+    kind = argv[0]
+    seeds = [int(x) for x in argv[1:]] or [0]
+    factory = {"brick_n12": w.brick_n12, "brick_n8": w.brick_n8}[kind]
+    out_path = os.path.join(ROOT, "tests", "golden", f"{kind}_oracle_runs.json")
+    runs = json.load(open(out_path)) if os.path.exists(out_path) else {}
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(os.cpu_count()) as pool:
+        for sd in seeds:
+            p = factory(target_seed=sd)
+            Psi, G0 = p.samples(), p.init_gates()
+            t = time.time()
+            r = lockstep_parallel(p.U @ Psi, Psi, G0, p.pairs, p.n, p.tol, p.max_sweeps, pool)
+            r.update(name=p.name, target_seed=sd, run_seed=p.seed, tol=p.tol,
+                     max_sweeps=p.max_sweeps, seconds=round(time.time() - t, 1),
+                     host_cores=os.cpu_count())
+            runs[str(sd)] = r
+            print(kind, sd, {k: r[k] for k in ("converged", "sweeps", "best_start", "cost")}, flush=True)
+            json.dump(runs, open(out_path, "w"), indent=1)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:])

@@ -1,0 +1,842 @@
+// Host engine and C-ABI of libqfs: argument checks, workspace, the sweep
+// sequence of QFactor-Sample (Section 3 of the paper) and the multistart run
+// with its stopping rules (Appendix A).  Every arithmetic step of the sweep
+// runs in the CUDA kernels; the host orders launches and reads back one cost
+// per start after each sweep.
+#include "../../include/qfs.h"
+#include "qfs_kernels.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <string>
+#include <vector>
+
+namespace qfs {
+void generate_samples(uint64_t seed, int n, int M, std::complex<double>* out);
+void generate_gates(uint64_t seed, int count, std::complex<double>* out);
+}  // namespace qfs
+
+using namespace qfs;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CK(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(e_ == cudaErrorMemoryAllocation ? QFS_ENOMEM : QFS_ECUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                  \
+  } while (0)
+
+#define TRY(expr)              \
+  do {                         \
+    int r_ = (expr);           \
+    if (r_ != QFS_OK) return r_; \
+  } while (0)
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+}  // namespace
+
+// Per-kernel timing with CUDA events on the context's stream (off unless
+// enabled); launches are counted always.
+struct ProfRec {
+  cudaEvent_t a, b;
+  int id;
+  double bytes;
+};
+struct Prof {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  std::vector<ProfRec> pending;
+  long long launches[QFS_PROF_KINDS] = {};
+  long long timed[QFS_PROF_KINDS] = {};
+  double ms[QFS_PROF_KINDS] = {};
+  double bytes[QFS_PROF_KINDS] = {};
+};
+
+struct qfs_ctx {
+  Prof prof;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int num_sms = 0;
+  size_t l2_bytes = 0;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  double* h_pinned = nullptr;  // cost read-back
+  size_t h_pinned_n = 0;
+};
+
+namespace {
+
+cudaEvent_t prof_event(qfs_ctx* ctx) {
+  if (!ctx->prof.pool.empty()) {
+    cudaEvent_t e = ctx->prof.pool.back();
+    ctx->prof.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Bracket one kernel launch; `bytes` is its algorithmic traffic.
+struct ProfScope {
+  qfs_ctx* ctx;
+  int id;
+  double bytes;
+  cudaEvent_t a = nullptr;
+  ProfScope(qfs_ctx* c, int i, double b) : ctx(c), id(i), bytes(b) {
+    ctx->prof.launches[id] += 1;
+    if (ctx->prof.on) {
+      a = prof_event(ctx);
+      cudaEventRecord(a, ctx->stream);
+    }
+  }
+  ~ProfScope() {
+    if (a) {
+      cudaEvent_t b = prof_event(ctx);
+      cudaEventRecord(b, ctx->stream);
+      ctx->prof.pending.push_back({a, b, id, bytes});
+    }
+  }
+};
+
+// After a stream synchronisation: fold finished timings into the totals.
+void prof_harvest(qfs_ctx* ctx) {
+  for (auto& r : ctx->prof.pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      ctx->prof.ms[r.id] += ms;
+      ctx->prof.timed[r.id] += 1;
+      ctx->prof.bytes[r.id] += r.bytes;
+    }
+    ctx->prof.pool.push_back(r.a);
+    ctx->prof.pool.push_back(r.b);
+  }
+  ctx->prof.pending.clear();
+}
+
+// Device buffers of one run, carved from the context's workspace.
+struct Run {
+  int n = 0, L = 0, M = 0, S = 0;
+  long long N = 0, sN = 0;
+  std::vector<int> pairs;
+  int prec = QFS_FP64;
+  double beta = 0.0;
+  Shape sh, sh64;          // sweep shape (prec) and the FP64 shape for S = 1
+  int nblk_max = 1, nblk64_max = 1;  // largest backward block count (partials size)
+  // inputs (device)
+  const double2* U = nullptr;  // N x N
+  double2* U_copy = nullptr;   // used by the host-pointer entry points
+  double2* psi64 = nullptr;
+  double2* phil64 = nullptr;
+  float2* psi32 = nullptr;
+  float2* phil32 = nullptr;
+  // state of the sweeps
+  void* B = nullptr;    // (L-1) x S x N x M in the sweep precision
+  void* phi = nullptr;  // S x N x M in the sweep precision
+  double2* g64 = nullptr;
+  float2* g32 = nullptr;
+  double* partials = nullptr;
+  double* costs = nullptr;
+  int* active = nullptr;
+  int* flag = nullptr;
+  double2* envs = nullptr;
+  // FP64 single-start buffers (mixed precision: cost check and refinement)
+  double2* B64r = nullptr;
+  double2* phi64r = nullptr;
+  double* partials64r = nullptr;
+  double* cost64r = nullptr;
+  int stream_b = 0;
+  int stream_b64 = 0;
+};
+
+size_t elem_bytes(Real r) { return r == R32 ? sizeof(float2) : sizeof(double2); }
+
+// Lays out (or, with base == nullptr, only measures) the buffers of a run.
+size_t carve(Run& R, char* base, bool need_U, bool need_envs) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* {
+    char* p = base ? base + off : nullptr;
+    off += align_up(bytes);
+    return p;
+  };
+  const Real rs = R.prec == QFS_MIXED ? R32 : R64;
+  const size_t es = elem_bytes(rs);
+  const size_t state64 = (size_t)R.sN * sizeof(double2);
+  R.U_copy = need_U ? (double2*)take((size_t)R.N * R.N * sizeof(double2)) : nullptr;
+  R.psi64 = (double2*)take(state64);
+  R.phil64 = (double2*)take(state64);
+  if (R.prec == QFS_MIXED) {
+    R.psi32 = (float2*)take((size_t)R.sN * sizeof(float2));
+    R.phil32 = (float2*)take((size_t)R.sN * sizeof(float2));
+  }
+  R.B = take((size_t)std::max(R.L - 1, 1) * R.S * R.sN * es);
+  R.phi = take((size_t)R.S * R.sN * es);
+  R.g64 = (double2*)take((size_t)R.S * R.L * 16 * sizeof(double2));
+  R.g32 = R.prec == QFS_MIXED ? (float2*)take((size_t)R.S * R.L * 16 * sizeof(float2)) : nullptr;
+  R.partials = (double*)take((size_t)R.S * R.nblk_max * 32 * sizeof(double));
+  R.costs = (double*)take((size_t)R.S * sizeof(double));
+  R.active = (int*)take((size_t)R.S * sizeof(int));
+  R.flag = (int*)take(sizeof(int) * 4);
+  R.envs = need_envs ? (double2*)take((size_t)R.S * R.L * 16 * sizeof(double2)) : nullptr;
+  if (R.prec == QFS_MIXED) {
+    R.B64r = (double2*)take((size_t)std::max(R.L - 1, 2) * state64);
+    R.phi64r = (double2*)take(state64);
+    R.partials64r = (double*)take((size_t)R.nblk64_max * 32 * sizeof(double));
+    R.cost64r = (double*)take(sizeof(double) * 2);
+  }
+  return off;
+}
+
+int check_circuit(const qfs_circuit* c) {
+  if (!c) return fail(QFS_EINVAL, "circuit is NULL");
+  if (c->n < 2) return fail(QFS_EINVAL, "n = %d: need at least 2 qubits", c->n);
+  if (c->n > QFS_MAX_QUBITS) return fail(QFS_EUNSUPPORTED, "n = %d > %d", c->n, QFS_MAX_QUBITS);
+  if (c->L < 1) return fail(QFS_EINVAL, "L = %d: need at least one gate", c->L);
+  if (!c->pairs) return fail(QFS_EINVAL, "pairs is NULL");
+  for (int k = 0; k < c->L; ++k) {
+    const int a = c->pairs[2 * k], b = c->pairs[2 * k + 1];
+    if (a < 0 || b < 0 || a >= c->n || b >= c->n)
+      return fail(QFS_EINVAL, "gate %d: qubit out of range (%d, %d) for n = %d", k, a, b, c->n);
+    if (a == b) return fail(QFS_EINVAL, "gate %d: both qubits are %d", k, a);
+  }
+  return QFS_OK;
+}
+
+int check_run_params(int n, int M, int S, int max_sweeps, int precision, double beta, double tol) {
+  if (M < 1 || (long long)M > (1LL << n))
+    return fail(QFS_EINVAL, "M = %d: need 1 <= M <= 2^n = %lld", M, 1LL << n);
+  if (S < 1) return fail(QFS_EINVAL, "multistarts = %d: need >= 1", S);
+  if (S > 65535) return fail(QFS_EUNSUPPORTED, "multistarts = %d > 65535", S);
+  if (max_sweeps < 1) return fail(QFS_EINVAL, "max_sweeps = %d: need >= 1", max_sweeps);
+  if (precision != QFS_FP64 && precision != QFS_MIXED)
+    return fail(QFS_EINVAL, "precision = %d: need QFS_FP64 or QFS_MIXED", precision);
+  if (!(beta >= 0.0 && beta < 1.0)) return fail(QFS_EINVAL, "beta = %g: need 0 <= beta < 1", beta);
+  if (!(tol >= 0.0) || std::isinf(tol)) return fail(QFS_EINVAL, "dist_tol = %g: need a finite value >= 0", tol);
+  return QFS_OK;
+}
+
+int ensure_ws(qfs_ctx* ctx, size_t bytes) {
+  if (ctx->ws_bytes >= bytes) return QFS_OK;
+  if (ctx->ws) {
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaFree(ctx->ws));
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+  }
+  cudaError_t e = cudaMalloc(&ctx->ws, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ctx->ws = nullptr;
+    return fail(QFS_ENOMEM, "cannot allocate %.3f GiB of device workspace: %s",
+                bytes / 1073741824.0, cudaGetErrorString(e));
+  }
+  ctx->ws_bytes = bytes;
+  return QFS_OK;
+}
+
+int ensure_pinned(qfs_ctx* ctx, size_t n) {
+  if (ctx->h_pinned_n >= n) return QFS_OK;
+  if (ctx->h_pinned) CK(cudaFreeHost(ctx->h_pinned));
+  ctx->h_pinned = nullptr;
+  ctx->h_pinned_n = 0;
+  CK(cudaMallocHost(&ctx->h_pinned, n * sizeof(double)));
+  ctx->h_pinned_n = n;
+  return QFS_OK;
+}
+
+int prepare(qfs_ctx* ctx, Run& R, const qfs_circuit* c, int M, int S, int prec, double beta,
+            bool need_U, bool need_envs) {
+  R.n = c->n;
+  R.L = c->L;
+  R.M = M;
+  R.S = S;
+  R.N = 1LL << c->n;
+  R.sN = (long long)M << c->n;
+  R.pairs.assign(c->pairs, c->pairs + 2 * c->L);
+  R.prec = prec;
+  R.beta = beta;
+  R.sh = make_shape(R.n, M, S, prec == QFS_MIXED ? R32 : R64, ctx->num_sms);
+  R.sh64 = make_shape(R.n, M, 1, R64, ctx->num_sms);
+  R.nblk_max = R.nblk64_max = 1;
+  for (int U = 2; U <= std::min(4, R.n); ++U) {
+    R.nblk_max = std::max(R.nblk_max,
+                          make_bwd_shape(R.n, M, S, prec == QFS_MIXED ? R32 : R64, ctx->num_sms, U).nblk);
+    R.nblk64_max = std::max(R.nblk64_max, make_bwd_shape(R.n, M, 1, R64, ctx->num_sms, U).nblk);
+  }
+  const size_t bytes = carve(R, nullptr, need_U, need_envs);
+  TRY(ensure_ws(ctx, bytes));
+  carve(R, ctx->ws, need_U, need_envs);
+  const size_t blist = (size_t)std::max(R.L - 1, 1) * S * R.sN * elem_bytes(prec == QFS_MIXED ? R32 : R64);
+  R.stream_b = blist > ctx->l2_bytes / 2;
+  R.stream_b64 = (size_t)std::max(R.L - 1, 1) * R.sN * sizeof(double2) > ctx->l2_bytes / 2;
+  TRY(ensure_pinned(ctx, (size_t)S + 8));
+  return QFS_OK;
+}
+
+// Phi_L = U Psi in FP64, complex64 copies for the mixed sweeps, gate copies.
+int setup_inputs(qfs_ctx* ctx, Run& R) {
+  cudaStream_t st = ctx->stream;
+  CK(cudaMemsetAsync(R.flag, 0, sizeof(int) * 4, st));
+  {
+    ProfScope ps(ctx, QFS_PROF_OTHER, 0.0);
+    launch_nonfinite_check(reinterpret_cast<const double*>(R.U), 2 * R.N * R.N, R.flag, st);
+  }
+  {
+    ProfScope ps(ctx, QFS_PROF_OTHER, 0.0);
+    launch_nonfinite_check(reinterpret_cast<const double*>(R.psi64), 2 * R.sN, R.flag, st);
+  }
+  {
+    ProfScope ps(ctx, QFS_PROF_OTHER, 0.0);
+    launch_nonfinite_check(reinterpret_cast<const double*>(R.g64), 2LL * R.S * R.L * 16, R.flag, st);
+  }
+  {
+    ProfScope ps(ctx, QFS_PROF_GEMM, 8.0 * R.N * R.N * R.M);  // flops, not bytes
+    launch_gemm_upsi(R.U, R.psi64, R.phil64, (int)R.N, R.M, st);
+  }
+  if (R.prec == QFS_MIXED) {
+    ProfScope ps(ctx, QFS_PROF_OTHER, 0.0);
+    launch_cast_c128_to_c64(R.psi64, R.psi32, R.sN, st);
+    launch_cast_c128_to_c64(R.phil64, R.phil32, R.sN, st);
+    launch_cast_c128_to_c64(R.g64, R.g32, (long long)R.S * R.L * 16, st);
+    ctx->prof.launches[QFS_PROF_OTHER] += 2;
+  }
+  std::vector<int> ones(R.S, 1);
+  CK(cudaMemcpyAsync(R.active, ones.data(), sizeof(int) * R.S, cudaMemcpyHostToDevice, st));
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, R.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  prof_harvest(ctx);
+  if (flag) return fail(QFS_ENONFINITE, "NaN or Inf in the target, samples or initial gates");
+  return QFS_OK;
+}
+
+// One sweep (Section 3) for S starts in precision r.  Forward: B_k = g_k
+// B_{k-1}, k = 1..L-1, with the current gates.  Backward, k = L..1: Phi_k =
+// g_{k+1}^dagger Phi_{k+1} fused with the environment partials of gate k
+// from B_{k-1} and Phi_k, then the warp update of gate k.  FP64 writes
+// cost = 2 - (2/M) Re Tr(g_1 E_1); complex64 adds a residual pass
+// (1/M) sum |g_1^dagger Phi_1 - Psi|^2 = (1/M) sum_j ||U psi_j - C psi_j||^2.
+void sweep(qfs_ctx* ctx, Run& R, Real r, int S, const Shape& sh, double2* g64, float2* g32,
+           const void* psi, const void* phil, void* B, void* phi, double* partials,
+           double* cost_out, double2* envs, const int* active, int stream_b) {
+  cudaStream_t st = ctx->stream;
+  const size_t es = elem_bytes(r);
+  const long long sN = R.sN;
+  const long long gstride = (long long)R.L * 16;
+  const char* gT = r == R32 ? reinterpret_cast<const char*>(g32) : reinterpret_cast<const char*>(g64);
+  auto gate_ptr = [&](int idx) { return (const void*)(gT + (size_t)idx * 16 * es); };
+  auto B_ptr = [&](int k) { return (void*)((char*)B + (size_t)(k - 1) * S * sN * es); };  // B_k, k >= 1
+  const int L = R.L;
+  for (int k = 1; k <= L - 1; ++k) {
+    const Geom gm = make_geom(R.n, R.M, R.pairs[2 * (k - 1)], R.pairs[2 * (k - 1) + 1]);
+    const void* in = k == 1 ? psi : B_ptr(k - 1);
+    ProfScope ps(ctx, QFS_PROF_FORWARD, 2.0 * S * sN * es);
+    launch_forward(r, gm, sh, S, in, k == 1 ? 0 : sN, B_ptr(k), gate_ptr(k - 1), gstride, active, st);
+  }
+  for (int k = L; k >= 1; --k) {
+    const int qa = R.pairs[2 * (k - 1)], qb = R.pairs[2 * (k - 1) + 1];
+    const void* bprev = k == 1 ? psi : B_ptr(k - 1);
+    const long long bstride = k == 1 ? 0 : sN;
+    const void* pin;
+    long long pstride;
+    void* pout;
+    const void* gate;
+    int ua = qa, ub = qb;  // pair of the gate carried into Phi (gate k+1)
+    if (k == L) {
+      pin = phil; pstride = 0; pout = nullptr; gate = nullptr;
+    } else {
+      pin = k == L - 1 ? phil : phi;
+      pstride = k == L - 1 ? 0 : sN;
+      pout = phi;
+      gate = gate_ptr(k);
+      ua = R.pairs[2 * k];
+      ub = R.pairs[2 * k + 1];
+    }
+    const BwdGeom bg = make_bwd_geom(R.n, R.M, ua, ub, qa, qb);
+    const Shape bsh = make_bwd_shape(R.n, R.M, S, r, ctx->num_sms, bg.U);
+    {
+      ProfScope ps(ctx, QFS_PROF_BACKWARD, (double)S * sN * es * (pout ? 3.0 : 2.0));
+      launch_backward(r, 0, bg, bsh, S, bprev, bstride, pin, pstride, pout, gate, gstride, partials,
+                      stream_b, active, st);
+    }
+    UpdateArgs ua_;
+    ua_.partials = partials;
+    ua_.nblk = bsh.nblk;
+    ua_.g64 = g64 + (size_t)(k - 1) * 16;
+    ua_.g_stride = gstride;
+    ua_.g32 = g32 ? g32 + (size_t)(k - 1) * 16 : nullptr;
+    ua_.beta = R.beta;
+    ua_.cost_out = (k == 1 && r == R64) ? cost_out : nullptr;
+    ua_.inv_M = 1.0 / R.M;
+    ua_.env_out = envs ? envs + (size_t)(k - 1) * 16 : nullptr;
+    ua_.env_stride = gstride;
+    ua_.S = S;
+    ua_.active = active;
+    ProfScope ps(ctx, QFS_PROF_UPDATE, (double)S * bsh.nblk * 32 * sizeof(double));
+    launch_update(ua_, st);
+  }
+  if (r == R32) {
+    const BwdGeom bg = make_bwd_geom(R.n, R.M, R.pairs[0], R.pairs[1], R.pairs[0], R.pairs[1]);
+    const Shape bsh = make_bwd_shape(R.n, R.M, S, r, ctx->num_sms, 2);
+    const void* pin = L == 1 ? phil : phi;
+    {
+      ProfScope ps(ctx, QFS_PROF_RESIDUAL, 2.0 * S * sN * es);
+      launch_backward(r, 1, bg, bsh, S, psi, 0, pin, L == 1 ? 0 : sN, nullptr, gate_ptr(0), gstride,
+                      partials, 0, active, st);
+    }
+    ProfScope ps(ctx, QFS_PROF_OTHER, 0.0);
+    launch_residual_finish(partials, bsh.nblk, S, 1.0 / R.M, cost_out, st);
+  }
+}
+
+// FP64 sample cost of start s's master gates: (1/M) ||Phi_L - C Psi||^2.
+int check64(qfs_ctx* ctx, Run& R, int s, double* out) {
+  cudaStream_t st = ctx->stream;
+  const double2* g = R.g64 + (size_t)s * R.L * 16;
+  const void* in = R.psi64;
+  for (int k = 1; k <= R.L; ++k) {
+    const Geom gm = make_geom(R.n, R.M, R.pairs[2 * (k - 1)], R.pairs[2 * (k - 1) + 1]);
+    double2* out_buf = R.B64r + (size_t)(k & 1) * R.sN;
+    ProfScope ps(ctx, QFS_PROF_CHECK, 2.0 * R.sN * sizeof(double2));
+    launch_forward(R64, gm, R.sh64, 1, in, 0, out_buf, g + (size_t)(k - 1) * 16, 16, nullptr, st);
+    in = out_buf;
+  }
+  const BwdGeom bg = make_bwd_geom(R.n, R.M, R.pairs[0], R.pairs[1], R.pairs[0], R.pairs[1]);
+  {
+    ProfScope ps(ctx, QFS_PROF_CHECK, 2.0 * R.sN * sizeof(double2));
+    launch_backward(R64, 1, bg, R.sh64, 1, in, 0, R.phil64, 0, nullptr, nullptr, 16, R.partials64r,
+                    0, nullptr, st);
+  }
+  {
+    ProfScope ps(ctx, QFS_PROF_OTHER, 0.0);
+    launch_residual_finish(R.partials64r, R.sh64.nblk, 1, 1.0 / R.M, R.cost64r, st);
+  }
+  CK(cudaMemcpyAsync(ctx->h_pinned, R.cost64r, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  prof_harvest(ctx);
+  *out = ctx->h_pinned[0];
+  return QFS_OK;
+}
+
+int read_costs(qfs_ctx* ctx, const double* dev, int S, std::vector<double>& out) {
+  CK(cudaMemcpyAsync(ctx->h_pinned, dev, sizeof(double) * S, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  prof_harvest(ctx);
+  out.assign(ctx->h_pinned, ctx->h_pinned + S);
+  return QFS_OK;
+}
+
+struct Outcome {
+  int best = 0;
+  double cost = std::numeric_limits<double>::infinity();
+  int sweeps = 0;
+  int converged = 0;
+  int fp64_sweeps = 0;
+  std::vector<double> start_costs;
+};
+
+// The multistart run.  Starts sweep in lock step; the run stops at the first
+// sweep after which some start's cost is <= tol and returns the lowest-cost
+// start of that sweep (lowest index on ties).  With plateau_window > 0 a
+// start stops once its cost failed plateau_window times in a row to improve
+// by diff_tol_r relative to the newer cost (Appendix A) after min_sweeps.
+int run_multistart(qfs_ctx* ctx, Run& R, const qfs_params* p, Outcome& out) {
+  cudaStream_t st = ctx->stream;
+  const int S = R.S;
+  const double tol = p->dist_tol;
+  std::vector<double> c, prev(S, std::numeric_limits<double>::infinity());
+  std::vector<int> stall(S, 0), act(S, 1);
+  std::vector<double> c64(S, std::numeric_limits<double>::quiet_NaN());
+  const Real rs = R.prec == QFS_MIXED ? R32 : R64;
+  const void* psi = rs == R32 ? (const void*)R.psi32 : (const void*)R.psi64;
+  const void* phil = rs == R32 ? (const void*)R.phil32 : (const void*)R.phil64;
+  int sweeps = 0;
+  bool done = false;
+  int fp64_sweeps = 0;
+  while (!done && sweeps < p->max_sweeps) {
+    ++sweeps;
+    sweep(ctx, R, rs, S, R.sh, R.g64, R.g32, psi, phil, R.B, R.phi, R.partials, R.costs, nullptr,
+          R.active, R.stream_b);
+    TRY(read_costs(ctx, R.costs, S, c));
+    for (int s = 0; s < S; ++s)
+      if (!act[s]) c[s] = prev[s];
+    if (R.prec == QFS_FP64) {
+      for (int s = 0; s < S; ++s)
+        if (act[s] && c[s] <= tol) done = true;
+    } else {
+      // Candidates by their complex64 cost; each is confirmed in FP64.
+      std::vector<int> cand;
+      for (int s = 0; s < S; ++s)
+        if (act[s] && c[s] <= tol) cand.push_back(s);
+      for (int s : cand) {
+        TRY(check64(ctx, R, s, &c64[s]));
+        if (c64[s] <= tol) done = true;
+      }
+      if (!done) {
+        // complex64 reached tol but FP64 did not: refine that start in FP64.
+        for (int s : cand) {
+          for (int it = 0; it < p->refine_sweeps_max && !done; ++it) {
+            sweep(ctx, R, R64, 1, R.sh64, R.g64 + (size_t)s * R.L * 16, R.g32 + (size_t)s * R.L * 16,
+                  R.psi64, R.phil64, R.B64r, R.phi64r, R.partials64r, R.cost64r, nullptr, nullptr,
+                  R.stream_b64);
+            ++fp64_sweeps;
+            std::vector<double> cr;
+            TRY(read_costs(ctx, R.cost64r, 1, cr));
+            if (cr[0] <= tol) {
+              TRY(check64(ctx, R, s, &c64[s]));
+              if (c64[s] <= tol) done = true;
+            }
+          }
+          if (done) break;
+        }
+      }
+      for (int s = 0; s < S; ++s)
+        if (!std::isnan(c64[s])) c[s] = c64[s];
+    }
+    if (!done && p->plateau_window > 0) {
+      bool changed = false;
+      for (int s = 0; s < S; ++s) {
+        if (!act[s]) continue;
+        if (std::isfinite(prev[s])) {
+          const bool improved = std::fabs(prev[s]) - std::fabs(c[s]) > p->diff_tol_r * std::fabs(c[s]);
+          stall[s] = improved ? 0 : stall[s] + 1;
+          if (stall[s] >= p->plateau_window && sweeps >= p->min_sweeps) {
+            act[s] = 0;
+            changed = true;
+          }
+        }
+      }
+      if (changed) {
+        bool any = false;
+        for (int s = 0; s < S; ++s) any |= act[s] != 0;
+        if (!any) done = true;
+        CK(cudaMemcpyAsync(R.active, act.data(), sizeof(int) * S, cudaMemcpyHostToDevice, st));
+      }
+    }
+    prev = c;
+    if (R.prec == QFS_MIXED)
+      std::fill(c64.begin(), c64.end(), std::numeric_limits<double>::quiet_NaN());
+  }
+  // Selection: lowest cost (FP64-confirmed where available), lowest index on ties.
+  int best = 0;
+  for (int s = 1; s < S; ++s)
+    if (prev[s] < prev[best]) best = s;
+  double cost = prev[best];
+  if (R.prec == QFS_MIXED) TRY(check64(ctx, R, best, &cost));
+  out.best = best;
+  out.cost = cost;
+  out.sweeps = sweeps;
+  out.converged = cost <= tol;
+  out.fp64_sweeps = fp64_sweeps;
+  out.start_costs = prev;
+  out.start_costs[best] = cost;
+  return QFS_OK;
+}
+
+int ctx_check(const qfs_ctx* ctx) {
+  if (!ctx) return fail(QFS_EINVAL, "context is NULL");
+  return QFS_OK;
+}
+
+int set_device(qfs_ctx* ctx) {
+  CK(cudaSetDevice(ctx->device));
+  return QFS_OK;
+}
+
+int instantiate_common(qfs_ctx* ctx, const qfs_circuit* c, const double* target, bool target_dev,
+                       const double* samples, bool samples_dev, const double* gates0,
+                       bool gates_dev, uint64_t seed, const qfs_params* p, double* gates_out,
+                       bool out_dev, qfs_result* result, double* start_costs) {
+  TRY(check_circuit(c));
+  if (!p) return fail(QFS_EINVAL, "params is NULL");
+  if (!target) return fail(QFS_EINVAL, "target is NULL");
+  if (!gates_out) return fail(QFS_EINVAL, "gates_out is NULL");
+  if (!result) return fail(QFS_EINVAL, "result is NULL");
+  TRY(check_run_params(c->n, p->M, p->multistarts, p->max_sweeps, p->precision, p->beta, p->dist_tol));
+  if (p->plateau_window < 0 || p->min_sweeps < 0 || !(p->diff_tol_r >= 0.0))
+    return fail(QFS_EINVAL, "plateau_window, min_sweeps and diff_tol_r must be >= 0");
+  if (p->precision == QFS_MIXED && p->refine_sweeps_max < 0)
+    return fail(QFS_EINVAL, "refine_sweeps_max must be >= 0");
+  TRY(ctx_check(ctx));
+  TRY(set_device(ctx));
+  Run R;
+  TRY(prepare(ctx, R, c, p->M, p->multistarts, p->precision, p->beta, !target_dev, false));
+  cudaStream_t st = ctx->stream;
+  const size_t gbytes = (size_t)R.S * R.L * 16 * sizeof(double2);
+  if (target_dev) {
+    R.U = reinterpret_cast<const double2*>(target);
+  } else {
+    CK(cudaMemcpyAsync(R.U_copy, target, (size_t)R.N * R.N * sizeof(double2), cudaMemcpyHostToDevice, st));
+    R.U = R.U_copy;
+  }
+  if (samples) {
+    CK(cudaMemcpyAsync(R.psi64, samples, (size_t)R.sN * sizeof(double2),
+                       samples_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  } else {
+    std::vector<std::complex<double>> h((size_t)R.sN);
+    generate_samples(seed, R.n, R.M, h.data());
+    CK(cudaMemcpyAsync(R.psi64, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  if (gates0) {
+    CK(cudaMemcpyAsync(R.g64, gates0, gbytes, gates_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  } else {
+    std::vector<std::complex<double>> h((size_t)R.S * R.L * 16);
+    generate_gates(seed, R.S * R.L, h.data());
+    CK(cudaMemcpyAsync(R.g64, h.data(), gbytes, cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  TRY(setup_inputs(ctx, R));
+  Outcome o;
+  TRY(run_multistart(ctx, R, p, o));
+  CK(cudaMemcpyAsync(gates_out, R.g64 + (size_t)o.best * R.L * 16, (size_t)R.L * 16 * sizeof(double2),
+                     out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  result->cost = o.cost;
+  result->sweeps = o.sweeps;
+  result->converged = o.converged;
+  result->best_start = o.best;
+  result->fp64_sweeps = o.fp64_sweeps;
+  if (start_costs) std::copy(o.start_costs.begin(), o.start_costs.end(), start_costs);
+  return QFS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void qfs_default_params(qfs_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof *p);
+  p->M = 2;
+  p->multistarts = 16;
+  p->max_sweeps = 10000;
+  p->min_sweeps = 6;
+  p->plateau_window = 0;
+  p->precision = QFS_FP64;
+  p->refine_sweeps_max = 50;
+  p->seed = 0;
+  p->dist_tol = 1e-8;
+  p->diff_tol_r = 1e-5;
+  p->beta = 0.0;
+}
+
+const char* qfs_last_error(void) { return g_err.c_str(); }
+
+int qfs_create(qfs_ctx** out, int device, void* cuda_stream) {
+  g_err.clear();
+  if (!out) return fail(QFS_EINVAL, "out is NULL");
+  *out = nullptr;
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess || count == 0)
+    return fail(QFS_ECUDA, "no CUDA device: %s", e != cudaSuccess ? cudaGetErrorString(e) : "count = 0");
+  if (device < 0 || device >= count) return fail(QFS_EINVAL, "device %d of %d", device, count);
+  qfs_ctx* ctx = new qfs_ctx();
+  ctx->device = device;
+  e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  int l2 = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device);
+  ctx->l2_bytes = (size_t)l2;
+  if (e == cudaSuccess) {
+    if (cuda_stream) {
+      ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    } else {
+      e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+      ctx->own_stream = e == cudaSuccess;
+    }
+  }
+  if (e != cudaSuccess) {
+    delete ctx;
+    return fail(QFS_ECUDA, "context set-up on device %d: %s", device, cudaGetErrorString(e));
+  }
+  *out = ctx;
+  return QFS_OK;
+}
+
+void qfs_destroy(qfs_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+  prof_harvest(ctx);
+  for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+int qfs_device_sms(const qfs_ctx* ctx) { return ctx ? ctx->num_sms : 0; }
+
+int qfs_profile_enable(qfs_ctx* ctx, int enable) {
+  g_err.clear();
+  TRY(ctx_check(ctx));
+  if (ctx->prof.on && !enable) {
+    CK(cudaStreamSynchronize(ctx->stream));
+    prof_harvest(ctx);
+  }
+  ctx->prof.on = enable != 0;
+  return QFS_OK;
+}
+
+int qfs_profile_reset(qfs_ctx* ctx) {
+  g_err.clear();
+  TRY(ctx_check(ctx));
+  CK(cudaStreamSynchronize(ctx->stream));
+  prof_harvest(ctx);
+  for (int i = 0; i < QFS_PROF_KINDS; ++i) {
+    ctx->prof.launches[i] = ctx->prof.timed[i] = 0;
+    ctx->prof.ms[i] = ctx->prof.bytes[i] = 0.0;
+  }
+  return QFS_OK;
+}
+
+int qfs_profile_read(qfs_ctx* ctx, int32_t kind, int64_t* launches, int64_t* timed,
+                     double* total_ms, double* total_bytes) {
+  g_err.clear();
+  TRY(ctx_check(ctx));
+  if (kind < -1 || kind >= QFS_PROF_KINDS) return fail(QFS_EINVAL, "kind = %d", kind);
+  CK(cudaStreamSynchronize(ctx->stream));
+  prof_harvest(ctx);
+  long long l = 0, t = 0;
+  double ms = 0.0, by = 0.0;
+  for (int i = 0; i < QFS_PROF_KINDS; ++i) {
+    if (kind != -1 && kind != i) continue;
+    l += ctx->prof.launches[i];
+    t += ctx->prof.timed[i];
+    ms += ctx->prof.ms[i];
+    by += ctx->prof.bytes[i];
+  }
+  if (launches) *launches = l;
+  if (timed) *timed = t;
+  if (total_ms) *total_ms = ms;
+  if (total_bytes) *total_bytes = by;
+  return QFS_OK;
+}
+
+int qfs_generate_inputs(uint64_t seed, int32_t n, int32_t M, int32_t S, int32_t L,
+                        double* samples_out, double* gates_out) {
+  g_err.clear();
+  if (n < 2 || n > QFS_MAX_QUBITS) return fail(QFS_EINVAL, "n = %d out of [2, %d]", n, QFS_MAX_QUBITS);
+  if (samples_out) {
+    if (M < 1 || (long long)M > (1LL << n)) return fail(QFS_EINVAL, "M = %d out of [1, 2^n]", M);
+    qfs::generate_samples(seed, n, M, reinterpret_cast<std::complex<double>*>(samples_out));
+  }
+  if (gates_out) {
+    if (S < 1 || L < 1) return fail(QFS_EINVAL, "S = %d, L = %d: need >= 1", S, L);
+    qfs::generate_gates(seed, S * L, reinterpret_cast<std::complex<double>*>(gates_out));
+  }
+  return QFS_OK;
+}
+
+int qfs_instantiate(qfs_ctx* ctx, const qfs_circuit* circuit, const double* target,
+                    const qfs_params* p, double* gates_out, qfs_result* result,
+                    double* start_costs) {
+  g_err.clear();
+  return instantiate_common(ctx, circuit, target, false, nullptr, false, nullptr, false,
+                            p ? p->seed : 0, p, gates_out, false, result, start_costs);
+}
+
+int qfs_instantiate_ex(qfs_ctx* ctx, const qfs_circuit* circuit, const double* target,
+                       const double* samples, const double* init_gates, const qfs_params* p,
+                       double* gates_out, qfs_result* result, double* start_costs) {
+  g_err.clear();
+  if (!samples || !init_gates) return fail(QFS_EINVAL, "samples and init_gates must be given");
+  return instantiate_common(ctx, circuit, target, false, samples, false, init_gates, false,
+                            0, p, gates_out, false, result, start_costs);
+}
+
+int qfs_instantiate_dev(qfs_ctx* ctx, const qfs_circuit* circuit, const double* target_dev,
+                        const double* samples_dev, const double* init_gates_dev,
+                        const qfs_params* p, double* gates_out_dev, qfs_result* result,
+                        double* start_costs) {
+  g_err.clear();
+  if (!samples_dev || !init_gates_dev) return fail(QFS_EINVAL, "samples and init_gates must be given");
+  return instantiate_common(ctx, circuit, target_dev, true, samples_dev, true, init_gates_dev, true,
+                            0, p, gates_out_dev, true, result, start_costs);
+}
+
+int qfs_sweep_once(qfs_ctx* ctx, const qfs_circuit* circuit, const double* target,
+                   const double* samples, int32_t M, int32_t S, const double* gates_in,
+                   int32_t precision, double beta, double* gates_out, double* envs_out,
+                   double* costs_out) {
+  g_err.clear();
+  TRY(check_circuit(circuit));
+  TRY(check_run_params(circuit->n, M, S, 1, precision, beta, 0.0));
+  if (!target || !samples || !gates_in || !gates_out)
+    return fail(QFS_EINVAL, "target, samples, gates_in and gates_out must be given");
+  TRY(ctx_check(ctx));
+  TRY(set_device(ctx));
+  Run R;
+  TRY(prepare(ctx, R, circuit, M, S, precision, beta, true, envs_out != nullptr));
+  cudaStream_t st = ctx->stream;
+  const size_t gbytes = (size_t)S * R.L * 16 * sizeof(double2);
+  CK(cudaMemcpyAsync(R.U_copy, target, (size_t)R.N * R.N * sizeof(double2), cudaMemcpyHostToDevice, st));
+  R.U = R.U_copy;
+  CK(cudaMemcpyAsync(R.psi64, samples, (size_t)R.sN * sizeof(double2), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(R.g64, gates_in, gbytes, cudaMemcpyHostToDevice, st));
+  TRY(setup_inputs(ctx, R));
+  const Real rs = precision == QFS_MIXED ? R32 : R64;
+  sweep(ctx, R, rs, S, R.sh, R.g64, R.g32, rs == R32 ? (const void*)R.psi32 : (const void*)R.psi64,
+        rs == R32 ? (const void*)R.phil32 : (const void*)R.phil64, R.B, R.phi, R.partials, R.costs,
+        R.envs, nullptr, R.stream_b);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(gates_out, R.g64, gbytes, cudaMemcpyDeviceToHost, st));
+  if (envs_out) CK(cudaMemcpyAsync(envs_out, R.envs, gbytes, cudaMemcpyDeviceToHost, st));
+  if (costs_out) CK(cudaMemcpyAsync(costs_out, R.costs, sizeof(double) * S, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return QFS_OK;
+}
+
+int qfs_gate_update(qfs_ctx* ctx, int32_t count, const double* envs, const double* gates_old,
+                    double beta, double* gates_out) {
+  g_err.clear();
+  if (count < 0) return fail(QFS_EINVAL, "count = %d", count);
+  if (count == 0) return QFS_OK;
+  if (!envs || !gates_out) return fail(QFS_EINVAL, "envs and gates_out must be given");
+  if (!(beta >= 0.0 && beta < 1.0)) return fail(QFS_EINVAL, "beta = %g: need 0 <= beta < 1", beta);
+  if (beta != 0.0 && !gates_old) return fail(QFS_EINVAL, "beta != 0 needs gates_old");
+  TRY(ctx_check(ctx));
+  TRY(set_device(ctx));
+  const size_t bytes = (size_t)count * 16 * sizeof(double2);
+  TRY(ensure_ws(ctx, 3 * align_up(bytes)));
+  double2* dE = reinterpret_cast<double2*>(ctx->ws);
+  double2* dG = reinterpret_cast<double2*>(ctx->ws + align_up(bytes));
+  double2* dO = reinterpret_cast<double2*>(ctx->ws + 2 * align_up(bytes));
+  cudaStream_t st = ctx->stream;
+  CK(cudaMemcpyAsync(dE, envs, bytes, cudaMemcpyHostToDevice, st));
+  if (gates_old) CK(cudaMemcpyAsync(dG, gates_old, bytes, cudaMemcpyHostToDevice, st));
+  ctx->prof.launches[QFS_PROF_UPDATE] += 1;
+  launch_gate_update_batch(count, dE, gates_old ? dG : nullptr, beta, dO, st);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(gates_out, dO, bytes, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return QFS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,485 @@
+// Streaming kernels of the QFactor-Sample sweep (Section 3 of the paper):
+// gate application to the stored list B of intermediate states, and the
+// fused backward step that carries the updated gate into Phi and reduces the
+// 4x4 environment of the next gate over the 2^(n-2)*M untouched amplitudes.
+//
+// These kernels are HBM-bound K=4 contractions: one 16-byte vector per row
+// per thread, four rows per group, coalesced because the M samples of a row
+// are contiguous.  No tensor cores: a 4x4 complex mat-vec per 64 bytes read
+// is far below any tensor-core ridge point.
+#include "qfs_common.cuh"
+#include "qfs_kernels.h"
+
+#include <algorithm>
+
+namespace qfs {
+
+Geom make_geom(int n, int M, int a, int b) {
+  Geom g;
+  g.n = n;
+  g.M = M;
+  g.pos_a = n - 1 - a;
+  g.pos_b = n - 1 - b;
+  g.lo = std::min(g.pos_a, g.pos_b);
+  g.hi = std::max(g.pos_a, g.pos_b);
+  g.sN = (long long)M << n;
+  return g;
+}
+
+Shape make_shape(int n, int M, int S, Real r, int num_sms) {
+  Shape sh;
+  sh.vec = (r == R32 && (M % 2) == 0) ? 2 : 1;
+  sh.units_per_start = (1 << (n - 2)) * (M / sh.vec);
+  const long long total = (long long)sh.units_per_start * S;
+  // Small problems use 128-thread blocks so more SMs take part.
+  sh.threads = total >= (long long)num_sms * 512 ? 256 : 128;
+  // Aim for about four blocks per SM over all starts.
+  long long want_blocks = (long long)num_sms * 4;
+  long long chunk = (total + want_blocks - 1) / want_blocks;
+  chunk = ((chunk + sh.threads - 1) / sh.threads) * sh.threads;
+  if (chunk < sh.threads) chunk = sh.threads;
+  if (chunk > sh.units_per_start) chunk = ((sh.units_per_start + 31) / 32) * 32;
+  sh.chunk = (int)chunk;
+  sh.nblk = (sh.units_per_start + sh.chunk - 1) / sh.chunk;
+  return sh;
+}
+
+template <typename T, int VEC> struct VecT;
+template <> struct VecT<float, 2> { using t = float4; };
+template <> struct VecT<float, 1> { using t = float2; };
+template <> struct VecT<double, 1> { using t = double2; };
+
+// Evict-first load for data read once per sweep.
+template <typename T, int VEC>
+__device__ __forceinline__ void ld(const typename C2<T>::t* p, typename C2<T>::t (&o)[VEC]) {
+  using V = typename VecT<T, VEC>::t;
+  V v = __ldcs(reinterpret_cast<const V*>(p));
+  if constexpr (VEC == 2) {
+    o[0] = float2{v.x, v.y};
+    o[1] = float2{v.z, v.w};
+  } else {
+    o[0] = v;
+  }
+}
+// Loads of data that a later kernel reads again (Phi, and the B list when it
+// fits in L2) use the default caching policy.
+template <typename T, int VEC>
+__device__ __forceinline__ void ld_keep(const typename C2<T>::t* p, typename C2<T>::t (&o)[VEC]) {
+  using V = typename VecT<T, VEC>::t;
+  V v = *reinterpret_cast<const V*>(p);
+  if constexpr (VEC == 2) {
+    o[0] = float2{v.x, v.y};
+    o[1] = float2{v.z, v.w};
+  } else {
+    o[0] = v;
+  }
+}
+template <typename T, int VEC>
+__device__ __forceinline__ void st(typename C2<T>::t* p, const typename C2<T>::t (&o)[VEC]) {
+  using V = typename VecT<T, VEC>::t;
+  if constexpr (VEC == 2) {
+    *reinterpret_cast<V*>(p) = V{o[0].x, o[0].y, o[1].x, o[1].y};
+  } else {
+    *reinterpret_cast<V*>(p) = o[0];
+  }
+}
+
+struct FwdArgs {
+  const void* in; long long in_stride;
+  void* out;
+  const void* gates; long long gate_stride;
+  Geom g; int units_per_start; int chunk;
+  const int* active;  // per-start flag, nullable (all active)
+};
+
+template <typename T, int VEC>
+__global__ void k_forward(FwdArgs a) {
+  using T2 = typename C2<T>::t;
+  const int s = blockIdx.y;
+  if (a.active && !a.active[s]) return;
+  __shared__ T2 gs[16];
+  if (threadIdx.x < 16) gs[threadIdx.x] = reinterpret_cast<const T2*>(a.gates)[s * a.gate_stride + threadIdx.x];
+  __syncthreads();
+  T2 gr[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) gr[i] = gs[i];
+  const T2* X = reinterpret_cast<const T2*>(a.in) + s * a.in_stride;
+  T2* Y = reinterpret_cast<T2*>(a.out) + s * a.g.sN;
+  const int MV = a.g.M / VEC;
+  const int u0 = blockIdx.x * a.chunk;
+  const int u1 = min(u0 + a.chunk, a.units_per_start);
+  for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
+    const int r = u / MV, jv = u - r * MV;
+    const uint32_t base = insert_two_zero_bits((uint32_t)r, a.g.lo, a.g.hi);
+    long long off[4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      const uint32_t row = base | ((uint32_t)(x >> 1) << a.g.pos_a) | ((uint32_t)(x & 1) << a.g.pos_b);
+      off[x] = (long long)row * a.g.M + (long long)jv * VEC;
+    }
+    T2 v[4][VEC];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) ld_keep<T, VEC>(X + off[x], v[x]);
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      T2 o[VEC];
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) {
+        T2 acc = cmul(gr[4 * x], v[0][q]);
+#pragma unroll
+        for (int xp = 1; xp < 4; ++xp) {
+          const T2 t = cmul(gr[4 * x + xp], v[xp][q]);
+          acc.x += t.x;
+          acc.y += t.y;
+        }
+        o[q] = acc;
+      }
+      st<T, VEC>(Y + off[x], o);
+    }
+  }
+}
+
+BwdGeom make_bwd_geom(int n, int M, int ua, int ub, int qa, int qb) {
+  BwdGeom g;
+  g.n = n;
+  g.M = M;
+  g.sN = (long long)M << n;
+  // Local bits U-1, U-2 carry the gate applied to Phi; the environment pair
+  // takes local bits of its own qubits, new qubits going to the low bits.
+  int q[4] = {ua, ub, -1, -1};
+  int U = 2;
+  for (int x : {qa, qb})
+    if (x != ua && x != ub) q[U++] = x;
+  g.U = U;
+  int local_of[4];
+  for (int i = 0; i < U; ++i) local_of[i] = U - 1 - i;  // q[0] -> U-1, q[1] -> U-2, q[2] -> U-3, ...
+  for (int i = 0; i < 4; ++i) g.pos[i] = 0;
+  for (int i = 0; i < U; ++i) g.pos[local_of[i]] = n - 1 - q[i];
+  auto local = [&](int qubit) {
+    for (int i = 0; i < U; ++i)
+      if (q[i] == qubit) return local_of[i];
+    return -1;
+  };
+  g.ea = local(qa);
+  g.eb = local(qb);
+  int srt[4];
+  for (int i = 0; i < U; ++i) srt[i] = g.pos[i];
+  std::sort(srt, srt + U);
+  for (int i = 0; i < 4; ++i) g.ins[i] = i < U ? srt[i] : 31;
+  return g;
+}
+
+Shape make_bwd_shape(int n, int M, int S, Real r, int num_sms, int U) {
+  Shape sh;
+  sh.vec = (r == R32 && (M % 2) == 0) ? 2 : 1;
+  sh.units_per_start = (1 << (n - U)) * (M / sh.vec);
+  const long long total = (long long)sh.units_per_start * S;
+  sh.threads = total >= (long long)num_sms * 512 ? 256 : 128;
+  long long want_blocks = (long long)num_sms * 4;
+  long long chunk = (total + want_blocks - 1) / want_blocks;
+  chunk = ((chunk + sh.threads - 1) / sh.threads) * sh.threads;
+  if (chunk < sh.threads) chunk = sh.threads;
+  if (chunk > sh.units_per_start) chunk = ((sh.units_per_start + 31) / 32) * 32;
+  sh.chunk = (int)chunk;
+  sh.nblk = (sh.units_per_start + sh.chunk - 1) / sh.chunk;
+  return sh;
+}
+
+struct BwdArgs {
+  const void* bprev; long long bprev_stride;
+  const void* phi_in; long long phi_in_stride;
+  void* phi_out;
+  const void* gates; long long gate_stride;
+  double* partials; int nblk;
+  BwdGeom g; int units_per_start; int chunk;
+  int stream_b;   // B_{k-1} is read once per sweep: load it evict-first
+  const int* active;
+};
+
+// Row t (0 <= t < 2^U) of a unit with the bits of j placed on the local
+// bits other than EA and EB.
+template <int U, int EA, int EB>
+__device__ __forceinline__ constexpr int spread_rest(int j) {
+  int t = 0, bit = 0;
+  for (int i = 0; i < U; ++i) {
+    if (i == EA || i == EB) continue;
+    t |= ((j >> bit) & 1) << i;
+    ++bit;
+  }
+  return t;
+}
+
+// One backward step.  A thread unit owns the 2^U rows spanned by the qubits
+// of gate k+1 (local bits U-1, U-2) and gate k (local bits EA, EB) for VEC
+// consecutive samples.  It carries the new gate k+1 into Phi
+// (Phi_k = g_{k+1}^dagger Phi_{k+1}), stores Phi_k, and accumulates
+// E_k[x][y] += B_{k-1}[x] conj(Phi_k[y]) over the groups of gate k.
+// MODE 1 accumulates sum |Phi_k - B|^2 instead (the residual cost).
+template <typename T, int VEC, int MODE, int U, int EA, int EB>
+__global__ void k_backward(BwdArgs a) {
+  using T2 = typename C2<T>::t;
+  constexpr int ROWS = 1 << U;
+  const int s = blockIdx.y;
+  if (a.active && !a.active[s]) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ T2 gs[16];
+  __shared__ double red[8][32];
+  const bool has_gate = a.gates != nullptr;
+  if (threadIdx.x < 16)
+    gs[threadIdx.x] = has_gate ? reinterpret_cast<const T2*>(a.gates)[s * a.gate_stride + threadIdx.x] : T2{};
+  __syncthreads();
+  // g^dagger[y][y'] = conj(g[y'][y]), read from shared memory (broadcast).
+  auto gd = [&](int y, int yp) {
+    const T2 t = gs[4 * yp + y];
+    return T2{t.x, -t.y};
+  };
+  const T2* B = reinterpret_cast<const T2*>(a.bprev) + s * a.bprev_stride;
+  const T2* P = reinterpret_cast<const T2*>(a.phi_in) + s * a.phi_in_stride;
+  T2* Po = a.phi_out ? reinterpret_cast<T2*>(a.phi_out) + s * a.g.sN : nullptr;
+  const uint32_t M = (uint32_t)a.g.M;
+  uint32_t dpos[U];
+#pragma unroll
+  for (int i = 0; i < U; ++i) dpos[i] = (1u << a.g.pos[i]) * M;
+
+  T acc[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) acc[i] = T(0);
+
+  const int MV = a.g.M / VEC;
+  const int u0 = blockIdx.x * a.chunk;
+  const int u1 = min(u0 + a.chunk, a.units_per_start);
+  for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
+    const int r = u / MV, jv = u - r * MV;
+    uint32_t base = (uint32_t)r;
+#pragma unroll
+    for (int i = 0; i < U; ++i) {
+      const int p = a.g.ins[i];
+      base = ((base >> p) << (p + 1)) | (base & ((1u << p) - 1u));
+    }
+    const uint32_t base_off = base * M + (uint32_t)jv * VEC;
+    auto off = [&](int t) {
+      uint32_t o = base_off;
+#pragma unroll
+      for (int i = 0; i < U; ++i)
+        if ((t >> i) & 1) o += dpos[i];
+      return o;
+    };
+    T2 ph[ROWS][VEC];
+#pragma unroll
+    for (int t = 0; t < ROWS; ++t) ld_keep<T, VEC>(P + off(t), ph[t]);
+    if (has_gate) {
+#pragma unroll
+      for (int t0 = 0; t0 < ROWS / 4; ++t0) {
+        T2 nw[4][VEC];
+#pragma unroll
+        for (int y = 0; y < 4; ++y)
+#pragma unroll
+          for (int q = 0; q < VEC; ++q) {
+            T2 acc2 = cmul(gd(y, 0), ph[(0 << (U - 2)) | t0][q]);
+#pragma unroll
+            for (int yp = 1; yp < 4; ++yp) {
+              const T2 w = cmul(gd(y, yp), ph[(yp << (U - 2)) | t0][q]);
+              acc2.x += w.x;
+              acc2.y += w.y;
+            }
+            nw[y][q] = acc2;
+          }
+#pragma unroll
+        for (int y = 0; y < 4; ++y)
+#pragma unroll
+          for (int q = 0; q < VEC; ++q) ph[(y << (U - 2)) | t0][q] = nw[y][q];
+      }
+      if (Po) {
+#pragma unroll
+        for (int t = 0; t < ROWS; ++t) st<T, VEC>(Po + off(t), ph[t]);
+      }
+    }
+    if constexpr (MODE == 0) {
+#pragma unroll
+      for (int j = 0; j < ROWS / 4; ++j) {
+        const int rest = spread_rest<U, EA, EB>(j);
+        T2 b[4][VEC];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          const int t = rest | ((x >> 1) << EA) | ((x & 1) << EB);
+          if (a.stream_b) ld<T, VEC>(B + off(t), b[x]);
+          else ld_keep<T, VEC>(B + off(t), b[x]);
+        }
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) {
+            const int ty = rest | ((y >> 1) << EA) | ((y & 1) << EB);
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) {
+              const T2 bb = b[x][q], pp = ph[ty][q];
+              acc[2 * (4 * x + y)] += bb.x * pp.x + bb.y * pp.y;
+              acc[2 * (4 * x + y) + 1] += bb.y * pp.x - bb.x * pp.y;
+            }
+          }
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < ROWS; ++t) {
+        T2 b[VEC];
+        ld_keep<T, VEC>(B + off(t), b);
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) {
+          const T dx = ph[t][q].x - b[q].x, dy = ph[t][q].y - b[q].y;
+          acc[0] += dx * dx + dy * dy;
+        }
+      }
+    }
+  }
+
+  double mine;
+  if constexpr (MODE == 0) {
+    mine = (double)warp_reduce_scatter32<T>(acc, lane);
+  } else {
+    double v = (double)acc[0];
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(FULL, v, m);
+    mine = lane == 0 ? v : 0.0;
+  }
+  red[warp][lane] = mine;
+  __syncthreads();
+  if (warp == 0) {
+    double t = 0.0;
+    const int nw = blockDim.x >> 5;
+    for (int w = 0; w < nw; ++w) t += red[w][lane];
+    a.partials[((long long)s * a.nblk + blockIdx.x) * 32 + lane] = t;
+  }
+}
+
+void launch_forward(Real r, const Geom& g, const Shape& sh, int S, const void* in,
+                    long long in_stride, void* out, const void* gates, long long gate_stride,
+                    const int* active, cudaStream_t st) {
+  FwdArgs a{in, in_stride, out, gates, gate_stride, g, sh.units_per_start, sh.chunk, active};
+  dim3 grid(sh.nblk, S);
+  if (r == R32) {
+    if (sh.vec == 2) k_forward<float, 2><<<grid, sh.threads, 0, st>>>(a);
+    else k_forward<float, 1><<<grid, sh.threads, 0, st>>>(a);
+  } else {
+    k_forward<double, 1><<<grid, sh.threads, 0, st>>>(a);
+  }
+}
+
+template <typename T, int VEC, int MODE>
+static void bwd_dispatch(const BwdArgs& a, dim3 grid, int threads, cudaStream_t st) {
+  const int U = a.g.U, ea = a.g.ea, eb = a.g.eb;
+  if constexpr (MODE == 1) {
+    k_backward<T, VEC, 1, 2, 1, 0><<<grid, threads, 0, st>>>(a);
+  } else {
+    if (U == 4) k_backward<T, VEC, 0, 4, 1, 0><<<grid, threads, 0, st>>>(a);
+    else if (U == 3) {
+      if (ea == 2 && eb == 0) k_backward<T, VEC, 0, 3, 2, 0><<<grid, threads, 0, st>>>(a);
+      else if (ea == 0 && eb == 2) k_backward<T, VEC, 0, 3, 0, 2><<<grid, threads, 0, st>>>(a);
+      else if (ea == 1 && eb == 0) k_backward<T, VEC, 0, 3, 1, 0><<<grid, threads, 0, st>>>(a);
+      else k_backward<T, VEC, 0, 3, 0, 1><<<grid, threads, 0, st>>>(a);
+    } else {
+      if (ea == 1) k_backward<T, VEC, 0, 2, 1, 0><<<grid, threads, 0, st>>>(a);
+      else k_backward<T, VEC, 0, 2, 0, 1><<<grid, threads, 0, st>>>(a);
+    }
+  }
+}
+
+void launch_backward(Real r, int mode, const BwdGeom& g, const Shape& sh, int S,
+                     const void* bprev, long long bprev_stride, const void* phi_in,
+                     long long phi_in_stride, void* phi_out, const void* gates,
+                     long long gate_stride, double* partials, int stream_b, const int* active,
+                     cudaStream_t st) {
+  BwdArgs a{bprev, bprev_stride, phi_in, phi_in_stride, phi_out, gates, gate_stride,
+            partials, sh.nblk, g, sh.units_per_start, sh.chunk, stream_b, active};
+  dim3 grid(sh.nblk, S);
+  if (r == R32) {
+    if (sh.vec == 2) {
+      if (mode == 0) bwd_dispatch<float, 2, 0>(a, grid, sh.threads, st);
+      else bwd_dispatch<float, 2, 1>(a, grid, sh.threads, st);
+    } else {
+      if (mode == 0) bwd_dispatch<float, 1, 0>(a, grid, sh.threads, st);
+      else bwd_dispatch<float, 1, 1>(a, grid, sh.threads, st);
+    }
+  } else {
+    if (mode == 0) bwd_dispatch<double, 1, 0>(a, grid, sh.threads, st);
+    else bwd_dispatch<double, 1, 1>(a, grid, sh.threads, st);
+  }
+}
+
+// ------------------------------------------------------------ U * Psi (FP64)
+
+// Each block computes 16 rows x 32 columns; each thread two rows of one column.
+__global__ void k_gemm_upsi(const double2* __restrict__ U, const double2* __restrict__ Psi,
+                            double2* __restrict__ out, int N, int M) {
+  __shared__ double2 Us[16][33];
+  __shared__ double2 Ps[32][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  const int row0 = blockIdx.x * 16;
+  const int col = blockIdx.y * 32 + tx;
+  double2 acc0{0.0, 0.0}, acc1{0.0, 0.0};
+  for (int k0 = 0; k0 < N; k0 += 32) {
+    for (int i = ty; i < 16; i += 8) {
+      const int row = row0 + i, k = k0 + tx;
+      Us[i][tx] = (row < N && k < N) ? U[(long long)row * N + k] : double2{0.0, 0.0};
+    }
+    for (int i = ty; i < 32; i += 8) {
+      const int k = k0 + i;
+      Ps[i][tx] = (k < N && col < M) ? Psi[(long long)k * M + col] : double2{0.0, 0.0};
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) {
+      const double2 p = Ps[k][tx];
+      const double2 u0 = Us[2 * ty][k], u1 = Us[2 * ty + 1][k];
+      acc0.x = fma(u0.x, p.x, fma(-u0.y, p.y, acc0.x));
+      acc0.y = fma(u0.x, p.y, fma(u0.y, p.x, acc0.y));
+      acc1.x = fma(u1.x, p.x, fma(-u1.y, p.y, acc1.x));
+      acc1.y = fma(u1.x, p.y, fma(u1.y, p.x, acc1.y));
+    }
+    __syncthreads();
+  }
+  if (col < M) {
+    const int r0 = row0 + 2 * ty;
+    if (r0 < N) out[(long long)r0 * M + col] = acc0;
+    if (r0 + 1 < N) out[(long long)(r0 + 1) * M + col] = acc1;
+  }
+}
+
+void launch_gemm_upsi(const double2* U, const double2* Psi, double2* out, int N, int M,
+                      cudaStream_t st) {
+  dim3 grid((N + 15) / 16, (M + 31) / 32);
+  k_gemm_upsi<<<grid, dim3(32, 8), 0, st>>>(U, Psi, out, N, M);
+}
+
+__global__ void k_cast(const double2* in, float2* out, long long count) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = in[i];
+    out[i] = float2{(float)v.x, (float)v.y};
+  }
+}
+
+void launch_cast_c128_to_c64(const double2* in, float2* out, long long count, cudaStream_t st) {
+  if (count <= 0) return;
+  long long blocks = (count + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  k_cast<<<(int)blocks, 256, 0, st>>>(in, out, count);
+}
+
+__global__ void k_nonfinite(const double* x, long long count, int* flag) {
+  int bad = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    bad |= !isfinite(v);
+  }
+  if (__any_sync(FULL, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
+void launch_nonfinite_check(const double* x, long long count, int* flag, cudaStream_t st) {
+  if (count <= 0) return;
+  long long blocks = (count + 255) / 256;
+  if (blocks > 2048) blocks = 2048;
+  k_nonfinite<<<(int)blocks, 256, 0, st>>>(x, count, flag);
+}
+
+}  // namespace qfs

@@ -1,0 +1,100 @@
+// Internal launcher interface between the engine (host C++) and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qfs {
+
+enum Real { R32 = 0, R64 = 1 };
+
+// Geometry of one gate step on one state shape.
+struct Geom {
+  int n;          // qubits
+  int M;          // samples (columns)
+  int pos_a;      // bit position of qubit a: n-1-a
+  int pos_b;      // bit position of qubit b
+  int lo, hi;     // min/max of the two positions
+  long long sN;   // N*M complex elements per state
+};
+Geom make_geom(int n, int M, int a, int b);
+
+// Geometry of a fused backward step: the union of the qubits of the gate
+// carried into Phi (ua, ub) and of the gate whose environment is reduced
+// (qa, qb).  Local bits U-1, U-2 are (ua, ub); EA, EB are the local bits of
+// (qa, qb).  pos[i] is the row-bit position of local bit i; ins[] the same
+// positions sorted ascending (for inserting zero bits into a unit index).
+struct BwdGeom {
+  int n, M;
+  long long sN;
+  int U;
+  int pos[4];
+  int ins[4];
+  int ea, eb;
+};
+BwdGeom make_bwd_geom(int n, int M, int ua, int ub, int qa, int qb);
+
+// Launch shape of the streaming kernels for one (n, M, S, precision).
+struct Shape {
+  int vec;              // complex samples per thread unit (2 for fp32, 1 for fp64)
+  int units_per_start;  // (N/4) * (M/vec)
+  int chunk;            // units per block
+  int nblk;             // blocks per start
+  int threads;          // block size
+};
+Shape make_shape(int n, int M, int S, Real r, int num_sms);
+// Shape of a backward step whose unit spans 2^U rows.
+Shape make_bwd_shape(int n, int M, int S, Real r, int num_sms, int U);
+
+// B_out[s] = g[s] B_in[s] for each start s (B_in shared when in_stride = 0).
+void launch_forward(Real r, const Geom& g, const Shape& sh, int S,
+                    const void* in, long long in_stride, void* out,
+                    const void* gates, long long gate_stride, const int* active,
+                    cudaStream_t st);
+
+// Environment partials of one backward step.  Phi_k = g^dagger Phi_in on
+// the pair (ua, ub) of the geometry when `gate` is non-null (else Phi_k =
+// Phi_in); Phi_k is stored to phi_out when non-null; per-block partial sums
+// of E[x][y] += Bprev[x] conj(Phi_k[y]) over the pair (qa, qb) go to
+// partials[(s*nblk + blk)*32 + 2*(4x+y) + {0: re, 1: im}].
+// mode 1: instead of E, slot 0 gets sum |Phi_k - Bprev|^2 (needs U = 2).
+void launch_backward(Real r, int mode, const BwdGeom& g, const Shape& sh, int S,
+                     const void* bprev, long long bprev_stride,
+                     const void* phi_in, long long phi_in_stride, void* phi_out,
+                     const void* gates, long long gate_stride,
+                     double* partials, int stream_b, const int* active, cudaStream_t st);
+
+// One warp per start: sum the partials, form (1-beta) E + beta g_old^dagger,
+// take the unitary polar factor of its adjoint (the SVD update of Eq. 2),
+// write it to g64 (and to g32 as complex64 when non-null).  When cost_out is
+// non-null it receives 2 - (2/M) Re Tr(g_new E).  When env_out is non-null
+// the environment itself is stored there (16 complex128 per start).
+struct UpdateArgs {
+  const double* partials; int nblk;
+  double2* g64; long long g_stride;     // gate to replace, per start
+  float2* g32;                           // complex64 copy (nullable)
+  double beta;
+  double* cost_out; double inv_M;        // nullable
+  double2* env_out; long long env_stride;  // nullable
+  int S;
+  const int* active;                     // nullable: all starts active
+};
+void launch_update(const UpdateArgs& a, cudaStream_t st);
+
+// Residual cost: cost[s] = sum_blk partial[s][blk][0] * inv_M.
+void launch_residual_finish(const double* partials, int nblk, int S, double inv_M,
+                            double* cost_out, cudaStream_t st);
+
+// Batched polar update of independent environments (the a4 step alone).
+void launch_gate_update_batch(int count, const double2* envs, const double2* g_old,
+                              double beta, double2* g_out, cudaStream_t st);
+
+// out (N x M, complex128) = U (N x N) * Psi (N x M), all row-major.
+void launch_gemm_upsi(const double2* U, const double2* Psi, double2* out, int N, int M,
+                      cudaStream_t st);
+
+void launch_cast_c128_to_c64(const double2* in, float2* out, long long count, cudaStream_t st);
+
+// flag[0] |= 1 when any of the `count` doubles is NaN or infinite.
+void launch_nonfinite_check(const double* x, long long count, int* flag, cudaStream_t st);
+
+}  // namespace qfs

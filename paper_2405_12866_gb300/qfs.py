@@ -1,0 +1,259 @@
+"""ctypes binding of libqfs (include/qfs.h).  Argument marshalling only.
+
+Every computation runs in the library's CUDA kernels.  The library must be
+built (``paper_2405_12866_gb300.build.build()``); if it is missing or cannot
+load, `lib()` raises instead of falling back to anything else.
+
+Host arrays are numpy complex128; device arrays are torch complex128 CUDA
+tensors (their data pointers are handed to the library as they are).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libqfs.so")
+
+QFS_OK = 0
+QFS_EINVAL = -1
+QFS_ENOMEM = -2
+QFS_ECUDA = -3
+QFS_ETIMEOUT = -4
+QFS_EUNSUPPORTED = -5
+QFS_ENONFINITE = -6
+QFS_FP64 = 0
+QFS_MIXED = 1
+
+# Every function the header declares; the CPU tests check the library exports them.
+EXPORTS = [
+    "qfs_default_params", "qfs_create", "qfs_destroy", "qfs_last_error", "qfs_device_sms",
+    "qfs_generate_inputs", "qfs_instantiate", "qfs_instantiate_ex", "qfs_instantiate_dev",
+    "qfs_sweep_once", "qfs_gate_update", "qfs_profile_enable", "qfs_profile_reset",
+    "qfs_profile_read",
+]
+PROF_BACKWARD, PROF_FORWARD, PROF_UPDATE, PROF_GEMM, PROF_RESIDUAL, PROF_CHECK, PROF_OTHER = range(7)
+PROF_NAMES = ["backward", "forward", "update", "gemm", "residual", "check", "other"]
+
+
+class QfsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"qfs error {code}: {msg}")
+        self.code = code
+
+
+class Circuit(C.Structure):
+    _fields_ = [("n", C.c_int32), ("L", C.c_int32), ("pairs", C.POINTER(C.c_int32))]
+
+
+class Params(C.Structure):
+    _fields_ = [("M", C.c_int32), ("multistarts", C.c_int32), ("max_sweeps", C.c_int32),
+                ("min_sweeps", C.c_int32), ("plateau_window", C.c_int32),
+                ("precision", C.c_int32), ("refine_sweeps_max", C.c_int32),
+                ("reserved0", C.c_int32), ("seed", C.c_uint64), ("dist_tol", C.c_double),
+                ("diff_tol_r", C.c_double), ("beta", C.c_double)]
+
+
+class Result(C.Structure):
+    _fields_ = [("cost", C.c_double), ("sweeps", C.c_int32), ("converged", C.c_int32),
+                ("best_start", C.c_int32), ("fp64_sweeps", C.c_int32)]
+
+
+_lib = None
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+
+
+def lib():
+    """Load libqfs.so (once).  Raises if it is not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built: run paper_2405_12866_gb300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    L.qfs_default_params.argtypes = [C.POINTER(Params)]
+    L.qfs_default_params.restype = None
+    L.qfs_create.argtypes = [C.POINTER(_P), C.c_int, _P]
+    L.qfs_destroy.argtypes = [_P]
+    L.qfs_destroy.restype = None
+    L.qfs_last_error.argtypes = []
+    L.qfs_last_error.restype = C.c_char_p
+    L.qfs_device_sms.argtypes = [_P]
+    L.qfs_generate_inputs.argtypes = [C.c_uint64, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P, _P]
+    L.qfs_instantiate.argtypes = [_P, C.POINTER(Circuit), _P, C.POINTER(Params), _P,
+                                  C.POINTER(Result), _P]
+    L.qfs_instantiate_ex.argtypes = [_P, C.POINTER(Circuit), _P, _P, _P, C.POINTER(Params), _P,
+                                     C.POINTER(Result), _P]
+    L.qfs_instantiate_dev.argtypes = [_P, C.POINTER(Circuit), _P, _P, _P, C.POINTER(Params), _P,
+                                      C.POINTER(Result), _P]
+    L.qfs_sweep_once.argtypes = [_P, C.POINTER(Circuit), _P, _P, C.c_int32, C.c_int32, _P,
+                                 C.c_int32, C.c_double, _P, _P, _P]
+    L.qfs_gate_update.argtypes = [_P, C.c_int32, _P, _P, C.c_double, _P]
+    L.qfs_profile_enable.argtypes = [_P, C.c_int]
+    L.qfs_profile_reset.argtypes = [_P]
+    L.qfs_profile_read.argtypes = [_P, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                   C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    _lib = L
+    return L
+
+
+def _check(code: int):
+    if code != QFS_OK:
+        raise QfsError(code, lib().qfs_last_error().decode())
+
+
+def _ptr(a) -> int | None:
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()  # torch tensor
+
+
+def _host_c128(a, shape=None) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    if shape is not None and a.size != int(np.prod(shape)):
+        raise ValueError(f"expected {int(np.prod(shape))} complex values, got {a.size}")
+    return a
+
+
+class _CircuitArg:
+    def __init__(self, n: int, pairs):
+        self.pairs = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1))
+        self.c = Circuit(n, len(self.pairs) // 2, self.pairs.ctypes.data_as(C.POINTER(C.c_int32)))
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    lib().qfs_default_params(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+@dataclasses.dataclass
+class InstantiateOutput:
+    gates: object          # (L, 4, 4) numpy, or the device tensor given as out
+    cost: float
+    sweeps: int
+    converged: bool
+    best_start: int
+    fp64_sweeps: int
+    start_costs: np.ndarray
+
+
+def generate_inputs(seed: int, n: int, M: int, S: int, L: int):
+    """The library's own draws of samples (N x M) and initial gates (S, L, 4, 4)."""
+    samples = np.zeros((1 << n, M), dtype=np.complex128)
+    gates = np.zeros((S, L, 4, 4), dtype=np.complex128)
+    _check(lib().qfs_generate_inputs(seed, n, M, S, L, samples.ctypes.data, gates.ctypes.data))
+    return samples, gates
+
+
+class Context:
+    """A libqfs context on one CUDA device (optionally on a given stream)."""
+
+    def __init__(self, device: int = 0, stream: int | None = None):
+        self._h = _P()
+        _check(lib().qfs_create(C.byref(self._h), device, stream))
+
+    def close(self):
+        if self._h:
+            lib().qfs_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def num_sms(self) -> int:
+        return lib().qfs_device_sms(self._h)
+
+    def instantiate(self, n, pairs, target, params: Params, samples=None, init_gates=None):
+        """Host arrays in, numpy gates out.  samples/init_gates None -> drawn from params.seed."""
+        cir = _CircuitArg(n, pairs)
+        N = 1 << n
+        target = _host_c128(target, (N, N))
+        out = np.zeros((cir.c.L, 4, 4), dtype=np.complex128)
+        res = Result()
+        costs = np.zeros(params.multistarts, dtype=np.float64)
+        if samples is None and init_gates is None:
+            _check(lib().qfs_instantiate(self._h, C.byref(cir.c), target.ctypes.data, C.byref(params),
+                                         out.ctypes.data, C.byref(res), costs.ctypes.data))
+        else:
+            samples = _host_c128(samples, (N, params.M))
+            init_gates = _host_c128(init_gates, (params.multistarts, cir.c.L, 4, 4))
+            _check(lib().qfs_instantiate_ex(self._h, C.byref(cir.c), target.ctypes.data,
+                                            samples.ctypes.data, init_gates.ctypes.data,
+                                            C.byref(params), out.ctypes.data, C.byref(res),
+                                            costs.ctypes.data))
+        return InstantiateOutput(out, res.cost, res.sweeps, bool(res.converged), res.best_start,
+                                 res.fp64_sweeps, costs)
+
+    def instantiate_dev(self, n, pairs, target, samples, init_gates, params: Params, out):
+        """Device (torch complex128 CUDA) tensors in and out."""
+        cir = _CircuitArg(n, pairs)
+        for name, t in (("target", target), ("samples", samples), ("init_gates", init_gates), ("out", out)):
+            if not (t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.complex128"):
+                raise ValueError(f"{name} must be a contiguous complex128 CUDA tensor")
+        res = Result()
+        costs = np.zeros(params.multistarts, dtype=np.float64)
+        _check(lib().qfs_instantiate_dev(self._h, C.byref(cir.c), target.data_ptr(), samples.data_ptr(),
+                                         init_gates.data_ptr(), C.byref(params), out.data_ptr(),
+                                         C.byref(res), costs.ctypes.data))
+        return InstantiateOutput(out, res.cost, res.sweeps, bool(res.converged), res.best_start,
+                                 res.fp64_sweeps, costs)
+
+    def sweep_once(self, n, pairs, target, samples, gates, precision=QFS_FP64, beta=0.0,
+                   want_envs=True):
+        """One sweep for S starts; returns (gates (S,L,4,4), envs or None, costs (S,))."""
+        cir = _CircuitArg(n, pairs)
+        N = 1 << n
+        gates = _host_c128(gates)
+        S = gates.shape[0] if gates.ndim == 4 else 1
+        gates = gates.reshape(S, cir.c.L, 4, 4)
+        samples = _host_c128(samples)
+        M = samples.shape[1]
+        target = _host_c128(target, (N, N))
+        out = np.zeros_like(gates)
+        envs = np.zeros_like(gates) if want_envs else None
+        costs = np.zeros(S)
+        _check(lib().qfs_sweep_once(self._h, C.byref(cir.c), target.ctypes.data, samples.ctypes.data,
+                                    M, S, gates.ctypes.data, precision, beta, out.ctypes.data,
+                                    envs.ctypes.data if envs is not None else None, costs.ctypes.data))
+        return out, envs, costs
+
+    def profile(self, enable: bool):
+        _check(lib().qfs_profile_enable(self._h, int(enable)))
+
+    def profile_reset(self):
+        _check(lib().qfs_profile_reset(self._h))
+
+    def profile_read(self, kind: int = -1) -> dict:
+        """Counters of one kernel kind (PROF_*), or of all with kind = -1."""
+        l, t, ms, by = C.c_int64(), C.c_int64(), C.c_double(), C.c_double()
+        _check(lib().qfs_profile_read(self._h, kind, C.byref(l), C.byref(t), C.byref(ms), C.byref(by)))
+        return {"launches": l.value, "timed": t.value, "ms": ms.value, "bytes": by.value}
+
+    def gate_update(self, envs, gates_old=None, beta=0.0):
+        envs = _host_c128(envs).reshape(-1, 4, 4)
+        out = np.zeros_like(envs)
+        g = None if gates_old is None else _host_c128(gates_old).reshape(-1, 4, 4)
+        _check(lib().qfs_gate_update(self._h, envs.shape[0], envs.ctypes.data,
+                                     g.ctypes.data if g is not None else None, beta, out.ctypes.data))
+        return out
