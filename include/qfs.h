@@ -183,6 +183,39 @@ int qfs_sweep_once(qfs_ctx* ctx, const qfs_circuit* circuit, const double* targe
 int qfs_gate_update(qfs_ctx* ctx, int32_t count, const double* envs, const double* gates_old,
                     double beta, double* gates_out);
 
+/* One FP64 sweep (as qfs_sweep_once with QFS_FP64) that allocates no
+ * memory, for callers that cannot call cudaMalloc: code running inside a
+ * host framework that owns every device byte through its own allocator or a
+ * fixed memory budget, and code that must not reach cudaMalloc/cudaFree
+ * because those calls can synchronise the whole device.  The paper has no
+ * counterpart; this is a deployment variant of the sweep.
+ *
+ * Every array is device memory supplied by the caller, on the current CUDA
+ * device: target_dev (N x N), samples_dev (N x M), gates_in_dev and
+ * gates_out_dev (S x L x 16; they may be the same buffer), costs_out_dev
+ * (S doubles, may be NULL: 2 - (2/M) Re Tr(g_1 E_1) per start) and
+ * envs_out_dev (S x L x 16, may be NULL).  The call is enqueued on
+ * `cuda_stream` (a cudaStream_t, NULL = the legacy default stream) and
+ * returns without waiting for it.
+ *
+ * The sweep's scratch (U Psi, the B list, Phi, reduction partials) is one
+ * statically sized device array of QFS_NOALLOC_SCRATCH_BYTES, which every
+ * GPU that loads the library holds until the process exits.  A problem
+ * whose scratch, N*M*16 * (1 + S*max(L-1,1) + S) bytes plus the partials,
+ * exceeds it is rejected with QFS_EUNSUPPORTED and a message giving the
+ * size it needs.  All calls on a device share the array and it keeps the
+ * last call's contents; every scratch word a sweep reads is written earlier
+ * in the same call, so nothing has to be cleared between calls, but calls
+ * that overlap on the GPU (two streams, or two host threads) race on it.
+ * The first call on each device looks up the array's device address with
+ * cudaGetSymbolAddress (with that device current) and caches it; make that
+ * first call before any stream capture. */
+#define QFS_NOALLOC_SCRATCH_BYTES (16u << 20)
+int qfs_sweep_once_noalloc(void* cuda_stream, const qfs_circuit* circuit, const double* target_dev,
+                           const double* samples_dev, int32_t M, int32_t S, double beta,
+                           const double* gates_in_dev, double* gates_out_dev,
+                           double* costs_out_dev, double* envs_out_dev);
+
 #ifdef __cplusplus
 }
 #endif

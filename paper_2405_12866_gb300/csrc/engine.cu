@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstring>
 #include <limits>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -840,3 +841,113 @@ int qfs_gate_update(qfs_ctx* ctx, int32_t count, const double* envs, const doubl
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free single sweep.  The scratch of the sweep (U Psi, the B list,
+// Phi and the reduction partials) lives in one statically sized device array
+// instead of the context's cudaMalloc'd workspace, for callers that may not
+// allocate device memory.  The paper has no counterpart.
+
+namespace {
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[QFS_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+int g_noalloc_sms[kMaxDevices] = {};
+int g_noalloc_l2[kMaxDevices] = {};
+
+// Once per device, with that device current: the device address of the
+// scratch array (host code cannot use the symbol itself) and the SM count.
+int noalloc_setup(int dev, void** ptr, int* sms, int* l2) {
+  if (dev < 0 || dev >= kMaxDevices) return fail(QFS_EUNSUPPORTED, "device %d >= %d", dev, kMaxDevices);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    int s = 0, l = 0;
+    CK(cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev));
+    CK(cudaDeviceGetAttribute(&l, cudaDevAttrL2CacheSize, dev));
+    g_noalloc_sms[dev] = s;
+    g_noalloc_l2[dev] = l;
+    g_noalloc_ptr[dev] = p;
+  }
+  *ptr = g_noalloc_ptr[dev];
+  *sms = g_noalloc_sms[dev];
+  *l2 = g_noalloc_l2[dev];
+  return QFS_OK;
+}
+
+}  // namespace
+
+extern "C" int qfs_sweep_once_noalloc(void* cuda_stream, const qfs_circuit* circuit,
+                                      const double* target_dev, const double* samples_dev,
+                                      int32_t M, int32_t S, double beta, const double* gates_in_dev,
+                                      double* gates_out_dev, double* costs_out_dev,
+                                      double* envs_out_dev) {
+  g_err.clear();
+  TRY(check_circuit(circuit));
+  TRY(check_run_params(circuit->n, M, S, 1, QFS_FP64, beta, 0.0));
+  if (!target_dev || !samples_dev || !gates_in_dev || !gates_out_dev)
+    return fail(QFS_EINVAL, "target, samples, gates_in and gates_out must be given");
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  void* scratch = nullptr;
+  int sms = 0, l2 = 0;
+  TRY(noalloc_setup(dev, &scratch, &sms, &l2));
+
+  // A context on the stack: no workspace, no pinned buffer, no events.
+  qfs_ctx tmp;
+  tmp.device = dev;
+  tmp.stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  tmp.num_sms = sms;
+  tmp.l2_bytes = (size_t)l2;
+
+  Run R;
+  R.n = circuit->n;
+  R.L = circuit->L;
+  R.M = M;
+  R.S = S;
+  R.N = 1LL << circuit->n;
+  R.sN = (long long)M << circuit->n;
+  R.pairs.assign(circuit->pairs, circuit->pairs + 2 * circuit->L);
+  R.prec = QFS_FP64;
+  R.beta = beta;
+  R.sh = make_shape(R.n, M, S, R64, sms);
+  R.nblk_max = 1;
+  for (int U = 2; U <= std::min(4, R.n); ++U)
+    R.nblk_max = std::max(R.nblk_max, make_bwd_shape(R.n, M, S, R64, sms, U).nblk);
+
+  const size_t state = (size_t)R.sN * sizeof(double2);
+  const size_t need = align_up(state) + align_up((size_t)std::max(R.L - 1, 1) * S * state) +
+                      align_up((size_t)S * state) + align_up((size_t)S * R.nblk_max * 32 * sizeof(double));
+  if (need > (size_t)QFS_NOALLOC_SCRATCH_BYTES)
+    return fail(QFS_EUNSUPPORTED, "this sweep needs %zu bytes of scratch; the static scratch holds %u bytes",
+                need, (unsigned)QFS_NOALLOC_SCRATCH_BYTES);
+  char* base = static_cast<char*>(scratch);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* p = base + off;
+    off += align_up(bytes);
+    return p;
+  };
+  R.phil64 = reinterpret_cast<double2*>(take(state));
+  R.B = take((size_t)std::max(R.L - 1, 1) * S * state);
+  R.phi = take((size_t)S * state);
+  R.partials = reinterpret_cast<double*>(take((size_t)S * R.nblk_max * 32 * sizeof(double)));
+  R.U = reinterpret_cast<const double2*>(target_dev);
+  R.psi64 = const_cast<double2*>(reinterpret_cast<const double2*>(samples_dev));
+  R.g64 = reinterpret_cast<double2*>(gates_out_dev);
+  const int stream_b = (size_t)std::max(R.L - 1, 1) * S * state > tmp.l2_bytes / 2;
+
+  cudaStream_t st = tmp.stream;
+  if (gates_out_dev != gates_in_dev)
+    CK(cudaMemcpyAsync(gates_out_dev, gates_in_dev, (size_t)S * R.L * 16 * sizeof(double2),
+                       cudaMemcpyDeviceToDevice, st));
+  launch_gemm_upsi(R.U, R.psi64, R.phil64, (int)R.N, M, st);
+  sweep(&tmp, R, R64, S, R.sh, R.g64, nullptr, R.psi64, R.phil64, R.B, R.phi, R.partials,
+        costs_out_dev, reinterpret_cast<double2*>(envs_out_dev), nullptr, stream_b);
+  CK(cudaGetLastError());
+  return QFS_OK;
+}

@@ -33,7 +33,7 @@ EXPORTS = [
     "qfs_default_params", "qfs_create", "qfs_destroy", "qfs_last_error", "qfs_device_sms",
     "qfs_generate_inputs", "qfs_instantiate", "qfs_instantiate_ex", "qfs_instantiate_dev",
     "qfs_sweep_once", "qfs_gate_update", "qfs_profile_enable", "qfs_profile_reset",
-    "qfs_profile_read",
+    "qfs_profile_read", "qfs_sweep_once_noalloc",
 ]
 PROF_BACKWARD, PROF_FORWARD, PROF_UPDATE, PROF_GEMM, PROF_RESIDUAL, PROF_CHECK, PROF_OTHER = range(7)
 PROF_NAMES = ["backward", "forward", "update", "gemm", "residual", "check", "other"]
@@ -93,6 +93,8 @@ def lib():
     L.qfs_sweep_once.argtypes = [_P, C.POINTER(Circuit), _P, _P, C.c_int32, C.c_int32, _P,
                                  C.c_int32, C.c_double, _P, _P, _P]
     L.qfs_gate_update.argtypes = [_P, C.c_int32, _P, _P, C.c_double, _P]
+    L.qfs_sweep_once_noalloc.argtypes = [_P, C.POINTER(Circuit), _P, _P, C.c_int32, C.c_int32,
+                                         C.c_double, _P, _P, _P, _P]
     L.qfs_profile_enable.argtypes = [_P, C.c_int]
     L.qfs_profile_reset.argtypes = [_P]
     L.qfs_profile_read.argtypes = [_P, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
