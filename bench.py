@@ -365,6 +365,21 @@ def run_ours(args):
     return 0
 
 
+def profile_case(args):
+    """One sweep of the workload (all starts) through qfs_sweep_once: a small,
+    fixed launch sequence for ncu captures of single kernels."""
+    import torch  # noqa: F401
+    from paper_2405_12866_gb300 import build as qbuild
+    from paper_2405_12866_gb300 import qfs
+    qbuild.build()
+    p = _problem(args.workload, 0)
+    prec = WORKLOADS[args.workload][1]
+    with qfs.Context(0) as ctx:
+        g, _, c = ctx.sweep_once(p.n, p.pairs, p.U, p.samples(), p.init_gates(), prec, want_envs=False)
+    print(json.dumps({"profile_case": p.name, "min_cost": float(np.min(c))}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -374,7 +389,11 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="brick_n12")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run one sweep of the workload and exit (for ncu captures)")
     args = ap.parse_args()
+    if args.profile_case:
+        return profile_case(args)
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

@@ -160,6 +160,7 @@ struct Run {
   void* phi = nullptr;  // S x N x M in the sweep precision
   double2* g64 = nullptr;
   float2* g32 = nullptr;
+  double2* vprev = nullptr;  // right singular vectors of each gate's last update
   double* partials = nullptr;
   double* costs = nullptr;
   int* active = nullptr;
@@ -198,6 +199,7 @@ size_t carve(Run& R, char* base, bool need_U, bool need_envs) {
   R.phi = take((size_t)R.S * R.sN * es);
   R.g64 = (double2*)take((size_t)R.S * R.L * 16 * sizeof(double2));
   R.g32 = R.prec == QFS_MIXED ? (float2*)take((size_t)R.S * R.L * 16 * sizeof(float2)) : nullptr;
+  R.vprev = (double2*)take((size_t)R.S * R.L * 16 * sizeof(double2));
   R.partials = (double*)take((size_t)R.S * R.nblk_max * 32 * sizeof(double));
   R.costs = (double*)take((size_t)R.S * sizeof(double));
   R.active = (int*)take((size_t)R.S * sizeof(int));
@@ -327,6 +329,10 @@ int setup_inputs(qfs_ctx* ctx, Run& R) {
   }
   std::vector<int> ones(R.S, 1);
   CK(cudaMemcpyAsync(R.active, ones.data(), sizeof(int) * R.S, cudaMemcpyHostToDevice, st));
+  {
+    ProfScope ps(ctx, QFS_PROF_OTHER, 0.0);
+    launch_set_identity4(R.vprev, (long long)R.S * R.L, st);
+  }
   int flag = 0;
   CK(cudaMemcpyAsync(&flag, R.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -343,7 +349,8 @@ int setup_inputs(qfs_ctx* ctx, Run& R) {
 // (1/M) sum |g_1^dagger Phi_1 - Psi|^2 = (1/M) sum_j ||U psi_j - C psi_j||^2.
 void sweep(qfs_ctx* ctx, Run& R, Real r, int S, const Shape& sh, double2* g64, float2* g32,
            const void* psi, const void* phil, void* B, void* phi, double* partials,
-           double* cost_out, double2* envs, const int* active, int stream_b) {
+           double* cost_out, double2* envs, const int* active, int stream_b,
+           double2* vprev = nullptr) {
   cudaStream_t st = ctx->stream;
   const size_t es = elem_bytes(r);
   const long long sN = R.sN;
@@ -397,6 +404,7 @@ void sweep(qfs_ctx* ctx, Run& R, Real r, int S, const Shape& sh, double2* g64, f
     ua_.env_stride = gstride;
     ua_.S = S;
     ua_.active = active;
+    ua_.vprev = vprev ? vprev + (size_t)(k - 1) * 16 : nullptr;
     ProfScope ps(ctx, QFS_PROF_UPDATE, (double)S * bsh.nblk * 32 * sizeof(double));
     launch_update(ua_, st);
   }
@@ -481,7 +489,7 @@ int run_multistart(qfs_ctx* ctx, Run& R, const qfs_params* p, Outcome& out) {
   while (!done && sweeps < p->max_sweeps) {
     ++sweeps;
     sweep(ctx, R, rs, S, R.sh, R.g64, R.g32, psi, phil, R.B, R.phi, R.partials, R.costs, nullptr,
-          R.active, R.stream_b);
+          R.active, R.stream_b, R.vprev);
     TRY(read_costs(ctx, R.costs, S, c));
     for (int s = 0; s < S; ++s)
       if (!act[s]) c[s] = prev[s];
@@ -503,7 +511,7 @@ int run_multistart(qfs_ctx* ctx, Run& R, const qfs_params* p, Outcome& out) {
           for (int it = 0; it < p->refine_sweeps_max && !done; ++it) {
             sweep(ctx, R, R64, 1, R.sh64, R.g64 + (size_t)s * R.L * 16, R.g32 + (size_t)s * R.L * 16,
                   R.psi64, R.phil64, R.B64r, R.phi64r, R.partials64r, R.cost64r, nullptr, nullptr,
-                  R.stream_b64);
+                  R.stream_b64, R.vprev + (size_t)s * R.L * 16);
             ++fp64_sweeps;
             std::vector<double> cr;
             TRY(read_costs(ctx, R.cost64r, 1, cr));

@@ -171,10 +171,12 @@ BwdGeom make_bwd_geom(int n, int M, int ua, int ub, int qa, int qb) {
 
 Shape make_bwd_shape(int n, int M, int S, Real r, int num_sms, int U) {
   Shape sh;
-  sh.vec = (r == R32 && (M % 2) == 0) ? 2 : 1;
+  // 8- and 16-row units hold one complex64 sample per thread (registers).
+  sh.vec = (r == R32 && (M % 2) == 0 && U == 2) ? 2 : 1;
   sh.units_per_start = (1 << (n - U)) * (M / sh.vec);
   const long long total = (long long)sh.units_per_start * S;
-  sh.threads = total >= (long long)num_sms * 512 ? 256 : 128;
+  sh.threads = 128;
+  // About four resident 128-thread blocks per SM over all starts (one wave).
   long long want_blocks = (long long)num_sms * 4;
   long long chunk = (total + want_blocks - 1) / want_blocks;
   chunk = ((chunk + sh.threads - 1) / sh.threads) * sh.threads;
@@ -216,14 +218,14 @@ __device__ __forceinline__ constexpr int spread_rest(int j) {
 // E_k[x][y] += B_{k-1}[x] conj(Phi_k[y]) over the groups of gate k.
 // MODE 1 accumulates sum |Phi_k - B|^2 instead (the residual cost).
 template <typename T, int VEC, int MODE, int U, int EA, int EB>
-__global__ void k_backward(BwdArgs a) {
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? (U == 4 ? 3 : 4) : 2) k_backward(BwdArgs a) {
   using T2 = typename C2<T>::t;
   constexpr int ROWS = 1 << U;
   const int s = blockIdx.y;
   if (a.active && !a.active[s]) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __shared__ T2 gs[16];
-  __shared__ double red[8][32];
+  __shared__ double red[4][32];
   const bool has_gate = a.gates != nullptr;
   if (threadIdx.x < 16)
     gs[threadIdx.x] = has_gate ? reinterpret_cast<const T2*>(a.gates)[s * a.gate_stride + threadIdx.x] : T2{};

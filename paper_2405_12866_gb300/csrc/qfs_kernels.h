@@ -77,8 +77,13 @@ struct UpdateArgs {
   double2* env_out; long long env_stride;  // nullable
   int S;
   const int* active;                     // nullable: all starts active
+  double2* vprev;                        // nullable: per-start right singular vectors of the
+                                         // gate's previous update (same strides as g64)
 };
 void launch_update(const UpdateArgs& a, cudaStream_t st);
+
+// Set `count` 4x4 complex128 matrices to the identity.
+void launch_set_identity4(double2* v, long long count, cudaStream_t st);
 
 // Residual cost: cost[s] = sum_blk partial[s][blk][0] * inv_M.
 void launch_residual_finish(const double* partials, int nblk, int S, double inv_M,
