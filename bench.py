@@ -249,7 +249,7 @@ def run_ours(args):
                        torch.from_numpy(np.ascontiguousarray(p.init_gates())).to(dev)))
     out = torch.zeros((L, 4, 4), dtype=torch.complex128, device=dev)
     prm = qfs.default_params(M=M, multistarts=S, max_sweeps=first.max_sweeps, dist_tol=first.tol,
-                             precision=prec)
+                             precision=prec, start_groups=args.start_groups)
 
     def step(i):
         U, Psi, G0 = dev_in[i]
@@ -389,6 +389,8 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="brick_n12")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--start-groups", type=int, default=0,
+                    help="concurrent groups of multistarts (0 = the library's choice)")
     ap.add_argument("--profile-case", action="store_true",
                     help="run one sweep of the workload and exit (for ncu captures)")
     args = ap.parse_args()

@@ -73,7 +73,8 @@ typedef struct {
   int32_t plateau_window;    /* plateau_windows_size; 0 disables plateau detection */
   int32_t precision;         /* QFS_FP64 or QFS_MIXED */
   int32_t refine_sweeps_max; /* QFS_MIXED: FP64 refinement sweeps allowed per start */
-  int32_t reserved0;
+  int32_t start_groups;      /* starts are swept in this many concurrent groups (0 = auto);
+                                results are bitwise the same for any value */
   uint64_t seed;             /* draws the training states and the initial gates */
   double dist_tol;           /* stop when a start's cost <= dist_tol */
   double diff_tol_r;         /* plateau: relative improvement threshold */
@@ -90,8 +91,9 @@ typedef struct {
 
 /* Fill *p with defaults: M = 2, multistarts = 16, max_sweeps = 10000,
  * min_sweeps = 6, plateau_window = 0, precision = QFS_FP64,
- * refine_sweeps_max = 50, seed = 0, dist_tol = 1e-8, diff_tol_r = 1e-5,
- * beta = 0 (the paper's suggested values, with plateau detection off). */
+ * refine_sweeps_max = 50, start_groups = 0, seed = 0, dist_tol = 1e-8,
+ * diff_tol_r = 1e-5, beta = 0 (the paper's suggested values, with plateau
+ * detection off). */
 void qfs_default_params(qfs_params* p);
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a

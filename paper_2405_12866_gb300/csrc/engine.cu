@@ -13,6 +13,7 @@
 #include <complex>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <limits>
 #include <mutex>
@@ -68,16 +69,28 @@ struct ProfRec {
 };
 struct Prof {
   bool on = false;
+  bool capturing = false;        // launches are being captured into a graph
   std::vector<cudaEvent_t> pool;
   std::vector<ProfRec> pending;
+  std::vector<ProfRec> graph;    // event pairs recorded by graph nodes
   long long launches[QFS_PROF_KINDS] = {};
   long long timed[QFS_PROF_KINDS] = {};
   double ms[QFS_PROF_KINDS] = {};
   double bytes[QFS_PROF_KINDS] = {};
 };
 
+constexpr int kMaxGroups = 8;
+
 struct qfs_ctx {
   Prof prof;
+  // Streams for groups of starts swept concurrently, forked from and joined
+  // back to `stream` with events (created on first use).
+  cudaStream_t gstream[kMaxGroups] = {};
+  cudaEvent_t gevent[kMaxGroups] = {};
+  cudaEvent_t fork_event = nullptr;
+  cudaStream_t cap_stream = nullptr;  // stream used only to capture sweep graphs
+  bool fuse_update = true;  // gate update inside the backward launch (QFS_FUSE_UPDATE=0: separate)
+  bool tma = false;         // shared-memory-staged backward steps (QFS_TMA=1); register kernels by default
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -107,22 +120,49 @@ struct ProfScope {
   qfs_ctx* ctx;
   int id;
   double bytes;
+  cudaStream_t st;
   cudaEvent_t a = nullptr;
-  ProfScope(qfs_ctx* c, int i, double b) : ctx(c), id(i), bytes(b) {
+  ProfScope(qfs_ctx* c, int i, double b, cudaStream_t s = nullptr)
+      : ctx(c), id(i), bytes(b), st(s ? s : c->stream) {
     ctx->prof.launches[id] += 1;
     if (ctx->prof.on) {
       a = prof_event(ctx);
-      cudaEventRecord(a, ctx->stream);
+      record(a);
     }
+  }
+  // Inside stream capture only externally visible event records can be timed.
+  void record(cudaEvent_t e) {
+    if (ctx->prof.capturing) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    else cudaEventRecord(e, st);
   }
   ~ProfScope() {
     if (a) {
       cudaEvent_t b = prof_event(ctx);
-      cudaEventRecord(b, ctx->stream);
-      ctx->prof.pending.push_back({a, b, id, bytes});
+      record(b);
+      (ctx->prof.capturing ? ctx->prof.graph : ctx->prof.pending).push_back({a, b, id, bytes});
     }
   }
 };
+
+// After a synchronised replay of a captured graph: fold its timings in.
+void prof_harvest_graph(qfs_ctx* ctx) {
+  for (auto& r : ctx->prof.graph) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      ctx->prof.ms[r.id] += ms;
+      ctx->prof.timed[r.id] += 1;
+      ctx->prof.bytes[r.id] += r.bytes;
+    }
+  }
+}
+
+void prof_release_graph(qfs_ctx* ctx) {
+  for (auto& r : ctx->prof.graph) {
+    ctx->prof.pool.push_back(r.a);
+    ctx->prof.pool.push_back(r.b);
+  }
+  ctx->prof.graph.clear();
+}
 
 // After a stream synchronisation: fold finished timings into the totals.
 void prof_harvest(qfs_ctx* ctx) {
@@ -148,6 +188,7 @@ struct Run {
   double beta = 0.0;
   Shape sh, sh64;          // sweep shape (prec) and the FP64 shape for S = 1
   int nblk_max = 1, nblk64_max = 1;  // largest backward block count (partials size)
+  int groups = 1, group_size = 0;    // starts swept concurrently in `groups` slices
   // inputs (device)
   const double2* U = nullptr;  // N x N
   double2* U_copy = nullptr;   // used by the host-pointer entry points
@@ -165,6 +206,8 @@ struct Run {
   double* costs = nullptr;
   int* active = nullptr;
   int* flag = nullptr;
+  unsigned* counters = nullptr;  // S + 1 "last block done" counters (fused update)
+  int* err = nullptr;            // device error word: bit 0 = a bounded device wait ran out
   double2* envs = nullptr;
   // FP64 single-start buffers (mixed precision: cost check and refinement)
   double2* B64r = nullptr;
@@ -176,6 +219,9 @@ struct Run {
 };
 
 size_t elem_bytes(Real r) { return r == R32 ? sizeof(float2) : sizeof(double2); }
+
+// Start count the launch shapes are computed for (see sweep()).
+int shape_starts(int S_total) { return S_total >= 4 ? (S_total + 3) / 4 : S_total; }
 
 // Lays out (or, with base == nullptr, only measures) the buffers of a run.
 size_t carve(Run& R, char* base, bool need_U, bool need_envs) {
@@ -203,7 +249,9 @@ size_t carve(Run& R, char* base, bool need_U, bool need_envs) {
   R.partials = (double*)take((size_t)R.S * R.nblk_max * 32 * sizeof(double));
   R.costs = (double*)take((size_t)R.S * sizeof(double));
   R.active = (int*)take((size_t)R.S * sizeof(int));
+  R.counters = (unsigned*)take((size_t)(R.S + 1) * sizeof(unsigned));
   R.flag = (int*)take(sizeof(int) * 4);
+  R.err = R.flag ? R.flag + 1 : nullptr;
   R.envs = need_envs ? (double2*)take((size_t)R.S * R.L * 16 * sizeof(double2)) : nullptr;
   if (R.prec == QFS_MIXED) {
     R.B64r = (double2*)take((size_t)std::max(R.L - 1, 2) * state64);
@@ -272,7 +320,7 @@ int ensure_pinned(qfs_ctx* ctx, size_t n) {
 }
 
 int prepare(qfs_ctx* ctx, Run& R, const qfs_circuit* c, int M, int S, int prec, double beta,
-            bool need_U, bool need_envs) {
+            bool need_U, bool need_envs, int groups = 1) {
   R.n = c->n;
   R.L = c->L;
   R.M = M;
@@ -284,11 +332,16 @@ int prepare(qfs_ctx* ctx, Run& R, const qfs_circuit* c, int M, int S, int prec, 
   R.beta = beta;
   R.sh = make_shape(R.n, M, S, prec == QFS_MIXED ? R32 : R64, ctx->num_sms);
   R.sh64 = make_shape(R.n, M, 1, R64, ctx->num_sms);
+  R.groups = std::max(1, std::min({groups, S, kMaxGroups}));
+  R.group_size = (S + R.groups - 1) / R.groups;
+  R.groups = (S + R.group_size - 1) / R.group_size;
   R.nblk_max = R.nblk64_max = 1;
   for (int U = 2; U <= std::min(4, R.n); ++U) {
-    R.nblk_max = std::max(R.nblk_max,
-                          make_bwd_shape(R.n, M, S, prec == QFS_MIXED ? R32 : R64, ctx->num_sms, U).nblk);
+    const Real rs = prec == QFS_MIXED ? R32 : R64;
+    R.nblk_max = std::max(R.nblk_max, make_bwd_shape(R.n, M, shape_starts(S), rs, ctx->num_sms, U).nblk);
+    R.nblk_max = std::max(R.nblk_max, make_tma_shape(R.n, M, shape_starts(S), rs, ctx->num_sms, U).nblk);
     R.nblk64_max = std::max(R.nblk64_max, make_bwd_shape(R.n, M, 1, R64, ctx->num_sms, U).nblk);
+    R.nblk64_max = std::max(R.nblk64_max, make_tma_shape(R.n, M, 1, R64, ctx->num_sms, U).nblk);
   }
   const size_t bytes = carve(R, nullptr, need_U, need_envs);
   TRY(ensure_ws(ctx, bytes));
@@ -304,6 +357,7 @@ int prepare(qfs_ctx* ctx, Run& R, const qfs_circuit* c, int M, int S, int prec, 
 int setup_inputs(qfs_ctx* ctx, Run& R) {
   cudaStream_t st = ctx->stream;
   CK(cudaMemsetAsync(R.flag, 0, sizeof(int) * 4, st));
+  CK(cudaMemsetAsync(R.counters, 0, sizeof(unsigned) * (R.S + 1), st));
   {
     ProfScope ps(ctx, QFS_PROF_OTHER, 0.0);
     launch_nonfinite_check(reinterpret_cast<const double*>(R.U), 2 * R.N * R.N, R.flag, st);
@@ -347,22 +401,50 @@ int setup_inputs(qfs_ctx* ctx, Run& R) {
 // from B_{k-1} and Phi_k, then the warp update of gate k.  FP64 writes
 // cost = 2 - (2/M) Re Tr(g_1 E_1); complex64 adds a residual pass
 // (1/M) sum |g_1^dagger Phi_1 - Psi|^2 = (1/M) sum_j ||U psi_j - C psi_j||^2.
-void sweep(qfs_ctx* ctx, Run& R, Real r, int S, const Shape& sh, double2* g64, float2* g32,
+// A group of starts swept together on one stream: starts s0 .. s0+S-1 of a
+// run with S_total starts (the B list is laid out [k][S_total][N*M]).
+struct Slice {
+  int s0 = 0;
+  int S = 0;
+  int S_total = 0;
+  cudaStream_t st = nullptr;
+};
+
+void sweep(qfs_ctx* ctx, Run& R, Real r, const Slice& sl, double2* g64, float2* g32,
            const void* psi, const void* phil, void* B, void* phi, double* partials,
-           double* cost_out, double2* envs, const int* active, int stream_b,
-           double2* vprev = nullptr) {
-  cudaStream_t st = ctx->stream;
+           int nblk_stride, double* cost_out, double2* envs, const int* active, int stream_b,
+           double2* vprev, unsigned* counters) {
+  cudaStream_t st = sl.st ? sl.st : ctx->stream;
+  const int S = sl.S, s0 = sl.s0;
   const size_t es = elem_bytes(r);
   const long long sN = R.sN;
   const long long gstride = (long long)R.L * 16;
+  const size_t goff = (size_t)s0 * R.L * 16;
+  g64 += goff;
+  if (g32) g32 += goff;
+  if (vprev) vprev += goff;
+  if (envs) envs += goff;
+  if (cost_out) cost_out += s0;
+  if (active) active += s0;
+  counters += s0;
+  phi = (char*)phi + (size_t)s0 * sN * es;
+  partials += (size_t)s0 * nblk_stride * 32;
+  // Shapes follow a fixed share of the run's starts (a quarter, the size of
+  // the library's largest concurrent group) so that the reduction order, and
+  // hence every result bit, does not depend on the grouping, while a group
+  // of that size still fills a wave.
+  const int S_shape = shape_starts(sl.S_total);
+  const Shape sh = make_shape(R.n, R.M, S_shape, r, ctx->num_sms);
   const char* gT = r == R32 ? reinterpret_cast<const char*>(g32) : reinterpret_cast<const char*>(g64);
   auto gate_ptr = [&](int idx) { return (const void*)(gT + (size_t)idx * 16 * es); };
-  auto B_ptr = [&](int k) { return (void*)((char*)B + (size_t)(k - 1) * S * sN * es); };  // B_k, k >= 1
+  auto B_ptr = [&](int k) {  // B_k, k >= 1
+    return (void*)((char*)B + ((size_t)(k - 1) * sl.S_total + s0) * sN * es);
+  };
   const int L = R.L;
   for (int k = 1; k <= L - 1; ++k) {
     const Geom gm = make_geom(R.n, R.M, R.pairs[2 * (k - 1)], R.pairs[2 * (k - 1) + 1]);
     const void* in = k == 1 ? psi : B_ptr(k - 1);
-    ProfScope ps(ctx, QFS_PROF_FORWARD, 2.0 * S * sN * es);
+    ProfScope ps(ctx, QFS_PROF_FORWARD, 2.0 * S * sN * es, st);
     launch_forward(r, gm, sh, S, in, k == 1 ? 0 : sN, B_ptr(k), gate_ptr(k - 1), gstride, active, st);
   }
   for (int k = L; k >= 1; --k) {
@@ -385,15 +467,13 @@ void sweep(qfs_ctx* ctx, Run& R, Real r, int S, const Shape& sh, double2* g64, f
       ub = R.pairs[2 * k + 1];
     }
     const BwdGeom bg = make_bwd_geom(R.n, R.M, ua, ub, qa, qb);
-    const Shape bsh = make_bwd_shape(R.n, R.M, S, r, ctx->num_sms, bg.U);
-    {
-      ProfScope ps(ctx, QFS_PROF_BACKWARD, (double)S * sN * es * (pout ? 3.0 : 2.0));
-      launch_backward(r, 0, bg, bsh, S, bprev, bstride, pin, pstride, pout, gate, gstride, partials,
-                      stream_b, active, st);
-    }
-    UpdateArgs ua_;
+    const bool use_tma = ctx->tma && R.err && tma_backward_supported(r, R.M, bg.U);
+    const Shape bsh = use_tma ? make_tma_shape(R.n, R.M, S_shape, r, ctx->num_sms, bg.U)
+                              : make_bwd_shape(R.n, R.M, S_shape, r, ctx->num_sms, bg.U);
+    UpdateArgs ua_{};
     ua_.partials = partials;
     ua_.nblk = bsh.nblk;
+    ua_.partials_f32 = r == R32;
     ua_.g64 = g64 + (size_t)(k - 1) * 16;
     ua_.g_stride = gstride;
     ua_.g32 = g32 ? g32 + (size_t)(k - 1) * 16 : nullptr;
@@ -405,19 +485,32 @@ void sweep(qfs_ctx* ctx, Run& R, Real r, int S, const Shape& sh, double2* g64, f
     ua_.S = S;
     ua_.active = active;
     ua_.vprev = vprev ? vprev + (size_t)(k - 1) * 16 : nullptr;
-    ProfScope ps(ctx, QFS_PROF_UPDATE, (double)S * bsh.nblk * 32 * sizeof(double));
-    launch_update(ua_, st);
+    // By default the backward step and the update of gate k run as one
+    // launch: the last block of each start to finish performs its update.
+    {
+      ProfScope ps(ctx, QFS_PROF_BACKWARD, (double)S * sN * es * (pout ? 3.0 : 2.0), st);
+      if (use_tma)
+        launch_backward_tma(r, bg, bsh, S, bprev, bstride, pin, pstride, pout, gate, gstride, partials,
+                            stream_b, active, st, ctx->fuse_update ? &ua_ : nullptr, counters, R.err);
+      else
+        launch_backward(r, 0, bg, bsh, S, bprev, bstride, pin, pstride, pout, gate, gstride, partials,
+                        stream_b, active, st, ctx->fuse_update ? &ua_ : nullptr, counters);
+    }
+    if (!ctx->fuse_update) {
+      ProfScope ps(ctx, QFS_PROF_UPDATE, (double)S * bsh.nblk * 32 * sizeof(double), st);
+      launch_update(ua_, st);
+    }
   }
   if (r == R32) {
     const BwdGeom bg = make_bwd_geom(R.n, R.M, R.pairs[0], R.pairs[1], R.pairs[0], R.pairs[1]);
-    const Shape bsh = make_bwd_shape(R.n, R.M, S, r, ctx->num_sms, 2);
+    const Shape bsh = make_bwd_shape(R.n, R.M, S_shape, r, ctx->num_sms, 2);
     const void* pin = L == 1 ? phil : phi;
     {
-      ProfScope ps(ctx, QFS_PROF_RESIDUAL, 2.0 * S * sN * es);
+      ProfScope ps(ctx, QFS_PROF_RESIDUAL, 2.0 * S * sN * es, st);
       launch_backward(r, 1, bg, bsh, S, psi, 0, pin, L == 1 ? 0 : sN, nullptr, gate_ptr(0), gstride,
                       partials, 0, active, st);
     }
-    ProfScope ps(ctx, QFS_PROF_OTHER, 0.0);
+    ProfScope ps(ctx, QFS_PROF_OTHER, 0.0, st);
     launch_residual_finish(partials, bsh.nblk, S, 1.0 / R.M, cost_out, st);
   }
 }
@@ -451,11 +544,91 @@ int check64(qfs_ctx* ctx, Run& R, int s, double* out) {
   return QFS_OK;
 }
 
-int read_costs(qfs_ctx* ctx, const double* dev, int S, std::vector<double>& out) {
+int read_costs(qfs_ctx* ctx, const double* dev, int S, std::vector<double>& out,
+               const int* err = nullptr) {
   CK(cudaMemcpyAsync(ctx->h_pinned, dev, sizeof(double) * S, cudaMemcpyDeviceToHost, ctx->stream));
+  if (err)
+    CK(cudaMemcpyAsync(ctx->h_pinned + S, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   prof_harvest(ctx);
   out.assign(ctx->h_pinned, ctx->h_pinned + S);
+  if (err) {
+    int e;
+    std::memcpy(&e, ctx->h_pinned + S, sizeof(int));
+    if (e) return fail(QFS_ETIMEOUT, "a bounded device wait ran out (error word %d)", e);
+  }
+  return QFS_OK;
+}
+
+int ensure_group_streams(qfs_ctx* ctx, int groups) {
+  if (!ctx->fork_event) CK(cudaEventCreateWithFlags(&ctx->fork_event, cudaEventDisableTiming));
+  for (int g = 0; g < groups; ++g) {
+    if (!ctx->gstream[g]) CK(cudaStreamCreateWithFlags(&ctx->gstream[g], cudaStreamNonBlocking));
+    if (!ctx->gevent[g]) CK(cudaEventCreateWithFlags(&ctx->gevent[g], cudaEventDisableTiming));
+  }
+  return QFS_OK;
+}
+
+// One sweep of every start: the run's starts are split into R.groups slices
+// swept concurrently on their own streams (one slice's SVD updates overlap
+// the others' streaming), forked from and joined back to ctx->stream.
+int sweep_all(qfs_ctx* ctx, Run& R, Real rs, const void* psi, const void* phil, cudaStream_t origin) {
+  if (R.groups <= 1) {
+    sweep(ctx, R, rs, Slice{0, R.S, R.S, origin}, R.g64, R.g32, psi, phil, R.B, R.phi, R.partials,
+          R.nblk_max, R.costs, nullptr, R.active, R.stream_b, R.vprev, R.counters);
+    return QFS_OK;
+  }
+  TRY(ensure_group_streams(ctx, R.groups));
+  CK(cudaEventRecord(ctx->fork_event, origin));
+  for (int g = 0; g < R.groups; ++g) {
+    const int s0 = g * R.group_size;
+    const int Sg = std::min(R.group_size, R.S - s0);
+    CK(cudaStreamWaitEvent(ctx->gstream[g], ctx->fork_event, 0));
+    sweep(ctx, R, rs, Slice{s0, Sg, R.S, ctx->gstream[g]}, R.g64, R.g32, psi, phil, R.B, R.phi,
+          R.partials, R.nblk_max, R.costs, nullptr, R.active, R.stream_b, R.vprev, R.counters);
+    CK(cudaEventRecord(ctx->gevent[g], ctx->gstream[g]));
+    CK(cudaStreamWaitEvent(origin, ctx->gevent[g], 0));
+  }
+  return QFS_OK;
+}
+
+// One sweep of all starts as a CUDA graph (captured once per run, replayed
+// every sweep): a single launch per sweep instead of ~3L per group.
+struct SweepGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  qfs_ctx* ctx = nullptr;
+  long long launches[QFS_PROF_KINDS] = {};  // kernel launches per replay
+  ~SweepGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (ctx) prof_release_graph(ctx);
+  }
+};
+
+int capture_sweep(qfs_ctx* ctx, Run& R, Real rs, const void* psi, const void* phil, SweepGraph& g) {
+  if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+  g.ctx = ctx;
+  long long before[QFS_PROF_KINDS];
+  for (int i = 0; i < QFS_PROF_KINDS; ++i) before[i] = ctx->prof.launches[i];
+  CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed));
+  ctx->prof.capturing = true;
+  const int rc = sweep_all(ctx, R, rs, psi, phil, ctx->cap_stream);
+  ctx->prof.capturing = false;
+  // Captured launches run at each replay, not now.
+  for (int i = 0; i < QFS_PROF_KINDS; ++i) {
+    g.launches[i] = ctx->prof.launches[i] - before[i];
+    ctx->prof.launches[i] = before[i];
+  }
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+  if (rc != QFS_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  CK(e);
+  g.graph = graph;
+  CK(cudaGraphInstantiate(&g.exec, graph, 0));
   return QFS_OK;
 }
 
@@ -486,11 +659,14 @@ int run_multistart(qfs_ctx* ctx, Run& R, const qfs_params* p, Outcome& out) {
   int sweeps = 0;
   bool done = false;
   int fp64_sweeps = 0;
+  SweepGraph graph;
+  TRY(capture_sweep(ctx, R, rs, psi, phil, graph));
   while (!done && sweeps < p->max_sweeps) {
     ++sweeps;
-    sweep(ctx, R, rs, S, R.sh, R.g64, R.g32, psi, phil, R.B, R.phi, R.partials, R.costs, nullptr,
-          R.active, R.stream_b, R.vprev);
-    TRY(read_costs(ctx, R.costs, S, c));
+    CK(cudaGraphLaunch(graph.exec, st));
+    for (int i = 0; i < QFS_PROF_KINDS; ++i) ctx->prof.launches[i] += graph.launches[i];
+    TRY(read_costs(ctx, R.costs, S, c, R.err));
+    if (ctx->prof.on) prof_harvest_graph(ctx);
     for (int s = 0; s < S; ++s)
       if (!act[s]) c[s] = prev[s];
     if (R.prec == QFS_FP64) {
@@ -509,9 +685,10 @@ int run_multistart(qfs_ctx* ctx, Run& R, const qfs_params* p, Outcome& out) {
         // complex64 reached tol but FP64 did not: refine that start in FP64.
         for (int s : cand) {
           for (int it = 0; it < p->refine_sweeps_max && !done; ++it) {
-            sweep(ctx, R, R64, 1, R.sh64, R.g64 + (size_t)s * R.L * 16, R.g32 + (size_t)s * R.L * 16,
-                  R.psi64, R.phil64, R.B64r, R.phi64r, R.partials64r, R.cost64r, nullptr, nullptr,
-                  R.stream_b64, R.vprev + (size_t)s * R.L * 16);
+            sweep(ctx, R, R64, Slice{0, 1, 1, ctx->stream}, R.g64 + (size_t)s * R.L * 16,
+                  R.g32 + (size_t)s * R.L * 16, R.psi64, R.phil64, R.B64r, R.phi64r, R.partials64r,
+                  R.nblk64_max, R.cost64r, nullptr, nullptr, R.stream_b64, R.vprev + (size_t)s * R.L * 16,
+                  R.counters + R.S);
             ++fp64_sweeps;
             std::vector<double> cr;
             TRY(read_costs(ctx, R.cost64r, 1, cr));
@@ -590,10 +767,13 @@ int instantiate_common(qfs_ctx* ctx, const qfs_circuit* c, const double* target,
     return fail(QFS_EINVAL, "plateau_window, min_sweeps and diff_tol_r must be >= 0");
   if (p->precision == QFS_MIXED && p->refine_sweeps_max < 0)
     return fail(QFS_EINVAL, "refine_sweeps_max must be >= 0");
+  if (p->start_groups < 0) return fail(QFS_EINVAL, "start_groups = %d: need >= 0", p->start_groups);
   TRY(ctx_check(ctx));
   TRY(set_device(ctx));
   Run R;
-  TRY(prepare(ctx, R, c, p->M, p->multistarts, p->precision, p->beta, !target_dev, false));
+  int groups = p->start_groups;
+  if (groups <= 0) groups = p->multistarts >= 8 ? 2 : 1;
+  TRY(prepare(ctx, R, c, p->M, p->multistarts, p->precision, p->beta, !target_dev, false, groups));
   cudaStream_t st = ctx->stream;
   const size_t gbytes = (size_t)R.S * R.L * 16 * sizeof(double2);
   if (target_dev) {
@@ -648,6 +828,7 @@ void qfs_default_params(qfs_params* p) {
   p->plateau_window = 0;
   p->precision = QFS_FP64;
   p->refine_sweeps_max = 50;
+  p->start_groups = 0;
   p->seed = 0;
   p->dist_tol = 1e-8;
   p->diff_tol_r = 1e-5;
@@ -667,11 +848,17 @@ int qfs_create(qfs_ctx** out, int device, void* cuda_stream) {
   if (device < 0 || device >= count) return fail(QFS_EINVAL, "device %d of %d", device, count);
   qfs_ctx* ctx = new qfs_ctx();
   ctx->device = device;
+  if (const char* f = std::getenv("QFS_FUSE_UPDATE")) ctx->fuse_update = std::atoi(f) != 0;
+  if (const char* f = std::getenv("QFS_TMA")) ctx->tma = std::atoi(f) != 0;
   e = cudaSetDevice(device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
   int l2 = 0;
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device);
   ctx->l2_bytes = (size_t)l2;
+  if (e == cudaSuccess) {
+    configure_tma_kernels();
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) {
     if (cuda_stream) {
       ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
@@ -696,6 +883,12 @@ void qfs_destroy(qfs_ctx* ctx) {
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
   prof_harvest(ctx);
   for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
+  for (int g = 0; g < kMaxGroups; ++g) {
+    if (ctx->gstream[g]) cudaStreamDestroy(ctx->gstream[g]);
+    if (ctx->gevent[g]) cudaEventDestroy(ctx->gevent[g]);
+  }
+  if (ctx->fork_event) cudaEventDestroy(ctx->fork_event);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
@@ -811,14 +1004,18 @@ int qfs_sweep_once(qfs_ctx* ctx, const qfs_circuit* circuit, const double* targe
   CK(cudaMemcpyAsync(R.g64, gates_in, gbytes, cudaMemcpyHostToDevice, st));
   TRY(setup_inputs(ctx, R));
   const Real rs = precision == QFS_MIXED ? R32 : R64;
-  sweep(ctx, R, rs, S, R.sh, R.g64, R.g32, rs == R32 ? (const void*)R.psi32 : (const void*)R.psi64,
-        rs == R32 ? (const void*)R.phil32 : (const void*)R.phil64, R.B, R.phi, R.partials, R.costs,
-        R.envs, nullptr, R.stream_b);
+  sweep(ctx, R, rs, Slice{0, S, S, ctx->stream}, R.g64, R.g32,
+        rs == R32 ? (const void*)R.psi32 : (const void*)R.psi64,
+        rs == R32 ? (const void*)R.phil32 : (const void*)R.phil64, R.B, R.phi, R.partials, R.nblk_max,
+        R.costs, R.envs, nullptr, R.stream_b, nullptr, R.counters);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(gates_out, R.g64, gbytes, cudaMemcpyDeviceToHost, st));
   if (envs_out) CK(cudaMemcpyAsync(envs_out, R.envs, gbytes, cudaMemcpyDeviceToHost, st));
   if (costs_out) CK(cudaMemcpyAsync(costs_out, R.costs, sizeof(double) * S, cudaMemcpyDeviceToHost, st));
+  int err = 0;
+  CK(cudaMemcpyAsync(&err, R.err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  if (err) return fail(QFS_ETIMEOUT, "a bounded device wait ran out (error word %d)", err);
   return QFS_OK;
 }
 
@@ -929,7 +1126,8 @@ extern "C" int qfs_sweep_once_noalloc(void* cuda_stream, const qfs_circuit* circ
 
   const size_t state = (size_t)R.sN * sizeof(double2);
   const size_t need = align_up(state) + align_up((size_t)std::max(R.L - 1, 1) * S * state) +
-                      align_up((size_t)S * state) + align_up((size_t)S * R.nblk_max * 32 * sizeof(double));
+                      align_up((size_t)S * state) + align_up((size_t)S * R.nblk_max * 32 * sizeof(double)) +
+                      align_up((size_t)S * sizeof(unsigned));
   if (need > (size_t)QFS_NOALLOC_SCRATCH_BYTES)
     return fail(QFS_EUNSUPPORTED, "this sweep needs %zu bytes of scratch; the static scratch holds %u bytes",
                 need, (unsigned)QFS_NOALLOC_SCRATCH_BYTES);
@@ -944,18 +1142,23 @@ extern "C" int qfs_sweep_once_noalloc(void* cuda_stream, const qfs_circuit* circ
   R.B = take((size_t)std::max(R.L - 1, 1) * S * state);
   R.phi = take((size_t)S * state);
   R.partials = reinterpret_cast<double*>(take((size_t)S * R.nblk_max * 32 * sizeof(double)));
+  R.counters = reinterpret_cast<unsigned*>(take((size_t)S * sizeof(unsigned)));
   R.U = reinterpret_cast<const double2*>(target_dev);
   R.psi64 = const_cast<double2*>(reinterpret_cast<const double2*>(samples_dev));
   R.g64 = reinterpret_cast<double2*>(gates_out_dev);
   const int stream_b = (size_t)std::max(R.L - 1, 1) * S * state > tmp.l2_bytes / 2;
 
   cudaStream_t st = tmp.stream;
+  // The fused update's counters must start at zero; a call that stopped
+  // part-way could have left them otherwise.
+  CK(cudaMemsetAsync(R.counters, 0, (size_t)S * sizeof(unsigned), st));
   if (gates_out_dev != gates_in_dev)
     CK(cudaMemcpyAsync(gates_out_dev, gates_in_dev, (size_t)S * R.L * 16 * sizeof(double2),
                        cudaMemcpyDeviceToDevice, st));
   launch_gemm_upsi(R.U, R.psi64, R.phil64, (int)R.N, M, st);
-  sweep(&tmp, R, R64, S, R.sh, R.g64, nullptr, R.psi64, R.phil64, R.B, R.phi, R.partials,
-        costs_out_dev, reinterpret_cast<double2*>(envs_out_dev), nullptr, stream_b);
+  sweep(&tmp, R, R64, Slice{0, S, S, st}, R.g64, nullptr, R.psi64, R.phil64, R.B, R.phi, R.partials,
+        R.nblk_max, costs_out_dev, reinterpret_cast<double2*>(envs_out_dev), nullptr, stream_b,
+        nullptr, R.counters);
   CK(cudaGetLastError());
   return QFS_OK;
 }

@@ -7,6 +7,7 @@
 // per thread, four rows per group, coalesced because the M samples of a row
 // are contiguous.  No tensor cores: a 4x4 complex mat-vec per 64 bytes read
 // is far below any tensor-core ridge point.
+#include "polar4.cuh"
 #include "qfs_common.cuh"
 #include "qfs_kernels.h"
 
@@ -169,34 +170,28 @@ BwdGeom make_bwd_geom(int n, int M, int ua, int ub, int qa, int qb) {
   return g;
 }
 
+int bwd_resident_blocks(Real r, int vec, int U);  // defined after the kernels
+
 Shape make_bwd_shape(int n, int M, int S, Real r, int num_sms, int U) {
   Shape sh;
-  // 8- and 16-row units hold one complex64 sample per thread (registers).
-  sh.vec = (r == R32 && (M % 2) == 0 && U == 2) ? 2 : 1;
+  // 8-row units hold one complex64 sample per thread (registers); 4- and
+  // 16-row units (the latter shared by four lanes) hold two.
+  sh.vec = (r == R32 && (M % 2) == 0 && U != 3) ? 2 : 1;
   sh.units_per_start = (1 << (n - U)) * (M / sh.vec);
-  const long long total = (long long)sh.units_per_start * S;
   sh.threads = 128;
-  // About four resident 128-thread blocks per SM over all starts (one wave).
-  long long want_blocks = (long long)num_sms * 4;
-  long long chunk = (total + want_blocks - 1) / want_blocks;
-  chunk = ((chunk + sh.threads - 1) / sh.threads) * sh.threads;
-  if (chunk < sh.threads) chunk = sh.threads;
-  if (chunk > sh.units_per_start) chunk = ((sh.units_per_start + 31) / 32) * 32;
+  // One full wave: as many blocks as can be resident, split evenly over the
+  // starts; a block's chunk is a multiple of 32 units.
+  const long long slots = (long long)num_sms * std::max(1, bwd_resident_blocks(r, sh.vec, U));
+  const long long per_start = std::max(1LL, slots / std::max(S, 1));
+  long long chunk = (sh.units_per_start + per_start - 1) / per_start;
+  chunk = ((chunk + 31) / 32) * 32;
+  if (chunk < 32) chunk = 32;
   sh.chunk = (int)chunk;
   sh.nblk = (sh.units_per_start + sh.chunk - 1) / sh.chunk;
   return sh;
 }
 
-struct BwdArgs {
-  const void* bprev; long long bprev_stride;
-  const void* phi_in; long long phi_in_stride;
-  void* phi_out;
-  const void* gates; long long gate_stride;
-  double* partials; int nblk;
-  BwdGeom g; int units_per_start; int chunk;
-  int stream_b;   // B_{k-1} is read once per sweep: load it evict-first
-  const int* active;
-};
+
 
 // Row t (0 <= t < 2^U) of a unit with the bits of j placed on the local
 // bits other than EA and EB.
@@ -226,6 +221,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (U == 4 ? 3 : 4) : 2) k_
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __shared__ T2 gs[16];
   __shared__ double red[4][32];
+  __shared__ double2 sm_polar[32];
+  __shared__ int is_last;
   const bool has_gate = a.gates != nullptr;
   if (threadIdx.x < 16)
     gs[threadIdx.x] = has_gate ? reinterpret_cast<const T2*>(a.gates)[s * a.gate_stride + threadIdx.x] : T2{};
@@ -349,7 +346,196 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (U == 4 ? 3 : 4) : 2) k_
     double t = 0.0;
     const int nw = blockDim.x >> 5;
     for (int w = 0; w < nw; ++w) t += red[w][lane];
-    a.partials[((long long)s * a.nblk + blockIdx.x) * 32 + lane] = t;
+    const long long slot = ((long long)s * a.nblk + blockIdx.x) * 32 + lane;
+    if (MODE == 0) reinterpret_cast<T*>(a.partials)[slot] = (T)t;
+    else reinterpret_cast<double*>(a.partials)[slot] = t;
+  }
+  if constexpr (MODE == 0) {
+    if (a.fuse) {
+      // Last block done: publish the partials, count the block, and let the
+      // last one of this start run the update (no block ever waits).
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) is_last = atomicAdd(a.counters + s, 1u) == (unsigned)(a.nblk - 1);
+      __syncthreads();
+      if (is_last && warp == 0) {
+        __threadfence();
+        update_one_start<T, sizeof(T) == 4 ? 1 : 2, true>(a.upd, s, sm_polar);
+        if (lane == 0) a.counters[s] = 0u;
+      }
+    }
+  }
+}
+
+// Backward step for 16-row units (gate k+1 and gate k on four distinct
+// qubits, the common case in brick walls).  Four lanes share a unit: lane
+// quad index x (lane bits 3..4) owns the rows with gate k's local index x
+// and all four values j of gate k+1's local index, for VEC samples.  It
+// applies g_{k+1}^dagger to its own four Phi rows, stores them, and
+// accumulates E_k[x][x^m] += sum_j B[(j, x)] conj(Phi_k[(j, x^m)]) with the
+// partner's rows fetched by shuffle (lane ^ 8m).  Registers stay low (all
+// eight loads of a lane are in flight together) and each unit's 16 rows are
+// read once.  Local bits: 3, 2 = gate k+1, 1, 0 = gate k.
+template <typename T, int VEC>
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2) k_backward_q4(BwdArgs a) {
+  using T2 = typename C2<T>::t;
+  const int s = blockIdx.y;
+  if (a.active && !a.active[s]) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int qx = lane >> 3, v = lane & 7;
+  __shared__ T2 gs[16];
+  __shared__ double red[4][32];
+  __shared__ double2 sm_polar[32];
+  __shared__ int is_last;
+  const bool has_gate = a.gates != nullptr;
+  if (threadIdx.x < 16)
+    gs[threadIdx.x] = has_gate ? reinterpret_cast<const T2*>(a.gates)[s * a.gate_stride + threadIdx.x] : T2{};
+  __syncthreads();
+  T2 gd[16];  // g^dagger[y][j] = conj(g[j][y])
+#pragma unroll
+  for (int y = 0; y < 4; ++y)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const T2 t = gs[4 * j + y];
+      gd[4 * y + j] = T2{t.x, -t.y};
+    }
+  const T2* B = reinterpret_cast<const T2*>(a.bprev) + s * a.bprev_stride;
+  const T2* P = reinterpret_cast<const T2*>(a.phi_in) + s * a.phi_in_stride;
+  T2* Po = a.phi_out ? reinterpret_cast<T2*>(a.phi_out) + s * a.g.sN : nullptr;
+  const uint32_t M = (uint32_t)a.g.M;
+  const uint32_t d0 = (1u << a.g.pos[0]) * M, d1 = (1u << a.g.pos[1]) * M;
+  const uint32_t d2 = (1u << a.g.pos[2]) * M, d3 = (1u << a.g.pos[3]) * M;
+  const uint32_t xoff = ((qx >> 1) ? d1 : 0u) + ((qx & 1) ? d0 : 0u);
+  const uint32_t joff[4] = {0u, d2, d3, d3 + d2};
+
+  T acc[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) acc[i] = T(0);
+
+  const int MV = a.g.M / VEC;
+  const int u0 = blockIdx.x * a.chunk;
+  const int u1 = min(u0 + a.chunk, a.units_per_start);
+  // Loads of unit u: four Phi rows and four B rows of this lane.
+  auto unit_off = [&](int u) {
+    const int r = u / MV, jv = u - r * MV;
+    uint32_t base = (uint32_t)r;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int p = a.g.ins[i];
+      base = ((base >> p) << (p + 1)) | (base & ((1u << p) - 1u));
+    }
+    return base * M + (uint32_t)jv * VEC + xoff;
+  };
+  auto load_unit = [&](int u, T2 (&ph)[4][VEC], T2 (&b)[4][VEC]) {
+    if (u < u1) {
+      const uint32_t o = unit_off(u);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) ld_keep<T, VEC>(P + o + joff[j], ph[j]);
+      if (a.stream_b) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ld<T, VEC>(B + o + joff[j], b[j]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ld_keep<T, VEC>(B + o + joff[j], b[j]);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) ph[j][q] = b[j][q] = T2{T(0), T(0)};
+    }
+  };
+  // Software pipeline: the next unit's eight loads are in flight while the
+  // current unit is computed.
+  T2 phn[4][VEC], bn[4][VEC];
+  int ub = u0 + warp * 8;
+  if (ub < u1) load_unit(ub + v, phn, bn);
+  for (; ub < u1; ub += 32) {
+    const int u = ub + v;
+    const bool valid = u < u1;
+    T2 ph[4][VEC], b[4][VEC];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) {
+        ph[j][q] = phn[j][q];
+        b[j][q] = bn[j][q];
+      }
+    if (ub + 32 < u1) load_unit(ub + 32 + v, phn, bn);
+    const uint32_t base_off = valid ? unit_off(u) : 0u;
+    if (has_gate) {
+      T2 nw[4][VEC];
+#pragma unroll
+      for (int y = 0; y < 4; ++y)
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) {
+          T2 t = cmul(gd[4 * y], ph[0][q]);
+#pragma unroll
+          for (int j = 1; j < 4; ++j) {
+            const T2 w = cmul(gd[4 * y + j], ph[j][q]);
+            t.x += w.x;
+            t.y += w.y;
+          }
+          nw[y][q] = t;
+        }
+#pragma unroll
+      for (int y = 0; y < 4; ++y)
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) ph[y][q] = nw[y][q];
+      if (Po && valid) {
+#pragma unroll
+        for (int y = 0; y < 4; ++y) st<T, VEC>(Po + base_off + joff[y], ph[y]);
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) {
+          T2 pp = ph[j][q];
+          if (m) {
+            pp.x = __shfl_xor_sync(FULL, pp.x, 8 * m);
+            pp.y = __shfl_xor_sync(FULL, pp.y, 8 * m);
+          }
+          const T2 bb = b[j][q];
+          acc[2 * m] += bb.x * pp.x + bb.y * pp.y;
+          acc[2 * m + 1] += bb.y * pp.x - bb.x * pp.y;
+        }
+    }
+  }
+  // Sum over the eight lanes of each quad index; lane (x, 0) holds E[x][x^m].
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    acc[i] += __shfl_xor_sync(FULL, acc[i], 1);
+    acc[i] += __shfl_xor_sync(FULL, acc[i], 2);
+    acc[i] += __shfl_xor_sync(FULL, acc[i], 4);
+  }
+  if (v == 0) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int e = 4 * qx + (qx ^ m);
+      red[warp][2 * e] = (double)acc[2 * m];
+      red[warp][2 * e + 1] = (double)acc[2 * m + 1];
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double t = 0.0;
+    const int nw = blockDim.x >> 5;
+    for (int w = 0; w < nw; ++w) t += red[w][lane];
+    reinterpret_cast<T*>(a.partials)[((long long)s * a.nblk + blockIdx.x) * 32 + lane] = (T)t;
+  }
+  if (a.fuse) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = atomicAdd(a.counters + s, 1u) == (unsigned)(a.nblk - 1);
+    __syncthreads();
+    if (is_last && warp == 0) {
+      __threadfence();
+      update_one_start<T, sizeof(T) == 4 ? 1 : 2, true>(a.upd, s, sm_polar);
+      if (lane == 0) a.counters[s] = 0u;
+    }
   }
 }
 
@@ -372,7 +558,7 @@ static void bwd_dispatch(const BwdArgs& a, dim3 grid, int threads, cudaStream_t 
   if constexpr (MODE == 1) {
     k_backward<T, VEC, 1, 2, 1, 0><<<grid, threads, 0, st>>>(a);
   } else {
-    if (U == 4) k_backward<T, VEC, 0, 4, 1, 0><<<grid, threads, 0, st>>>(a);
+    if (U == 4) k_backward_q4<T, VEC><<<grid, threads, 0, st>>>(a);
     else if (U == 3) {
       if (ea == 2 && eb == 0) k_backward<T, VEC, 0, 3, 2, 0><<<grid, threads, 0, st>>>(a);
       else if (ea == 0 && eb == 2) k_backward<T, VEC, 0, 3, 0, 2><<<grid, threads, 0, st>>>(a);
@@ -385,13 +571,42 @@ static void bwd_dispatch(const BwdArgs& a, dim3 grid, int threads, cudaStream_t 
   }
 }
 
+// Resident 128-thread blocks per SM of the backward kernel a shape uses
+// (cached per instance; the unit shape decides the instance).
+int bwd_resident_blocks(Real r, int vec, int U) {
+  static int cache[2][3][5] = {};
+  const int ri = r == R32 ? 0 : 1;
+  int& c = cache[ri][vec][U];
+  if (c) return c;
+  int b = 0;
+  cudaError_t e = cudaSuccess;
+  if (r == R32) {
+    if (U == 4) e = vec == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_backward_q4<float, 2>, 128, 0)
+                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_backward_q4<float, 1>, 128, 0);
+    else if (U == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_backward<float, 1, 0, 3, 1, 0>, 128, 0);
+    else e = vec == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_backward<float, 2, 0, 2, 1, 0>, 128, 0)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_backward<float, 1, 0, 2, 1, 0>, 128, 0);
+  } else {
+    if (U == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_backward_q4<double, 1>, 128, 0);
+    else if (U == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_backward<double, 1, 0, 3, 1, 0>, 128, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_backward<double, 1, 0, 2, 1, 0>, 128, 0);
+  }
+  if (e != cudaSuccess || b < 1) {
+    cudaGetLastError();
+    b = 2;
+  }
+  c = b;
+  return c;
+}
+
 void launch_backward(Real r, int mode, const BwdGeom& g, const Shape& sh, int S,
                      const void* bprev, long long bprev_stride, const void* phi_in,
                      long long phi_in_stride, void* phi_out, const void* gates,
-                     long long gate_stride, double* partials, int stream_b, const int* active,
-                     cudaStream_t st) {
+                     long long gate_stride, void* partials, int stream_b, const int* active,
+                     cudaStream_t st, const UpdateArgs* fuse, unsigned* counters) {
   BwdArgs a{bprev, bprev_stride, phi_in, phi_in_stride, phi_out, gates, gate_stride,
-            partials, sh.nblk, g, sh.units_per_start, sh.chunk, stream_b, active};
+            partials, sh.nblk, g, sh.units_per_start, sh.chunk, stream_b, active,
+            fuse ? 1 : 0, counters, fuse ? *fuse : UpdateArgs{}};
   dim3 grid(sh.nblk, S);
   if (r == R32) {
     if (sh.vec == 2) {

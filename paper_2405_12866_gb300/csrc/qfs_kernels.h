@@ -51,25 +51,14 @@ void launch_forward(Real r, const Geom& g, const Shape& sh, int S,
                     const void* gates, long long gate_stride, const int* active,
                     cudaStream_t st);
 
-// Environment partials of one backward step.  Phi_k = g^dagger Phi_in on
-// the pair (ua, ub) of the geometry when `gate` is non-null (else Phi_k =
-// Phi_in); Phi_k is stored to phi_out when non-null; per-block partial sums
-// of E[x][y] += Bprev[x] conj(Phi_k[y]) over the pair (qa, qb) go to
-// partials[(s*nblk + blk)*32 + 2*(4x+y) + {0: re, 1: im}].
-// mode 1: instead of E, slot 0 gets sum |Phi_k - Bprev|^2 (needs U = 2).
-void launch_backward(Real r, int mode, const BwdGeom& g, const Shape& sh, int S,
-                     const void* bprev, long long bprev_stride,
-                     const void* phi_in, long long phi_in_stride, void* phi_out,
-                     const void* gates, long long gate_stride,
-                     double* partials, int stream_b, const int* active, cudaStream_t st);
-
 // One warp per start: sum the partials, form (1-beta) E + beta g_old^dagger,
 // take the unitary polar factor of its adjoint (the SVD update of Eq. 2),
 // write it to g64 (and to g32 as complex64 when non-null).  When cost_out is
 // non-null it receives 2 - (2/M) Re Tr(g_new E).  When env_out is non-null
 // the environment itself is stored there (16 complex128 per start).
 struct UpdateArgs {
-  const double* partials; int nblk;
+  const void* partials; int nblk;
+  int partials_f32;                      // partials are float (complex64 steps) or double
   double2* g64; long long g_stride;     // gate to replace, per start
   float2* g32;                           // complex64 copy (nullable)
   double beta;
@@ -84,6 +73,55 @@ void launch_update(const UpdateArgs& a, cudaStream_t st);
 
 // Set `count` 4x4 complex128 matrices to the identity.
 void launch_set_identity4(double2* v, long long count, cudaStream_t st);
+
+// Environment partials of one backward step.  Phi_k = g^dagger Phi_in on
+// the pair (ua, ub) of the geometry when `gate` is non-null (else Phi_k =
+// Phi_in); Phi_k is stored to phi_out when non-null; per-block partial sums
+// of E[x][y] += Bprev[x] conj(Phi_k[y]) over the pair (qa, qb) go to
+// partials[(s*nblk + blk)*32 + 2*(4x+y) + {0: re, 1: im}].
+// mode 1: instead of E, slot 0 gets sum |Phi_k - Bprev|^2 (needs U = 2).
+// Partials are float for complex64 steps in mode 0, double otherwise.
+// With `fuse`, the last block of each start to finish performs that start's
+// update (as launch_update would); `counters` (one per start) must be zero
+// before the launch and are zero again after it.
+void launch_backward(Real r, int mode, const BwdGeom& g, const Shape& sh, int S,
+                     const void* bprev, long long bprev_stride,
+                     const void* phi_in, long long phi_in_stride, void* phi_out,
+                     const void* gates, long long gate_stride,
+                     void* partials, int stream_b, const int* active, cudaStream_t st,
+                     const UpdateArgs* fuse = nullptr, unsigned* counters = nullptr);
+
+// Arguments of the backward kernels.
+struct BwdArgs {
+  const void* bprev; long long bprev_stride;
+  const void* phi_in; long long phi_in_stride;
+  void* phi_out;
+  const void* gates; long long gate_stride;
+  void* partials; int nblk;   // T per slot in MODE 0, double in MODE 1
+  BwdGeom g; int units_per_start; int chunk;
+  int stream_b;   // B_{k-1} is read once per sweep: load it evict-first
+  const int* active;
+  // Fused update (MODE 0): the last block of start s to finish updates gate
+  // k of start s from all blocks' partials.
+  int fuse;
+  unsigned* counters;  // per start, zero between launches
+  UpdateArgs upd;
+};
+
+// TMA-staged backward step (mode 0): rows are staged in shared memory by
+// bulk copies.  Supported when a row is a multiple of 16 bytes and a unit
+// (Phi and B rows) fits a stage.  Shapes from make_tma_shape.  A bounded
+// wait that runs out sets bit 0 of *err.
+bool tma_backward_supported(Real r, int M, int U);
+Shape make_tma_shape(int n, int M, int S, Real r, int num_sms, int U);
+void launch_backward_tma(Real r, const BwdGeom& g, const Shape& sh, int S, const void* bprev,
+                         long long bprev_stride, const void* phi_in, long long phi_in_stride,
+                         void* phi_out, const void* gates, long long gate_stride, void* partials,
+                         int stream_b, const int* active, cudaStream_t st, const UpdateArgs* fuse,
+                         unsigned* counters, int* err);
+// Set kernel attributes (large dynamic shared memory) once per process and
+// device, outside any stream capture.
+void configure_tma_kernels();
 
 // Residual cost: cost[s] = sum_blk partial[s][blk][0] * inv_M.
 void launch_residual_finish(const double* partials, int nblk, int S, double inv_M,

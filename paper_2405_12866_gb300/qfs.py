@@ -53,7 +53,7 @@ class Params(C.Structure):
     _fields_ = [("M", C.c_int32), ("multistarts", C.c_int32), ("max_sweeps", C.c_int32),
                 ("min_sweeps", C.c_int32), ("plateau_window", C.c_int32),
                 ("precision", C.c_int32), ("refine_sweeps_max", C.c_int32),
-                ("reserved0", C.c_int32), ("seed", C.c_uint64), ("dist_tol", C.c_double),
+                ("start_groups", C.c_int32), ("seed", C.c_uint64), ("dist_tol", C.c_double),
                 ("diff_tol_r", C.c_double), ("beta", C.c_double)]
 
 

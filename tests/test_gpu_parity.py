@@ -227,6 +227,24 @@ def test_mixed_converges_on_the_same_targets(ctx, name, n, pairs, M, S, seed):
             assert np.max(np.abs(g.conj().T @ g - np.eye(4))) < 1e-12
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_start_groups_do_not_change_results(ctx, precision):
+    """Concurrent groups of starts give bitwise the same run as one group."""
+    qfs = _qfs()
+    n, pairs, M, S = 6, w.brick_pairs(6, 3), 16, 12
+    p = w.make_problem("g", n, pairs, M, S, 61, 62, 1e-8, 300)
+    Psi, G0 = p.samples(), p.init_gates()
+    runs = []
+    for groups in (1, 3, 5):
+        prm = qfs.default_params(M=M, multistarts=S, max_sweeps=300, dist_tol=1e-8,
+                                 precision=precision, start_groups=groups)
+        runs.append(ctx.instantiate(n, pairs, p.U, prm, Psi, G0))
+    for r in runs[1:]:
+        assert r.sweeps == runs[0].sweeps and r.best_start == runs[0].best_start
+        assert np.array_equal(r.gates, runs[0].gates)
+        assert np.array_equal(r.start_costs, runs[0].start_costs)
+
+
 def test_seeded_entry_point_equals_explicit_inputs(ctx):
     qfs = _qfs()
     n, pairs, M, S = 4, w.brick_pairs(4, 3), 8, 3
