@@ -123,7 +123,8 @@ int qfs_device_sms(const qfs_ctx* ctx);
 #define QFS_PROF_RESIDUAL 4 /* complex64 residual cost pass */
 #define QFS_PROF_CHECK 5    /* FP64 cost check of a candidate start */
 #define QFS_PROF_OTHER 6    /* casts, input checks, finishing reductions */
-#define QFS_PROF_KINDS 7
+#define QFS_PROF_BATCH 7    /* persistent batched sweep kernel */
+#define QFS_PROF_KINDS 8
 int qfs_profile_enable(qfs_ctx* ctx, int enable);
 int qfs_profile_reset(qfs_ctx* ctx);
 int qfs_profile_read(qfs_ctx* ctx, int32_t kind, int64_t* launches, int64_t* timed,
@@ -184,6 +185,30 @@ int qfs_sweep_once(qfs_ctx* ctx, const qfs_circuit* circuit, const double* targe
  * beta = 0.  For a rank-deficient E any unitary completion is returned. */
 int qfs_gate_update(qfs_ctx* ctx, int32_t count, const double* envs, const double* gates_old,
                     double beta, double* gates_out);
+
+/* Batched instantiation of P small problems (e.g. thousands of uneven 3-5
+ * qubit partition blocks) in one persistent launch.  Problem i has ns[i] qubits
+ * (2..6) and Ls[i] gates (1..32); pairs (host) holds 2*Ls[i] qubit indices
+ * per problem, concatenated.  targets (host) holds the N_i x N_i targets
+ * concatenated.  M_i = p->M if p->M > 0 (capped at N_i), else N_i / 2, with
+ * N_i * M_i <= 1024.  samples (host, the N_i x M_i matrices concatenated)
+ * and init_gates (host, multistarts x L_i x 16 per problem, concatenated)
+ * may be NULL: then problem i draws them as qfs_generate_inputs does with
+ * seed p->seed + i.  Every start sweeps in complex64 (FP32 polar update)
+ * until its residual cost is <= p->dist_tol or p->max_sweeps; the problem's
+ * answer is the lowest-cost start among those that converged at its
+ * earliest converged sweep (the lock-step rule of qfs_instantiate), made
+ * unitary in FP64, checked in FP64 and refined with up to
+ * p->refine_sweeps_max FP64 sweeps if the check is above tol.  gates_out
+ * (host) receives L_i x 16 complex per problem, concatenated; results
+ * (host) one qfs_result per problem (fp64_sweeps = refinement sweeps).
+ * The warps per block of the persistent kernel are tuned on the first call
+ * for a given (largest N*M, largest L) and cached.  beta must be 0;
+ * multistarts 1..64. */
+int qfs_instantiate_batch(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls,
+                          const int32_t* pairs, const double* targets, const double* samples,
+                          const double* init_gates, const qfs_params* p, double* gates_out,
+                          qfs_result* results);
 
 /* One FP64 sweep (as qfs_sweep_once with QFS_FP64) that allocates no
  * memory, for callers that cannot call cudaMalloc: code running inside a

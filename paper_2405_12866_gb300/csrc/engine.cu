@@ -152,6 +152,8 @@ void prof_harvest_graph(qfs_ctx* ctx) {
       ctx->prof.ms[r.id] += ms;
       ctx->prof.timed[r.id] += 1;
       ctx->prof.bytes[r.id] += r.bytes;
+    } else {
+      cudaGetLastError();  // an untimed pair must not surface as a later error
     }
   }
 }
@@ -172,6 +174,8 @@ void prof_harvest(qfs_ctx* ctx) {
       ctx->prof.ms[r.id] += ms;
       ctx->prof.timed[r.id] += 1;
       ctx->prof.bytes[r.id] += r.bytes;
+    } else {
+      cudaGetLastError();
     }
     ctx->prof.pool.push_back(r.a);
     ctx->prof.pool.push_back(r.b);
@@ -1160,5 +1164,230 @@ extern "C" int qfs_sweep_once_noalloc(void* cuda_stream, const qfs_circuit* circ
         R.nblk_max, costs_out_dev, reinterpret_cast<double2*>(envs_out_dev), nullptr, stream_b,
         nullptr, R.counters);
   CK(cudaGetLastError());
+  return QFS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched instantiation of many small problems (one persistent launch).
+
+namespace {
+
+struct BatchPlan {
+  int warps = 4;  // warps per block of the persistent sweep kernel
+};
+
+// Calibrates the warps per block of the persistent kernel on this batch:
+// each candidate runs a few sweeps of every problem, the fastest wins.
+// Cached per (largest N*M, largest L) of the batch.
+int autotune_batch(qfs_ctx* ctx, BatchArgs a, int max_sweeps_run, int* warps_out) {
+  static std::mutex mu;
+  static std::vector<std::pair<long long, int>> cache;
+  const long long key = (long long)a.max_elems * 1000 + a.max_L;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    for (auto& kv : cache)
+      if (kv.first == key) {
+        *warps_out = kv.second;
+        return QFS_OK;
+      }
+  }
+  cudaStream_t st = ctx->stream;
+  a.max_sweeps = std::min(max_sweeps_run, 6);
+  float best_ms = 1e30f;
+  int best = 4;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  for (int w : {2, 4, 8}) {
+    const size_t smem = batch_sweep_smem(w, a.max_elems, a.max_L);
+    if (smem > 200 * 1024) continue;
+    const int bps = batch_sweep_blocks_per_sm(w, smem);
+    launch_batch_prep(a, st);
+    CK(cudaMemsetAsync(a.queue, 0, sizeof(int), st));
+    CK(cudaEventRecord(e0, st));
+    launch_batch_sweep(a, ctx->num_sms * bps, w, smem, st);
+    CK(cudaEventRecord(e1, st));
+    CK(cudaEventSynchronize(e1));
+    CK(cudaGetLastError());
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = w;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    cache.push_back({key, best});
+  }
+  *warps_out = best;
+  return QFS_OK;
+}
+
+}  // namespace
+
+extern "C" int qfs_instantiate_batch(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls,
+                                     const int32_t* pairs, const double* targets,
+                                     const double* samples, const double* init_gates,
+                                     const qfs_params* p, double* gates_out, qfs_result* results) {
+  g_err.clear();
+  if (P < 1) return fail(QFS_EINVAL, "P = %d: need >= 1", P);
+  if (!ns || !Ls || !pairs || !targets || !p || !gates_out || !results)
+    return fail(QFS_EINVAL, "ns, Ls, pairs, targets, params, gates_out and results must be given");
+  const int S = p->multistarts;
+  if (S < 1 || S > 64) return fail(QFS_EUNSUPPORTED, "multistarts = %d: the batched form takes 1..64", S);
+  if (p->max_sweeps < 1) return fail(QFS_EINVAL, "max_sweeps = %d: need >= 1", p->max_sweeps);
+  if (!(p->dist_tol >= 0.0)) return fail(QFS_EINVAL, "dist_tol = %g", p->dist_tol);
+  if (p->beta != 0.0) return fail(QFS_EUNSUPPORTED, "the batched form runs beta = 0 only");
+  std::vector<BatchProblem> probs(P);
+  long long pair_off = 0, state_off = 0, target_off = 0, gate_off = 0, gout_off = 0;
+  int max_elems = 0, max_L = 0;
+  for (int i = 0; i < P; ++i) {
+    const int n = ns[i], L = Ls[i];
+    if (n < 2 || n > 6) return fail(QFS_EUNSUPPORTED, "problem %d: n = %d (batched form: 2..6)", i, n);
+    if (L < 1 || L > 32) return fail(QFS_EUNSUPPORTED, "problem %d: L = %d (batched form: 1..32)", i, L);
+    const int N = 1 << n;
+    int M = p->M > 0 ? std::min(p->M, N) : N / 2;
+    if (M * N > 1024) return fail(QFS_EUNSUPPORTED, "problem %d: N*M = %d > 1024", i, M * N);
+    qfs_circuit c{n, L, pairs + pair_off};
+    TRY(check_circuit(&c));
+    probs[i] = BatchProblem{n, L, M, (int)pair_off, state_off, target_off, gate_off, gout_off};
+    pair_off += 2 * L;
+    state_off += (long long)N * M;
+    target_off += (long long)N * N;
+    gate_off += (long long)S * L * 16;
+    gout_off += (long long)L * 16;
+    max_elems = std::max(max_elems, N * M);
+    max_L = std::max(max_L, L);
+  }
+  TRY(ctx_check(ctx));
+  TRY(set_device(ctx));
+  // Largest work first (L * N * M per sweep), ties by index.
+  std::vector<int> order(P);
+  for (int i = 0; i < P; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return (long long)probs[x].L * probs[x].M << probs[x].n > (long long)probs[y].L * probs[y].M << probs[y].n;
+  });
+  // Workspace.
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += align_up(bytes);
+    return o;
+  };
+  const size_t o_probs = take(sizeof(BatchProblem) * P), o_order = take(sizeof(int) * P),
+               o_pairs = take(sizeof(int) * pair_off), o_tgt = take(sizeof(double2) * target_off),
+               o_psi64 = take(sizeof(double2) * state_off), o_phil64 = take(sizeof(double2) * state_off),
+               o_psi32 = take(sizeof(float2) * state_off), o_phil32 = take(sizeof(float2) * state_off),
+               o_g0 = take(sizeof(double2) * gate_off), o_g32 = take(sizeof(float2) * gate_off),
+               o_conv = take(sizeof(int) * P * S), o_cost = take(sizeof(double) * P * S),
+               o_swr = take(sizeof(int) * P * S), o_sstar = take(sizeof(int) * P), o_q = take(sizeof(int) * 4),
+               o_gout = take(sizeof(double2) * gout_off), o_rc = take(sizeof(double) * P),
+               o_rs = take(sizeof(int) * P), o_rb = take(sizeof(int) * P), o_rr = take(sizeof(int) * P);
+  TRY(ensure_ws(ctx, off));
+  char* w = ctx->ws;
+  cudaStream_t st = ctx->stream;
+  BatchArgs a{};
+  a.probs = reinterpret_cast<BatchProblem*>(w + o_probs);
+  a.P = P;
+  a.S = S;
+  a.targets = reinterpret_cast<double2*>(w + o_tgt);
+  a.psi64 = reinterpret_cast<double2*>(w + o_psi64);
+  a.phil64 = reinterpret_cast<double2*>(w + o_phil64);
+  a.psi32 = reinterpret_cast<float2*>(w + o_psi32);
+  a.phil32 = reinterpret_cast<float2*>(w + o_phil32);
+  a.pairs = reinterpret_cast<int*>(w + o_pairs);
+  a.init_gates = reinterpret_cast<double2*>(w + o_g0);
+  a.gates32 = reinterpret_cast<float2*>(w + o_g32);
+  a.conv_sweep = reinterpret_cast<int*>(w + o_conv);
+  a.final_cost = reinterpret_cast<double*>(w + o_cost);
+  a.sweeps_run = reinterpret_cast<int*>(w + o_swr);
+  a.s_star = reinterpret_cast<int*>(w + o_sstar);
+  a.queue = reinterpret_cast<int*>(w + o_q);
+  a.order = reinterpret_cast<int*>(w + o_order);
+  a.max_sweeps = p->max_sweeps;
+  a.tol = p->dist_tol;
+  a.max_elems = max_elems;
+  a.max_L = max_L;
+  a.gates_out = reinterpret_cast<double2*>(w + o_gout);
+  a.res_cost = reinterpret_cast<double*>(w + o_rc);
+  a.res_sweeps = reinterpret_cast<int*>(w + o_rs);
+  a.res_best = reinterpret_cast<int*>(w + o_rb);
+  a.res_refine = reinterpret_cast<int*>(w + o_rr);
+  a.refine_max = std::max(0, p->refine_sweeps_max);
+  a.refine_unconverged = 0;
+  CK(cudaMemcpyAsync(w + o_probs, probs.data(), sizeof(BatchProblem) * P, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(w + o_order, order.data(), sizeof(int) * P, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(w + o_pairs, pairs, sizeof(int) * pair_off, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(w + o_tgt, targets, sizeof(double2) * target_off, cudaMemcpyHostToDevice, st));
+  // Training states and initial gates: given, or drawn per problem from
+  // seed + problem index (the library's Philox draws).
+  std::vector<std::complex<double>> hs, hg;
+  if (samples) {
+    CK(cudaMemcpyAsync(w + o_psi64, samples, sizeof(double2) * state_off, cudaMemcpyHostToDevice, st));
+  } else {
+    hs.resize(state_off);
+    for (int i = 0; i < P; ++i)
+      generate_samples(p->seed + (uint64_t)i, probs[i].n, probs[i].M, hs.data() + probs[i].state_off);
+    CK(cudaMemcpyAsync(w + o_psi64, hs.data(), sizeof(double2) * state_off, cudaMemcpyHostToDevice, st));
+  }
+  if (init_gates) {
+    CK(cudaMemcpyAsync(w + o_g0, init_gates, sizeof(double2) * gate_off, cudaMemcpyHostToDevice, st));
+  } else {
+    hg.resize(gate_off);
+    for (int i = 0; i < P; ++i)
+      generate_gates(p->seed + (uint64_t)i, S * probs[i].L, hg.data() + probs[i].gate_off);
+    CK(cudaMemcpyAsync(w + o_g0, hg.data(), sizeof(double2) * gate_off, cudaMemcpyHostToDevice, st));
+  }
+  int warps = 4;
+  TRY(autotune_batch(ctx, a, p->max_sweeps, &warps));
+  const size_t smem = batch_sweep_smem(warps, max_elems, max_L);
+  const int bps = batch_sweep_blocks_per_sm(warps, smem);
+  // Set-up, the persistent sweep and the finishing kernel as one graph.
+  if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed));
+  ctx->prof.capturing = true;
+  CK(cudaMemsetAsync(a.queue, 0, sizeof(int), ctx->cap_stream));
+  {
+    ProfScope ps(ctx, QFS_PROF_OTHER, 0.0, ctx->cap_stream);
+    launch_batch_prep(a, ctx->cap_stream);
+  }
+  {
+    ProfScope ps(ctx, QFS_PROF_BATCH, 0.0, ctx->cap_stream);
+    launch_batch_sweep(a, ctx->num_sms * bps, warps, smem, ctx->cap_stream);
+  }
+  {
+    ProfScope ps(ctx, QFS_PROF_CHECK, 0.0, ctx->cap_stream);
+    launch_batch_finalize(a, ctx->cap_stream);
+  }
+  ctx->prof.capturing = false;
+  CK(cudaStreamEndCapture(ctx->cap_stream, &graph));
+  cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+  if (e == cudaSuccess) e = cudaGraphLaunch(exec, st);
+  if (exec) cudaGraphExecDestroy(exec);
+  cudaGraphDestroy(graph);
+  CK(e);
+  std::vector<double> rc(P);
+  std::vector<int> rs(P), rb(P), rr(P);
+  CK(cudaMemcpyAsync(gates_out, a.gates_out, sizeof(double2) * gout_off, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(rc.data(), a.res_cost, sizeof(double) * P, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(rs.data(), a.res_sweeps, sizeof(int) * P, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(rb.data(), a.res_best, sizeof(int) * P, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(rr.data(), a.res_refine, sizeof(int) * P, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  prof_harvest(ctx);
+  if (ctx->prof.on) prof_harvest_graph(ctx);
+  prof_release_graph(ctx);
+  for (int i = 0; i < P; ++i) {
+    results[i].cost = rc[i];
+    results[i].sweeps = rs[i];
+    results[i].converged = rc[i] <= p->dist_tol;
+    results[i].best_start = rb[i];
+    results[i].fp64_sweeps = rr[i];
+  }
   return QFS_OK;
 }

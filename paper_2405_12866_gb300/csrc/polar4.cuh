@@ -299,6 +299,60 @@ __device__ __forceinline__ float2 skew_correction(float2 k32, float2 v, float si
   return float2{0.5f * (om.x - omt.x), 0.5f * (om.y + omt.y)};  // exactly skew-Hermitian
 }
 
+// FP32 one-sided Jacobi sweeps on X (lanes 0..15, X[r][c] at 4c + r) with
+// the accumulated right rotations V in lanes 16..31, until every column pair
+// has |gamma|^2 <= 1e-13 alpha beta (FP32 accuracy) or 12 sweeps.
+__device__ __forceinline__ float2 jacobi32_sweeps(float2 x) {
+  const int lane = threadIdx.x & 31;
+  const int l16 = lane & 15, col = l16 >> 2;
+  const int c = col;
+  for (int sweep = 0; sweep < 12; ++sweep) {
+    int rotated = 0;
+#pragma unroll
+    for (int m = 1; m <= 3; ++m) {
+      const float2 y = shfl_c(x, lane ^ (4 * m));
+      const bool isP = c < (c ^ m);
+      float nown = x.x * x.x + x.y * x.y;
+      float npar = y.x * y.x + y.y * y.y;
+      float2 g = isP ? float2{x.x * y.x + x.y * y.y, x.x * y.y - x.y * y.x}
+                     : float2{y.x * x.x + y.y * x.y, y.x * x.y - y.y * x.x};
+#pragma unroll
+      for (int o = 1; o <= 2; o <<= 1) {
+        nown += __shfl_xor_sync(FULL, nown, o);
+        npar += __shfl_xor_sync(FULL, npar, o);
+        g.x += __shfl_xor_sync(FULL, g.x, o);
+        g.y += __shfl_xor_sync(FULL, g.y, o);
+      }
+      nown = __shfl_sync(FULL, nown, l16);
+      npar = __shfl_sync(FULL, npar, l16);
+      g = shfl_c(g, l16);
+      const float alpha = isP ? nown : npar, beta = isP ? npar : nown;
+      const float ag2 = g.x * g.x + g.y * g.y;
+      float cs = 1.f, sn = 0.f, px = 1.f, py = 0.f;
+      if (ag2 > 1e-13f * alpha * beta && ag2 > 1e-36f) {
+        const float rg = rsqrtf(ag2);
+        const float zeta = 0.5f * (beta - alpha) * rg;
+        const float t = fabsf(zeta) > 1e18f ? 0.5f / zeta
+                                             : copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+        cs = rsqrtf(fmaf(t, t, 1.f));
+        sn = t * cs;
+        px = g.x * rg;
+        py = -g.y * rg;
+        rotated = 1;
+      }
+      if (isP) {
+        const float tx = px * y.x - py * y.y, ty = px * y.y + py * y.x;
+        x = float2{cs * x.x - sn * tx, cs * x.y - sn * ty};
+      } else {
+        const float tx = px * x.x - py * x.y, ty = px * x.y + py * x.x;
+        x = float2{sn * y.x + cs * tx, sn * y.y + cs * ty};
+      }
+    }
+    if (!__any_sync(FULL, rotated)) break;
+  }
+  return x;
+}
+
 // POLISH = 2 (FP64 sweeps): two polish steps, accurate to FP64 rounding.
 // POLISH = 1 (complex64 sweeps, whose environments are accurate to ~1e-7
 // anyway): one polish step, ~1e-12.  Both are unitary to rounding.
@@ -350,51 +404,7 @@ __device__ __forceinline__ bool warp_polar4_fast(double2 a, double2 v0, double2*
     }
     x = isV ? v032 : acc;
   }
-  const int c = col;
-  for (int sweep = 0; sweep < 12; ++sweep) {
-    int rotated = 0;
-#pragma unroll
-    for (int m = 1; m <= 3; ++m) {
-      const float2 y = shfl_c(x, lane ^ (4 * m));
-      const bool isP = c < (c ^ m);
-      float nown = x.x * x.x + x.y * x.y;
-      float npar = y.x * y.x + y.y * y.y;
-      float2 g = isP ? float2{x.x * y.x + x.y * y.y, x.x * y.y - x.y * y.x}
-                     : float2{y.x * x.x + y.y * x.y, y.x * x.y - y.y * x.x};
-#pragma unroll
-      for (int o = 1; o <= 2; o <<= 1) {
-        nown += __shfl_xor_sync(FULL, nown, o);
-        npar += __shfl_xor_sync(FULL, npar, o);
-        g.x += __shfl_xor_sync(FULL, g.x, o);
-        g.y += __shfl_xor_sync(FULL, g.y, o);
-      }
-      nown = __shfl_sync(FULL, nown, l16);
-      npar = __shfl_sync(FULL, npar, l16);
-      g = shfl_c(g, l16);
-      const float alpha = isP ? nown : npar, beta = isP ? npar : nown;
-      const float ag2 = g.x * g.x + g.y * g.y;
-      float cs = 1.f, sn = 0.f, px = 1.f, py = 0.f;
-      if (ag2 > 1e-13f * alpha * beta && ag2 > 1e-36f) {
-        const float rg = rsqrtf(ag2);
-        const float zeta = 0.5f * (beta - alpha) * rg;
-        const float t = fabsf(zeta) > 1e18f ? 0.5f / zeta
-                                             : copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
-        cs = rsqrtf(fmaf(t, t, 1.f));
-        sn = t * cs;
-        px = g.x * rg;
-        py = -g.y * rg;
-        rotated = 1;
-      }
-      if (isP) {
-        const float tx = px * y.x - py * y.y, ty = px * y.y + py * y.x;
-        x = float2{cs * x.x - sn * tx, cs * x.y - sn * ty};
-      } else {
-        const float tx = px * x.x - py * x.y, ty = px * x.y + py * x.x;
-        x = float2{sn * y.x + cs * tx, sn * y.y + cs * ty};
-      }
-    }
-    if (!__any_sync(FULL, rotated)) break;
-  }
+  x = jacobi32_sweeps(x);
   // Every lane: W[row][col] and V[row][col] at index l16; sigma per column.
   float2 w = shfl_c(x, l16);
   const float2 v = shfl_c(x, 16 + l16);
@@ -446,6 +456,36 @@ __device__ __forceinline__ bool warp_polar4_fast(double2 a, double2 v0, double2*
   }
   *p_out = q;
   if (v_out && lane < 16) v_out[l16] = double2{(double)v.x, (double)v.y};
+  return true;
+}
+
+// Polar factor in FP32 (batched complex64 sweeps): A (lanes 0..15, A[r][c]
+// at 4c + r, FP32), Jacobi from the identity, Q = W V^H, one Newton-Schulz
+// step.  Returns false when sigma_min < 1e-3 sigma_max (the caller then
+// takes the FP64 Jacobi, which also completes rank-deficient cases).
+__device__ __forceinline__ bool warp_polar4_f32(float2 a, float2* q_out) {
+  const int lane = threadIdx.x & 31;
+  const int l16 = lane & 15, row = l16 & 3, col = l16 >> 2;
+  const bool isV = lane >= 16;
+  float2 x = isV ? float2{row == col ? 1.f : 0.f, 0.f} : a;
+  x = jacobi32_sweeps(x);
+  float2 w = shfl_c(x, l16);
+  const float2 v = shfl_c(x, 16 + l16);
+  float nrm = w.x * w.x + w.y * w.y;
+  nrm += __shfl_xor_sync(FULL, nrm, 1);
+  nrm += __shfl_xor_sync(FULL, nrm, 2);
+  float smax = nrm, smin = nrm;
+  smax = fmaxf(smax, __shfl_xor_sync(FULL, smax, 4));
+  smax = fmaxf(smax, __shfl_xor_sync(FULL, smax, 8));
+  smin = fminf(smin, __shfl_xor_sync(FULL, smin, 4));
+  smin = fminf(smin, __shfl_xor_sync(FULL, smin, 8));
+  if (!(smin > 1e-6f * smax)) return false;
+  const float inv = rsqrtf(nrm);
+  w = float2{w.x * inv, w.y * inv};
+  float2 q = mm_bh(w, v, row, col);
+  const float2 gq = mm_ah(q, q, row, col);
+  const float2 t{(row == col ? 1.5f : 0.f) - 0.5f * gq.x, -0.5f * gq.y};
+  *q_out = mm(q, t, row, col);
   return true;
 }
 

@@ -140,4 +140,54 @@ void launch_cast_c128_to_c64(const double2* in, float2* out, long long count, cu
 // flag[0] |= 1 when any of the `count` doubles is NaN or infinite.
 void launch_nonfinite_check(const double* x, long long count, int* flag, cudaStream_t st);
 
+// ---------------------------------------------------------------- batches
+
+constexpr int kBatchMaxWarps = 8;
+
+// One instantiation problem of a batch; offsets are in complex elements
+// (pairs: in ints) into the packed arrays of BatchArgs.
+struct BatchProblem {
+  int n, L, M;
+  int pair_off;
+  long long state_off;   // psi/phil (N x M)
+  long long target_off;  // targets (N x N)
+  long long gate_off;    // init_gates/gates32 (S x L x 16)
+  long long gate_out_off;  // gates_out (L x 16)
+};
+
+struct BatchArgs {
+  const BatchProblem* probs;
+  int P, S;
+  const double2* targets;
+  double2* psi64;
+  double2* phil64;
+  float2* psi32;
+  float2* phil32;
+  const int* pairs;
+  const double2* init_gates;
+  float2* gates32;        // each start's gates after its sweeps
+  int* conv_sweep;        // P x S: sweep at which the start converged (INT_MAX if not)
+  double* final_cost;     // P x S: complex64 residual cost after its last sweep
+  int* sweeps_run;        // P x S
+  int* s_star;            // P: earliest converged sweep of each problem
+  int* queue;             // work counter, zero before the sweep launch
+  const int* order;       // problem indices, largest work first
+  int max_sweeps;
+  double tol;
+  int max_elems, max_L;   // largest N*M and L in the batch (shared-memory slices)
+  double2* gates_out;     // selected gates, FP64 (L x 16 per problem)
+  double* res_cost;
+  int* res_sweeps;
+  int* res_best;
+  int* res_refine;
+  int refine_max;
+  int refine_unconverged;  // also refine problems whose starts never reached tol
+};
+
+void launch_batch_prep(const BatchArgs& a, cudaStream_t st);
+size_t batch_sweep_smem(int warps, int max_elems, int max_L);
+int batch_sweep_blocks_per_sm(int warps, size_t smem);
+void launch_batch_sweep(const BatchArgs& a, int blocks, int warps, size_t smem, cudaStream_t st);
+void launch_batch_finalize(const BatchArgs& a, cudaStream_t st);
+
 }  // namespace qfs

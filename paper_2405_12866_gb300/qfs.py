@@ -33,10 +33,10 @@ EXPORTS = [
     "qfs_default_params", "qfs_create", "qfs_destroy", "qfs_last_error", "qfs_device_sms",
     "qfs_generate_inputs", "qfs_instantiate", "qfs_instantiate_ex", "qfs_instantiate_dev",
     "qfs_sweep_once", "qfs_gate_update", "qfs_profile_enable", "qfs_profile_reset",
-    "qfs_profile_read", "qfs_sweep_once_noalloc",
+    "qfs_profile_read", "qfs_sweep_once_noalloc", "qfs_instantiate_batch",
 ]
-PROF_BACKWARD, PROF_FORWARD, PROF_UPDATE, PROF_GEMM, PROF_RESIDUAL, PROF_CHECK, PROF_OTHER = range(7)
-PROF_NAMES = ["backward", "forward", "update", "gemm", "residual", "check", "other"]
+PROF_BACKWARD, PROF_FORWARD, PROF_UPDATE, PROF_GEMM, PROF_RESIDUAL, PROF_CHECK, PROF_OTHER, PROF_BATCH = range(8)
+PROF_NAMES = ["backward", "forward", "update", "gemm", "residual", "check", "other", "batch"]
 
 
 class QfsError(RuntimeError):
@@ -93,6 +93,7 @@ def lib():
     L.qfs_sweep_once.argtypes = [_P, C.POINTER(Circuit), _P, _P, C.c_int32, C.c_int32, _P,
                                  C.c_int32, C.c_double, _P, _P, _P]
     L.qfs_gate_update.argtypes = [_P, C.c_int32, _P, _P, C.c_double, _P]
+    L.qfs_instantiate_batch.argtypes = [_P, C.c_int32, _P, _P, _P, _P, _P, _P, C.POINTER(Params), _P, _P]
     L.qfs_sweep_once_noalloc.argtypes = [_P, C.POINTER(Circuit), _P, _P, C.c_int32, C.c_int32,
                                          C.c_double, _P, _P, _P, _P]
     L.qfs_profile_enable.argtypes = [_P, C.c_int]
@@ -239,6 +240,32 @@ class Context:
                                     M, S, gates.ctypes.data, precision, beta, out.ctypes.data,
                                     envs.ctypes.data if envs is not None else None, costs.ctypes.data))
         return out, envs, costs
+
+    def instantiate_batch(self, problems, params: Params, samples=None, init_gates=None):
+        """problems: list of (n, pairs, U).  samples/init_gates: lists per problem or None
+        (drawn from params.seed + index).  Returns (list of (L,4,4) gates, list of dicts)."""
+        P = len(problems)
+        ns = np.array([pr[0] for pr in problems], dtype=np.int32)
+        Ls = np.array([len(pr[1]) for pr in problems], dtype=np.int32)
+        pairs = np.ascontiguousarray(np.concatenate([np.asarray(pr[1], dtype=np.int32).reshape(-1)
+                                                     for pr in problems]))
+        targets = np.ascontiguousarray(np.concatenate([_host_c128(pr[2]).reshape(-1) for pr in problems]))
+        sm = None if samples is None else np.ascontiguousarray(
+            np.concatenate([_host_c128(x).reshape(-1) for x in samples]))
+        ig = None if init_gates is None else np.ascontiguousarray(
+            np.concatenate([_host_c128(x).reshape(-1) for x in init_gates]))
+        out = np.zeros(int(Ls.sum()) * 16, dtype=np.complex128)
+        res = (Result * P)()
+        _check(lib().qfs_instantiate_batch(self._h, P, ns.ctypes.data, Ls.ctypes.data, pairs.ctypes.data,
+                                           targets.ctypes.data, sm.ctypes.data if sm is not None else None,
+                                           ig.ctypes.data if ig is not None else None, C.byref(params),
+                                           out.ctypes.data, res))
+        gates, offs = [], np.concatenate([[0], np.cumsum(Ls * 16)])
+        for i in range(P):
+            gates.append(out[offs[i]:offs[i + 1]].reshape(Ls[i], 4, 4))
+        info = [dict(cost=r.cost, sweeps=r.sweeps, converged=bool(r.converged), best_start=r.best_start,
+                     fp64_sweeps=r.fp64_sweeps) for r in res]
+        return gates, info
 
     def profile(self, enable: bool):
         _check(lib().qfs_profile_enable(self._h, int(enable)))
