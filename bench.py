@@ -42,6 +42,8 @@ WORKLOADS = {
     "brick_n12": ("brick_n12", 1, "n=12 brick wall 17 gates, M=32, 32 starts, complex64 sweeps + FP64 SVD/refine/check"),
     "brick_n8": ("brick_n8", 0, "n=8 brick wall 28 gates, M=16, 16 starts, FP64"),
     "chain_n3": ("chain_n3", 0, "n=3 chain of 4 gates, M=4, 1 start, FP64, tol 1e-10"),
+    "uneven_blocks": ("uneven_blocks", 1, "4096 problems, n uniform in {3,4,5}, 2-10 nearest-neighbour gates, "
+                      "M=2^(n-1), 8 starts, complex64 sweeps + FP64 check/refine, one persistent launch"),
 }
 HW_BAD = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown")
 
@@ -380,6 +382,109 @@ def profile_case(args):
     return 0
 
 
+def _pack_batch(probs, S):
+    ns = np.array([p.n for p in probs], dtype=np.int32)
+    Ls = np.array([p.L for p in probs], dtype=np.int32)
+    pairs = np.concatenate([np.asarray(p.pairs, dtype=np.int32).reshape(-1) for p in probs])
+    tg = np.concatenate([p.U.reshape(-1) for p in probs])
+    sm = np.concatenate([p.samples().reshape(-1) for p in probs])
+    ig = np.concatenate([p.init_gates()[:S].reshape(-1) for p in probs])
+    return ns, Ls, pairs, tg, sm, ig
+
+
+def run_ours_batch(args):
+    """The batched form: one step = one whole batch of problems."""
+    import torch
+    from paper_2405_12866_gb300 import build as qbuild
+    from paper_2405_12866_gb300 import qfs
+    from paper_2405_12866_gb300 import workloads as w
+    qbuild.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    ctx = qfs.Context(0, stream.cuda_stream)
+    S, P = 8, args.batch_problems
+    batches = []
+    for seed in (4, 5):
+        probs = w.uneven_blocks(P=P, seed=seed, S=S)
+        ns, Ls, pairs, tg, sm, ig = _pack_batch(probs, S)
+        batches.append((ns, Ls, pairs, torch.from_numpy(tg).to(dev), torch.from_numpy(sm).to(dev),
+                        torch.from_numpy(ig).to(dev), probs, (tg, sm, ig)))
+    prm = qfs.default_params(M=0, multistarts=S, max_sweeps=500, dist_tol=1e-8, refine_sweeps_max=20)
+    outs = [torch.zeros(int(b[1].sum()) * 16, dtype=torch.complex128, device=dev) for b in batches]
+
+    def step(i):
+        b = batches[i % 2]
+        return ctx.instantiate_batch_dev(b[0], b[1], b[2], b[3], b[4], b[5], prm, outs[i % 2])
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize(dev)
+    clocks = Clocks(0)
+    clocks.start()
+    ctx.profile_reset()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = [step(args.warmup + i) for i in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    launches = ctx.profile_read(-1)["launches"]
+    conv = sum(r["converged"] for inf in infos for r in inf)
+    value = conv / (ms / 1e3)
+    # Algorithmic FP32 sweep arithmetic, 96 L N M flops per start-sweep,
+    # counting every start at its problem's reported sweep count.
+    flops = 0.0
+    for i, inf in enumerate(infos):
+        probs = batches[(args.warmup + i) % 2][6]
+        for pr, r in zip(probs, inf):
+            flops += S * r["sweeps"] * 96.0 * pr.L * (pr.M << pr.n)
+    achieved = flops / (ms / 1e3) / 1e12
+    fp32_peak = 72.9
+    b = batches[0]
+    hin = [torch.from_numpy(x).pin_memory().numpy() for x in b[7]]
+    e2e_problems = [(pr.n, pr.pairs, pr.U) for pr in b[6]]
+    e2e_samples = [pr.samples() for pr in b[6]]
+    e2e_inits = [pr.init_gates()[:S] for pr in b[6]]
+    t0 = time.perf_counter()
+    e2e_infos = ctx.instantiate_batch(e2e_problems, prm, e2e_samples, e2e_inits)
+    t_e2e = time.perf_counter() - t0
+    conv_e2e = sum(r["converged"] for r in e2e_infos[1])
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64+f64", "data": "synthetic (seeded Haar-random targets of the stated structures)",
+        "config": {"workload": WORKLOADS["uneven_blocks"][2], "problems_per_step": P, "multistarts": S,
+                   "tol": 1e-8, "max_sweeps": 500, "l2": "working set on chip; no flush"},
+        "converged": int(conv), "instantiations": P * args.steps,
+        "roofline": {"bound": "alu", "kernel": "k_batch_sweep (persistent)", "achieved": achieved,
+                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                     "peak_source": "FP32 FMA probe (paper_2405_12866_gb300/probes/alu_peak.cu): 72.9 TFLOP/s",
+                     "traffic": None, "algorithmic_flops_per_step": flops / args.steps},
+        "clocks": clk,
+        "e2e": {"value": conv_e2e / t_e2e, "unit": UNIT, "note": "host API incl. host-side packing and copies",
+                "h2d_bytes_per_step": int(sum(x.nbytes for x in hin)), "d2h_bytes_per_step": int(b[1].sum()) * 256},
+        "gpu_launches": int(launches),
+    }
+    if args.cpu_baseline:
+        t0 = time.perf_counter()
+        n_sample = 0
+        conv_o = 0
+        for pr in b[6]:
+            Psi, G0 = pr.samples(), pr.init_gates()[:S]
+            r = __import__("oracle.qfs_oracle", fromlist=["x"]).instantiate(pr.U, Psi, G0, pr.pairs, pr.n, 1e-8, 500)
+            conv_o += r.converged
+            n_sample += 1
+            if time.perf_counter() - t0 > 15.0:
+                break
+        t_o = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": conv_o / t_o, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"the first {n_sample} problems of the batch, run to completion by the oracle on one core ({t_o:.1f} s)"}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -389,6 +494,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="brick_n12")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--batch-problems", type=int, default=4096)
     ap.add_argument("--start-groups", type=int, default=0,
                     help="concurrent groups of multistarts (0 = the library's choice)")
     ap.add_argument("--profile-case", action="store_true",
@@ -400,6 +506,8 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "uneven_blocks":
+        return run_ours_batch(args)
     return run_ours(args)
 
 

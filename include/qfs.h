@@ -210,6 +210,13 @@ int qfs_instantiate_batch(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int3
                           const double* init_gates, const qfs_params* p, double* gates_out,
                           qfs_result* results);
 
+/* As qfs_instantiate_batch with targets, samples, init_gates (all required)
+ * and gates_out in device memory; ns, Ls, pairs and results stay host. */
+int qfs_instantiate_batch_dev(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls,
+                              const int32_t* pairs, const double* targets_dev,
+                              const double* samples_dev, const double* init_gates_dev,
+                              const qfs_params* p, double* gates_out_dev, qfs_result* results);
+
 /* One FP64 sweep (as qfs_sweep_once with QFS_FP64) that allocates no
  * memory, for callers that cannot call cudaMalloc: code running inside a
  * host framework that owns every device byte through its own allocator or a

@@ -1228,11 +1228,15 @@ int autotune_batch(qfs_ctx* ctx, BatchArgs a, int max_sweeps_run, int* warps_out
 
 }  // namespace
 
-extern "C" int qfs_instantiate_batch(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls,
-                                     const int32_t* pairs, const double* targets,
-                                     const double* samples, const double* init_gates,
-                                     const qfs_params* p, double* gates_out, qfs_result* results) {
-  g_err.clear();
+namespace {
+
+int batch_common(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls, const int32_t* pairs,
+                 const double* targets, const double* samples, const double* init_gates,
+                 const qfs_params* p, double* gates_out, qfs_result* results, bool dev) {
+  if (dev && (!samples || !init_gates))
+    return fail(QFS_EINVAL, "the device-pointer batch needs samples and init_gates");
+  const cudaMemcpyKind h2d = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const cudaMemcpyKind d2h = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (P < 1) return fail(QFS_EINVAL, "P = %d: need >= 1", P);
   if (!ns || !Ls || !pairs || !targets || !p || !gates_out || !results)
     return fail(QFS_EINVAL, "ns, Ls, pairs, targets, params, gates_out and results must be given");
@@ -1321,12 +1325,12 @@ extern "C" int qfs_instantiate_batch(qfs_ctx* ctx, int32_t P, const int32_t* ns,
   CK(cudaMemcpyAsync(w + o_probs, probs.data(), sizeof(BatchProblem) * P, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(w + o_order, order.data(), sizeof(int) * P, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(w + o_pairs, pairs, sizeof(int) * pair_off, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(w + o_tgt, targets, sizeof(double2) * target_off, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(w + o_tgt, targets, sizeof(double2) * target_off, h2d, st));
   // Training states and initial gates: given, or drawn per problem from
   // seed + problem index (the library's Philox draws).
   std::vector<std::complex<double>> hs, hg;
   if (samples) {
-    CK(cudaMemcpyAsync(w + o_psi64, samples, sizeof(double2) * state_off, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(w + o_psi64, samples, sizeof(double2) * state_off, h2d, st));
   } else {
     hs.resize(state_off);
     for (int i = 0; i < P; ++i)
@@ -1334,7 +1338,7 @@ extern "C" int qfs_instantiate_batch(qfs_ctx* ctx, int32_t P, const int32_t* ns,
     CK(cudaMemcpyAsync(w + o_psi64, hs.data(), sizeof(double2) * state_off, cudaMemcpyHostToDevice, st));
   }
   if (init_gates) {
-    CK(cudaMemcpyAsync(w + o_g0, init_gates, sizeof(double2) * gate_off, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(w + o_g0, init_gates, sizeof(double2) * gate_off, h2d, st));
   } else {
     hg.resize(gate_off);
     for (int i = 0; i < P; ++i)
@@ -1373,7 +1377,7 @@ extern "C" int qfs_instantiate_batch(qfs_ctx* ctx, int32_t P, const int32_t* ns,
   CK(e);
   std::vector<double> rc(P);
   std::vector<int> rs(P), rb(P), rr(P);
-  CK(cudaMemcpyAsync(gates_out, a.gates_out, sizeof(double2) * gout_off, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(gates_out, a.gates_out, sizeof(double2) * gout_off, d2h, st));
   CK(cudaMemcpyAsync(rc.data(), a.res_cost, sizeof(double) * P, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(rs.data(), a.res_sweeps, sizeof(int) * P, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(rb.data(), a.res_best, sizeof(int) * P, cudaMemcpyDeviceToHost, st));
@@ -1390,4 +1394,23 @@ extern "C" int qfs_instantiate_batch(qfs_ctx* ctx, int32_t P, const int32_t* ns,
     results[i].fp64_sweeps = rr[i];
   }
   return QFS_OK;
+}
+
+}  // namespace
+
+extern "C" int qfs_instantiate_batch(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls,
+                                     const int32_t* pairs, const double* targets,
+                                     const double* samples, const double* init_gates,
+                                     const qfs_params* p, double* gates_out, qfs_result* results) {
+  g_err.clear();
+  return batch_common(ctx, P, ns, Ls, pairs, targets, samples, init_gates, p, gates_out, results, false);
+}
+
+extern "C" int qfs_instantiate_batch_dev(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls,
+                                         const int32_t* pairs, const double* targets_dev,
+                                         const double* samples_dev, const double* init_gates_dev,
+                                         const qfs_params* p, double* gates_out_dev, qfs_result* results) {
+  g_err.clear();
+  return batch_common(ctx, P, ns, Ls, pairs, targets_dev, samples_dev, init_gates_dev, p, gates_out_dev,
+                      results, true);
 }

@@ -34,6 +34,7 @@ EXPORTS = [
     "qfs_generate_inputs", "qfs_instantiate", "qfs_instantiate_ex", "qfs_instantiate_dev",
     "qfs_sweep_once", "qfs_gate_update", "qfs_profile_enable", "qfs_profile_reset",
     "qfs_profile_read", "qfs_sweep_once_noalloc", "qfs_instantiate_batch",
+    "qfs_instantiate_batch_dev",
 ]
 PROF_BACKWARD, PROF_FORWARD, PROF_UPDATE, PROF_GEMM, PROF_RESIDUAL, PROF_CHECK, PROF_OTHER, PROF_BATCH = range(8)
 PROF_NAMES = ["backward", "forward", "update", "gemm", "residual", "check", "other", "batch"]
@@ -94,6 +95,7 @@ def lib():
                                  C.c_int32, C.c_double, _P, _P, _P]
     L.qfs_gate_update.argtypes = [_P, C.c_int32, _P, _P, C.c_double, _P]
     L.qfs_instantiate_batch.argtypes = [_P, C.c_int32, _P, _P, _P, _P, _P, _P, C.POINTER(Params), _P, _P]
+    L.qfs_instantiate_batch_dev.argtypes = [_P, C.c_int32, _P, _P, _P, _P, _P, _P, C.POINTER(Params), _P, _P]
     L.qfs_sweep_once_noalloc.argtypes = [_P, C.POINTER(Circuit), _P, _P, C.c_int32, C.c_int32,
                                          C.c_double, _P, _P, _P, _P]
     L.qfs_profile_enable.argtypes = [_P, C.c_int]
@@ -266,6 +268,20 @@ class Context:
         info = [dict(cost=r.cost, sweeps=r.sweeps, converged=bool(r.converged), best_start=r.best_start,
                      fp64_sweeps=r.fp64_sweeps) for r in res]
         return gates, info
+
+    def instantiate_batch_dev(self, ns, Ls, pairs, targets, samples, init_gates, params: Params, out):
+        """Packed device tensors (torch complex128): targets, samples, init_gates, out;
+        ns, Ls, pairs host int32 arrays.  Returns the list of per-problem result dicts."""
+        ns = np.ascontiguousarray(ns, dtype=np.int32)
+        Ls = np.ascontiguousarray(Ls, dtype=np.int32)
+        pairs = np.ascontiguousarray(pairs, dtype=np.int32)
+        P = len(ns)
+        res = (Result * P)()
+        _check(lib().qfs_instantiate_batch_dev(self._h, P, ns.ctypes.data, Ls.ctypes.data, pairs.ctypes.data,
+                                               targets.data_ptr(), samples.data_ptr(), init_gates.data_ptr(),
+                                               C.byref(params), out.data_ptr(), res))
+        return [dict(cost=r.cost, sweeps=r.sweeps, converged=bool(r.converged), best_start=r.best_start,
+                     fp64_sweeps=r.fp64_sweeps) for r in res]
 
     def profile(self, enable: bool):
         _check(lib().qfs_profile_enable(self._h, int(enable)))
