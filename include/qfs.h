@@ -124,7 +124,8 @@ int qfs_device_sms(const qfs_ctx* ctx);
 #define QFS_PROF_CHECK 5    /* FP64 cost check of a candidate start */
 #define QFS_PROF_OTHER 6    /* casts, input checks, finishing reductions */
 #define QFS_PROF_BATCH 7    /* persistent batched sweep kernel */
-#define QFS_PROF_KINDS 8
+#define QFS_PROF_MLP 8      /* tensor-core GEMMs of the learned warm start (FLOPs) */
+#define QFS_PROF_KINDS 9
 int qfs_profile_enable(qfs_ctx* ctx, int enable);
 int qfs_profile_reset(qfs_ctx* ctx);
 int qfs_profile_read(qfs_ctx* ctx, int32_t kind, int64_t* launches, int64_t* timed,
@@ -216,6 +217,16 @@ int qfs_instantiate_batch_dev(qfs_ctx* ctx, int32_t P, const int32_t* ns, const 
                               const int32_t* pairs, const double* targets_dev,
                               const double* samples_dev, const double* init_gates_dev,
                               const qfs_params* p, double* gates_out_dev, qfs_result* results);
+
+/* BF16 GEMM on the tcgen05 tensor cores (the learned warm start's layers):
+ * C = A B^T (+ bias, optional GELU), A (M x K, leading dimension lda) and B
+ * (N x K, ldb) bf16 row-major in device memory, accumulation in FP32; C32
+ * (fp32) and/or C16 (bf16, GELU applied when gelu != 0) receive M_valid
+ * (<= M, 0 = M) rows with leading dimension ldc.  M and N multiples of 128,
+ * K of 64, lda and ldb multiples of 8 and A, B 16-byte aligned. */
+int qfs_gemm_bf16_dev(qfs_ctx* ctx, int32_t M, int32_t N, int32_t K, const void* A, int32_t lda,
+                      const void* B, int32_t ldb, float* C32, void* C16, int32_t ldc,
+                      const float* bias, int32_t gelu, int32_t M_valid);
 
 /* One FP64 sweep (as qfs_sweep_once with QFS_FP64) that allocates no
  * memory, for callers that cannot call cudaMalloc: code running inside a

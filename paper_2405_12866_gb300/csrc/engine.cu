@@ -1414,3 +1414,39 @@ extern "C" int qfs_instantiate_batch_dev(qfs_ctx* ctx, int32_t P, const int32_t*
   return batch_common(ctx, P, ns, Ls, pairs, targets_dev, samples_dev, init_gates_dev, p, gates_out_dev,
                       results, true);
 }
+
+// ---------------------------------------------------------------------------
+// Learned warm start: tensor-core GEMM entry point.
+
+extern "C" int qfs_gemm_bf16_dev(qfs_ctx* ctx, int32_t M, int32_t N, int32_t K, const void* A, int32_t lda,
+                                 const void* B, int32_t ldb, float* C32, void* C16, int32_t ldc,
+                                 const float* bias, int32_t gelu, int32_t M_valid) {
+  g_err.clear();
+  if (M <= 0 || N <= 0 || K <= 0 || M % 128 || N % 128 || K % 64)
+    return fail(QFS_EINVAL, "M, N multiples of 128 and K of 64 needed (M=%d N=%d K=%d)", M, N, K);
+  if (lda % 8 || ldb % 8 || lda < K || ldb < K || ldc < N)
+    return fail(QFS_EINVAL, "lda, ldb >= K and multiples of 8, ldc >= N needed");
+  if (!A || !B || (!C32 && !C16)) return fail(QFS_EINVAL, "A, B and an output must be given");
+  if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15)
+    return fail(QFS_EINVAL, "A and B must be 16-byte aligned");
+  TRY(ctx_check(ctx));
+  TRY(set_device(ctx));
+  TRY(ensure_ws(ctx, 256));
+  int* err = reinterpret_cast<int*>(ctx->ws);
+  cudaStream_t st = ctx->stream;
+  CK(cudaMemsetAsync(err, 0, sizeof(int), st));
+  GemmArgs g{reinterpret_cast<const __nv_bfloat16*>(A), lda, reinterpret_cast<const __nv_bfloat16*>(B), ldb,
+             C32, reinterpret_cast<__nv_bfloat16*>(C16), ldc, bias, gelu, M, N, K,
+             M_valid > 0 ? M_valid : M, err};
+  {
+    ProfScope ps(ctx, QFS_PROF_MLP, 2.0 * M * N * K, st);
+    launch_gemm_bf16_tc(g, st);
+  }
+  CK(cudaGetLastError());
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  prof_harvest(ctx);
+  if (h) return fail(QFS_ETIMEOUT, "a bounded tensor-core wait ran out");
+  return QFS_OK;
+}

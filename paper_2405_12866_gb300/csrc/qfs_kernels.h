@@ -1,5 +1,6 @@
 // Internal launcher interface between the engine (host C++) and the kernels.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -189,5 +190,26 @@ size_t batch_sweep_smem(int warps, int max_elems, int max_L);
 int batch_sweep_blocks_per_sm(int warps, size_t smem);
 void launch_batch_sweep(const BatchArgs& a, int blocks, int warps, size_t smem, cudaStream_t st);
 void launch_batch_finalize(const BatchArgs& a, cudaStream_t st);
+
+// ---------------------------------------------------------- learned part
+
+// C[M x N] = A[M x K] B[N x K]^T (+ bias) with tcgen05 tensor cores.  M, N
+// multiples of 128, K of 64; lda, ldb multiples of 8; rows >= M_valid are
+// computed but not stored.  C32 (fp32) and/or C16 (bf16, after GELU if
+// gelu) receive the result with leading dimension ldc.
+struct GemmArgs {
+  const __nv_bfloat16* A;
+  int lda;
+  const __nv_bfloat16* B;
+  int ldb;
+  float* C32;
+  __nv_bfloat16* C16;
+  int ldc;
+  const float* bias;
+  int gelu;
+  int M, N, K, M_valid;
+  int* err;
+};
+void launch_gemm_bf16_tc(const GemmArgs& g, cudaStream_t st);
 
 }  // namespace qfs

@@ -34,10 +34,11 @@ EXPORTS = [
     "qfs_generate_inputs", "qfs_instantiate", "qfs_instantiate_ex", "qfs_instantiate_dev",
     "qfs_sweep_once", "qfs_gate_update", "qfs_profile_enable", "qfs_profile_reset",
     "qfs_profile_read", "qfs_sweep_once_noalloc", "qfs_instantiate_batch",
-    "qfs_instantiate_batch_dev",
+    "qfs_instantiate_batch_dev", "qfs_gemm_bf16_dev",
 ]
-PROF_BACKWARD, PROF_FORWARD, PROF_UPDATE, PROF_GEMM, PROF_RESIDUAL, PROF_CHECK, PROF_OTHER, PROF_BATCH = range(8)
-PROF_NAMES = ["backward", "forward", "update", "gemm", "residual", "check", "other", "batch"]
+(PROF_BACKWARD, PROF_FORWARD, PROF_UPDATE, PROF_GEMM, PROF_RESIDUAL, PROF_CHECK, PROF_OTHER, PROF_BATCH,
+ PROF_MLP) = range(9)
+PROF_NAMES = ["backward", "forward", "update", "gemm", "residual", "check", "other", "batch", "mlp"]
 
 
 class QfsError(RuntimeError):
@@ -96,6 +97,8 @@ def lib():
     L.qfs_gate_update.argtypes = [_P, C.c_int32, _P, _P, C.c_double, _P]
     L.qfs_instantiate_batch.argtypes = [_P, C.c_int32, _P, _P, _P, _P, _P, _P, C.POINTER(Params), _P, _P]
     L.qfs_instantiate_batch_dev.argtypes = [_P, C.c_int32, _P, _P, _P, _P, _P, _P, C.POINTER(Params), _P, _P]
+    L.qfs_gemm_bf16_dev.argtypes = [_P, C.c_int32, C.c_int32, C.c_int32, _P, C.c_int32, _P, C.c_int32, _P, _P,
+                                    C.c_int32, _P, C.c_int32, C.c_int32]
     L.qfs_sweep_once_noalloc.argtypes = [_P, C.POINTER(Circuit), _P, _P, C.c_int32, C.c_int32,
                                          C.c_double, _P, _P, _P, _P]
     L.qfs_profile_enable.argtypes = [_P, C.c_int]
@@ -282,6 +285,19 @@ class Context:
                                                C.byref(params), out.data_ptr(), res))
         return [dict(cost=r.cost, sweeps=r.sweeps, converged=bool(r.converged), best_start=r.best_start,
                      fp64_sweeps=r.fp64_sweeps) for r in res]
+
+    def gemm_bf16(self, A, B, bias=None, gelu=False, want_f32=True, want_bf16=False, M_valid=0):
+        """C = A B^T (+ bias, GELU) for bf16 CUDA tensors A (M x K), B (N x K)."""
+        import torch
+        M, K = A.shape
+        N = B.shape[0]
+        C32 = torch.empty((M, N), dtype=torch.float32, device=A.device) if want_f32 else None
+        C16 = torch.empty((M, N), dtype=torch.bfloat16, device=A.device) if want_bf16 else None
+        _check(lib().qfs_gemm_bf16_dev(self._h, M, N, K, A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0),
+                                       C32.data_ptr() if C32 is not None else None,
+                                       C16.data_ptr() if C16 is not None else None, N,
+                                       bias.data_ptr() if bias is not None else None, int(gelu), M_valid))
+        return C32, C16
 
     def profile(self, enable: bool):
         _check(lib().qfs_profile_enable(self._h, int(enable)))
