@@ -228,6 +228,35 @@ int qfs_gemm_bf16_dev(qfs_ctx* ctx, int32_t M, int32_t N, int32_t K, const void*
                       const void* B, int32_t ldb, float* C32, void* C16, int32_t ldc,
                       const float* bias, int32_t gelu, int32_t M_valid);
 
+/* Learned warm start.  A multilayer perceptron maps the target of a 4-qubit
+ * block applied to 8 fixed states (16 x 8 complex = 256 reals) through three
+ * hidden layers of 1024 (GELU, tanh form) to 6 gates (192 reals: gate g,
+ * entry 4r + c, re/im), projected onto U(4) by their polar factors.  It is
+ * trained on (target, converged gates) pairs that the method produces,
+ * with mean squared error on the 192 reals and Adam; all products run on
+ * the tcgen05 GEMM (BF16 operands, FP32 accumulation, FP32 master weights).
+ * The paper has no learned part; the sweep judges every proposal.
+ *
+ * qfs_ws_create: weights N(0, 2/fan_in) from Philox (seed), biases zero;
+ *   batch_cap (multiple of 128) bounds the rows of one pass.
+ * qfs_ws_params: copy the FP32 parameters out (out) and/or in (in), layer
+ *   by layer W[out x in] then b[out], dims 256->1024->1024->1024->256 (the
+ *   last 64 outputs are padding); *count receives the number of floats.
+ * qfs_ws_loss_grad: loss and gradients (same layout) on one batch of
+ *   targets (host, count x 16 x 16 complex) and labels (host, count x 192).
+ * qfs_ws_train: epochs of shuffled mini-batches with Adam (lr, beta1 0.9,
+ *   beta2 0.999, eps 1e-8); epoch_loss (may be NULL) gets the mean loss.
+ * qfs_ws_predict: gates_out (host, count x 6 x 16 complex, unitary). */
+typedef struct qfs_ws qfs_ws;
+int qfs_ws_create(qfs_ctx* ctx, uint64_t seed, int32_t batch_cap, qfs_ws** out);
+void qfs_ws_destroy(qfs_ws* ws);
+int qfs_ws_params(qfs_ws* ws, float* out, const float* in, int64_t* count);
+int qfs_ws_loss_grad(qfs_ws* ws, int32_t count, const double* targets, const double* labels, double* loss,
+                     float* grads_out);
+int qfs_ws_train(qfs_ws* ws, int32_t count, const double* targets, const double* labels, int32_t epochs,
+                 int32_t batch, double lr, uint64_t shuffle_seed, double* epoch_loss);
+int qfs_ws_predict(qfs_ws* ws, int32_t count, const double* targets, double* gates_out);
+
 /* One FP64 sweep (as qfs_sweep_once with QFS_FP64) that allocates no
  * memory, for callers that cannot call cudaMalloc: code running inside a
  * host framework that owns every device byte through its own allocator or a

@@ -1450,3 +1450,356 @@ extern "C" int qfs_gemm_bf16_dev(qfs_ctx* ctx, int32_t M, int32_t N, int32_t K, 
   if (h) return fail(QFS_ETIMEOUT, "a bounded tensor-core wait ran out");
   return QFS_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Learned warm start: a multilayer perceptron mapping the target applied to
+// eight fixed states of a 4-qubit block (16 x 8 complex = 256 reals) through
+// three hidden layers of 1024 (GELU) to 6 gates (192 reals), trained on
+// (target, converged gates) pairs that the method itself produces.  All
+// products run on the tcgen05 GEMM; weights are FP32 masters with BF16
+// copies, activations BF16, accumulation FP32, Adam on the masters.
+
+namespace qfs {
+void generate_samples(uint64_t seed, int n, int M, std::complex<double>* out);
+std::complex<double> complex_normal(uint64_t seed, uint32_t stream, uint64_t index);
+}
+
+namespace {
+// A normal draw with variance 1/2 (the real part of a standard complex normal).
+inline double qfs_normal_re(uint64_t seed, uint32_t stream, uint64_t index) {
+  return qfs::complex_normal(seed, stream, index).real();
+}
+}  // namespace
+
+struct qfs_ws {
+  qfs_ctx* ctx = nullptr;
+  static constexpr int kLayers = 4;
+  int din[kLayers] = {256, 1024, 1024, 1024};
+  int dout[kLayers] = {1024, 1024, 1024, 256};  // the last 64 outputs are padding
+  int n_out = 192;
+  int B_cap = 0;
+  long long step = 0;
+  char* mem = nullptr;
+  float *W[kLayers], *b[kLayers], *mW[kLayers], *vW[kLayers], *mb[kLayers], *vb[kLayers], *gW[kLayers], *gb[kLayers];
+  __nv_bfloat16 *W16[kLayers], *WT16[kLayers];
+  double2* phif = nullptr;      // 16 x 8 fixed states
+  __nv_bfloat16* X16 = nullptr;  // B_cap x 256
+  __nv_bfloat16* H16[kLayers];   // B_cap x dout
+  float* Z32[kLayers];           // B_cap x dout
+  float *dA32, *dB32;            // B_cap x 1024 scratch (fp32 gradients)
+  __nv_bfloat16 *dA16, *dB16, *T1, *T2;  // bf16 gradient and transposes (1024 x B_cap)
+  float* Tlab = nullptr;         // B_cap x 192 labels
+  double* loss_part = nullptr;   // 1024
+  double2* tgt = nullptr;        // B_cap x 256 complex (targets of a batch)
+  double2* envs = nullptr;       // B_cap x 6 x 16 (projection scratch)
+  int* err = nullptr;
+};
+
+namespace {
+
+long long ws_param_count(const qfs_ws* m) {
+  long long c = 0;
+  for (int l = 0; l < qfs_ws::kLayers; ++l) c += (long long)m->dout[l] * m->din[l] + m->dout[l];
+  return c;
+}
+
+int ws_gemm(qfs_ws* m, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K,
+            float* C32, __nv_bfloat16* C16, int ldc, const float* bias, int gelu, int M_valid) {
+  GemmArgs g{A, lda, B, ldb, C32, C16, ldc, bias, gelu, M, N, K, M_valid, m->err};
+  ProfScope ps(m->ctx, QFS_PROF_MLP, 2.0 * M * N * K);
+  launch_gemm_bf16_tc(g, m->ctx->stream);
+  return QFS_OK;
+}
+
+// Forward pass on B rows (multiple of 128) of m->X16: Z32[l], H16[l].
+void ws_forward(qfs_ws* m, int B) {
+  const __nv_bfloat16* in = m->X16;
+  for (int l = 0; l < qfs_ws::kLayers; ++l) {
+    const bool last = l == qfs_ws::kLayers - 1;
+    ws_gemm(m, in, m->din[l], m->W16[l], m->din[l], B, m->dout[l], m->din[l], m->Z32[l], last ? nullptr : m->H16[l],
+            m->dout[l], m->b[l], last ? 0 : 1, B);
+    in = m->H16[l];
+  }
+}
+
+// Loss and gradients for B rows (B_valid real) with labels in m->Tlab.
+int ws_backward(qfs_ws* m, int B, int B_valid, double* loss) {
+  cudaStream_t st = m->ctx->stream;
+  const int L = qfs_ws::kLayers;
+  const int nparts = launch_ws_loss_grad(m->Z32[L - 1], m->dout[L - 1], m->Tlab, m->n_out, B, B_valid, m->dA32,
+                                         m->dA16, m->loss_part, st);
+  float* g32 = m->dA32;
+  __nv_bfloat16* g16 = m->dA16;
+  for (int l = L - 1; l >= 0; --l) {
+    const int N = m->dout[l], K = m->din[l];
+    launch_colsum(g32, B, N, m->gb[l], st);
+    launch_transpose_bf16(g16, B, N, m->T1, st);  // N x B
+    const __nv_bfloat16* hin = l == 0 ? m->X16 : m->H16[l - 1];
+    launch_transpose_bf16(hin, B, K, m->T2, st);  // K x B
+    TRY(ws_gemm(m, m->T1, B, m->T2, B, N, K, B, m->gW[l], nullptr, K, nullptr, 0, N));
+    if (l > 0) {
+      float* o32 = g32 == m->dA32 ? m->dB32 : m->dA32;
+      __nv_bfloat16* o16 = g16 == m->dA16 ? m->dB16 : m->dA16;
+      // dH = g W (B x K), then dZ = dH * gelu'(Z_{l-1}).
+      TRY(ws_gemm(m, g16, N, m->WT16[l], N, B, K, N, o32, nullptr, K, nullptr, 0, B));
+      launch_gelu_back(o32, m->Z32[l - 1], (long long)B * K, K, B_valid, o32, o16, st);
+      g32 = o32;
+      g16 = o16;
+    }
+  }
+  if (loss) {
+    std::vector<double> parts(nparts);
+    CK(cudaMemcpyAsync(parts.data(), m->loss_part, sizeof(double) * nparts, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    double s = 0.0;
+    for (double x : parts) s += x;
+    *loss = s / ((double)B_valid * m->n_out);
+  }
+  return QFS_OK;
+}
+
+void ws_refresh_bf16(qfs_ws* m) {
+  cudaStream_t st = m->ctx->stream;
+  for (int l = 0; l < qfs_ws::kLayers; ++l) {
+    launch_cast_f32_bf16(m->W[l], m->W16[l], (long long)m->dout[l] * m->din[l], st);
+    launch_transpose_bf16(m->W16[l], m->dout[l], m->din[l], m->WT16[l], st);
+  }
+}
+
+// Features of `count` host targets (16 x 16 each) into m->X16 rows (B_pad).
+int ws_load_features(qfs_ws* m, const double* targets, int count, int B_pad) {
+  cudaStream_t st = m->ctx->stream;
+  CK(cudaMemcpyAsync(m->tgt, targets, sizeof(double2) * 256 * (size_t)count, cudaMemcpyHostToDevice, st));
+  launch_ws_features(m->tgt, m->phif, count, B_pad, m->X16, st);
+  return QFS_OK;
+}
+
+int check_err_word(qfs_ws* m) {
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, m->err, sizeof(int), cudaMemcpyDeviceToHost, m->ctx->stream));
+  CK(cudaStreamSynchronize(m->ctx->stream));
+  if (h) return fail(QFS_ETIMEOUT, "a bounded tensor-core wait ran out");
+  return QFS_OK;
+}
+
+}  // namespace
+
+extern "C" int qfs_ws_create(qfs_ctx* ctx, uint64_t seed, int32_t batch_cap, qfs_ws** out) {
+  g_err.clear();
+  if (!out) return fail(QFS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (batch_cap < 128 || batch_cap % 128) return fail(QFS_EINVAL, "batch_cap = %d: a multiple of 128 needed", batch_cap);
+  TRY(ctx_check(ctx));
+  TRY(set_device(ctx));
+  qfs_ws* m = new qfs_ws();
+  m->ctx = ctx;
+  m->B_cap = batch_cap;
+  const int L = qfs_ws::kLayers;
+  size_t off = 0;
+  std::vector<size_t> o;
+  auto take = [&](size_t bytes) {
+    o.push_back(off);
+    off += align_up(bytes);
+    return o.back();
+  };
+  size_t oW[L], ob[L], omW[L], ovW[L], omb[L], ovb[L], ogW[L], ogb[L], oW16[L], oWT[L], oH[L], oZ[L];
+  for (int l = 0; l < L; ++l) {
+    const size_t nw = (size_t)m->dout[l] * m->din[l], nb = m->dout[l];
+    oW[l] = take(nw * 4); ob[l] = take(nb * 4); omW[l] = take(nw * 4); ovW[l] = take(nw * 4);
+    omb[l] = take(nb * 4); ovb[l] = take(nb * 4); ogW[l] = take(nw * 4); ogb[l] = take(nb * 4);
+    oW16[l] = take(nw * 2); oWT[l] = take(nw * 2);
+    oH[l] = take((size_t)batch_cap * m->dout[l] * 2); oZ[l] = take((size_t)batch_cap * m->dout[l] * 4);
+  }
+  const size_t ophif = take(sizeof(double2) * 128), oX = take((size_t)batch_cap * 256 * 2),
+               odA32 = take((size_t)batch_cap * 1024 * 4), odB32 = take((size_t)batch_cap * 1024 * 4),
+               odA16 = take((size_t)batch_cap * 1024 * 2), odB16 = take((size_t)batch_cap * 1024 * 2),
+               oT1 = take((size_t)batch_cap * 1024 * 2), oT2 = take((size_t)batch_cap * 1024 * 2),
+               oT = take((size_t)batch_cap * 192 * 4), olp = take(1024 * sizeof(double)),
+               otg = take(sizeof(double2) * 256 * (size_t)batch_cap), oenv = take(sizeof(double2) * 96 * (size_t)batch_cap),
+               oerr = take(sizeof(int) * 4);
+  cudaError_t e = cudaMalloc(&m->mem, off);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete m;
+    return fail(QFS_ENOMEM, "warm-start model: cannot allocate %.2f GiB", off / 1073741824.0);
+  }
+  char* b = m->mem;
+  for (int l = 0; l < L; ++l) {
+    m->W[l] = (float*)(b + oW[l]); m->b[l] = (float*)(b + ob[l]); m->mW[l] = (float*)(b + omW[l]);
+    m->vW[l] = (float*)(b + ovW[l]); m->mb[l] = (float*)(b + omb[l]); m->vb[l] = (float*)(b + ovb[l]);
+    m->gW[l] = (float*)(b + ogW[l]); m->gb[l] = (float*)(b + ogb[l]);
+    m->W16[l] = (__nv_bfloat16*)(b + oW16[l]); m->WT16[l] = (__nv_bfloat16*)(b + oWT[l]);
+    m->H16[l] = (__nv_bfloat16*)(b + oH[l]); m->Z32[l] = (float*)(b + oZ[l]);
+  }
+  m->phif = (double2*)(b + ophif);
+  m->X16 = (__nv_bfloat16*)(b + oX);
+  m->dA32 = (float*)(b + odA32); m->dB32 = (float*)(b + odB32);
+  m->dA16 = (__nv_bfloat16*)(b + odA16); m->dB16 = (__nv_bfloat16*)(b + odB16);
+  m->T1 = (__nv_bfloat16*)(b + oT1); m->T2 = (__nv_bfloat16*)(b + oT2);
+  m->Tlab = (float*)(b + oT); m->loss_part = (double*)(b + olp);
+  m->tgt = (double2*)(b + otg); m->envs = (double2*)(b + oenv); m->err = (int*)(b + oerr);
+  cudaStream_t st = ctx->stream;
+  // Initial weights: normal with variance 1/fan_in from Philox (stream 6);
+  // the padded output rows and all biases start at zero; Adam moments zero.
+  std::vector<float> h;
+  for (int l = 0; l < L; ++l) {
+    const size_t nw = (size_t)m->dout[l] * m->din[l];
+    h.assign(nw, 0.f);
+    const double sd = 1.0 / std::sqrt((double)m->din[l]);
+    const int rows = l == L - 1 ? m->n_out : m->dout[l];
+    for (size_t i = 0; i < (size_t)rows * m->din[l]; ++i)
+      h[i] = (float)(sd * std::sqrt(2.0) * qfs_normal_re(seed, 6u, ((uint64_t)l << 40) + i));
+    CK(cudaMemcpyAsync(m->W[l], h.data(), nw * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaMemsetAsync(m->b[l], 0, (size_t)m->dout[l] * 4, st));
+    CK(cudaMemsetAsync(m->mW[l], 0, nw * 4, st));
+    CK(cudaMemsetAsync(m->vW[l], 0, nw * 4, st));
+    CK(cudaMemsetAsync(m->mb[l], 0, (size_t)m->dout[l] * 4, st));
+    CK(cudaMemsetAsync(m->vb[l], 0, (size_t)m->dout[l] * 4, st));
+  }
+  // Fixed feature states: 8 orthonormal states of 4 qubits drawn from the seed.
+  std::vector<std::complex<double>> pf(128);
+  qfs::generate_samples(seed ^ 0x5eedf1c5ULL, 4, 8, pf.data());
+  CK(cudaMemcpyAsync(m->phif, pf.data(), sizeof(double2) * 128, cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(m->err, 0, sizeof(int) * 4, st));
+  ws_refresh_bf16(m);
+  CK(cudaStreamSynchronize(st));
+  *out = m;
+  return QFS_OK;
+}
+
+extern "C" void qfs_ws_destroy(qfs_ws* m) {
+  if (!m) return;
+  cudaSetDevice(m->ctx->device);
+  cudaStreamSynchronize(m->ctx->stream);
+  cudaFree(m->mem);
+  delete m;
+}
+
+extern "C" int qfs_ws_params(qfs_ws* m, float* out, const float* in, int64_t* count) {
+  g_err.clear();
+  if (!m) return fail(QFS_EINVAL, "model is NULL");
+  const long long n = ws_param_count(m);
+  if (count) *count = n;
+  TRY(set_device(m->ctx));
+  cudaStream_t st = m->ctx->stream;
+  long long off = 0;
+  for (int l = 0; l < qfs_ws::kLayers; ++l) {
+    const size_t nw = (size_t)m->dout[l] * m->din[l], nb = m->dout[l];
+    if (out) {
+      CK(cudaMemcpyAsync(out + off, m->W[l], nw * 4, cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(out + off + nw, m->b[l], nb * 4, cudaMemcpyDeviceToHost, st));
+    }
+    if (in) {
+      CK(cudaMemcpyAsync(m->W[l], in + off, nw * 4, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(m->b[l], in + off + nw, nb * 4, cudaMemcpyHostToDevice, st));
+    }
+    off += nw + nb;
+  }
+  if (in) ws_refresh_bf16(m);
+  CK(cudaStreamSynchronize(st));
+  return QFS_OK;
+}
+
+extern "C" int qfs_ws_loss_grad(qfs_ws* m, int32_t count, const double* targets, const double* labels,
+                                double* loss, float* grads_out) {
+  g_err.clear();
+  if (!m || !targets || !labels) return fail(QFS_EINVAL, "model, targets and labels must be given");
+  if (count < 1 || count > m->B_cap) return fail(QFS_EINVAL, "count = %d: 1..%d", count, m->B_cap);
+  TRY(set_device(m->ctx));
+  cudaStream_t st = m->ctx->stream;
+  const int B = (count + 127) / 128 * 128;
+  TRY(ws_load_features(m, targets, count, B));
+  std::vector<float> t((size_t)count * 192);
+  for (size_t i = 0; i < t.size(); ++i) t[i] = (float)labels[i];
+  CK(cudaMemcpyAsync(m->Tlab, t.data(), t.size() * 4, cudaMemcpyHostToDevice, st));
+  ws_forward(m, B);
+  TRY(ws_backward(m, B, count, loss));
+  if (grads_out) {
+    long long off = 0;
+    for (int l = 0; l < qfs_ws::kLayers; ++l) {
+      const size_t nw = (size_t)m->dout[l] * m->din[l], nb = m->dout[l];
+      CK(cudaMemcpyAsync(grads_out + off, m->gW[l], nw * 4, cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(grads_out + off + nw, m->gb[l], nb * 4, cudaMemcpyDeviceToHost, st));
+      off += nw + nb;
+    }
+  }
+  CK(cudaStreamSynchronize(st));
+  return check_err_word(m);
+}
+
+extern "C" int qfs_ws_train(qfs_ws* m, int32_t count, const double* targets, const double* labels, int32_t epochs,
+                            int32_t batch, double lr, uint64_t shuffle_seed, double* epoch_loss) {
+  g_err.clear();
+  if (!m || !targets || !labels) return fail(QFS_EINVAL, "model, targets and labels must be given");
+  if (count < 1 || epochs < 1) return fail(QFS_EINVAL, "count and epochs must be >= 1");
+  if (batch < 128 || batch % 128 || batch > m->B_cap)
+    return fail(QFS_EINVAL, "batch = %d: a multiple of 128 up to %d", batch, m->B_cap);
+  if (!(lr > 0.0)) return fail(QFS_EINVAL, "lr must be > 0");
+  TRY(set_device(m->ctx));
+  cudaStream_t st = m->ctx->stream;
+  std::vector<int> idx(count);
+  std::vector<double> tb((size_t)batch * 256 * 2);
+  std::vector<float> lb((size_t)batch * 192);
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  for (int ep = 0; ep < epochs; ++ep) {
+    for (int i = 0; i < count; ++i) idx[i] = i;
+    // Fisher-Yates with Philox draws (deterministic per seed and epoch).
+    for (int i = count - 1; i > 0; --i) {
+      const double u = 0.5 + 0.5 * std::erf(qfs_normal_re(shuffle_seed, 7u, ((uint64_t)ep << 32) + i) / std::sqrt(2.0));
+      int j = (int)(u * (i + 1));
+      if (j > i) j = i;
+      std::swap(idx[i], idx[j]);
+    }
+    double ep_loss = 0.0;
+    int nb = 0;
+    for (int s0 = 0; s0 < count; s0 += batch) {
+      const int bv = std::min(batch, count - s0);
+      const int B = (bv + 127) / 128 * 128;
+      for (int r = 0; r < bv; ++r) {
+        std::memcpy(&tb[(size_t)r * 512], targets + (size_t)idx[s0 + r] * 512, 512 * sizeof(double));
+        for (int c = 0; c < 192; ++c) lb[(size_t)r * 192 + c] = (float)labels[(size_t)idx[s0 + r] * 192 + c];
+      }
+      TRY(ws_load_features(m, tb.data(), bv, B));
+      CK(cudaMemcpyAsync(m->Tlab, lb.data(), (size_t)bv * 192 * 4, cudaMemcpyHostToDevice, st));
+      ws_forward(m, B);
+      double l = 0.0;
+      TRY(ws_backward(m, B, bv, &l));
+      ep_loss += l;
+      ++nb;
+      ++m->step;
+      const float bc1 = 1.f - std::pow(b1, (float)m->step), bc2 = 1.f - std::pow(b2, (float)m->step);
+      for (int k = 0; k < qfs_ws::kLayers; ++k) {
+        launch_adam(m->W[k], m->mW[k], m->vW[k], m->gW[k], (long long)m->dout[k] * m->din[k], (float)lr, b1, b2, eps,
+                    bc1, bc2, m->W16[k], st);
+        launch_adam(m->b[k], m->mb[k], m->vb[k], m->gb[k], m->dout[k], (float)lr, b1, b2, eps, bc1, bc2, nullptr, st);
+        launch_transpose_bf16(m->W16[k], m->dout[k], m->din[k], m->WT16[k], st);
+      }
+    }
+    if (epoch_loss) epoch_loss[ep] = ep_loss / std::max(nb, 1);
+  }
+  CK(cudaStreamSynchronize(st));
+  return check_err_word(m);
+}
+
+extern "C" int qfs_ws_predict(qfs_ws* m, int32_t count, const double* targets, double* gates_out) {
+  g_err.clear();
+  if (!m || !targets || !gates_out) return fail(QFS_EINVAL, "model, targets and gates_out must be given");
+  if (count < 1) return fail(QFS_EINVAL, "count must be >= 1");
+  TRY(set_device(m->ctx));
+  cudaStream_t st = m->ctx->stream;
+  for (int s0 = 0; s0 < count; s0 += m->B_cap) {
+    const int bv = std::min(m->B_cap, count - s0);
+    const int B = (bv + 127) / 128 * 128;
+    TRY(ws_load_features(m, targets + (size_t)s0 * 512, bv, B));
+    ws_forward(m, B);
+    // Output rows -> 6 gates each; project each onto U(4) by its polar
+    // factor (the update routine returns polar(E^dagger), so pass G^dagger).
+    launch_ws_gates_adjoint(m->Z32[qfs_ws::kLayers - 1], m->dout[qfs_ws::kLayers - 1], bv, m->envs, st);
+    launch_gate_update_batch(bv * 6, m->envs, nullptr, 0.0, m->envs, st);
+    CK(cudaMemcpyAsync(gates_out + (size_t)s0 * 192, m->envs, sizeof(double2) * 96 * (size_t)bv,
+                       cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  return check_err_word(m);
+}

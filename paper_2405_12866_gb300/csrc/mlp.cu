@@ -1,0 +1,172 @@
+// Elementwise and reduction kernels of the learned warm start (the network
+// proposes initial gates; the sweep judges them).  The matrix products run
+// on the tensor cores (mlp_gemm.cu); these kernels build the features, cast
+// and transpose operands, form the loss gradient, back-propagate GELU, sum
+// bias gradients and apply Adam.
+#include <cuda_bf16.h>
+
+#include "qfs_common.cuh"
+#include "qfs_kernels.h"
+
+namespace qfs {
+
+namespace {
+__device__ __forceinline__ float gelu_grad_f(float x) {
+  const float k0 = 0.7978845608028654f, k1 = 0.044715f;
+  const float t = tanhf(k0 * (x + k1 * x * x * x));
+  return 0.5f * (1.f + t) + 0.5f * x * (1.f - t * t) * k0 * (1.f + 3.f * k1 * x * x);
+}
+}  // namespace
+
+// Features of target t: the 16 x 8 complex matrix U_t Phi_fix as 256 reals
+// (row-major, re/im interleaved), bf16, row t of X (ld = 256).  Rows
+// count..rows-1 are zero.
+__global__ void k_ws_features(const double2* __restrict__ U, const double2* __restrict__ phif, int count,
+                              int rows, __nv_bfloat16* __restrict__ X) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;  // one complex output
+  if (e >= (long long)rows * 128) return;
+  const int t = (int)(e / 128), k = (int)(e % 128), i = k / 8, j = k % 8;
+  float re = 0.f, im = 0.f;
+  if (t < count) {
+    const double2* u = U + (size_t)t * 256 + i * 16;
+    for (int q = 0; q < 16; ++q) {
+      const double2 a = u[q], b = phif[q * 8 + j];
+      re += (float)(a.x * b.x - a.y * b.y);
+      im += (float)(a.x * b.y + a.y * b.x);
+    }
+  }
+  X[(size_t)t * 256 + 2 * k] = __float2bfloat16(re);
+  X[(size_t)t * 256 + 2 * k + 1] = __float2bfloat16(im);
+}
+
+// dst[c][r] = src[r][c] (bf16), 32 x 32 tiles; R, C multiples of 32.
+__global__ void k_transpose_bf16(const __nv_bfloat16* __restrict__ src, int R, int C,
+                                 __nv_bfloat16* __restrict__ dst) {
+  __shared__ __nv_bfloat16 tile[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int y = threadIdx.y; y < 32; y += 8) tile[y][threadIdx.x] = src[(size_t)(r0 + y) * C + c0 + threadIdx.x];
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += 8) dst[(size_t)(c0 + y) * R + r0 + threadIdx.x] = tile[threadIdx.x][y];
+}
+
+__global__ void k_cast_f32_bf16(const float* __restrict__ a, __nv_bfloat16* __restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = __float2bfloat16(a[i]);
+}
+
+// Output gradient of the mean squared error over the first n_out columns of
+// the first B_valid rows: dY = 2 (Y - T) / (B_valid n_out) (fp32 and bf16),
+// zero elsewhere; loss partial sums per block into loss_part[blockIdx.x].
+__global__ void k_ws_loss_grad(const float* __restrict__ Y, int ldy, const float* __restrict__ T, int n_out,
+                               int rows, int B_valid, float* __restrict__ dY32, __nv_bfloat16* __restrict__ dY16,
+                               double* __restrict__ loss_part) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  const double scale = 2.0 / ((double)B_valid * n_out);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)rows * ldy;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e / ldy), c = (int)(e % ldy);
+    float g = 0.f;
+    if (r < B_valid && c < n_out) {
+      const double d = (double)Y[e] - (double)T[(size_t)r * n_out + c];
+      acc += d * d;
+      g = (float)(scale * d);
+    }
+    dY32[e] = g;
+    dY16[e] = __float2bfloat16(g);
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) loss_part[blockIdx.x] = red[0];
+}
+
+// dZ = dH * gelu'(Z) (fp32 and bf16), rows >= B_valid zeroed.
+__global__ void k_gelu_back(const float* __restrict__ dH, const float* __restrict__ Z, long long n, int ld,
+                            int B_valid, float* __restrict__ dZ32, __nv_bfloat16* __restrict__ dZ16) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float g = (i / ld) < B_valid ? dH[i] * gelu_grad_f(Z[i]) : 0.f;
+    dZ32[i] = g;
+    dZ16[i] = __float2bfloat16(g);
+  }
+}
+
+// db[c] = sum over rows of G[r][c] (fp32), one thread per column.
+__global__ void k_colsum(const float* __restrict__ G, int rows, int cols, float* __restrict__ db) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  double s = 0.0;
+  for (int r = 0; r < rows; ++r) s += G[(size_t)r * cols + c];
+  db[c] = (float)s;
+}
+
+// Adam (Kingma & Ba 2015) on fp32 master parameters with a bf16 copy.
+__global__ void k_adam(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
+                       const float* __restrict__ g, long long n, float lr, float b1, float b2, float eps,
+                       float bc1, float bc2, __nv_bfloat16* __restrict__ w16) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    w[i] = wi;
+    if (w16) w16[i] = __float2bfloat16(wi);
+  }
+}
+
+// Network outputs -> 6 gates per row (G[r][c] from outputs 2(16g + 4r + c),
+// +1) -> E = G^dagger, so that the polar update (which returns the polar
+// factor of E^dagger) projects G onto U(4).
+__global__ void k_ws_gates_adjoint(const float* __restrict__ Y, int ldy, int count, double2* __restrict__ E) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)count * 96) return;
+  const int t = (int)(e / 96), q = (int)(e % 96), g = q / 16, x = (q % 16) / 4, y = q % 4;
+  const float* row = Y + (size_t)t * ldy + 32 * g;
+  // E[x][y] = conj(G[y][x])
+  E[e] = double2{(double)row[2 * (4 * y + x)], -(double)row[2 * (4 * y + x) + 1]};
+}
+
+static int blocks_for(long long n, int threads = 256, int cap = 4096) {
+  long long b = (n + threads - 1) / threads;
+  return (int)(b > cap ? cap : (b < 1 ? 1 : b));
+}
+
+void launch_ws_features(const double2* U, const double2* phif, int count, int rows, __nv_bfloat16* X,
+                        cudaStream_t st) {
+  const long long n = (long long)rows * 128;
+  k_ws_features<<<(int)((n + 255) / 256), 256, 0, st>>>(U, phif, count, rows, X);
+}
+void launch_ws_gates_adjoint(const float* Y, int ldy, int count, double2* E, cudaStream_t st) {
+  const long long n = (long long)count * 96;
+  k_ws_gates_adjoint<<<(int)((n + 255) / 256), 256, 0, st>>>(Y, ldy, count, E);
+}
+void launch_transpose_bf16(const __nv_bfloat16* src, int R, int C, __nv_bfloat16* dst, cudaStream_t st) {
+  k_transpose_bf16<<<dim3(C / 32, R / 32), dim3(32, 8), 0, st>>>(src, R, C, dst);
+}
+void launch_cast_f32_bf16(const float* a, __nv_bfloat16* b, long long n, cudaStream_t st) {
+  k_cast_f32_bf16<<<blocks_for(n), 256, 0, st>>>(a, b, n);
+}
+int launch_ws_loss_grad(const float* Y, int ldy, const float* T, int n_out, int rows, int B_valid, float* dY32,
+                        __nv_bfloat16* dY16, double* loss_part, cudaStream_t st) {
+  const int blocks = blocks_for((long long)rows * ldy, 256, 1024);
+  k_ws_loss_grad<<<blocks, 256, 0, st>>>(Y, ldy, T, n_out, rows, B_valid, dY32, dY16, loss_part);
+  return blocks;
+}
+void launch_gelu_back(const float* dH, const float* Z, long long n, int ld, int B_valid, float* dZ32,
+                      __nv_bfloat16* dZ16, cudaStream_t st) {
+  k_gelu_back<<<blocks_for(n), 256, 0, st>>>(dH, Z, n, ld, B_valid, dZ32, dZ16);
+}
+void launch_colsum(const float* G, int rows, int cols, float* db, cudaStream_t st) {
+  k_colsum<<<(cols + 127) / 128, 128, 0, st>>>(G, rows, cols, db);
+}
+void launch_adam(float* w, float* m, float* v, const float* g, long long n, float lr, float b1, float b2, float eps,
+                 float bc1, float bc2, __nv_bfloat16* w16, cudaStream_t st) {
+  k_adam<<<blocks_for(n), 256, 0, st>>>(w, m, v, g, n, lr, b1, b2, eps, bc1, bc2, w16);
+}
+
+}  // namespace qfs

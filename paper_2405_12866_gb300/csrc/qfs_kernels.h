@@ -212,4 +212,18 @@ struct GemmArgs {
 };
 void launch_gemm_bf16_tc(const GemmArgs& g, cudaStream_t st);
 
+void launch_ws_features(const double2* U, const double2* phif, int count, int rows, __nv_bfloat16* X,
+                        cudaStream_t st);
+void launch_transpose_bf16(const __nv_bfloat16* src, int R, int C, __nv_bfloat16* dst, cudaStream_t st);
+void launch_ws_gates_adjoint(const float* Y, int ldy, int count, double2* E, cudaStream_t st);
+void launch_cast_f32_bf16(const float* a, __nv_bfloat16* b, long long n, cudaStream_t st);
+// Returns the number of loss partial sums written.
+int launch_ws_loss_grad(const float* Y, int ldy, const float* T, int n_out, int rows, int B_valid, float* dY32,
+                        __nv_bfloat16* dY16, double* loss_part, cudaStream_t st);
+void launch_gelu_back(const float* dH, const float* Z, long long n, int ld, int B_valid, float* dZ32,
+                      __nv_bfloat16* dZ16, cudaStream_t st);
+void launch_colsum(const float* G, int rows, int cols, float* db, cudaStream_t st);
+void launch_adam(float* w, float* m, float* v, const float* g, long long n, float lr, float b1, float b2, float eps,
+                 float bc1, float bc2, __nv_bfloat16* w16, cudaStream_t st);
+
 }  // namespace qfs

@@ -34,7 +34,8 @@ EXPORTS = [
     "qfs_generate_inputs", "qfs_instantiate", "qfs_instantiate_ex", "qfs_instantiate_dev",
     "qfs_sweep_once", "qfs_gate_update", "qfs_profile_enable", "qfs_profile_reset",
     "qfs_profile_read", "qfs_sweep_once_noalloc", "qfs_instantiate_batch",
-    "qfs_instantiate_batch_dev", "qfs_gemm_bf16_dev",
+    "qfs_instantiate_batch_dev", "qfs_gemm_bf16_dev", "qfs_ws_create", "qfs_ws_destroy", "qfs_ws_params",
+    "qfs_ws_loss_grad", "qfs_ws_train", "qfs_ws_predict",
 ]
 (PROF_BACKWARD, PROF_FORWARD, PROF_UPDATE, PROF_GEMM, PROF_RESIDUAL, PROF_CHECK, PROF_OTHER, PROF_BATCH,
  PROF_MLP) = range(9)
@@ -99,6 +100,13 @@ def lib():
     L.qfs_instantiate_batch_dev.argtypes = [_P, C.c_int32, _P, _P, _P, _P, _P, _P, C.POINTER(Params), _P, _P]
     L.qfs_gemm_bf16_dev.argtypes = [_P, C.c_int32, C.c_int32, C.c_int32, _P, C.c_int32, _P, C.c_int32, _P, _P,
                                     C.c_int32, _P, C.c_int32, C.c_int32]
+    L.qfs_ws_create.argtypes = [_P, C.c_uint64, C.c_int32, C.POINTER(_P)]
+    L.qfs_ws_destroy.argtypes = [_P]
+    L.qfs_ws_destroy.restype = None
+    L.qfs_ws_params.argtypes = [_P, _P, _P, C.POINTER(C.c_int64)]
+    L.qfs_ws_loss_grad.argtypes = [_P, C.c_int32, _P, _P, C.POINTER(C.c_double), _P]
+    L.qfs_ws_train.argtypes = [_P, C.c_int32, _P, _P, C.c_int32, C.c_int32, C.c_double, C.c_uint64, _P]
+    L.qfs_ws_predict.argtypes = [_P, C.c_int32, _P, _P]
     L.qfs_sweep_once_noalloc.argtypes = [_P, C.POINTER(Circuit), _P, _P, C.c_int32, C.c_int32,
                                          C.c_double, _P, _P, _P, _P]
     L.qfs_profile_enable.argtypes = [_P, C.c_int]
@@ -317,4 +325,77 @@ class Context:
         g = None if gates_old is None else _host_c128(gates_old).reshape(-1, 4, 4)
         _check(lib().qfs_gate_update(self._h, envs.shape[0], envs.ctypes.data,
                                      g.ctypes.data if g is not None else None, beta, out.ctypes.data))
+        return out
+
+
+class WarmStart:
+    """The learned warm-start network (weights on the context's device)."""
+
+    DIMS = [(256, 1024), (1024, 1024), (1024, 1024), (1024, 256)]   # (in, out) per layer
+
+    def __init__(self, ctx: Context, seed: int = 0, batch_cap: int = 4096):
+        self._h = _P()
+        self.ctx = ctx
+        _check(lib().qfs_ws_create(ctx._h, seed, batch_cap, C.byref(self._h)))
+
+    def close(self):
+        if self._h:
+            lib().qfs_ws_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self) -> np.ndarray:
+        n = C.c_int64()
+        _check(lib().qfs_ws_params(self._h, None, None, C.byref(n)))
+        out = np.zeros(n.value, dtype=np.float32)
+        _check(lib().qfs_ws_params(self._h, out.ctypes.data, None, C.byref(n)))
+        return out
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        n = C.c_int64()
+        _check(lib().qfs_ws_params(self._h, None, flat.ctypes.data, C.byref(n)))
+
+    @classmethod
+    def unflatten(cls, flat):
+        """Flat parameter vector -> list of (W [out, in], b [out])."""
+        out, off = [], 0
+        for din, dout in cls.DIMS:
+            W = flat[off:off + din * dout].reshape(dout, din)
+            off += din * dout
+            b = flat[off:off + dout]
+            off += dout
+            out.append((W, b))
+        return out
+
+    def loss_grad(self, targets, labels):
+        t = _host_c128(targets)
+        lab = np.ascontiguousarray(labels, dtype=np.float64)
+        count = t.size // 256
+        loss = C.c_double()
+        n = C.c_int64()
+        _check(lib().qfs_ws_params(self._h, None, None, C.byref(n)))
+        g = np.zeros(n.value, dtype=np.float32)
+        _check(lib().qfs_ws_loss_grad(self._h, count, t.ctypes.data, lab.ctypes.data, C.byref(loss), g.ctypes.data))
+        return loss.value, g
+
+    def train(self, targets, labels, epochs=1, batch=4096, lr=1e-3, seed=0):
+        t = _host_c128(targets)
+        lab = np.ascontiguousarray(labels, dtype=np.float64)
+        count = t.size // 256
+        losses = np.zeros(epochs)
+        _check(lib().qfs_ws_train(self._h, count, t.ctypes.data, lab.ctypes.data, epochs, batch, lr, seed,
+                                  losses.ctypes.data))
+        return losses
+
+    def predict(self, targets):
+        t = _host_c128(targets)
+        count = t.size // 256
+        out = np.zeros((count, 6, 4, 4), dtype=np.complex128)
+        _check(lib().qfs_ws_predict(self._h, count, t.ctypes.data, out.ctypes.data))
         return out

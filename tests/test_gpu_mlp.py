@@ -38,3 +38,46 @@ def test_gemm_bf16_matches_reference(ctx, M, N, K):
     assert np.max(np.abs(got - ref)) < 1e-4 * max(1.0, np.max(np.abs(ref)))
     gelu = 0.5 * ref * (1 + np.tanh(0.7978845608028654 * (ref + 0.044715 * ref ** 3)))
     assert np.max(np.abs(C16.cpu().double().numpy() - gelu)) < 1e-2 * max(1.0, np.max(np.abs(gelu)))
+
+
+def _learned_targets(count, seed):
+    from paper_2405_12866_gb300 import workloads as w
+    gs = w.haar_gates(seed, w.STREAM_TARGET_GATES, 6 * count).reshape(count, 6, 4, 4)
+    return np.stack([w.target_unitary(g, w.LEARNED_PAIRS, 4) for g in gs]), gs
+
+
+def test_warm_start_gradients_match_oracle(ctx):
+    from oracle import mlp_oracle as mo
+    from paper_2405_12866_gb300 import qfs
+    from paper_2405_12866_gb300 import workloads as w
+    seed = 3
+    model = qfs.WarmStart(ctx, seed=seed, batch_cap=256)
+    U, gs = _learned_targets(200, 17)
+    labels = np.stack([np.stack([gs[i].reshape(-1).real, gs[i].reshape(-1).imag], axis=-1).reshape(-1)
+                       for i in range(200)])
+    loss, g = model.loss_grad(U, labels)
+    params = qfs.WarmStart.unflatten(model.get_params().astype(np.float64))
+    phif = w.sample_states(seed ^ 0x5EEDF1C5, 4, 8)
+    F = np.einsum("tij,jk->tik", U, phif)
+    X = np.stack([F.real, F.imag], axis=-1).reshape(200, 256)
+    want_loss, want = mo.loss_and_grads(params, X, labels, 192, round_bf16=True)
+    assert abs(loss - want_loss) < 1e-3 * want_loss
+    got = qfs.WarmStart.unflatten(g.astype(np.float64))
+    for (gw, gb), (ww, wb) in zip(got, want):
+        assert np.linalg.norm(gw - ww) < 3e-2 * np.linalg.norm(ww) + 1e-12
+        assert np.linalg.norm(gb - wb) < 3e-2 * np.linalg.norm(wb) + 1e-12
+    model.close()
+
+
+def test_warm_start_trains_and_predicts_unitaries(ctx):
+    from paper_2405_12866_gb300 import qfs
+    model = qfs.WarmStart(ctx, seed=5, batch_cap=512)
+    U, gs = _learned_targets(1024, 23)
+    labels = np.stack([np.stack([gs[i].reshape(-1).real, gs[i].reshape(-1).imag], axis=-1).reshape(-1)
+                       for i in range(1024)])
+    losses = model.train(U, labels, epochs=30, batch=256, lr=1e-3, seed=1)
+    assert losses[-1] < 0.5 * losses[0]
+    pred = model.predict(U[:64])
+    for g in pred.reshape(-1, 4, 4):
+        assert np.max(np.abs(g.conj().T @ g - np.eye(4))) < 1e-12
+    model.close()
