@@ -44,6 +44,8 @@ WORKLOADS = {
     "chain_n3": ("chain_n3", 0, "n=3 chain of 4 gates, M=4, 1 start, FP64, tol 1e-10"),
     "uneven_blocks": ("uneven_blocks", 1, "4096 problems, n uniform in {3,4,5}, 2-10 nearest-neighbour gates, "
                       "M=2^(n-1), 8 starts, complex64 sweeps + FP64 check/refine, one persistent launch"),
+    "learned": ("learned", 1, "learned warm start: 4-qubit 6-gate structure, MLP 256-3x1024-192 trained on "
+                "method-generated pairs; 65536 fresh targets, predicted start then 8 random starts as fallback"),
 }
 HW_BAD = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown")
 
@@ -121,6 +123,17 @@ def peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def bf16_peak(sustained=True):
+    """Dense bf16 tensor peak (TFLOP/s) and its source."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        key = "bf16_tflops_sustained" if sustained and "bf16_tflops_sustained" in d else "bf16_tflops"
+        return float(d[key]), "measured (" + key + ")"
+    except Exception:
+        return (1700.0 if sustained else 1900.0), "fallback"
 
 
 def traffic_record(kernel_src_hash):
@@ -485,6 +498,97 @@ def run_ours_batch(args):
     return 0
 
 
+def run_ours_learned(args):
+    """The learned form: labels from the method, training on the GPU, then
+    one step = the whole evaluation set through the warm-start policy
+    (predicted start, random multistarts as the fallback), host arrays in
+    and out (so value and e2e are the same end-to-end measurement)."""
+    import torch
+    from paper_2405_12866_gb300 import build as qbuild
+    from paper_2405_12866_gb300 import learned, qfs
+    qbuild.build()
+    dev = torch.device("cuda", 0)
+    ctx = qfs.Context(0)
+    workers = max(1, min(16, os.cpu_count() or 1))
+    ntrain, neval, epochs = args.learned_train, args.learned_eval, args.learned_epochs
+    t0 = time.perf_counter()
+    Ttr = learned.make_targets(11, ntrain, workers=workers)
+    Tev = learned.make_targets(12, neval, workers=workers)
+    t_targets = time.perf_counter() - t0
+    ls = learned.method_labels(ctx, Ttr, workers=workers)
+    ws = qfs.WarmStart(ctx, seed=3, batch_cap=4096)
+    ctx.profile(True)
+    ctx.profile_reset()
+    t0 = time.perf_counter()
+    losses = ws.train(ls.targets, ls.labels, epochs=epochs, batch=4096, lr=2e-3, lr_final=4e-5, seed=1)
+    t_train = time.perf_counter() - t0
+    mlp = ctx.profile_read(qfs.PROF_NAMES.index("mlp"))
+    ctx.profile(False)
+    gemm_tflops = mlp["bytes"] / (mlp["ms"] / 1e3) / 1e12 if mlp["ms"] > 0 else None
+    first_rand = learned.random_starts(5000, neval, 1)[:, 0]
+
+    def step(i):
+        return learned.two_stage(ctx, Tev, None, ws=ws, seed=7000 + i, name="learned")
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize(dev)
+    clocks = Clocks(0)
+    clocks.start()
+    ctx.profile(True)
+    ctx.profile_reset()
+    stats = [step(args.warmup + i) for i in range(args.steps)]
+    clk = clocks.stop()
+    launches = ctx.profile_read(-1)["launches"]
+    ctx.profile(False)
+    secs = sum(s.seconds for s in stats)
+    conv = sum(s.converged for s in stats)
+    value = conv / secs
+    rand = learned.two_stage(ctx, Tev, first_rand, seed=7000, name="random first start")
+    base = learned.multistart(ctx, Tev, S=8, seed=7000, name="8 random starts")
+    # The plain FP64 GPU path (one problem per call, 8 starts) on a sample.
+    nfp = min(64, neval)
+    p64 = qfs.default_params(M=learned.M_SAMPLES, multistarts=8, max_sweeps=300, dist_tol=1e-8,
+                             precision=qfs.QFS_FP64, seed=0)
+    t0 = time.perf_counter()
+    c64 = sum(ctx.instantiate(learned.N_QUBITS, learned.PAIRS, Tev[i], p64).converged for i in range(nfp))
+    t64 = time.perf_counter() - t0
+    tc_peak, tc_src = bf16_peak(sustained=True)
+
+    def pol(s):
+        return {"converged": s.converged, "of": s.P, "seconds": s.seconds, "converged_per_s": s.converged_per_s,
+                "first_start_converged": s.first_stage_converged, "start_sweeps": s.start_sweeps}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64 sweeps, bf16 MLP",
+        "data": "synthetic (seeded Haar-random circuits of the learned structure)",
+        "config": {"workload": WORKLOADS["learned"][2], "train_pairs_generated": ntrain,
+                   "train_pairs_converged": int(len(ls.labels)), "eval_targets": neval, "epochs": epochs,
+                   "first_sweeps": 100, "fallback_starts": 8, "max_sweeps": 300, "tol": 1e-8,
+                   "l2": "eval targets 256 MiB > L2; no flush"},
+        "learned": {"policy": pol(stats[-1]), "random_first_start_policy": pol(rand),
+                    "eight_random_starts": pol(base),
+                    "plain_fp64_gpu_path": {"converged": int(c64), "of": nfp, "converged_per_s": c64 / t64},
+                    "train_seconds": t_train, "train_samples_per_s": len(ls.labels) * epochs / t_train,
+                    "epoch_loss_first_last": [float(losses[0]), float(losses[-1])],
+                    "label_generation_seconds": ls.seconds, "target_generation_seconds": t_targets},
+        "roofline": {"bound": "tensor", "kernel": "k_gemm_bf16_tma (training GEMMs, all shapes)",
+                     "achieved": gemm_tflops, "peak": tc_peak, "unit": "TFLOP/s",
+                     "frac": gemm_tflops / tc_peak if gemm_tflops else None, "peak_source": tc_src,
+                     "traffic": None},
+        "clocks": clk,
+        "e2e": {"value": value, "unit": UNIT, "note": "host targets in, host gates out: value is end to end",
+                "h2d_bytes_per_step": int(Tev.nbytes), "d2h_bytes_per_step": int(neval * 6 * 256)},
+        "gpu_launches": int(launches),
+    }
+    print(json.dumps(line), flush=True)
+    ws.close()
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -495,6 +599,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--batch-problems", type=int, default=4096)
+    ap.add_argument("--learned-train", type=int, default=1 << 20)
+    ap.add_argument("--learned-eval", type=int, default=65536)
+    ap.add_argument("--learned-epochs", type=int, default=40)
     ap.add_argument("--start-groups", type=int, default=0,
                     help="concurrent groups of multistarts (0 = the library's choice)")
     ap.add_argument("--profile-case", action="store_true",
@@ -508,6 +615,8 @@ def main():
         return run_reference(args)
     if args.workload == "uneven_blocks":
         return run_ours_batch(args)
+    if args.workload == "learned":
+        return run_ours_learned(args)
     return run_ours(args)
 
 

@@ -223,7 +223,11 @@ int qfs_instantiate_batch_dev(qfs_ctx* ctx, int32_t P, const int32_t* ns, const 
  * (N x K, ldb) bf16 row-major in device memory, accumulation in FP32; C32
  * (fp32) and/or C16 (bf16, GELU applied when gelu != 0) receive M_valid
  * (<= M, 0 = M) rows with leading dimension ldc.  M and N multiples of 128,
- * K of 64, lda and ldb multiples of 8 and A, B 16-byte aligned. */
+ * K of 64, lda and ldb multiples of 8, ldc of 8, and A, B, C32, C16, bias
+ * 16-byte aligned.  A product with only C32 (no bias, no GELU) whose tiles
+ * would leave most SMs idle is split along K; the partial tiles are added
+ * into C32 (zeroed first) with atomics, so the summation order, and the
+ * last bits of C32, can vary from call to call. */
 int qfs_gemm_bf16_dev(qfs_ctx* ctx, int32_t M, int32_t N, int32_t K, const void* A, int32_t lda,
                       const void* B, int32_t ldb, float* C32, void* C16, int32_t ldc,
                       const float* bias, int32_t gelu, int32_t M_valid);
@@ -244,8 +248,11 @@ int qfs_gemm_bf16_dev(qfs_ctx* ctx, int32_t M, int32_t N, int32_t K, const void*
  *   last 64 outputs are padding); *count receives the number of floats.
  * qfs_ws_loss_grad: loss and gradients (same layout) on one batch of
  *   targets (host, count x 16 x 16 complex) and labels (host, count x 192).
- * qfs_ws_train: epochs of shuffled mini-batches with Adam (lr, beta1 0.9,
- *   beta2 0.999, eps 1e-8); epoch_loss (may be NULL) gets the mean loss.
+ * qfs_ws_train: epochs of shuffled mini-batches with Adam (beta1 0.9,
+ *   beta2 0.999, eps 1e-8), the step size decaying from lr to lr_final on a
+ *   cosine over the call's steps (lr_final = lr: constant); the training set
+ *   stays on the device for the call; epoch_loss (may be NULL) gets each
+ *   epoch's mean loss.  Features are 4 U Phi_fix (unit variance).
  * qfs_ws_predict: gates_out (host, count x 6 x 16 complex, unitary). */
 typedef struct qfs_ws qfs_ws;
 int qfs_ws_create(qfs_ctx* ctx, uint64_t seed, int32_t batch_cap, qfs_ws** out);
@@ -254,7 +261,7 @@ int qfs_ws_params(qfs_ws* ws, float* out, const float* in, int64_t* count);
 int qfs_ws_loss_grad(qfs_ws* ws, int32_t count, const double* targets, const double* labels, double* loss,
                      float* grads_out);
 int qfs_ws_train(qfs_ws* ws, int32_t count, const double* targets, const double* labels, int32_t epochs,
-                 int32_t batch, double lr, uint64_t shuffle_seed, double* epoch_loss);
+                 int32_t batch, double lr, double lr_final, uint64_t shuffle_seed, double* epoch_loss);
 int qfs_ws_predict(qfs_ws* ws, int32_t count, const double* targets, double* gates_out);
 
 /* One FP64 sweep (as qfs_sweep_once with QFS_FP64) that allocates no

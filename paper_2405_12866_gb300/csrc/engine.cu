@@ -18,6 +18,7 @@
 #include <limits>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 namespace qfs {
@@ -1230,6 +1231,24 @@ int autotune_batch(qfs_ctx* ctx, BatchArgs a, int max_sweeps_run, int* warps_out
 
 namespace {
 
+// fn(0 .. n-1) over the host cores (at most 16 threads); the draws it runs
+// are pure functions of their index writing disjoint ranges.
+template <class F>
+void host_parallel_for(int n, F fn) {
+  const int hw = (int)std::thread::hardware_concurrency();
+  const int T = std::max(1, std::min({hw > 0 ? hw : 1, 16, n / 64}));
+  if (T <= 1) {
+    for (int i = 0; i < n; ++i) fn(i);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (int t = 0; t < T; ++t)
+    th.emplace_back([&, t]() {
+      for (int i = (int)((long long)n * t / T); i < (int)((long long)n * (t + 1) / T); ++i) fn(i);
+    });
+  for (auto& x : th) x.join();
+}
+
 int batch_common(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls, const int32_t* pairs,
                  const double* targets, const double* samples, const double* init_gates,
                  const qfs_params* p, double* gates_out, qfs_result* results, bool dev) {
@@ -1333,16 +1352,18 @@ int batch_common(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls, 
     CK(cudaMemcpyAsync(w + o_psi64, samples, sizeof(double2) * state_off, h2d, st));
   } else {
     hs.resize(state_off);
-    for (int i = 0; i < P; ++i)
+    host_parallel_for(P, [&](int i) {
       generate_samples(p->seed + (uint64_t)i, probs[i].n, probs[i].M, hs.data() + probs[i].state_off);
+    });
     CK(cudaMemcpyAsync(w + o_psi64, hs.data(), sizeof(double2) * state_off, cudaMemcpyHostToDevice, st));
   }
   if (init_gates) {
     CK(cudaMemcpyAsync(w + o_g0, init_gates, sizeof(double2) * gate_off, h2d, st));
   } else {
     hg.resize(gate_off);
-    for (int i = 0; i < P; ++i)
+    host_parallel_for(P, [&](int i) {
       generate_gates(p->seed + (uint64_t)i, S * probs[i].L, hg.data() + probs[i].gate_off);
+    });
     CK(cudaMemcpyAsync(w + o_g0, hg.data(), sizeof(double2) * gate_off, cudaMemcpyHostToDevice, st));
   }
   int warps = 4;
@@ -1427,8 +1448,10 @@ extern "C" int qfs_gemm_bf16_dev(qfs_ctx* ctx, int32_t M, int32_t N, int32_t K, 
   if (lda % 8 || ldb % 8 || lda < K || ldb < K || ldc < N)
     return fail(QFS_EINVAL, "lda, ldb >= K and multiples of 8, ldc >= N needed");
   if (!A || !B || (!C32 && !C16)) return fail(QFS_EINVAL, "A, B and an output must be given");
-  if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15)
-    return fail(QFS_EINVAL, "A and B must be 16-byte aligned");
+  if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B) | reinterpret_cast<uintptr_t>(C32) |
+       reinterpret_cast<uintptr_t>(C16) | reinterpret_cast<uintptr_t>(bias)) & 15)
+    return fail(QFS_EINVAL, "A, B, C32, C16 and bias must be 16-byte aligned");
+  if (ldc % 8) return fail(QFS_EINVAL, "ldc must be a multiple of 8");
   TRY(ctx_check(ctx));
   TRY(set_device(ctx));
   TRY(ensure_ws(ctx, 256));
@@ -1438,9 +1461,10 @@ extern "C" int qfs_gemm_bf16_dev(qfs_ctx* ctx, int32_t M, int32_t N, int32_t K, 
   GemmArgs g{reinterpret_cast<const __nv_bfloat16*>(A), lda, reinterpret_cast<const __nv_bfloat16*>(B), ldb,
              C32, reinterpret_cast<__nv_bfloat16*>(C16), ldc, bias, gelu, M, N, K,
              M_valid > 0 ? M_valid : M, err};
+  g.splitk = gemm_splitk_for(g, ctx->num_sms > 0 ? ctx->num_sms : 148);
   {
     ProfScope ps(ctx, QFS_PROF_MLP, 2.0 * M * N * K, st);
-    launch_gemm_bf16_tc(g, st);
+    CK(launch_gemm_bf16_tc(g, st));
   }
   CK(cudaGetLastError());
   int h = 0;
@@ -1506,8 +1530,9 @@ long long ws_param_count(const qfs_ws* m) {
 int ws_gemm(qfs_ws* m, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K,
             float* C32, __nv_bfloat16* C16, int ldc, const float* bias, int gelu, int M_valid) {
   GemmArgs g{A, lda, B, ldb, C32, C16, ldc, bias, gelu, M, N, K, M_valid, m->err};
+  g.splitk = gemm_splitk_for(g, m->ctx->num_sms > 0 ? m->ctx->num_sms : 148);
   ProfScope ps(m->ctx, QFS_PROF_MLP, 2.0 * M * N * K);
-  launch_gemm_bf16_tc(g, m->ctx->stream);
+  CK(launch_gemm_bf16_tc(g, m->ctx->stream));
   return QFS_OK;
 }
 
@@ -1522,8 +1547,10 @@ void ws_forward(qfs_ws* m, int B) {
   }
 }
 
-// Loss and gradients for B rows (B_valid real) with labels in m->Tlab.
-int ws_backward(qfs_ws* m, int B, int B_valid, double* loss) {
+// Loss and gradients for B rows (B_valid real) with labels in m->Tlab.  The
+// mean loss goes to *loss (host, synchronising) and/or is added to
+// *loss_acc_dev (device, asynchronous).
+int ws_backward(qfs_ws* m, int B, int B_valid, double* loss, double* loss_acc_dev = nullptr) {
   cudaStream_t st = m->ctx->stream;
   const int L = qfs_ws::kLayers;
   const int nparts = launch_ws_loss_grad(m->Z32[L - 1], m->dout[L - 1], m->Tlab, m->n_out, B, B_valid, m->dA32,
@@ -1547,6 +1574,7 @@ int ws_backward(qfs_ws* m, int B, int B_valid, double* loss) {
       g16 = o16;
     }
   }
+  if (loss_acc_dev) launch_loss_accumulate(m->loss_part, nparts, 1.0 / ((double)B_valid * m->n_out), loss_acc_dev, st);
   if (loss) {
     std::vector<double> parts(nparts);
     CK(cudaMemcpyAsync(parts.data(), m->loss_part, sizeof(double) * nparts, cudaMemcpyDeviceToHost, st));
@@ -1614,7 +1642,7 @@ extern "C" int qfs_ws_create(qfs_ctx* ctx, uint64_t seed, int32_t batch_cap, qfs
                odA32 = take((size_t)batch_cap * 1024 * 4), odB32 = take((size_t)batch_cap * 1024 * 4),
                odA16 = take((size_t)batch_cap * 1024 * 2), odB16 = take((size_t)batch_cap * 1024 * 2),
                oT1 = take((size_t)batch_cap * 1024 * 2), oT2 = take((size_t)batch_cap * 1024 * 2),
-               oT = take((size_t)batch_cap * 192 * 4), olp = take(1024 * sizeof(double)),
+               oT = take((size_t)batch_cap * 192 * 4), olp = take(1040 * sizeof(double)),
                otg = take(sizeof(double2) * 256 * (size_t)batch_cap), oenv = take(sizeof(double2) * 96 * (size_t)batch_cap),
                oerr = take(sizeof(int) * 4);
   cudaError_t e = cudaMalloc(&m->mem, off);
@@ -1729,56 +1757,106 @@ extern "C" int qfs_ws_loss_grad(qfs_ws* m, int32_t count, const double* targets,
 }
 
 extern "C" int qfs_ws_train(qfs_ws* m, int32_t count, const double* targets, const double* labels, int32_t epochs,
-                            int32_t batch, double lr, uint64_t shuffle_seed, double* epoch_loss) {
+                            int32_t batch, double lr, double lr_final, uint64_t shuffle_seed, double* epoch_loss) {
   g_err.clear();
   if (!m || !targets || !labels) return fail(QFS_EINVAL, "model, targets and labels must be given");
   if (count < 1 || epochs < 1) return fail(QFS_EINVAL, "count and epochs must be >= 1");
   if (batch < 128 || batch % 128 || batch > m->B_cap)
     return fail(QFS_EINVAL, "batch = %d: a multiple of 128 up to %d", batch, m->B_cap);
-  if (!(lr > 0.0)) return fail(QFS_EINVAL, "lr must be > 0");
+  if (!(lr > 0.0) || !(lr_final >= 0.0)) return fail(QFS_EINVAL, "lr must be > 0 and lr_final >= 0");
   TRY(set_device(m->ctx));
   cudaStream_t st = m->ctx->stream;
+  const long long steps_total = (long long)epochs * ((count + batch - 1) / batch);
+  long long step_i = 0;
+  // The whole training set stays on the device: features (bf16, count x
+  // 256) computed once, labels (fp32, count x 192), and the shuffled order.
+  __nv_bfloat16* Xall = nullptr;
+  float* Tall = nullptr;
+  int* didx = nullptr;
+  auto release = [&]() {
+    if (Xall) cudaFree(Xall);
+    if (Tall) cudaFree(Tall);
+    if (didx) cudaFree(didx);
+  };
+  if (cudaMalloc(&Xall, (size_t)count * 256 * 2) != cudaSuccess ||
+      cudaMalloc(&Tall, (size_t)count * 192 * 4) != cudaSuccess ||
+      cudaMalloc(&didx, (size_t)count * 4) != cudaSuccess) {
+    cudaGetLastError();
+    release();
+    return fail(QFS_ENOMEM, "training set of %d samples does not fit on the device", count);
+  }
+  int rc = QFS_OK;
+  {
+    std::vector<float> lb((size_t)m->B_cap * 192);
+    for (int s0 = 0; s0 < count && rc == QFS_OK; s0 += m->B_cap) {
+      const int bv = std::min(m->B_cap, count - s0);
+      if (cudaMemcpyAsync(m->tgt, targets + (size_t)s0 * 512, sizeof(double2) * 256 * (size_t)bv,
+                          cudaMemcpyHostToDevice, st) != cudaSuccess)
+        rc = fail(QFS_ECUDA, "copy of targets failed");
+      launch_ws_features(m->tgt, m->phif, bv, bv, Xall + (size_t)s0 * 256, st);
+      for (size_t i = 0; i < (size_t)bv * 192; ++i) lb[i] = (float)labels[(size_t)s0 * 192 + i];
+      if (cudaMemcpyAsync(Tall + (size_t)s0 * 192, lb.data(), sizeof(float) * 192 * (size_t)bv,
+                          cudaMemcpyHostToDevice, st) != cudaSuccess)
+        rc = fail(QFS_ECUDA, "copy of labels failed");
+      cudaStreamSynchronize(st);
+    }
+  }
   std::vector<int> idx(count);
-  std::vector<double> tb((size_t)batch * 256 * 2);
-  std::vector<float> lb((size_t)batch * 192);
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-  for (int ep = 0; ep < epochs; ++ep) {
+  for (int ep = 0; ep < epochs && rc == QFS_OK; ++ep) {
     for (int i = 0; i < count; ++i) idx[i] = i;
     // Fisher-Yates with Philox draws (deterministic per seed and epoch).
     for (int i = count - 1; i > 0; --i) {
-      const double u = 0.5 + 0.5 * std::erf(qfs_normal_re(shuffle_seed, 7u, ((uint64_t)ep << 32) + i) / std::sqrt(2.0));
+      const double u = 0.5 + 0.5 * std::erf(qfs_normal_re(shuffle_seed, 7u, ((uint64_t)ep << 32) + i) * std::sqrt(2.0));
       int j = (int)(u * (i + 1));
       if (j > i) j = i;
       std::swap(idx[i], idx[j]);
     }
-    double ep_loss = 0.0;
+    if (cudaMemcpyAsync(didx, idx.data(), sizeof(int) * count, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      rc = fail(QFS_ECUDA, "copy of the sample order failed");
+      break;
+    }
+    // The epoch's loss is summed on the device (no per-step synchronisation).
+    double* ep_acc = m->loss_part + 1032;
+    if (cudaMemsetAsync(ep_acc, 0, sizeof(double), st) != cudaSuccess) {
+      rc = fail(QFS_ECUDA, "cudaMemsetAsync failed");
+      break;
+    }
     int nb = 0;
     for (int s0 = 0; s0 < count; s0 += batch) {
       const int bv = std::min(batch, count - s0);
       const int B = (bv + 127) / 128 * 128;
-      for (int r = 0; r < bv; ++r) {
-        std::memcpy(&tb[(size_t)r * 512], targets + (size_t)idx[s0 + r] * 512, 512 * sizeof(double));
-        for (int c = 0; c < 192; ++c) lb[(size_t)r * 192 + c] = (float)labels[(size_t)idx[s0 + r] * 192 + c];
-      }
-      TRY(ws_load_features(m, tb.data(), bv, B));
-      CK(cudaMemcpyAsync(m->Tlab, lb.data(), (size_t)bv * 192 * 4, cudaMemcpyHostToDevice, st));
+      launch_ws_gather(Xall, Tall, didx + s0, bv, B, m->X16, m->Tlab, st);
       ws_forward(m, B);
-      double l = 0.0;
-      TRY(ws_backward(m, B, bv, &l));
-      ep_loss += l;
+      rc = ws_backward(m, B, bv, nullptr, ep_acc);
+      if (rc != QFS_OK) break;
       ++nb;
       ++m->step;
       const float bc1 = 1.f - std::pow(b1, (float)m->step), bc2 = 1.f - std::pow(b2, (float)m->step);
+      // Cosine decay from lr to lr_final over this call's steps.
+      const double frac = steps_total > 1 ? (double)step_i / (double)(steps_total - 1) : 0.0;
+      const float lr_t = (float)(lr_final + 0.5 * (lr - lr_final) * (1.0 + std::cos(3.141592653589793 * frac)));
+      ++step_i;
       for (int k = 0; k < qfs_ws::kLayers; ++k) {
-        launch_adam(m->W[k], m->mW[k], m->vW[k], m->gW[k], (long long)m->dout[k] * m->din[k], (float)lr, b1, b2, eps,
+        launch_adam(m->W[k], m->mW[k], m->vW[k], m->gW[k], (long long)m->dout[k] * m->din[k], lr_t, b1, b2, eps,
                     bc1, bc2, m->W16[k], st);
-        launch_adam(m->b[k], m->mb[k], m->vb[k], m->gb[k], m->dout[k], (float)lr, b1, b2, eps, bc1, bc2, nullptr, st);
+        launch_adam(m->b[k], m->mb[k], m->vb[k], m->gb[k], m->dout[k], lr_t, b1, b2, eps, bc1, bc2, nullptr, st);
         launch_transpose_bf16(m->W16[k], m->dout[k], m->din[k], m->WT16[k], st);
       }
     }
+    if (rc != QFS_OK) break;
+    double ep_loss = 0.0;
+    if (cudaMemcpyAsync(&ep_loss, ep_acc, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      rc = fail(QFS_ECUDA, "reading the epoch loss failed");
+      break;
+    }
     if (epoch_loss) epoch_loss[ep] = ep_loss / std::max(nb, 1);
   }
-  CK(cudaStreamSynchronize(st));
+  cudaStreamSynchronize(st);
+  release();
+  if (rc != QFS_OK) return rc;
+  CK(cudaGetLastError());
   return check_err_word(m);
 }
 

@@ -8,6 +8,8 @@
 #include "qfs_common.cuh"
 #include "qfs_kernels.h"
 
+#include <algorithm>
+
 namespace qfs {
 
 namespace {
@@ -35,8 +37,10 @@ __global__ void k_ws_features(const double2* __restrict__ U, const double2* __re
       im += (float)(a.x * b.y + a.y * b.x);
     }
   }
-  X[(size_t)t * 256 + 2 * k] = __float2bfloat16(re);
-  X[(size_t)t * 256 + 2 * k + 1] = __float2bfloat16(im);
+  // Scaled by sqrt(16) = 4 so that the features have unit variance per
+  // complex entry (the columns of U Phi_fix are unit vectors of length 16).
+  X[(size_t)t * 256 + 2 * k] = __float2bfloat16(4.f * re);
+  X[(size_t)t * 256 + 2 * k + 1] = __float2bfloat16(4.f * im);
 }
 
 // dst[c][r] = src[r][c] (bf16), 32 x 32 tiles; R, C multiples of 32.
@@ -94,13 +98,37 @@ __global__ void k_gelu_back(const float* __restrict__ dH, const float* __restric
   }
 }
 
-// db[c] = sum over rows of G[r][c] (fp32), one thread per column.
+// db[c] += sum over rows of G[r][c]: block (32 columns x 8 row lanes) over a
+// slice of the rows, reduced in shared memory, one atomic per column and
+// block (db is zeroed by the launcher).
 __global__ void k_colsum(const float* __restrict__ G, int rows, int cols, float* __restrict__ db) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= cols) return;
+  __shared__ float red[8][33];
+  const int c = blockIdx.x * 32 + threadIdx.x;
+  float s = 0.f;
+  if (c < cols)
+    for (int r = blockIdx.y * 8 + threadIdx.y; r < rows; r += 8 * gridDim.y) s += G[(size_t)r * cols + c];
+  red[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.y == 0 && c < cols) {
+    float t = 0.f;
+#pragma unroll
+    for (int y = 0; y < 8; ++y) t += red[y][threadIdx.x];
+    atomicAdd(db + c, t);
+  }
+}
+
+// acc += (sum of parts[0..n)) * scale (one block).
+__global__ void k_loss_accumulate(const double* __restrict__ parts, int n, double scale, double* __restrict__ acc) {
+  __shared__ double red[256];
   double s = 0.0;
-  for (int r = 0; r < rows; ++r) s += G[(size_t)r * cols + c];
-  db[c] = (float)s;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += parts[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *acc += red[0] * scale;
 }
 
 // Adam (Kingma & Ba 2015) on fp32 master parameters with a bf16 copy.
@@ -131,6 +159,22 @@ __global__ void k_ws_gates_adjoint(const float* __restrict__ Y, int ldy, int cou
   E[e] = double2{(double)row[2 * (4 * y + x)], -(double)row[2 * (4 * y + x) + 1]};
 }
 
+// Mini-batch gather: rows idx[0..bv) of the device training set into the
+// batch buffers; rows bv..B-1 of X are zeroed.
+__global__ void k_ws_gather(const __nv_bfloat16* __restrict__ Xall, const float* __restrict__ Tall,
+                            const int* __restrict__ idx, int bv, int B, __nv_bfloat16* __restrict__ X,
+                            float* __restrict__ T) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e < (long long)B * 256) {
+    const int r = (int)(e / 256), c = (int)(e % 256);
+    X[e] = r < bv ? Xall[(size_t)idx[r] * 256 + c] : __float2bfloat16(0.f);
+  }
+  if (e < (long long)bv * 192) {
+    const int r = (int)(e / 192), c = (int)(e % 192);
+    T[e] = Tall[(size_t)idx[r] * 192 + c];
+  }
+}
+
 static int blocks_for(long long n, int threads = 256, int cap = 4096) {
   long long b = (n + threads - 1) / threads;
   return (int)(b > cap ? cap : (b < 1 ? 1 : b));
@@ -144,6 +188,11 @@ void launch_ws_features(const double2* U, const double2* phif, int count, int ro
 void launch_ws_gates_adjoint(const float* Y, int ldy, int count, double2* E, cudaStream_t st) {
   const long long n = (long long)count * 96;
   k_ws_gates_adjoint<<<(int)((n + 255) / 256), 256, 0, st>>>(Y, ldy, count, E);
+}
+void launch_ws_gather(const __nv_bfloat16* Xall, const float* Tall, const int* idx, int bv, int B,
+                      __nv_bfloat16* X, float* T, cudaStream_t st) {
+  const long long n = (long long)B * 256;
+  k_ws_gather<<<(int)((n + 255) / 256), 256, 0, st>>>(Xall, Tall, idx, bv, B, X, T);
 }
 void launch_transpose_bf16(const __nv_bfloat16* src, int R, int C, __nv_bfloat16* dst, cudaStream_t st) {
   k_transpose_bf16<<<dim3(C / 32, R / 32), dim3(32, 8), 0, st>>>(src, R, C, dst);
@@ -162,7 +211,12 @@ void launch_gelu_back(const float* dH, const float* Z, long long n, int ld, int 
   k_gelu_back<<<blocks_for(n), 256, 0, st>>>(dH, Z, n, ld, B_valid, dZ32, dZ16);
 }
 void launch_colsum(const float* G, int rows, int cols, float* db, cudaStream_t st) {
-  k_colsum<<<(cols + 127) / 128, 128, 0, st>>>(G, rows, cols, db);
+  cudaMemsetAsync(db, 0, sizeof(float) * (size_t)cols, st);
+  const int ychunks = std::max(1, std::min(64, rows / 64));
+  k_colsum<<<dim3((cols + 31) / 32, ychunks), dim3(32, 8), 0, st>>>(G, rows, cols, db);
+}
+void launch_loss_accumulate(const double* parts, int n, double scale, double* acc, cudaStream_t st) {
+  k_loss_accumulate<<<1, 256, 0, st>>>(parts, n, scale, acc);
 }
 void launch_adam(float* w, float* m, float* v, const float* g, long long n, float lr, float b1, float b2, float eps,
                  float bc1, float bc2, __nv_bfloat16* w16, cudaStream_t st) {

@@ -1,9 +1,20 @@
-// BF16 GEMM on the fifth-generation tensor cores (tcgen05) for the learned
+// BF16 GEMMs on the fifth-generation tensor cores (tcgen05) for the learned
 // warm start:  C[M x N] = A[M x K] * B[N x K]^T  (+ bias[N], optional GELU),
 // A and B bf16 row-major (both K-major), accumulation in FP32 in tensor
-// memory (TMEM).
+// memory (TMEM).  Two kernels:
 //
-// One CTA of 128 threads computes a 128 x 128 tile.  Per K step of 64 the
+// k_gemm_bf16_tma (the one used): a warp-specialised pipeline.  Warp 0
+// issues TMA tile loads (128-byte swizzle) into a ring of kStages shared
+// stages, each tracked by a "full" mbarrier (transaction bytes) and an
+// "empty" mbarrier; warp 1 owns the TMEM accumulator (128 x BN fp32
+// columns) and one of its threads issues the tcgen05.mma chain, releasing
+// each stage with tcgen05.commit; warps 2-5 wait for the final commit and
+// run the epilogue (tcgen05.ld, bias, GELU, stores).  With split-K (grid z)
+// each CTA reduces a K range and adds its tile into C32 with vector atomics.
+//
+// k_gemm_bf16_simple: the first version, kept as a reference point and as
+// the path for QFS_GEMM_SIMPLE=1.  One CTA of 128 threads computes a
+// 128 x 128 tile.  Per K step of 64 the
 // threads stage the A and B tiles in shared memory in the canonical
 // no-swizzle K-major layout (8-row x 16-byte core matrices, K-adjacent core
 // matrices 128 B apart, 8-row groups 1024 B apart), one elected thread
@@ -13,7 +24,11 @@
 // accumulator with tcgen05.ld (each warp its 32 TMEM lanes = rows), applies
 // bias and GELU and stores FP32 and/or BF16.  A wait that runs out sets the
 // error word, and the CTA still frees its TMEM before returning.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+
+#include <cstdlib>
 
 #include "qfs_kernels.h"
 
@@ -63,7 +78,7 @@ __device__ __forceinline__ float gelu_tanh(float x) {
 
 }  // namespace
 
-__global__ void __launch_bounds__(128, 1) k_gemm_bf16_tc(GemmArgs g) {
+__global__ void __launch_bounds__(128, 1) k_gemm_bf16_simple(GemmArgs g) {
   __shared__ __align__(128) unsigned char sa[kTM * kTK * 2];
   __shared__ __align__(128) unsigned char sb[kTN * kTK * 2];
   __shared__ uint64_t mbar;
@@ -169,9 +184,310 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16_tc(GemmArgs g) {
   }
 }
 
-void launch_gemm_bf16_tc(const GemmArgs& g, cudaStream_t st) {
-  dim3 grid(g.N / kTN, g.M / kTM);
-  k_gemm_bf16_tc<<<grid, 128, 0, st>>>(g);
+// ------------------------------------------------------------ TMA pipeline
+
+namespace {
+
+constexpr int kBM = 128, kBK = 64, kStages = 4, kTmaThreads = 192;
+
+template <int BN>
+struct TmaCfg {
+  static constexpr int kABytes = kBM * kBK * 2;
+  static constexpr int kBBytes = BN * kBK * 2;
+  static constexpr int kStageBytes = kABytes + kBBytes;
+  static constexpr int kSmem = kStages * kStageBytes + 1024 + 256;
+  static constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                     ((uint32_t)(kBM >> 4) << 24);
+};
+
+// K-major operand with the 128-byte swizzle: rows of 64 bf16 (128 B), 8-row
+// groups 1024 B apart (stride byte offset); the leading byte offset is not
+// used by swizzled K-major layouts.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+__device__ __forceinline__ void mbar_init1(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], "
+      "[%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(su32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+}  // namespace
+
+template <int BN>
+__global__ void __launch_bounds__(kTmaThreads, 1)
+    k_gemm_bf16_tma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, GemmArgs g) {
+  using Cfg = TmaCfg<BN>;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const uint32_t raw = su32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char* sb = smem_raw + (base - raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sb + kStages * Cfg::kStageBytes);
+  uint64_t* empty = full + kStages;
+  uint64_t* accf = empty + kStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accf + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
+  const int KT = g.K / kBK;
+  const int splitk = gridDim.z;
+  const int kb = (int)((long long)blockIdx.z * KT / splitk), ke = (int)((long long)(blockIdx.z + 1) * KT / splitk);
+  const int nk = ke - kb;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init1(&full[s]);
+      mbar_init1(&empty[s]);
+    }
+    mbar_init1(accf);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapB)) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                 "r"(BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // Producer: one thread issues the TMA loads of both operands per stage.
+    if (lane == 0) {
+      int issued = 0;
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % kStages;
+        const unsigned ph = (unsigned)(i / kStages) & 1u;
+        if (!mbar_wait_bounded(&empty[s], ph ^ 1u) || *abort_flag) {
+          *abort_flag = 1;
+          break;
+        }
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&full[s])),
+                     "r"(Cfg::kStageBytes)
+                     : "memory");
+        const uint32_t dst = base + (uint32_t)(s * Cfg::kStageBytes);
+        tma_load_2d(dst, &mapA, &full[s], (kb + i) * kBK, m0);
+        tma_load_2d(dst + Cfg::kABytes, &mapB, &full[s], (kb + i) * kBK, n0);
+        ++issued;
+      }
+      if (*abort_flag) {
+        // Wait (bounded) for every copy this CTA issued before leaving.
+        for (int i = 0; i < issued; ++i) mbar_wait_bounded(&full[i % kStages], (unsigned)(i / kStages) & 1u);
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // MMA issuer.
+    if (lane == 0) {
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % kStages;
+        const unsigned ph = (unsigned)(i / kStages) & 1u;
+        if (!mbar_wait_bounded(&full[s], ph) || *abort_flag) {
+          *abort_flag = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a0 = base + (uint32_t)(s * Cfg::kStageBytes), b0 = a0 + Cfg::kABytes;
+#pragma unroll
+        for (int kk = 0; kk < kBK / 16; ++kk) {
+          const uint64_t ad = desc_sw128(a0 + kk * 32), bd = desc_sw128(b0 + kk * 32);
+          const uint32_t acc = (i > 0 || kk > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+              "l"(ad), "l"(bd), "r"(Cfg::kIdesc), "r"(acc)
+              : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         su32(&empty[s]))
+                     : "memory");
+      }
+      // Arrives once every MMA issued above has completed.
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(accf))
+                   : "memory");
+    }
+    __syncwarp();
+  } else {
+    // Epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows of the tile).
+    const int q = warp & 3;
+    const int row = m0 + q * 32 + lane;
+    const bool ok = mbar_wait_bounded(accf, 0) && !*abort_flag;
+    if (!ok) {
+      *abort_flag = 1;
+    } else {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int cb = 0; cb < BN; cb += 32) {
+        uint32_t v[32];
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)cb;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+            "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+              "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+              "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+              "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            : "r"(taddr)
+            : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (row >= g.M_valid) continue;
+        float x[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) x[j] = __uint_as_float(v[j]);
+        const int col = n0 + cb;
+        if (splitk > 1) {
+          float4* dst = reinterpret_cast<float4*>(g.C32 + (size_t)row * g.ldc + col);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) atomicAdd(dst + j, make_float4(x[4 * j], x[4 * j + 1], x[4 * j + 2], x[4 * j + 3]));
+          continue;
+        }
+        if (g.bias) {
+          const float4* bp = reinterpret_cast<const float4*>(g.bias + col);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const float4 b4 = bp[j];
+            x[4 * j] += b4.x;
+            x[4 * j + 1] += b4.y;
+            x[4 * j + 2] += b4.z;
+            x[4 * j + 3] += b4.w;
+          }
+        }
+        if (g.C32) {
+          float4* dst = reinterpret_cast<float4*>(g.C32 + (size_t)row * g.ldc + col);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) dst[j] = make_float4(x[4 * j], x[4 * j + 1], x[4 * j + 2], x[4 * j + 3]);
+        }
+        if (g.C16) {
+          uint4* dst = reinterpret_cast<uint4*>(g.C16 + (size_t)row * g.ldc + col);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            uint32_t w[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              float a = x[8 * j + 2 * h], b = x[8 * j + 2 * h + 1];
+              if (g.gelu) {
+                a = gelu_tanh(a);
+                b = gelu_tanh(b);
+              }
+              const __nv_bfloat162 p = __floats2bfloat162_rn(a, b);
+              w[h] = *reinterpret_cast<const uint32_t*>(&p);
+            }
+            dst[j] = make_uint4(w[0], w[1], w[2], w[3]);
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x == 0 && *abort_flag) atomicOr(g.err, 1);
+  if (warp == 1) {
+    // After a give-up, let the MMAs already issued finish (bounded) before
+    // the accumulator is released.
+    if (lane == 0 && *abort_flag) mbar_wait_bounded(accf, 0);
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+  }
+}
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+
+// Row-major bf16 matrix (rows x K, leading dimension ld) as TMA tiles of
+// box_rows x 64 with the 128-byte swizzle.
+bool encode_kmajor(CUtensorMap* map, const void* ptr, int rows, int K, int ld, int box_rows) {
+  auto fn = tensor_map_encoder();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN>
+cudaError_t launch_tma(const GemmArgs& g, int splitk, cudaStream_t st) {
+  static const cudaError_t attr = cudaFuncSetAttribute(k_gemm_bf16_tma<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       TmaCfg<BN>::kSmem);
+  if (attr != cudaSuccess) return attr;
+  CUtensorMap ma, mb;
+  if (!encode_kmajor(&ma, g.A, g.M, g.K, g.lda, kBM) || !encode_kmajor(&mb, g.B, g.N, g.K, g.ldb, BN))
+    return cudaErrorInvalidValue;
+  dim3 grid(g.N / BN, g.M / kBM, splitk);
+  k_gemm_bf16_tma<BN><<<grid, kTmaThreads, TmaCfg<BN>::kSmem, st>>>(ma, mb, g);
+  return cudaGetLastError();
+}
+
+bool gemm_simple_requested() {
+  static const bool v = [] {
+    const char* e = std::getenv("QFS_GEMM_SIMPLE");
+    return e && e[0] == '1';
+  }();
+  return v;
+}
+
+}  // namespace
+
+int gemm_splitk_for(const GemmArgs& g, int num_sms) {
+  if (g.C16 || g.bias || g.gelu || !g.C32) return 1;
+  const int BN = g.N % 256 == 0 ? 256 : 128;
+  const int tiles = (g.N / BN) * (g.M / kBM);
+  const int KT = g.K / kBK;
+  int s = 1;
+  while (tiles * s * 2 <= num_sms && KT / (s * 2) >= 4) s *= 2;
+  return s;
+}
+
+cudaError_t launch_gemm_bf16_tc(const GemmArgs& g, cudaStream_t st) {
+  if (gemm_simple_requested()) {
+    dim3 grid(g.N / kTN, g.M / kTM);
+    k_gemm_bf16_simple<<<grid, 128, 0, st>>>(g);
+    return cudaGetLastError();
+  }
+  const int splitk = g.splitk > 1 ? g.splitk : 1;
+  if (splitk > 1) {
+    // The split CTAs add into C32, which starts from zero.
+    const cudaError_t e = cudaMemset2DAsync(g.C32, (size_t)g.ldc * 4, 0, (size_t)g.N * 4, g.M_valid, st);
+    if (e != cudaSuccess) return e;
+  }
+  return g.N % 256 == 0 ? launch_tma<256>(g, splitk, st) : launch_tma<128>(g, splitk, st);
 }
 
 }  // namespace qfs

@@ -209,13 +209,19 @@ struct GemmArgs {
   int gelu;
   int M, N, K, M_valid;
   int* err;
+  int splitk = 1;  // > 1: K split over grid z, partial tiles added into C32 (C32 only)
 };
-void launch_gemm_bf16_tc(const GemmArgs& g, cudaStream_t st);
+cudaError_t launch_gemm_bf16_tc(const GemmArgs& g, cudaStream_t st);
+// Split-K factor that fills the GPU for a C32-only product (1 otherwise).
+int gemm_splitk_for(const GemmArgs& g, int num_sms);
 
 void launch_ws_features(const double2* U, const double2* phif, int count, int rows, __nv_bfloat16* X,
                         cudaStream_t st);
 void launch_transpose_bf16(const __nv_bfloat16* src, int R, int C, __nv_bfloat16* dst, cudaStream_t st);
 void launch_ws_gates_adjoint(const float* Y, int ldy, int count, double2* E, cudaStream_t st);
+void launch_loss_accumulate(const double* parts, int n, double scale, double* acc, cudaStream_t st);
+void launch_ws_gather(const __nv_bfloat16* Xall, const float* Tall, const int* idx, int bv, int B,
+                      __nv_bfloat16* X, float* T, cudaStream_t st);
 void launch_cast_f32_bf16(const float* a, __nv_bfloat16* b, long long n, cudaStream_t st);
 // Returns the number of loss partial sums written.
 int launch_ws_loss_grad(const float* Y, int ldy, const float* T, int n_out, int rows, int B_valid, float* dY32,

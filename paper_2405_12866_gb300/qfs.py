@@ -105,7 +105,7 @@ def lib():
     L.qfs_ws_destroy.restype = None
     L.qfs_ws_params.argtypes = [_P, _P, _P, C.POINTER(C.c_int64)]
     L.qfs_ws_loss_grad.argtypes = [_P, C.c_int32, _P, _P, C.POINTER(C.c_double), _P]
-    L.qfs_ws_train.argtypes = [_P, C.c_int32, _P, _P, C.c_int32, C.c_int32, C.c_double, C.c_uint64, _P]
+    L.qfs_ws_train.argtypes = [_P, C.c_int32, _P, _P, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_uint64, _P]
     L.qfs_ws_predict.argtypes = [_P, C.c_int32, _P, _P]
     L.qfs_sweep_once_noalloc.argtypes = [_P, C.POINTER(Circuit), _P, _P, C.c_int32, C.c_int32,
                                          C.c_double, _P, _P, _P, _P]
@@ -135,6 +135,18 @@ def _host_c128(a, shape=None) -> np.ndarray:
     if shape is not None and a.size != int(np.prod(shape)):
         raise ValueError(f"expected {int(np.prod(shape))} complex values, got {a.size}")
     return a
+
+
+def _wait_torch(*tensors):
+    """The library runs on its own stream: finish the work torch queued on
+    its current stream (which may still be writing these tensors, or reading
+    memory the caching allocator hands out next) before the call."""
+    import torch
+    seen = set()
+    for t in tensors:
+        if t is not None and t.is_cuda and t.device not in seen:
+            seen.add(t.device)
+            torch.cuda.current_stream(t.device).synchronize()
 
 
 class _CircuitArg:
@@ -229,6 +241,7 @@ class Context:
                 raise ValueError(f"{name} must be a contiguous complex128 CUDA tensor")
         res = Result()
         costs = np.zeros(params.multistarts, dtype=np.float64)
+        _wait_torch(target, samples, init_gates, out)
         _check(lib().qfs_instantiate_dev(self._h, C.byref(cir.c), target.data_ptr(), samples.data_ptr(),
                                          init_gates.data_ptr(), C.byref(params), out.data_ptr(),
                                          C.byref(res), costs.ctypes.data))
@@ -280,6 +293,28 @@ class Context:
                      fp64_sweeps=r.fp64_sweeps) for r in res]
         return gates, info
 
+    def instantiate_batch_uniform(self, n, pairs, targets, params: Params, init_gates=None):
+        """P problems of one structure: targets (P, N, N), init_gates (P, S, L, 4, 4)
+        or None (drawn from params.seed + index), samples drawn from params.seed +
+        index.  Returns (gates (P, L, 4, 4), cost, sweeps, converged, best_start)."""
+        t = _host_c128(targets)
+        P = t.shape[0]
+        L = len(pairs)
+        ns = np.full(P, n, dtype=np.int32)
+        Ls = np.full(P, L, dtype=np.int32)
+        pr = np.ascontiguousarray(np.tile(np.asarray(pairs, dtype=np.int32).reshape(-1), P))
+        ig = None if init_gates is None else _host_c128(init_gates)
+        if ig is not None and ig.size != P * params.multistarts * L * 16:
+            raise ValueError("init_gates must hold P x multistarts x L gates")
+        out = np.zeros((P, L, 4, 4), dtype=np.complex128)
+        res = (Result * P)()
+        _check(lib().qfs_instantiate_batch(self._h, P, ns.ctypes.data, Ls.ctypes.data, pr.ctypes.data,
+                                           t.ctypes.data, None, ig.ctypes.data if ig is not None else None,
+                                           C.byref(params), out.ctypes.data, res))
+        r = np.frombuffer(res, dtype=np.dtype([("cost", "f8"), ("sweeps", "i4"), ("converged", "i4"),
+                                                ("best_start", "i4"), ("fp64_sweeps", "i4")]), count=P)
+        return out, r["cost"].copy(), r["sweeps"].copy(), r["converged"].astype(bool), r["best_start"].copy()
+
     def instantiate_batch_dev(self, ns, Ls, pairs, targets, samples, init_gates, params: Params, out):
         """Packed device tensors (torch complex128): targets, samples, init_gates, out;
         ns, Ls, pairs host int32 arrays.  Returns the list of per-problem result dicts."""
@@ -288,6 +323,7 @@ class Context:
         pairs = np.ascontiguousarray(pairs, dtype=np.int32)
         P = len(ns)
         res = (Result * P)()
+        _wait_torch(targets, samples, init_gates, out)
         _check(lib().qfs_instantiate_batch_dev(self._h, P, ns.ctypes.data, Ls.ctypes.data, pairs.ctypes.data,
                                                targets.data_ptr(), samples.data_ptr(), init_gates.data_ptr(),
                                                C.byref(params), out.data_ptr(), res))
@@ -301,6 +337,7 @@ class Context:
         N = B.shape[0]
         C32 = torch.empty((M, N), dtype=torch.float32, device=A.device) if want_f32 else None
         C16 = torch.empty((M, N), dtype=torch.bfloat16, device=A.device) if want_bf16 else None
+        _wait_torch(A, B, C32, C16, bias)
         _check(lib().qfs_gemm_bf16_dev(self._h, M, N, K, A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0),
                                        C32.data_ptr() if C32 is not None else None,
                                        C16.data_ptr() if C16 is not None else None, N,
@@ -384,13 +421,13 @@ class WarmStart:
         _check(lib().qfs_ws_loss_grad(self._h, count, t.ctypes.data, lab.ctypes.data, C.byref(loss), g.ctypes.data))
         return loss.value, g
 
-    def train(self, targets, labels, epochs=1, batch=4096, lr=1e-3, seed=0):
+    def train(self, targets, labels, epochs=1, batch=4096, lr=1e-3, seed=0, lr_final=None):
         t = _host_c128(targets)
         lab = np.ascontiguousarray(labels, dtype=np.float64)
         count = t.size // 256
         losses = np.zeros(epochs)
-        _check(lib().qfs_ws_train(self._h, count, t.ctypes.data, lab.ctypes.data, epochs, batch, lr, seed,
-                                  losses.ctypes.data))
+        _check(lib().qfs_ws_train(self._h, count, t.ctypes.data, lab.ctypes.data, epochs, batch, lr,
+                                  lr if lr_final is None else lr_final, seed, losses.ctypes.data))
         return losses
 
     def predict(self, targets):

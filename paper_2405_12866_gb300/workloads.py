@@ -65,13 +65,19 @@ def philox4x32_10(ctr: np.ndarray, key) -> np.ndarray:
 
 
 def _blocks(seed: int, stream: int, first: int, count: int) -> np.ndarray:
-    idx = np.arange(first, first + count, dtype=np.uint64)
-    ctr = np.zeros((count, 4), dtype=np.uint32)
-    ctr[:, 0] = (idx & _MASK32).astype(np.uint32)
-    ctr[:, 1] = (idx >> np.uint64(32)).astype(np.uint32)
-    ctr[:, 2] = np.uint32(stream)
     seed = int(seed) & 0xFFFFFFFFFFFFFFFF
-    return philox4x32_10(ctr, (seed & 0xFFFFFFFF, seed >> 32))
+    key = (seed & 0xFFFFFFFF, seed >> 32)
+    out = np.empty((count, 4), dtype=np.uint32)
+    step = 1 << 15   # cache-sized pieces; the values do not depend on it
+    for c0 in range(0, count, step):
+        c1 = min(count, c0 + step)
+        idx = np.arange(first + c0, first + c1, dtype=np.uint64)
+        ctr = np.zeros((c1 - c0, 4), dtype=np.uint32)
+        ctr[:, 0] = (idx & _MASK32).astype(np.uint32)
+        ctr[:, 1] = (idx >> np.uint64(32)).astype(np.uint32)
+        ctr[:, 2] = np.uint32(stream)
+        out[c0:c1] = philox4x32_10(ctr, key)
+    return out
 
 
 def _u53(hi: np.ndarray, lo: np.ndarray) -> np.ndarray:
@@ -168,6 +174,29 @@ def embed_apply(gate: np.ndarray, pair, n: int, X: np.ndarray) -> np.ndarray:
     return np.ascontiguousarray(np.moveaxis(T, (0, 1), (a, b))).reshape(1 << n, K)
 
 
+def target_unitaries(gates: np.ndarray, pairs, n: int) -> np.ndarray:
+    """Stack of targets for gates of shape (B, L, 4, 4): (B, N, N), each the
+    product of its embedded gates (the vectorised form of target_unitary)."""
+    B = gates.shape[0]
+    N = 1 << n
+    U = np.broadcast_to(np.eye(N, dtype=np.complex128), (B, N, N)).copy()
+    for k, (a, b) in enumerate(pairs):
+        T = U.reshape((B,) + (2,) * n + (N,))
+        T = np.moveaxis(T, (1 + a, 1 + b), (1, 2))
+        shp = T.shape
+        T = np.matmul(gates[:, k], T.reshape(B, 4, -1)).reshape(shp)
+        U = np.ascontiguousarray(np.moveaxis(T, (1, 2), (1 + a, 1 + b))).reshape(B, N, N)
+    return U
+
+
+def haar_gates_batched(seed: int, stream: int, count: int, first_gate: int = 0) -> np.ndarray:
+    """Same draws as haar_gates (gate i from counters 16 i .. 16 i + 15), QR batched."""
+    z = complex_normals(seed, stream, 16 * first_gate, 16 * count).reshape(count, 4, 4)
+    q, r = np.linalg.qr(z)
+    d = np.diagonal(r, axis1=1, axis2=2)
+    return q * (d / np.abs(d))[:, None, :]
+
+
 def target_unitary(gates: np.ndarray, pairs, n: int) -> np.ndarray:
     """U = g_L ... g_1 as a dense N x N complex128 matrix."""
     U = np.eye(1 << n, dtype=np.complex128)
@@ -247,3 +276,13 @@ def uneven_blocks(P: int = 4096, seed: int = 4, S: int = 8, max_sweeps: int = 50
         probs.append(make_problem(f"uneven_{p}", n, pairs, 1 << (n - 1), S,
                                   tseed, tseed + (1 << 40), 1e-8, max_sweeps))
     return probs
+
+
+# ------------------------------------------------------------ learned form
+
+def learned_targets(seed: int, first: int, count: int) -> np.ndarray:
+    """Targets (count, 16, 16) of problems first .. first+count-1: each the
+    product of 6 Haar U(4) gates on LEARNED_PAIRS (4 qubits)."""
+    L = len(LEARNED_PAIRS)
+    g = haar_gates_batched(seed, STREAM_TARGET_GATES, count * L, first * L).reshape(count, L, 4, 4)
+    return target_unitaries(g, LEARNED_PAIRS, 4)

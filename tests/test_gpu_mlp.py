@@ -40,6 +40,33 @@ def test_gemm_bf16_matches_reference(ctx, M, N, K):
     assert np.max(np.abs(C16.cpu().double().numpy() - gelu)) < 1e-2 * max(1.0, np.max(np.abs(gelu)))
 
 
+@pytest.mark.parametrize("M,N,K", [(128, 256, 4096), (256, 128, 2048), (1024, 1024, 512)])
+def test_gemm_bf16_fp32_only_split_k(ctx, M, N, K):
+    """C32-only products (the weight gradients) take the split-K path when
+    their tiles alone would leave SMs idle."""
+    import torch
+    rng = np.random.default_rng(7 * M + N + K)
+    A = _bf16(rng.standard_normal((M, K)))
+    B = _bf16(rng.standard_normal((N, K)))
+    dev = torch.device("cuda:0")
+    C32, _ = ctx.gemm_bf16(A.to(dev), B.to(dev))
+    ref = A.double().numpy() @ B.double().numpy().T
+    got = C32.cpu().double().numpy()
+    assert np.max(np.abs(got - ref)) < 2e-4 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_gemm_bf16_m_valid_rows(ctx):
+    import torch
+    rng = np.random.default_rng(11)
+    A = _bf16(rng.standard_normal((256, 128)))
+    B = _bf16(rng.standard_normal((256, 128)))
+    dev = torch.device("cuda:0")
+    C32, _ = ctx.gemm_bf16(A.to(dev), B.to(dev), M_valid=200)
+    ref = A.double().numpy() @ B.double().numpy().T
+    got = C32.cpu().double().numpy()
+    assert np.max(np.abs(got[:200] - ref[:200])) < 1e-4 * max(1.0, np.max(np.abs(ref)))
+
+
 def _learned_targets(count, seed):
     from paper_2405_12866_gb300 import workloads as w
     gs = w.haar_gates(seed, w.STREAM_TARGET_GATES, 6 * count).reshape(count, 6, 4, 4)
@@ -58,7 +85,7 @@ def test_warm_start_gradients_match_oracle(ctx):
     loss, g = model.loss_grad(U, labels)
     params = qfs.WarmStart.unflatten(model.get_params().astype(np.float64))
     phif = w.sample_states(seed ^ 0x5EEDF1C5, 4, 8)
-    F = np.einsum("tij,jk->tik", U, phif)
+    F = 4.0 * np.einsum("tij,jk->tik", U, phif)
     X = np.stack([F.real, F.imag], axis=-1).reshape(200, 256)
     want_loss, want = mo.loss_and_grads(params, X, labels, 192, round_bf16=True)
     assert abs(loss - want_loss) < 1e-3 * want_loss
