@@ -125,11 +125,25 @@ int qfs_device_sms(const qfs_ctx* ctx);
 #define QFS_PROF_OTHER 6    /* casts, input checks, finishing reductions */
 #define QFS_PROF_BATCH 7    /* persistent batched sweep kernel */
 #define QFS_PROF_MLP 8      /* tensor-core GEMMs of the learned warm start (FLOPs) */
-#define QFS_PROF_KINDS 9
+#define QFS_PROF_DATAFLOW 9 /* one whole sweep of all starts as one persistent launch */
+#define QFS_PROF_KINDS 10
 int qfs_profile_enable(qfs_ctx* ctx, int enable);
 int qfs_profile_reset(qfs_ctx* ctx);
 int qfs_profile_read(qfs_ctx* ctx, int32_t kind, int64_t* launches, int64_t* timed,
                      double* total_ms, double* total_bytes);
+
+/* Step time stamps of the dataflow sweep (a measurement aid; the paper has
+ * no counterpart).  qfs_dataflow_trace_enable allocates room for `capacity`
+ * stamps on the device (0 frees it and turns tracing off); while enabled,
+ * every dataflow sweep whose steps x multistarts x 4 stamps fit records, per
+ * (step, start), the device global timer (ns) when its first chunk started,
+ * when its last chunk finished, when the environment partials were summed
+ * (gate updates only; 0 otherwise) and when the step was published.
+ * qfs_dataflow_trace_read copies the stamps of the last traced sweep, laid
+ * out [step][start][4], to out (host, capacity entries; may be NULL to query
+ * *steps and *S only). */
+int qfs_dataflow_trace_enable(qfs_ctx* ctx, int64_t capacity);
+int qfs_dataflow_trace_read(qfs_ctx* ctx, uint64_t* out, int64_t capacity, int32_t* steps, int32_t* S);
 
 /* The method's own random draws (host only, no GPU): the M training states
  * (Section 3 and Appendix A: columns of a Haar-random unitary, here the Q

@@ -92,6 +92,12 @@ struct qfs_ctx {
   cudaStream_t cap_stream = nullptr;  // stream used only to capture sweep graphs
   bool fuse_update = true;  // gate update inside the backward launch (QFS_FUSE_UPDATE=0: separate)
   bool tma = false;         // shared-memory-staged backward steps (QFS_TMA=1); register kernels by default
+  bool dataflow = true;     // whole sweeps as one cooperative persistent launch (QFS_DATAFLOW=0: per-step launches)
+  unsigned long long* df_trace = nullptr;  // device buffer for step time stamps (qfs_dataflow_trace_*)
+  size_t df_trace_n = 0;
+  int df_trace_steps = 0, df_trace_S = 0;  // shape of the last traced sweep
+  double df_item_bytes = 256.0 * 1024.0;   // largest streaming bytes of one dataflow work item (QFS_DF_ITEM_KB)
+  int coop = 0;             // device supports cooperative launches
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -221,6 +227,18 @@ struct Run {
   double* cost64r = nullptr;
   int stream_b = 0;
   int stream_b64 = 0;
+  // Dataflow sweep: step table (device), control words, partial sums.
+  DfStep* df_steps = nullptr;
+  unsigned* df_ctrl = nullptr;
+  double* df_partials = nullptr;
+  double* df_resid = nullptr;
+  int df_cap = 0;           // steps the table holds
+  int df_max_nchunk = 0;    // largest chunks per start of any step
+  int df_nsteps = 0;
+  long long df_items = 0;
+  double df_bytes = 0.0;    // algorithmic bytes of one dataflow sweep (all starts)
+  const void* df_key[4] = {};  // what the uploaded table was built for
+  int df_key_r = -1;
 };
 
 size_t elem_bytes(Real r) { return r == R32 ? sizeof(float2) : sizeof(double2); }
@@ -258,6 +276,13 @@ size_t carve(Run& R, char* base, bool need_U, bool need_envs) {
   R.flag = (int*)take(sizeof(int) * 4);
   R.err = R.flag ? R.flag + 1 : nullptr;
   R.envs = need_envs ? (double2*)take((size_t)R.S * R.L * 16 * sizeof(double2)) : nullptr;
+  R.df_steps = (DfStep*)take((size_t)std::max(R.df_cap, 1) * sizeof(DfStep));
+  R.df_ctrl = (unsigned*)take(sizeof(unsigned) * (1 + ((size_t)R.df_cap + 1) * R.S));
+  R.df_partials = (double*)take(sizeof(double) * 32 * (size_t)R.S * std::max(R.df_max_nchunk, 1));
+  // The residual pass keeps its double partials apart: in complex64 the
+  // environment partials are floats, and one start's residual slots would
+  // overlap another start's environment slots while that start still sweeps.
+  R.df_resid = (double*)take(sizeof(double) * 32 * (size_t)R.S * std::max(R.df_max_nchunk, 1));
   if (R.prec == QFS_MIXED) {
     R.B64r = (double2*)take((size_t)std::max(R.L - 1, 2) * state64);
     R.phi64r = (double2*)take(state64);
@@ -324,6 +349,121 @@ int ensure_pinned(qfs_ctx* ctx, size_t n) {
   return QFS_OK;
 }
 
+// ---------------------------------------------------------------- dataflow
+
+// Whether one sweep in precision r can run as a single dataflow launch.
+bool df_usable(const qfs_ctx* ctx, const Run& R, Real r) {
+  return ctx->dataflow && ctx->coop && (r == R64 || R.M % 2 == 0) && df_blocks_per_sm(r) > 0;
+}
+
+// The step table of one sweep (the same steps, in the same order, as
+// sweep()), chunked so that each step offers about two items per resident
+// CTA.  With null buffers in R it only sizes the table.
+void df_build(const qfs_ctx* ctx, const Run& R, Real r, const void* psi, const void* phil, double2* envs,
+              const int* active, double2* vprev, std::vector<DfStep>& steps, double* bytes) {
+  steps.clear();
+  *bytes = 0.0;
+  const size_t es = elem_bytes(r);
+  const int vec = r == R32 ? 2 : 1;
+  const long long sN = R.sN;
+  const int L = R.L, S = R.S, n = R.n, M = R.M;
+  const long long gstride = (long long)L * 16;
+  const char* gT = r == R32 ? reinterpret_cast<const char*>(R.g32) : reinterpret_cast<const char*>(R.g64);
+  auto gate_ptr = [&](int idx) -> const void* { return gT ? gT + (size_t)idx * 16 * es : nullptr; };
+  auto B_ptr = [&](int k) -> void* {
+    return R.B ? (void*)((char*)R.B + (size_t)(k - 1) * S * sN * es) : nullptr;
+  };
+  const double resident = (double)std::max(1, df_blocks_per_sm(r)) * std::max(1, ctx->num_sms);
+  auto chunk_it = [&](DfStep& st, double bytes_per_unit) {
+    const double step_bytes = bytes_per_unit * st.units * S;
+    const double target = std::min(ctx->df_item_bytes, std::max(16.0 * 1024.0, step_bytes / (2.0 * resident)));
+    df_chunking(st, bytes_per_unit, target);
+    *bytes += step_bytes;
+  };
+  for (int k = 1; k <= L - 1; ++k) {
+    DfStep st{};
+    st.kind = DF_FWD;
+    st.fg = make_geom(n, M, R.pairs[2 * (k - 1)], R.pairs[2 * (k - 1) + 1]);
+    st.in = k == 1 ? psi : B_ptr(k - 1);
+    st.in_stride = k == 1 ? 0 : sN;
+    st.out = B_ptr(k);
+    st.gate = gate_ptr(k - 1);
+    st.gate_stride = gstride;
+    st.units = (1 << (n - 2)) * (M / vec);
+    chunk_it(st, 4.0 * vec * es * 2.0);
+    steps.push_back(st);
+  }
+  for (int k = L; k >= 1; --k) {
+    DfStep st{};
+    const int qa = R.pairs[2 * (k - 1)], qb = R.pairs[2 * (k - 1) + 1];
+    int ua = qa, ub = qb;
+    st.in = k == 1 ? psi : B_ptr(k - 1);
+    st.in_stride = k == 1 ? 0 : sN;
+    if (k == L) {
+      st.phi_in = phil;
+      st.phi_in_stride = 0;
+      st.phi_out = nullptr;
+      st.gate = nullptr;
+    } else {
+      st.phi_in = k == L - 1 ? phil : R.phi;
+      st.phi_in_stride = k == L - 1 ? 0 : sN;
+      st.phi_out = R.phi;
+      st.gate = gate_ptr(k);
+      ua = R.pairs[2 * k];
+      ub = R.pairs[2 * k + 1];
+    }
+    st.gate_stride = gstride;
+    st.bg = make_bwd_geom(n, M, ua, ub, qa, qb);
+    const int U = st.bg.U, ea = st.bg.ea, eb = st.bg.eb;
+    int v = vec;
+    if (U == 4) st.kind = DF_BWD4;
+    else if (U == 2) st.kind = ea == 1 ? DF_BWD2_10 : DF_BWD2_01;
+    else {
+      v = 1;
+      st.kind = ea == 2 ? DF_BWD3_20 : eb == 2 ? DF_BWD3_02 : ea == 1 ? DF_BWD3_10 : DF_BWD3_01;
+    }
+    st.units = (1 << (n - U)) * (M / v);
+    // Phi_k is stored by every backward step but the first (k = L).
+    chunk_it(st, (double)(1 << U) * v * es * (k < L ? 3.0 : 2.0));
+    UpdateArgs& u = st.upd;
+    u.partials = R.df_partials;
+    u.nblk = st.nchunk;
+    u.partials_f32 = r == R32;
+    u.g64 = R.g64 ? R.g64 + (size_t)(k - 1) * 16 : nullptr;
+    u.g_stride = gstride;
+    u.g32 = R.g32 ? R.g32 + (size_t)(k - 1) * 16 : nullptr;
+    u.beta = R.beta;
+    u.cost_out = (k == 1 && r == R64) ? R.costs : nullptr;
+    u.inv_M = 1.0 / M;
+    u.env_out = envs ? envs + (size_t)(k - 1) * 16 : nullptr;
+    u.env_stride = gstride;
+    u.S = S;
+    u.active = active;
+    u.vprev = vprev ? vprev + (size_t)(k - 1) * 16 : nullptr;
+    steps.push_back(st);
+  }
+  if (r == R32) {
+    DfStep st{};
+    st.kind = DF_RESID;
+    st.in = psi;
+    st.in_stride = 0;
+    st.phi_in = L == 1 ? phil : R.phi;
+    st.phi_in_stride = L == 1 ? 0 : sN;
+    st.phi_out = nullptr;
+    st.gate = gate_ptr(0);
+    st.gate_stride = gstride;
+    st.bg = make_bwd_geom(n, M, R.pairs[0], R.pairs[1], R.pairs[0], R.pairs[1]);
+    st.units = (1 << (n - 2)) * (M / vec);
+    chunk_it(st, 4.0 * vec * es * 2.0);
+    steps.push_back(st);
+  }
+  long long item = 0;
+  for (DfStep& st : steps) {
+    st.item0 = item;
+    item += (long long)S * st.nchunk;
+  }
+}
+
 int prepare(qfs_ctx* ctx, Run& R, const qfs_circuit* c, int M, int S, int prec, double beta,
             bool need_U, bool need_envs, int groups = 1) {
   R.n = c->n;
@@ -347,6 +487,19 @@ int prepare(qfs_ctx* ctx, Run& R, const qfs_circuit* c, int M, int S, int prec, 
     R.nblk_max = std::max(R.nblk_max, make_tma_shape(R.n, M, shape_starts(S), rs, ctx->num_sms, U).nblk);
     R.nblk64_max = std::max(R.nblk64_max, make_bwd_shape(R.n, M, 1, R64, ctx->num_sms, U).nblk);
     R.nblk64_max = std::max(R.nblk64_max, make_tma_shape(R.n, M, 1, R64, ctx->num_sms, U).nblk);
+  }
+  R.df_cap = 0;
+  R.df_max_nchunk = 0;
+  R.df_key_r = -1;
+  {
+    const Real rs = prec == QFS_MIXED ? R32 : R64;
+    if (df_usable(ctx, R, rs)) {
+      std::vector<DfStep> steps;
+      double b = 0.0;
+      df_build(ctx, R, rs, nullptr, nullptr, nullptr, nullptr, nullptr, steps, &b);
+      R.df_cap = (int)steps.size();
+      for (const DfStep& st : steps) R.df_max_nchunk = std::max(R.df_max_nchunk, st.nchunk);
+    }
   }
   const size_t bytes = carve(R, nullptr, need_U, need_envs);
   TRY(ensure_ws(ctx, bytes));
@@ -520,6 +673,54 @@ void sweep(qfs_ctx* ctx, Run& R, Real r, const Slice& sl, double2* g64, float2* 
   }
 }
 
+// One sweep of all starts of R as one dataflow launch (same results as
+// sweep() up to the order of the reduction sums).  The step table is built
+// and uploaded once per (precision, outputs) and reused by later sweeps.
+int df_sweep(qfs_ctx* ctx, Run& R, Real r, const void* psi, const void* phil, double2* envs, const int* active,
+             double2* vprev, cudaStream_t st) {
+  const void* key[4] = {psi, envs, active, vprev};
+  if (R.df_key_r != (int)r || std::memcmp(key, R.df_key, sizeof(key)) != 0) {
+    std::vector<DfStep> steps;
+    double bytes = 0.0;
+    df_build(ctx, R, r, psi, phil, envs, active, vprev, steps, &bytes);
+    int mx = 0;
+    for (const DfStep& s : steps) mx = std::max(mx, s.nchunk);
+    if ((int)steps.size() > R.df_cap || mx > R.df_max_nchunk)
+      return fail(QFS_EUNSUPPORTED, "dataflow table does not fit its buffers (%d steps, %d chunks)",
+                  (int)steps.size(), mx);
+    CK(cudaMemcpyAsync(R.df_steps, steps.data(), sizeof(DfStep) * steps.size(), cudaMemcpyHostToDevice, st));
+    R.df_nsteps = (int)steps.size();
+    R.df_items = steps.back().item0 + (long long)R.S * steps.back().nchunk;
+    R.df_bytes = bytes;
+    std::memcpy(R.df_key, key, sizeof(key));
+    R.df_key_r = (int)r;
+  }
+  const size_t nctrl = 1 + ((size_t)R.df_nsteps + 1) * R.S;
+  CK(cudaMemsetAsync(R.df_ctrl, 0, sizeof(unsigned) * nctrl, st));
+  DfArgs a{};
+  a.steps = R.df_steps;
+  a.nsteps = R.df_nsteps;
+  a.S = R.S;
+  a.total_items = R.df_items;
+  a.active = active;
+  a.queue = R.df_ctrl;
+  a.chunk_cnt = R.df_ctrl + 1;
+  a.done = R.df_ctrl + 1 + (size_t)R.df_nsteps * R.S;
+  a.err = R.err;
+  a.partials = R.df_partials;
+  a.resid_partials = R.df_resid;
+  a.resid_cost = R.costs;
+  a.inv_M = 1.0 / R.M;
+  a.trace = ctx->df_trace && ctx->df_trace_n >= (size_t)R.df_nsteps * R.S * 4 ? ctx->df_trace : nullptr;
+  if (a.trace) {
+    ctx->df_trace_steps = R.df_nsteps;
+    ctx->df_trace_S = R.S;
+  }
+  ProfScope ps(ctx, QFS_PROF_DATAFLOW, R.df_bytes, st);
+  CK(launch_sweep_df(r, a, ctx->num_sms, st));
+  return QFS_OK;
+}
+
 // FP64 sample cost of start s's master gates: (1/M) ||Phi_L - C Psi||^2.
 int check64(qfs_ctx* ctx, Run& R, int s, double* out) {
   cudaStream_t st = ctx->stream;
@@ -665,13 +866,18 @@ int run_multistart(qfs_ctx* ctx, Run& R, const qfs_params* p, Outcome& out) {
   bool done = false;
   int fp64_sweeps = 0;
   SweepGraph graph;
-  TRY(capture_sweep(ctx, R, rs, psi, phil, graph));
+  const bool df = df_usable(ctx, R, rs);
+  if (!df) TRY(capture_sweep(ctx, R, rs, psi, phil, graph));
   while (!done && sweeps < p->max_sweeps) {
     ++sweeps;
-    CK(cudaGraphLaunch(graph.exec, st));
-    for (int i = 0; i < QFS_PROF_KINDS; ++i) ctx->prof.launches[i] += graph.launches[i];
+    if (df) {
+      TRY(df_sweep(ctx, R, rs, psi, phil, nullptr, R.active, R.vprev, st));
+    } else {
+      CK(cudaGraphLaunch(graph.exec, st));
+      for (int i = 0; i < QFS_PROF_KINDS; ++i) ctx->prof.launches[i] += graph.launches[i];
+    }
     TRY(read_costs(ctx, R.costs, S, c, R.err));
-    if (ctx->prof.on) prof_harvest_graph(ctx);
+    if (ctx->prof.on && !df) prof_harvest_graph(ctx);
     for (int s = 0; s < S; ++s)
       if (!act[s]) c[s] = prev[s];
     if (R.prec == QFS_FP64) {
@@ -855,8 +1061,11 @@ int qfs_create(qfs_ctx** out, int device, void* cuda_stream) {
   ctx->device = device;
   if (const char* f = std::getenv("QFS_FUSE_UPDATE")) ctx->fuse_update = std::atoi(f) != 0;
   if (const char* f = std::getenv("QFS_TMA")) ctx->tma = std::atoi(f) != 0;
+  if (const char* f = std::getenv("QFS_DATAFLOW")) ctx->dataflow = std::atoi(f) != 0;
+  if (const char* f = std::getenv("QFS_DF_ITEM_KB")) ctx->df_item_bytes = std::max(16, std::atoi(f)) * 1024.0;
   e = cudaSetDevice(device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->coop, cudaDevAttrCooperativeLaunch, device);
   int l2 = 0;
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device);
   ctx->l2_bytes = (size_t)l2;
@@ -880,11 +1089,45 @@ int qfs_create(qfs_ctx** out, int device, void* cuda_stream) {
   return QFS_OK;
 }
 
+int qfs_dataflow_trace_enable(qfs_ctx* ctx, int64_t capacity) {
+  g_err.clear();
+  TRY(ctx_check(ctx));
+  if (capacity < 0) return fail(QFS_EINVAL, "capacity = %lld", (long long)capacity);
+  TRY(set_device(ctx));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (ctx->df_trace) CK(cudaFree(ctx->df_trace));
+  ctx->df_trace = nullptr;
+  ctx->df_trace_n = 0;
+  ctx->df_trace_steps = ctx->df_trace_S = 0;
+  if (capacity > 0) {
+    CK(cudaMalloc(&ctx->df_trace, sizeof(unsigned long long) * (size_t)capacity));
+    CK(cudaMemset(ctx->df_trace, 0, sizeof(unsigned long long) * (size_t)capacity));
+    ctx->df_trace_n = (size_t)capacity;
+  }
+  return QFS_OK;
+}
+
+int qfs_dataflow_trace_read(qfs_ctx* ctx, uint64_t* out, int64_t capacity, int32_t* steps, int32_t* S) {
+  g_err.clear();
+  TRY(ctx_check(ctx));
+  if (!steps || !S) return fail(QFS_EINVAL, "steps and S must be given");
+  *steps = ctx->df_trace_steps;
+  *S = ctx->df_trace_S;
+  const size_t n = (size_t)ctx->df_trace_steps * ctx->df_trace_S * 4;
+  if (!out || n == 0) return QFS_OK;
+  if ((size_t)capacity < n) return fail(QFS_EINVAL, "capacity %lld < %zu stamps", (long long)capacity, n);
+  TRY(set_device(ctx));
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaMemcpy(out, ctx->df_trace, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost));
+  return QFS_OK;
+}
+
 void qfs_destroy(qfs_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->df_trace) cudaFree(ctx->df_trace);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
   prof_harvest(ctx);
   for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
@@ -1009,10 +1252,13 @@ int qfs_sweep_once(qfs_ctx* ctx, const qfs_circuit* circuit, const double* targe
   CK(cudaMemcpyAsync(R.g64, gates_in, gbytes, cudaMemcpyHostToDevice, st));
   TRY(setup_inputs(ctx, R));
   const Real rs = precision == QFS_MIXED ? R32 : R64;
-  sweep(ctx, R, rs, Slice{0, S, S, ctx->stream}, R.g64, R.g32,
-        rs == R32 ? (const void*)R.psi32 : (const void*)R.psi64,
-        rs == R32 ? (const void*)R.phil32 : (const void*)R.phil64, R.B, R.phi, R.partials, R.nblk_max,
-        R.costs, R.envs, nullptr, R.stream_b, nullptr, R.counters);
+  const void* psi = rs == R32 ? (const void*)R.psi32 : (const void*)R.psi64;
+  const void* phil = rs == R32 ? (const void*)R.phil32 : (const void*)R.phil64;
+  if (df_usable(ctx, R, rs))
+    TRY(df_sweep(ctx, R, rs, psi, phil, R.envs, nullptr, nullptr, st));
+  else
+    sweep(ctx, R, rs, Slice{0, S, S, ctx->stream}, R.g64, R.g32, psi, phil, R.B, R.phi, R.partials, R.nblk_max,
+          R.costs, R.envs, nullptr, R.stream_b, nullptr, R.counters);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(gates_out, R.g64, gbytes, cudaMemcpyDeviceToHost, st));
   if (envs_out) CK(cudaMemcpyAsync(envs_out, R.envs, gbytes, cudaMemcpyDeviceToHost, st));

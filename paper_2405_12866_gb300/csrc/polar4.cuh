@@ -524,20 +524,16 @@ __device__ __forceinline__ void polar_update_warp(double2 e_cr, const double2* g
 }
 
 
-// The update of gate k for start s from the backward step's block partials
-// (one warp): sum the partials in a fixed order, form (1 - beta) E +
-// beta g_old^dagger, replace the gate with the polar factor of its adjoint,
-// and optionally write E, the cost 2 - (2/M) Re Tr(g E) and the new V.
-// PT is the partials' type (float after complex64 steps, double after FP64).
-template <typename PT, int POLISH, bool COHERENT>
-__device__ __forceinline__ void update_one_start(const UpdateArgs& a, int s, double2* sm) {
+// The update of gate k for start s once the environment is summed (one
+// warp; lane j holds value j = 2(4x+y) + {re, im} of E[x][y]): form
+// (1 - beta) E + beta g_old^dagger, replace the gate with the polar factor
+// of its adjoint, and optionally write E, the cost 2 - (2/M) Re Tr(g E) and
+// the new V.
+template <int POLISH>
+__device__ __forceinline__ void update_from_sum(const UpdateArgs& a, int s, double v, double2* sm) {
   const int lane = threadIdx.x & 31;
-  const PT* pp = reinterpret_cast<const PT*>(a.partials) + (long long)s * a.nblk * 32;
-  PT acc = PT(0);
-  for (int b = 0; b < a.nblk; ++b) acc += COHERENT ? __ldcg(pp + b * 32 + lane) : pp[b * 32 + lane];
-  const double v = (double)acc;
-  // value j = 2*(4x+y) + {re, im} of E[x][y]; lane 4c + r needs E[c][r],
-  // i.e. entry e = 4c + r = l16: real part at 2*l16, imaginary at 2*l16 + 1.
+  // Lane 4c + r needs E[c][r], i.e. entry e = 4c + r = l16: real part at
+  // 2*l16, imaginary at 2*l16 + 1.
   const int l16 = lane & 15;
   const double re = __shfl_sync(FULL, v, 2 * l16);
   const double im = __shfl_sync(FULL, v, 2 * l16 + 1);
@@ -554,6 +550,18 @@ __device__ __forceinline__ void update_one_start(const UpdateArgs& a, int s, dou
     for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
     if (lane == 0) a.cost_out[s] = 2.0 - 2.0 * a.inv_M * t;
   }
+}
+
+// The update of gate k for start s from the backward step's block partials
+// (one warp): the partials are summed in a fixed order, then as above.
+// PT is the partials' type (float after complex64 steps, double after FP64).
+template <typename PT, int POLISH, bool COHERENT>
+__device__ __forceinline__ void update_one_start(const UpdateArgs& a, int s, double2* sm) {
+  const int lane = threadIdx.x & 31;
+  const PT* pp = reinterpret_cast<const PT*>(a.partials) + (long long)s * a.nblk * 32;
+  PT acc = PT(0);
+  for (int b = 0; b < a.nblk; ++b) acc += COHERENT ? __ldcg(pp + b * 32 + lane) : pp[b * 32 + lane];
+  update_from_sum<POLISH>(a, s, (double)acc, sm);
 }
 
 }  // namespace qfs

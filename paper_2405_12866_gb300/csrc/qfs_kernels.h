@@ -72,6 +72,50 @@ struct UpdateArgs {
 };
 void launch_update(const UpdateArgs& a, cudaStream_t st);
 
+// Dataflow sweep (sweep_df.cu): one cooperative launch runs every step of a
+// sweep for every start as (step, start, chunk) work items.
+enum DfKind {
+  DF_FWD = 0,      // B_k = g_k B_{k-1} on the pair of fg
+  DF_BWD4 = 1,     // backward step, gates k+1 and k on four distinct qubits (16-row units)
+  DF_BWD2_10 = 2,  // backward step on one pair (no gate, or gate k+1 on the same pair)
+  DF_BWD2_01 = 3,  //   ... with the pair of gate k in the other order
+  DF_BWD3_20 = 4,  // backward step, gates k+1 and k sharing one qubit (ea, eb)
+  DF_BWD3_02 = 5,
+  DF_BWD3_10 = 6,
+  DF_BWD3_01 = 7,
+  DF_RESID = 8,    // residual cost (1/M) sum |g_1^dagger Phi_1 - Psi|^2
+};
+struct DfStep {
+  int kind;
+  int units, chunk, nchunk;             // units per start, units per chunk, chunks per start
+  long long item0;                      // first work item of this step
+  const void* in; long long in_stride;  // forward input / backward B_{k-1} / residual Psi
+  void* out;                            // forward output B_k (start stride fg.sN)
+  const void* phi_in; long long phi_in_stride;
+  void* phi_out;                        // start stride bg.sN; null: not stored
+  const void* gate; long long gate_stride;  // gate applied (null: none)
+  Geom fg;
+  BwdGeom bg;
+  UpdateArgs upd;                       // backward steps: the update of gate k
+};
+struct DfArgs {
+  const DfStep* steps; int nsteps; int S;
+  long long total_items;
+  const int* active;                    // nullable
+  unsigned* queue;                      // 1: next work item
+  unsigned* chunk_cnt;                  // nsteps x S finished chunks
+  unsigned* done;                       // S: steps finished per start
+  int* err;                             // bit 0: a bounded wait ran out
+  void* partials;                       // S x max chunks x 32 environment partials (float or double)
+  double* resid_partials;               // S x max chunks x 32, residual step only
+  double* resid_cost; double inv_M;     // residual step output
+  unsigned long long* trace;            // nullable: per (step, start) 4 global-timer stamps (first
+                                        // chunk started, last chunk done, partials summed, published)
+};
+int df_blocks_per_sm(Real r);
+cudaError_t launch_sweep_df(Real r, const DfArgs& a, int num_sms, cudaStream_t st);
+void df_chunking(DfStep& st, double bytes_per_unit, double target);
+
 // Set `count` 4x4 complex128 matrices to the identity.
 void launch_set_identity4(double2* v, long long count, cudaStream_t st);
 

@@ -36,10 +36,11 @@ EXPORTS = [
     "qfs_profile_read", "qfs_sweep_once_noalloc", "qfs_instantiate_batch",
     "qfs_instantiate_batch_dev", "qfs_gemm_bf16_dev", "qfs_ws_create", "qfs_ws_destroy", "qfs_ws_params",
     "qfs_ws_loss_grad", "qfs_ws_train", "qfs_ws_predict",
+    "qfs_dataflow_trace_enable", "qfs_dataflow_trace_read",
 ]
 (PROF_BACKWARD, PROF_FORWARD, PROF_UPDATE, PROF_GEMM, PROF_RESIDUAL, PROF_CHECK, PROF_OTHER, PROF_BATCH,
- PROF_MLP) = range(9)
-PROF_NAMES = ["backward", "forward", "update", "gemm", "residual", "check", "other", "batch", "mlp"]
+ PROF_MLP, PROF_DATAFLOW) = range(10)
+PROF_NAMES = ["backward", "forward", "update", "gemm", "residual", "check", "other", "batch", "mlp", "dataflow"]
 
 
 class QfsError(RuntimeError):
@@ -107,6 +108,8 @@ def lib():
     L.qfs_ws_loss_grad.argtypes = [_P, C.c_int32, _P, _P, C.POINTER(C.c_double), _P]
     L.qfs_ws_train.argtypes = [_P, C.c_int32, _P, _P, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_uint64, _P]
     L.qfs_ws_predict.argtypes = [_P, C.c_int32, _P, _P]
+    L.qfs_dataflow_trace_enable.argtypes = [_P, C.c_int64]
+    L.qfs_dataflow_trace_read.argtypes = [_P, _P, C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     L.qfs_sweep_once_noalloc.argtypes = [_P, C.POINTER(Circuit), _P, _P, C.c_int32, C.c_int32,
                                          C.c_double, _P, _P, _P, _P]
     L.qfs_profile_enable.argtypes = [_P, C.c_int]
@@ -343,6 +346,20 @@ class Context:
                                        C16.data_ptr() if C16 is not None else None, N,
                                        bias.data_ptr() if bias is not None else None, int(gelu), M_valid))
         return C32, C16
+
+    def dataflow_trace(self, capacity: int):
+        """Record step time stamps of dataflow sweeps (capacity stamps; 0: off)."""
+        _check(lib().qfs_dataflow_trace_enable(self._h, capacity))
+
+    def dataflow_trace_read(self) -> np.ndarray:
+        """Stamps of the last traced sweep as (steps, starts, 4) uint64 ns: first chunk
+        started, last chunk done, partials summed (updates only), step published."""
+        st, S = C.c_int32(), C.c_int32()
+        _check(lib().qfs_dataflow_trace_read(self._h, None, 0, C.byref(st), C.byref(S)))
+        out = np.zeros((st.value, S.value, 4), dtype=np.uint64)
+        if out.size:
+            _check(lib().qfs_dataflow_trace_read(self._h, out.ctypes.data, out.size, C.byref(st), C.byref(S)))
+        return out
 
     def profile(self, enable: bool):
         _check(lib().qfs_profile_enable(self._h, int(enable)))
