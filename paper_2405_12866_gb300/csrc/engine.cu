@@ -427,7 +427,7 @@ void df_build(const qfs_ctx* ctx, const Run& R, Real r, const void* psi, const v
     chunk_it(st, (double)(1 << U) * v * es * (k < L ? 3.0 : 2.0));
     UpdateArgs& u = st.upd;
     u.partials = R.df_partials;
-    u.nblk = st.nchunk;
+    u.nblk = st.nchunk;  // (the dataflow kernel sums the chunk slots itself)
     u.partials_f32 = r == R32;
     u.g64 = R.g64 ? R.g64 + (size_t)(k - 1) * 16 : nullptr;
     u.g_stride = gstride;
@@ -709,6 +709,7 @@ int df_sweep(qfs_ctx* ctx, Run& R, Real r, const void* psi, const void* phil, do
   a.err = R.err;
   a.partials = R.df_partials;
   a.resid_partials = R.df_resid;
+  a.part_stride = R.df_max_nchunk;
   a.resid_cost = R.costs;
   a.inv_M = 1.0 / R.M;
   a.trace = ctx->df_trace && ctx->df_trace_n >= (size_t)R.df_nsteps * R.S * 4 ? ctx->df_trace : nullptr;

@@ -106,8 +106,9 @@ struct DfArgs {
   unsigned* chunk_cnt;                  // nsteps x S finished chunks
   unsigned* done;                       // S: steps finished per start
   int* err;                             // bit 0: a bounded wait ran out
-  void* partials;                       // S x max chunks x 32 environment partials (float or double)
-  double* resid_partials;               // S x max chunks x 32, residual step only
+  void* partials;                       // S x part_stride x 32 environment partials (float or double)
+  double* resid_partials;               // S x part_stride x 32, residual step only
+  int part_stride;                      // slots per start: the most chunks of any step
   double* resid_cost; double inv_M;     // residual step output
   unsigned long long* trace;            // nullable: per (step, start) 4 global-timer stamps (first
                                         // chunk started, last chunk done, partials summed, published)

@@ -75,11 +75,24 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
   return t;
 }
 
+// Scratch of the CTA-wide gate update (4x4 matrices in the lane layout
+// M[r][c] at 4c + r).
+struct DfUpd {
+  double2 A[16];             // A = E^dagger scaled by a power of two
+  double2 Q[2][16];          // iterate (double buffer)
+  double2 T[16];             // products
+  double2 X[16];             // the correction factor of the polish step
+  float2 V[16];              // right singular vectors (FP32 Jacobi)
+  float sig[16];             // singular value of column (lane >> 2)
+  int ok;
+};
+
 template <typename T>
 struct DfShared {
   typename C2<T>::t gs[16];
   double red[4][32];
   double2 polar[32];
+  DfUpd u;
   long long item;
   int flag;
 };
@@ -121,18 +134,16 @@ __device__ void df_forward(const DfStep& st, int s, int c, DfShared<T>& sh) {
   T2* Y = reinterpret_cast<T2*>(st.out) + s * st.fg.sN;
   const int MV = st.fg.M / VEC;
   const int u0 = c * st.chunk, u1 = min(u0 + st.chunk, st.units);
-  for (int u = u0 + threadIdx.x; u < u1; u += kDfThreads) {
+  auto offsets = [&](int u, uint32_t (&off)[4]) {
     const int r = u / MV, jv = u - r * MV;
     const uint32_t base = insert_two_zero_bits((uint32_t)r, st.fg.lo, st.fg.hi);
-    uint32_t off[4];
 #pragma unroll
     for (int x = 0; x < 4; ++x) {
       const uint32_t row = base | ((uint32_t)(x >> 1) << st.fg.pos_a) | ((uint32_t)(x & 1) << st.fg.pos_b);
       off[x] = row * (uint32_t)st.fg.M + (uint32_t)jv * VEC;
     }
-    T2 v[4][VEC];
-#pragma unroll
-    for (int x = 0; x < 4; ++x) ldg<T, VEC>(X + off[x], v[x]);
+  };
+  auto apply = [&](const T2 (&v)[4][VEC], const uint32_t (&off)[4]) {
 #pragma unroll
     for (int x = 0; x < 4; ++x) {
       T2 o[VEC];
@@ -149,6 +160,28 @@ __device__ void df_forward(const DfStep& st, int s, int c, DfShared<T>& sh) {
       }
       stg<T, VEC>(Y + off[x], o);
     }
+  };
+  // Two units per thread per round: eight loads in flight.
+  int u = u0 + threadIdx.x;
+  for (; u + kDfThreads < u1; u += 2 * kDfThreads) {
+    uint32_t oa[4], ob[4];
+    offsets(u, oa);
+    offsets(u + kDfThreads, ob);
+    T2 va[4][VEC], vb[4][VEC];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) ldg<T, VEC>(X + oa[x], va[x]);
+#pragma unroll
+    for (int x = 0; x < 4; ++x) ldg<T, VEC>(X + ob[x], vb[x]);
+    apply(va, oa);
+    apply(vb, ob);
+  }
+  if (u < u1) {
+    uint32_t oa[4];
+    offsets(u, oa);
+    T2 va[4][VEC];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) ldg<T, VEC>(X + oa[x], va[x]);
+    apply(va, oa);
   }
 }
 
@@ -413,11 +446,193 @@ __device__ void df_backward_gen(const DfStep& st, int s, int c, DfShared<T>& sh,
   }
 }
 
+// C = op(X) Y for 4x4 complex matrices in shared memory (lane layout),
+// op(X) = X^dagger when AH, by all 128 threads of the CTA.  FP64 arithmetic
+// issues at a fixed cost per warp instruction on this GPU whatever the
+// number of active lanes, so the 256 real products are packed two per
+// thread over four warps (one per SM sub-partition): thread t forms the real
+// (t even) or imaginary part of X[r][k] Y[k][c] for entry t/8, k = (t/2)%4,
+// and the k terms are summed by two shuffles.  POST = 1 stores
+// 1.5 I - 0.5 C instead (the Newton-Schulz factor).  The caller
+// synchronises before and after.
+template <bool AH, int POST>
+__device__ __forceinline__ void mm64_cta(const double2* X, const double2* Y, double2* C) {
+  const int t = threadIdx.x;
+  const int e = t >> 3, k = (t >> 1) & 3, part = t & 1;
+  const int r = e & 3, c = e >> 2;
+  double2 x = AH ? X[4 * r + k] : X[4 * k + r];
+  if (AH) x.y = -x.y;
+  const double2 y = Y[4 * c + k];
+  double v = part ? fma(x.x, y.y, x.y * y.x) : fma(x.x, y.x, -(x.y * y.y));
+  v += __shfl_xor_sync(FULL, v, 2);
+  v += __shfl_xor_sync(FULL, v, 4);
+  if (k == 0) {
+    if (POST == 1) v = fma(-0.5, v, (part == 0 && r == c) ? 1.5 : 0.0);
+    reinterpret_cast<double*>(C + e)[part] = v;
+  }
+}
+
+// FP32 part of the update on warp 0 (as in warp_polar4_fast): scale A by an
+// exact power of two, one-sided Jacobi on A V0, Q0 = W V^H.  Leaves the
+// scaled A, Q0 (promoted), V and the singular values in u; returns false
+// when A is zero or too ill-conditioned for the fast path.
+__device__ __forceinline__ bool df_polar_begin(double2 a, double2 v0, DfUpd& u) {
+  const int lane = threadIdx.x & 31;
+  const int l16 = lane & 15, row = l16 & 3, col = l16 >> 2;
+  const bool isV = lane >= 16;
+  int e = 0;
+  if (!isV) {
+    const int ex = (__double2hiint(a.x) >> 20) & 0x7ff, ey = (__double2hiint(a.y) >> 20) & 0x7ff;
+    e = max(ex, ey);
+  }
+  e = __reduce_max_sync(FULL, e);
+  if (e == 0) return false;
+  const double sc = __hiloint2double((2046 - e) << 20, 0);
+  const double2 as{a.x * sc, a.y * sc};
+  if (!isV) u.A[l16] = as;
+  const float2 a32{(float)as.x, (float)as.y};
+  const float2 v032{(float)v0.x, (float)v0.y};
+  float2 x;
+  {
+    float2 acc{0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float2 ak = shfl_c(a32, 4 * k + row), vk = shfl_c(v032, 16 + 4 * col + k);
+      acc.x += ak.x * vk.x - ak.y * vk.y;
+      acc.y += ak.x * vk.y + ak.y * vk.x;
+    }
+    x = isV ? v032 : acc;
+  }
+  x = jacobi32_sweeps(x);
+  float2 w = shfl_c(x, l16);
+  const float2 v = shfl_c(x, 16 + l16);
+  float nrm = w.x * w.x + w.y * w.y;
+  nrm += __shfl_xor_sync(FULL, nrm, 1);
+  nrm += __shfl_xor_sync(FULL, nrm, 2);
+  float smax = nrm, smin = nrm;
+  smax = fmaxf(smax, __shfl_xor_sync(FULL, smax, 4));
+  smax = fmaxf(smax, __shfl_xor_sync(FULL, smax, 8));
+  smin = fminf(smin, __shfl_xor_sync(FULL, smin, 4));
+  smin = fminf(smin, __shfl_xor_sync(FULL, smin, 8));
+  if (!(smin > 1e-6f * smax)) return false;
+  const float sig = sqrtf(nrm);
+  const float inv = 1.f / sig;
+  w = float2{w.x * inv, w.y * inv};
+  const float2 q32 = mm_bh(w, v, row, col);
+  if (!isV) {
+    u.Q[0][l16] = double2{(double)q32.x, (double)q32.y};
+    u.V[l16] = v;
+    u.sig[l16] = sig;
+  }
+  return true;
+}
+
+// The update of gate k for start s by the whole CTA: the same mathematics as
+// polar_update_warp / update_from_sum (FP32 Jacobi, two FP64 Newton-Schulz
+// steps, POLISH skew-Hermitian corrections), with the FP64 products spread
+// over the four warps.  Warp 0 holds the summed environment value v (lane j
+// = value j of E).  All threads call it.
+template <typename T, int POLISH>
+__device__ void df_update(const UpdateArgs& ua, int s, DfShared<T>& sh, double v) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int l16 = lane & 15, row = l16 & 3, col = l16 >> 2;
+  DfUpd& u = sh.u;
+  double2* vio = ua.vprev ? ua.vprev + s * ua.g_stride : nullptr;
+  double2* g64 = ua.g64 + s * ua.g_stride;
+  double2 e{0.0, 0.0}, a{0.0, 0.0};
+  if (warp == 0) {
+    e = double2{__shfl_sync(FULL, v, 2 * l16), __shfl_sync(FULL, v, 2 * l16 + 1)};
+    if (ua.env_out && lane < 16) ua.env_out[s * ua.env_stride + l16] = e;
+    double2 m = e;
+    if (ua.beta != 0.0 && lane < 16) {
+      const double2 go = g64[4 * row + col];
+      m = double2{(1.0 - ua.beta) * m.x + ua.beta * go.x, (1.0 - ua.beta) * m.y - ua.beta * go.y};
+    }
+    a = double2{m.x, -m.y};
+    double2 v0{row == col ? 1.0 : 0.0, 0.0};
+    if (vio && lane >= 16) v0 = vio[l16];
+    const bool ok = df_polar_begin(a, v0, u);
+    if (lane == 0) u.ok = ok ? 1 : 0;
+  }
+  __syncthreads();
+  bool ok = u.ok != 0;
+  int cur = 0;
+  if (ok) {
+#pragma unroll 1
+    for (int it = 0; it < 2; ++it) {
+      mm64_cta<true, 1>(u.Q[cur], u.Q[cur], u.T);  // T = (3I - Q^H Q) / 2
+      __syncthreads();
+      mm64_cta<false, 0>(u.Q[cur], u.T, u.Q[cur ^ 1]);
+      __syncthreads();
+      cur ^= 1;
+    }
+#pragma unroll 1
+    for (int it = 0; it < POLISH; ++it) {
+      mm64_cta<true, 0>(u.Q[cur], u.A, u.T);  // B = Q^H A
+      __syncthreads();
+      if (warp == 0) {
+        const double2 bm = u.T[l16];
+        const double2 bt = u.T[4 * row + col];  // B[col][row]
+        const float2 k32{(float)(0.5 * (bm.x - bt.x)), (float)(0.5 * (bm.y + bt.y))};
+        const float2 om = skew_correction(k32, u.V[l16], u.sig[l16], row, col);
+        int good = 1;
+        if (it == 0) {
+          float big = fabsf(om.x) + fabsf(om.y);
+          big = fmaxf(big, __shfl_xor_sync(FULL, big, 1));
+          big = fmaxf(big, __shfl_xor_sync(FULL, big, 2));
+          big = fmaxf(big, __shfl_xor_sync(FULL, big, 4));
+          big = fmaxf(big, __shfl_xor_sync(FULL, big, 8));
+          good = big < 1e-3f ? 1 : 0;
+        }
+        const float2 om2 = mm(om, om, row, col);
+        const float2 om3 = mm(om2, om, row, col);
+        if (lane < 16)
+          u.X[l16] = double2{(row == col ? 1.0 : 0.0) + (double)om.x + 0.5 * (double)om2.x + (double)om3.x / 6.0,
+                             (double)om.y + 0.5 * (double)om2.y + (double)om3.y / 6.0};
+        if (lane == 0) u.ok = good;
+      }
+      __syncthreads();
+      if (!u.ok) {
+        ok = false;
+        break;
+      }
+      mm64_cta<false, 0>(u.Q[cur], u.X, u.Q[cur ^ 1]);
+      __syncthreads();
+      cur ^= 1;
+    }
+  }
+  if (warp == 0) {
+    double2 p;
+    if (ok) {
+      p = u.Q[cur][l16];
+      if (vio && lane < 16) vio[l16] = double2{(double)u.V[l16].x, (double)u.V[l16].y};
+    } else {
+      // Zero, ill-conditioned or not converging: the FP64 Jacobi (which
+      // also completes rank-deficient cases), from the identity.
+      p = warp_polar4(a, double2{row == col ? 1.0 : 0.0, 0.0}, sh.polar, vio);
+    }
+    if (lane < 16) {
+      g64[4 * row + col] = p;
+      if (ua.g32) (ua.g32 + s * ua.g_stride)[4 * row + col] = float2{(float)p.x, (float)p.y};
+    }
+    if (ua.cost_out) {
+      double t = lane < 16 ? (p.x * e.x - p.y * e.y) : 0.0;
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
+      if (lane == 0) ua.cost_out[s] = 2.0 - 2.0 * ua.inv_M * t;
+    }
+  }
+}
+
+// Partial-sum slots: start s owns slots s * stride .. s * stride + stride - 1
+// (stride = the most chunks of any step), so starts that are at different
+// steps, with different chunk counts, never share a slot.
 template <typename T>
-__device__ void df_process(const DfStep& st, int s, int c, DfShared<T>& sh, void* partials, double* resid) {
+__device__ void df_process(const DfStep& st, int s, int c, DfShared<T>& sh, void* partials, double* resid,
+                           int stride) {
   constexpr int V2 = sizeof(T) == 4 ? 2 : 1;  // samples per thread for 4- and 16-row units
-  T* part = reinterpret_cast<T*>(partials) + ((long long)s * st.nchunk + c) * 32;
-  double* part64 = resid + ((long long)s * st.nchunk + c) * 32;
+  T* part = reinterpret_cast<T*>(partials) + ((long long)s * stride + c) * 32;
+  double* part64 = resid + ((long long)s * stride + c) * 32;
   switch (st.kind) {
     case DF_FWD: df_forward<T, V2>(st, s, c, sh); break;
     case DF_BWD4: df_backward_q4<T, V2>(st, s, c, sh, part); break;
@@ -438,19 +653,24 @@ template <typename T>
 __global__ void __launch_bounds__(kDfThreads, sizeof(T) == 4 ? 3 : 2) k_sweep_df(DfArgs a) {
   __shared__ DfShared<T> sh;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // Thread 0 reserves the next item while the current one is processed, so
+  // the queue's atomic round trip is off the critical path.  A CTA's items
+  // increase, so the step search resumes where it stopped.
+  unsigned reserved = 0;
+  if (threadIdx.x == 0) reserved = atomicAdd(a.queue, 1u);
+  int i = 0;
   for (;;) {
     if (threadIdx.x == 0) {
       long long w = -1;
-      if (!ld_volatile_i32(a.err)) {
-        const unsigned x = atomicAdd(a.queue, 1u);
-        if ((long long)x < a.total_items) w = x;
+      if (!ld_volatile_i32(a.err) && (long long)reserved < a.total_items) {
+        w = reserved;
+        reserved = atomicAdd(a.queue, 1u);
       }
       sh.item = w;
     }
     __syncthreads();
     const long long w = sh.item;
     if (w < 0) return;
-    int i = 0;
     while (i + 1 < a.nsteps && a.steps[i + 1].item0 <= w) ++i;
     const DfStep& st = a.steps[i];
     const int rel = (int)(w - st.item0);
@@ -473,7 +693,7 @@ __global__ void __launch_bounds__(kDfThreads, sizeof(T) == 4 ? 3 : 2) k_sweep_df
     if (!sh.flag) return;
     const bool act = a.active == nullptr || a.active[s] != 0;
     if (a.trace && threadIdx.x == 0 && c == 0) a.trace[((long long)i * a.S + s) * 4] = globaltimer_ns();
-    if (act) df_process<T>(st, s, c, sh, a.partials, a.resid_partials);
+    if (act) df_process<T>(st, s, c, sh, a.partials, a.resid_partials, a.part_stride);
     // Publish this chunk; the last chunk of (step, start) finishes the step.
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -489,7 +709,7 @@ __global__ void __launch_bounds__(kDfThreads, sizeof(T) == 4 ? 3 : 2) k_sweep_df
         __threadfence();
         if (st.kind == DF_RESID) {
           if (warp == 0) {
-            const double* pp = a.resid_partials + (long long)s * st.nchunk * 32;
+            const double* pp = a.resid_partials + (long long)s * a.part_stride * 32;
             double t = 0.0;
             for (int b = lane; b < st.nchunk; b += 32) t += __ldcg(pp + (long long)b * 32);
 #pragma unroll
@@ -499,7 +719,7 @@ __global__ void __launch_bounds__(kDfThreads, sizeof(T) == 4 ? 3 : 2) k_sweep_df
         } else {
           // Sum the chunk partials with all four warps (warp w takes chunks
           // w, w+4, ...; fixed order), then one warp runs the update.
-          const T* pp = reinterpret_cast<const T*>(a.partials) + (long long)s * st.nchunk * 32;
+          const T* pp = reinterpret_cast<const T*>(a.partials) + (long long)s * a.part_stride * 32;
           T acc[4] = {T(0), T(0), T(0), T(0)};
           int b = warp;
           for (; b + 12 < st.nchunk; b += 16) {
@@ -510,10 +730,9 @@ __global__ void __launch_bounds__(kDfThreads, sizeof(T) == 4 ? 3 : 2) k_sweep_df
           sh.red[warp][lane] = (double)((acc[0] + acc[1]) + (acc[2] + acc[3]));
           __syncthreads();
           if (tr && threadIdx.x == 0) tr[2] = globaltimer_ns();
-          if (warp == 0) {
-            const double v = ((sh.red[0][lane] + sh.red[1][lane]) + (sh.red[2][lane] + sh.red[3][lane]));
-            update_from_sum<sizeof(T) == 4 ? 1 : 2>(st.upd, s, v, sh.polar);
-          }
+          const double v =
+              warp == 0 ? ((sh.red[0][lane] + sh.red[1][lane]) + (sh.red[2][lane] + sh.red[3][lane])) : 0.0;
+          df_update<T, sizeof(T) == 4 ? 1 : 2>(st.upd, s, sh, v);
         }
       }
       __syncthreads();

@@ -114,3 +114,29 @@ def test_dataflow_instantiation_matches_step_launches(ctxs):
     b = steps.instantiate(p.n, p.pairs, p.U, prm, p.samples(), p.init_gates())
     assert a.sweeps == b.sweeps == 40
     assert abs(a.cost - b.cost) < 1e-9
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_dataflow_full_size_sweeps_repeat_exactly(ctxs, prec):
+    """Starts run at different steps at the same time; steps differ in chunk
+    count.  Repeated full-size sweeps must agree with the per-step launches
+    every time (a slot shared by two starts would show up as a wrong start)."""
+    from paper_2405_12866_gb300 import qfs
+    from paper_2405_12866_gb300 import workloads as w
+    df, steps = ctxs
+    p = w.brick_n12(target_seed=3) if prec == "mixed" else w.brick_n8(target_seed=3)
+    pr = qfs.QFS_MIXED if prec == "mixed" else qfs.QFS_FP64
+    Psi, G = p.samples(), p.init_gates()
+    g2, _, c2 = steps.sweep_once(p.n, p.pairs, p.U, Psi, G, pr, want_envs=False)
+    tol_g = 1e-4 if prec == "mixed" else 1e-11
+    tol_c = 1e-5 if prec == "mixed" else 1e-12
+    first = None
+    for rep in range(4):
+        g1, _, c1 = df.sweep_once(p.n, p.pairs, p.U, Psi, G, pr, want_envs=False)
+        assert np.max(np.abs(g1 - g2)) < tol_g, f"repeat {rep}"
+        assert np.max(np.abs(c1 - c2)) < tol_c, f"repeat {rep}"
+        if first is None:
+            first = (g1, c1)
+        else:
+            # the reduction order is fixed: repeats are bitwise identical
+            assert np.array_equal(first[0], g1) and np.array_equal(first[1], c1), f"repeat {rep}"
