@@ -138,12 +138,16 @@ int qfs_profile_read(qfs_ctx* ctx, int32_t kind, int64_t* launches, int64_t* tim
  * every dataflow sweep whose steps x multistarts x 4 stamps fit records, per
  * (step, start), the device global timer (ns) when its first chunk started,
  * when its last chunk finished, when the environment partials were summed
- * (gate updates only; 0 otherwise) and when the step was published.
+ * (gate updates only; 0 otherwise) and when the step was published; when
+ * the capacity also covers them, every work item (step, start, chunk, in
+ * the order they are handed out) gets 4 more entries: dequeued, ready
+ * (after its wait), processed (ns) and (CTA << 40) | (step << 20) | start.
  * qfs_dataflow_trace_read copies the stamps of the last traced sweep, laid
- * out [step][start][4], to out (host, capacity entries; may be NULL to query
- * *steps and *S only). */
+ * out [step][start][4] then [item][4], to out (host, capacity entries; may
+ * be NULL to query *steps, *S and *items only; items may be NULL). */
 int qfs_dataflow_trace_enable(qfs_ctx* ctx, int64_t capacity);
-int qfs_dataflow_trace_read(qfs_ctx* ctx, uint64_t* out, int64_t capacity, int32_t* steps, int32_t* S);
+int qfs_dataflow_trace_read(qfs_ctx* ctx, uint64_t* out, int64_t capacity, int32_t* steps, int32_t* S,
+                            int64_t* items);
 
 /* The method's own random draws (host only, no GPU): the M training states
  * (Section 3 and Appendix A: columns of a Haar-random unitary, here the Q

@@ -96,6 +96,7 @@ struct qfs_ctx {
   unsigned long long* df_trace = nullptr;  // device buffer for step time stamps (qfs_dataflow_trace_*)
   size_t df_trace_n = 0;
   int df_trace_steps = 0, df_trace_S = 0;  // shape of the last traced sweep
+  long long df_trace_items = 0;            // work items with stamps in that sweep (0: none)
   double df_item_bytes = 256.0 * 1024.0;   // largest streaming bytes of one dataflow work item (QFS_DF_ITEM_KB)
   int coop = 0;             // device supports cooperative launches
   int device = 0;
@@ -712,10 +713,13 @@ int df_sweep(qfs_ctx* ctx, Run& R, Real r, const void* psi, const void* phil, do
   a.part_stride = R.df_max_nchunk;
   a.resid_cost = R.costs;
   a.inv_M = 1.0 / R.M;
-  a.trace = ctx->df_trace && ctx->df_trace_n >= (size_t)R.df_nsteps * R.S * 4 ? ctx->df_trace : nullptr;
+  const size_t nstep_stamps = (size_t)R.df_nsteps * R.S * 4;
+  a.trace = ctx->df_trace && ctx->df_trace_n >= nstep_stamps ? ctx->df_trace : nullptr;
+  a.item_trace = a.trace && ctx->df_trace_n >= nstep_stamps + (size_t)R.df_items * 4 ? a.trace + nstep_stamps : nullptr;
   if (a.trace) {
     ctx->df_trace_steps = R.df_nsteps;
     ctx->df_trace_S = R.S;
+    ctx->df_trace_items = a.item_trace ? R.df_items : 0;
   }
   ProfScope ps(ctx, QFS_PROF_DATAFLOW, R.df_bytes, st);
   CK(launch_sweep_df(r, a, ctx->num_sms, st));
@@ -1100,6 +1104,7 @@ int qfs_dataflow_trace_enable(qfs_ctx* ctx, int64_t capacity) {
   ctx->df_trace = nullptr;
   ctx->df_trace_n = 0;
   ctx->df_trace_steps = ctx->df_trace_S = 0;
+  ctx->df_trace_items = 0;
   if (capacity > 0) {
     CK(cudaMalloc(&ctx->df_trace, sizeof(unsigned long long) * (size_t)capacity));
     CK(cudaMemset(ctx->df_trace, 0, sizeof(unsigned long long) * (size_t)capacity));
@@ -1108,13 +1113,15 @@ int qfs_dataflow_trace_enable(qfs_ctx* ctx, int64_t capacity) {
   return QFS_OK;
 }
 
-int qfs_dataflow_trace_read(qfs_ctx* ctx, uint64_t* out, int64_t capacity, int32_t* steps, int32_t* S) {
+int qfs_dataflow_trace_read(qfs_ctx* ctx, uint64_t* out, int64_t capacity, int32_t* steps, int32_t* S,
+                            int64_t* items) {
   g_err.clear();
   TRY(ctx_check(ctx));
   if (!steps || !S) return fail(QFS_EINVAL, "steps and S must be given");
   *steps = ctx->df_trace_steps;
   *S = ctx->df_trace_S;
-  const size_t n = (size_t)ctx->df_trace_steps * ctx->df_trace_S * 4;
+  if (items) *items = ctx->df_trace_items;
+  const size_t n = (size_t)ctx->df_trace_steps * ctx->df_trace_S * 4 + (size_t)ctx->df_trace_items * 4;
   if (!out || n == 0) return QFS_OK;
   if ((size_t)capacity < n) return fail(QFS_EINVAL, "capacity %lld < %zu stamps", (long long)capacity, n);
   TRY(set_device(ctx));

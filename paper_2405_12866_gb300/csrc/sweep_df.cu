@@ -32,7 +32,15 @@ namespace qfs {
 namespace {
 
 constexpr long long kDfSpinLimit = 1LL << 25;  // polls of 32+ ns before giving up (> 1 s)
-constexpr int kDfThreads = 128;
+
+// One CTA per SM holding all the warps the registers allow (12 for complex64,
+// 8 for complex128): an item is streamed by the whole SM, so the chunks of
+// one start finish sooner than with several smaller CTAs sharing the SM.
+template <typename T>
+__host__ __device__ constexpr int df_threads() {
+  return sizeof(T) == 4 ? 512 : 256;
+}
+constexpr int kDfMaxWarps = 16;
 
 template <typename T, int VEC> struct DfV;
 template <> struct DfV<float, 2> { using t = float4; };
@@ -90,7 +98,7 @@ struct DfUpd {
 template <typename T>
 struct DfShared {
   typename C2<T>::t gs[16];
-  double red[4][32];
+  double red[kDfMaxWarps][32];
   double2 polar[32];
   DfUpd u;
   long long item;
@@ -107,7 +115,7 @@ __device__ __forceinline__ void block_partials32(double mine, DfShared<T>& sh, P
   if (warp == 0) {
     double t = 0.0;
 #pragma unroll
-    for (int w = 0; w < kDfThreads / 32; ++w) t += sh.red[w][lane];
+    for (int w = 0; w < df_threads<T>() / 32; ++w) t += sh.red[w][lane];
     __stcg(out + lane, (PT)t);
   }
 }
@@ -162,11 +170,12 @@ __device__ void df_forward(const DfStep& st, int s, int c, DfShared<T>& sh) {
     }
   };
   // Two units per thread per round: eight loads in flight.
+  constexpr int NT = df_threads<T>();
   int u = u0 + threadIdx.x;
-  for (; u + kDfThreads < u1; u += 2 * kDfThreads) {
+  for (; u + NT < u1; u += 2 * NT) {
     uint32_t oa[4], ob[4];
     offsets(u, oa);
-    offsets(u + kDfThreads, ob);
+    offsets(u + NT, ob);
     T2 va[4][VEC], vb[4][VEC];
 #pragma unroll
     for (int x = 0; x < 4; ++x) ldg<T, VEC>(X + oa[x], va[x]);
@@ -185,12 +194,41 @@ __device__ void df_forward(const DfStep& st, int s, int c, DfShared<T>& sh) {
   }
 }
 
+// Asynchronous 16-byte copies global -> shared (L2 only), in groups.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Stages of the backward step's copy pipeline.  Each thread copies the
+// sixteen bytes it will itself consume (eight rows of its unit: four of Phi,
+// four of B) into its own slots of a stage, so completion needs only the
+// thread's own cp.async.wait_group, never a block barrier; with kDfStages
+// stages, kDfStages - 1 rounds of loads are in flight per thread while one
+// round is computed, held in shared memory instead of registers.  Slot
+// (stage, row j, thread t) sits at ((stage * 8 + j) * threads + t) * 16
+// bytes: a warp reads 512 contiguous bytes, free of bank conflicts.
+constexpr int kDfStages = 3;
+template <typename T>
+__host__ __device__ constexpr int df_stage_bytes() {
+  return kDfStages * 8 * df_threads<T>() * 16;
+}
+
 // Backward step on 16-row units (gate k+1 and gate k on four distinct
 // qubits): four lanes share a unit as in the per-step kernel; the partial
 // sums of E_k go to partials slot (s, c).
 template <typename T, int VEC>
-__device__ void df_backward_q4(const DfStep& st, int s, int c, DfShared<T>& sh, T* part) {
+__device__ void df_backward_q4(const DfStep& st, int s, int c, DfShared<T>& sh, T* part, uint4* stage) {
   using T2 = typename C2<T>::t;
+  static_assert(sizeof(T2) * VEC == 16, "one 16-byte slot per row");
+  constexpr int NT = df_threads<T>();
+  constexpr int NW = NT / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int qx = lane >> 3, v = lane & 7;
   load_gate<T>(st, s, sh);
@@ -215,6 +253,8 @@ __device__ void df_backward_q4(const DfStep& st, int s, int c, DfShared<T>& sh, 
   for (int i = 0; i < 8; ++i) acc[i] = T(0);
   const int MV = st.bg.M / VEC;
   const int u0 = c * st.chunk, u1 = min(u0 + st.chunk, st.units);
+  constexpr int per_round = 8 * NW;  // units of one round (eight per warp)
+  const int rounds = (u1 - u0 + per_round - 1) / per_round;
   auto unit_off = [&](int u) {
     const int r = u / MV, jv = u - r * MV;
     uint32_t base = (uint32_t)r;
@@ -225,35 +265,39 @@ __device__ void df_backward_q4(const DfStep& st, int s, int c, DfShared<T>& sh, 
     }
     return base * M + (uint32_t)jv * VEC + xoff;
   };
-  auto load_unit = [&](int u, T2 (&ph)[4][VEC], T2 (&b)[4][VEC]) {
-    if (u < u1) {
+  auto issue = [&](int rd) {
+    const int u = u0 + rd * per_round + warp * 8 + v;
+    if (rd < rounds && u < u1) {
+      uint4* slot = stage + (size_t)((rd % kDfStages) * 8) * NT + threadIdx.x;
       const uint32_t o = unit_off(u);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) ldg<T, VEC>(P + o + joff[j], ph[j]);
+      for (int j = 0; j < 4; ++j) cp_async16(slot + (size_t)j * NT, P + o + joff[j]);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) ldg<T, VEC>(B + o + joff[j], b[j]);
-    } else {
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int q = 0; q < VEC; ++q) ph[j][q] = b[j][q] = T2{T(0), T(0)};
+      for (int j = 0; j < 4; ++j) cp_async16(slot + (size_t)(4 + j) * NT, B + o + joff[j]);
     }
+    cp_async_commit();  // (an empty group keeps the group count uniform)
   };
-  T2 phn[4][VEC], bn[4][VEC];
-  int ub = u0 + warp * 8;
-  if (ub < u1) load_unit(ub + v, phn, bn);
-  for (; ub < u1; ub += 32) {
-    const int u = ub + v;
+#pragma unroll
+  for (int rd = 0; rd < kDfStages - 1; ++rd) issue(rd);
+  for (int rd = 0; rd < rounds; ++rd) {
+    issue(rd + kDfStages - 1);
+    cp_async_wait<kDfStages - 1>();  // this thread's copies of round rd have landed
+    const int u = u0 + rd * per_round + warp * 8 + v;
     const bool valid = u < u1;
     T2 ph[4][VEC], b[4][VEC];
+    {
+      const uint4* slot = stage + (size_t)((rd % kDfStages) * 8) * NT + threadIdx.x;
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+      for (int j = 0; j < 8; ++j) {
+        uint4 w4 = valid ? slot[(size_t)j * NT] : make_uint4(0u, 0u, 0u, 0u);
+        const T2* e = reinterpret_cast<const T2*>(&w4);
 #pragma unroll
-      for (int q = 0; q < VEC; ++q) {
-        ph[j][q] = phn[j][q];
-        b[j][q] = bn[j][q];
+        for (int q = 0; q < VEC; ++q) {
+          if (j < 4) ph[j][q] = e[q];
+          else b[j - 4][q] = e[q];
+        }
       }
-    if (ub + 32 < u1) load_unit(ub + 32 + v, phn, bn);
+    }
     const uint32_t base_off = valid ? unit_off(u) : 0u;
     {
       T2 nw[4][VEC];
@@ -296,6 +340,7 @@ __device__ void df_backward_q4(const DfStep& st, int s, int c, DfShared<T>& sh, 
         }
     }
   }
+  cp_async_wait<0>();
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     acc[i] += __shfl_xor_sync(FULL, acc[i], 1);
@@ -315,7 +360,7 @@ __device__ void df_backward_q4(const DfStep& st, int s, int c, DfShared<T>& sh, 
   if (warp == 0) {
     double t = 0.0;
 #pragma unroll
-    for (int w = 0; w < kDfThreads / 32; ++w) t += sh.red[w][lane];
+    for (int w = 0; w < NW; ++w) t += sh.red[w][lane];
     __stcg(part + lane, (T)t);
   }
 }
@@ -356,7 +401,7 @@ __device__ void df_backward_gen(const DfStep& st, int s, int c, DfShared<T>& sh,
   for (int i = 0; i < (MODE == 0 ? 32 : 1); ++i) acc[i] = T(0);
   const int MV = st.bg.M / VEC;
   const int u0 = c * st.chunk, u1 = min(u0 + st.chunk, st.units);
-  for (int u = u0 + threadIdx.x; u < u1; u += kDfThreads) {
+  for (int u = u0 + threadIdx.x; u < u1; u += df_threads<T>()) {
     const int r = u / MV, jv = u - r * MV;
     uint32_t base = (uint32_t)r;
 #pragma unroll
@@ -458,6 +503,7 @@ __device__ void df_backward_gen(const DfStep& st, int s, int c, DfShared<T>& sh,
 template <bool AH, int POST>
 __device__ __forceinline__ void mm64_cta(const double2* X, const double2* Y, double2* C) {
   const int t = threadIdx.x;
+  if (t >= 128) return;  // four warps take part
   const int e = t >> 3, k = (t >> 1) & 3, part = t & 1;
   const int r = e & 3, c = e >> 2;
   double2 x = AH ? X[4 * r + k] : X[4 * k + r];
@@ -629,13 +675,13 @@ __device__ void df_update(const UpdateArgs& ua, int s, DfShared<T>& sh, double v
 // steps, with different chunk counts, never share a slot.
 template <typename T>
 __device__ void df_process(const DfStep& st, int s, int c, DfShared<T>& sh, void* partials, double* resid,
-                           int stride) {
+                           int stride, uint4* stage) {
   constexpr int V2 = sizeof(T) == 4 ? 2 : 1;  // samples per thread for 4- and 16-row units
   T* part = reinterpret_cast<T*>(partials) + ((long long)s * stride + c) * 32;
   double* part64 = resid + ((long long)s * stride + c) * 32;
   switch (st.kind) {
     case DF_FWD: df_forward<T, V2>(st, s, c, sh); break;
-    case DF_BWD4: df_backward_q4<T, V2>(st, s, c, sh, part); break;
+    case DF_BWD4: df_backward_q4<T, V2>(st, s, c, sh, part, stage); break;
     case DF_BWD2_10: df_backward_gen<T, V2, 0, 2, 1, 0>(st, s, c, sh, part); break;
     case DF_BWD2_01: df_backward_gen<T, V2, 0, 2, 0, 1>(st, s, c, sh, part); break;
     case DF_BWD3_20: df_backward_gen<T, 1, 0, 3, 2, 0>(st, s, c, sh, part); break;
@@ -650,21 +696,21 @@ __device__ void df_process(const DfStep& st, int s, int c, DfShared<T>& sh, void
 }  // namespace
 
 template <typename T>
-__global__ void __launch_bounds__(kDfThreads, sizeof(T) == 4 ? 3 : 2) k_sweep_df(DfArgs a) {
+__global__ void __launch_bounds__(df_threads<T>(), 1) k_sweep_df(DfArgs a) {
   __shared__ DfShared<T> sh;
+  extern __shared__ __align__(16) uint4 df_stage[];  // df_stage_bytes<T>() of copy stages
+  constexpr int NW = df_threads<T>() / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // Thread 0 reserves the next item while the current one is processed, so
-  // the queue's atomic round trip is off the critical path.  A CTA's items
-  // increase, so the step search resumes where it stopped.
-  unsigned reserved = 0;
-  if (threadIdx.x == 0) reserved = atomicAdd(a.queue, 1u);
+  // Thread 0 takes the next item when the CTA is free (a reservation held
+  // while the current item runs would delay that item by a whole item).
+  // A CTA's items increase, so the step search resumes where it stopped.
   int i = 0;
   for (;;) {
     if (threadIdx.x == 0) {
       long long w = -1;
-      if (!ld_volatile_i32(a.err) && (long long)reserved < a.total_items) {
-        w = reserved;
-        reserved = atomicAdd(a.queue, 1u);
+      if (!ld_volatile_i32(a.err)) {
+        const unsigned x = atomicAdd(a.queue, 1u);
+        if ((long long)x < a.total_items) w = x;
       }
       sh.item = w;
     }
@@ -675,6 +721,11 @@ __global__ void __launch_bounds__(kDfThreads, sizeof(T) == 4 ? 3 : 2) k_sweep_df
     const DfStep& st = a.steps[i];
     const int rel = (int)(w - st.item0);
     const int s = rel / st.nchunk, c = rel - s * st.nchunk;
+    unsigned long long* itr = a.item_trace ? a.item_trace + w * 4 : nullptr;
+    if (itr && threadIdx.x == 0) {
+      itr[0] = globaltimer_ns();
+      itr[3] = ((unsigned long long)blockIdx.x << 40) | ((unsigned long long)i << 20) | (unsigned)s;
+    }
     // Wait until start s has completed steps 0 .. i-1.
     if (threadIdx.x == 0) {
       int ok = 1;
@@ -693,10 +744,12 @@ __global__ void __launch_bounds__(kDfThreads, sizeof(T) == 4 ? 3 : 2) k_sweep_df
     if (!sh.flag) return;
     const bool act = a.active == nullptr || a.active[s] != 0;
     if (a.trace && threadIdx.x == 0 && c == 0) a.trace[((long long)i * a.S + s) * 4] = globaltimer_ns();
-    if (act) df_process<T>(st, s, c, sh, a.partials, a.resid_partials, a.part_stride);
+    if (itr && threadIdx.x == 0) itr[1] = globaltimer_ns();
+    if (act) df_process<T>(st, s, c, sh, a.partials, a.resid_partials, a.part_stride, df_stage);
     // Publish this chunk; the last chunk of (step, start) finishes the step.
     __syncthreads();
     if (threadIdx.x == 0) {
+      if (itr) itr[2] = globaltimer_ns();
       __threadfence();
       const unsigned old = atomicAdd(a.chunk_cnt + (long long)i * a.S + s, 1u);
       sh.flag = old == (unsigned)(st.nchunk - 1);
@@ -717,21 +770,24 @@ __global__ void __launch_bounds__(kDfThreads, sizeof(T) == 4 ? 3 : 2) k_sweep_df
             if (lane == 0) a.resid_cost[s] = t * a.inv_M;
           }
         } else {
-          // Sum the chunk partials with all four warps (warp w takes chunks
-          // w, w+4, ...; fixed order), then one warp runs the update.
+          // Sum the chunk partials with all warps (warp w takes chunks w,
+          // w + NW, ...; fixed order), then the update.
           const T* pp = reinterpret_cast<const T*>(a.partials) + (long long)s * a.part_stride * 32;
           T acc[4] = {T(0), T(0), T(0), T(0)};
           int b = warp;
-          for (; b + 12 < st.nchunk; b += 16) {
+          for (; b + 3 * NW < st.nchunk; b += 4 * NW) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] += __ldcg(pp + (long long)(b + 4 * q) * 32 + lane);
+            for (int q = 0; q < 4; ++q) acc[q] += __ldcg(pp + (long long)(b + q * NW) * 32 + lane);
           }
-          for (; b < st.nchunk; b += 4) acc[0] += __ldcg(pp + (long long)b * 32 + lane);
+          for (; b < st.nchunk; b += NW) acc[0] += __ldcg(pp + (long long)b * 32 + lane);
           sh.red[warp][lane] = (double)((acc[0] + acc[1]) + (acc[2] + acc[3]));
           __syncthreads();
           if (tr && threadIdx.x == 0) tr[2] = globaltimer_ns();
-          const double v =
-              warp == 0 ? ((sh.red[0][lane] + sh.red[1][lane]) + (sh.red[2][lane] + sh.red[3][lane])) : 0.0;
+          double v = 0.0;
+          if (warp == 0) {
+#pragma unroll
+            for (int w = 0; w < NW; ++w) v += sh.red[w][lane];
+          }
           df_update<T, sizeof(T) == 4 ? 1 : 2>(st.upd, s, sh, v);
         }
       }
@@ -751,8 +807,19 @@ int df_blocks_per_sm(Real r) {
   int& c = cache[r == R32 ? 0 : 1];
   if (c) return c;
   int b = 0;
-  const cudaError_t e = r == R32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sweep_df<float>, kDfThreads, 0)
-                                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sweep_df<double>, kDfThreads, 0);
+  cudaError_t e;
+  if (r == R32) {
+    e = cudaFuncSetAttribute(k_sweep_df<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, df_stage_bytes<float>());
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sweep_df<float>, df_threads<float>(),
+                                                        df_stage_bytes<float>());
+  } else {
+    e = cudaFuncSetAttribute(k_sweep_df<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             df_stage_bytes<double>());
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sweep_df<double>, df_threads<double>(),
+                                                        df_stage_bytes<double>());
+  }
   if (e != cudaSuccess || b < 1) {
     cudaGetLastError();
     return 0;
@@ -767,10 +834,10 @@ cudaError_t launch_sweep_df(Real r, const DfArgs& a, int num_sms, cudaStream_t s
   const int grid = (int)std::min<long long>((long long)bps * num_sms, std::max<long long>(a.total_items, 1));
   DfArgs args = a;
   void* params[] = {&args};
-  return r == R32 ? cudaLaunchCooperativeKernel((const void*)k_sweep_df<float>, dim3(grid), dim3(kDfThreads), params,
-                                                0, st)
-                  : cudaLaunchCooperativeKernel((const void*)k_sweep_df<double>, dim3(grid), dim3(kDfThreads),
-                                                params, 0, st);
+  return r == R32 ? cudaLaunchCooperativeKernel((const void*)k_sweep_df<float>, dim3(grid),
+                                                dim3(df_threads<float>()), params, df_stage_bytes<float>(), st)
+                  : cudaLaunchCooperativeKernel((const void*)k_sweep_df<double>, dim3(grid),
+                                                dim3(df_threads<double>()), params, df_stage_bytes<double>(), st);
 }
 
 // Chunking of one step: about `target` bytes of streaming per item, a

@@ -109,7 +109,8 @@ def lib():
     L.qfs_ws_train.argtypes = [_P, C.c_int32, _P, _P, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_uint64, _P]
     L.qfs_ws_predict.argtypes = [_P, C.c_int32, _P, _P]
     L.qfs_dataflow_trace_enable.argtypes = [_P, C.c_int64]
-    L.qfs_dataflow_trace_read.argtypes = [_P, _P, C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    L.qfs_dataflow_trace_read.argtypes = [_P, _P, C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                          C.POINTER(C.c_int64)]
     L.qfs_sweep_once_noalloc.argtypes = [_P, C.POINTER(Circuit), _P, _P, C.c_int32, C.c_int32,
                                          C.c_double, _P, _P, _P, _P]
     L.qfs_profile_enable.argtypes = [_P, C.c_int]
@@ -351,15 +352,19 @@ class Context:
         """Record step time stamps of dataflow sweeps (capacity stamps; 0: off)."""
         _check(lib().qfs_dataflow_trace_enable(self._h, capacity))
 
-    def dataflow_trace_read(self) -> np.ndarray:
-        """Stamps of the last traced sweep as (steps, starts, 4) uint64 ns: first chunk
-        started, last chunk done, partials summed (updates only), step published."""
-        st, S = C.c_int32(), C.c_int32()
-        _check(lib().qfs_dataflow_trace_read(self._h, None, 0, C.byref(st), C.byref(S)))
-        out = np.zeros((st.value, S.value, 4), dtype=np.uint64)
-        if out.size:
-            _check(lib().qfs_dataflow_trace_read(self._h, out.ctypes.data, out.size, C.byref(st), C.byref(S)))
-        return out
+    def dataflow_trace_read(self):
+        """Stamps of the last traced sweep: (steps, starts, 4) uint64 ns (first chunk
+        started, last chunk done, partials summed (updates only), step published) and
+        (items, 4) per work item (dequeued, ready, processed, CTA index) or None."""
+        st, S, it = C.c_int32(), C.c_int32(), C.c_int64()
+        _check(lib().qfs_dataflow_trace_read(self._h, None, 0, C.byref(st), C.byref(S), C.byref(it)))
+        n = st.value * S.value * 4 + it.value * 4
+        out = np.zeros(n, dtype=np.uint64)
+        if n:
+            _check(lib().qfs_dataflow_trace_read(self._h, out.ctypes.data, n, C.byref(st), C.byref(S), C.byref(it)))
+        steps = out[:st.value * S.value * 4].reshape(st.value, S.value, 4)
+        items = out[st.value * S.value * 4:].reshape(it.value, 4) if it.value else None
+        return steps, items
 
     def profile(self, enable: bool):
         _check(lib().qfs_profile_enable(self._h, int(enable)))
