@@ -97,7 +97,9 @@ struct qfs_ctx {
   size_t df_trace_n = 0;
   int df_trace_steps = 0, df_trace_S = 0;  // shape of the last traced sweep
   long long df_trace_items = 0;            // work items with stamps in that sweep (0: none)
-  double df_item_bytes = 256.0 * 1024.0;   // largest streaming bytes of one dataflow work item (QFS_DF_ITEM_KB)
+  double df_item_bytes = 1024.0 * 1024.0;  // largest streaming bytes of one dataflow work item (QFS_DF_ITEM_KB)
+  double df_items_per_cta = 1.5;           // work items per CTA and backward step (QFS_DF_ITEMS_PER_CTA)
+  double df_items_per_cta_fwd = 1.0;       // ... and forward step (QFS_DF_ITEMS_PER_CTA_FWD)
   int coop = 0;             // device supports cooperative launches
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -375,9 +377,13 @@ void df_build(const qfs_ctx* ctx, const Run& R, Real r, const void* psi, const v
     return R.B ? (void*)((char*)R.B + (size_t)(k - 1) * S * sN * es) : nullptr;
   };
   const double resident = (double)std::max(1, df_blocks_per_sm(r)) * std::max(1, ctx->num_sms);
+  // Items per CTA and step: forward steps have no update on the chain, so
+  // fewer, larger items pay off; backward steps keep more, smaller items so
+  // that a start's chunks finish sooner and its update starts earlier.
   auto chunk_it = [&](DfStep& st, double bytes_per_unit) {
     const double step_bytes = bytes_per_unit * st.units * S;
-    const double target = std::min(ctx->df_item_bytes, std::max(16.0 * 1024.0, step_bytes / (2.0 * resident)));
+    const double per_cta = st.kind == DF_FWD ? ctx->df_items_per_cta_fwd : ctx->df_items_per_cta;
+    const double target = std::min(ctx->df_item_bytes, std::max(16.0 * 1024.0, step_bytes / (per_cta * resident)));
     df_chunking(st, bytes_per_unit, target);
     *bytes += step_bytes;
   };
@@ -1068,6 +1074,9 @@ int qfs_create(qfs_ctx** out, int device, void* cuda_stream) {
   if (const char* f = std::getenv("QFS_TMA")) ctx->tma = std::atoi(f) != 0;
   if (const char* f = std::getenv("QFS_DATAFLOW")) ctx->dataflow = std::atoi(f) != 0;
   if (const char* f = std::getenv("QFS_DF_ITEM_KB")) ctx->df_item_bytes = std::max(16, std::atoi(f)) * 1024.0;
+  if (const char* f = std::getenv("QFS_DF_ITEMS_PER_CTA")) ctx->df_items_per_cta = std::max(0.25, std::atof(f));
+  if (const char* f = std::getenv("QFS_DF_ITEMS_PER_CTA_FWD"))
+    ctx->df_items_per_cta_fwd = std::max(0.25, std::atof(f));
   e = cudaSetDevice(device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->coop, cudaDevAttrCooperativeLaunch, device);
