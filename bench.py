@@ -59,10 +59,8 @@ def _problem(kind, seed):
 # ------------------------------------------------------------- env / ranks
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    from paper_2405_12866_gb300.ranks import dist_env as _env
+    return _env()
 
 
 class Clocks:
@@ -262,7 +260,8 @@ def run_ours(args):
 
     # Inputs for every step, generated on the host and made resident before timing.
     n_steps = args.warmup + args.steps
-    probs = [_problem(kind, rank * 100000 + i) for i in range(n_steps)]
+    from paper_2405_12866_gb300.ranks import combine, target_seeds
+    probs = [_problem(kind, seed) for seed in target_seeds(rank, n_steps)]
     first = probs[0]
     L, S, M, n = first.L, first.S, first.M, first.n
     dev_in = []
@@ -302,15 +301,7 @@ def run_ours(args):
     conv = sum(r.converged for r in results)
     sweeps = [r.sweeps for r in results]
 
-    if world > 1:
-        t = torch.tensor([ms, float(conv), float(launches)], device=dev, dtype=torch.float64)
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        tsum = t.clone()
-        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-        ms_all, conv_all, launches_all = tmax[0].item(), tsum[1].item(), tsum[2].item()
-    else:
-        ms_all, conv_all, launches_all = ms, float(conv), float(launches)
+    (ms_all,), (conv_all, launches_all) = combine([ms], [conv, launches], dev)
     value = conv_all / (ms_all / 1e3)
 
     # End to end through the public host-pointer API: pinned host inputs,
@@ -332,13 +323,7 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
         t_e2e = time.perf_counter() - t0
         conv_e2e = sum(r.converged for r in e2e_res)
-        if world > 1:
-            t = torch.tensor([t_e2e, float(conv_e2e)], device=dev, dtype=torch.float64)
-            tm = t.clone()
-            dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-            ts = t.clone()
-            dist.all_reduce(ts, op=dist.ReduceOp.SUM)
-            t_e2e, conv_e2e = tm[0].item(), ts[1].item()
+        (t_e2e,), (conv_e2e,) = combine([t_e2e], [conv_e2e], dev)
         N = 1 << n
         e2e = {"value": conv_e2e / t_e2e, "unit": UNIT,
                "h2d_bytes_per_step": 16 * (N * N + N * M + S * L * 16),
