@@ -147,16 +147,16 @@ def kernel_source_hash(kernel):
     return h.hexdigest()
 
 
-def traffic_record(kernel):
-    """DRAM bytes per launch of a kernel from the committed ncu summary
-    (profiles/traffic.json), used only while the kernel's sources are
+def traffic_record(kernel, workload):
+    """DRAM bytes per launch of a kernel on a workload from the committed ncu
+    summary (profiles/traffic.json), used only while the kernel's sources are
     unchanged since the capture."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path)).get(kernel)
     except Exception:
         return None
-    if not rec or rec.get("source_sha256") != kernel_source_hash(kernel):
+    if not rec or rec.get("source_sha256") != kernel_source_hash(kernel) or rec.get("bench_workload") != workload:
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -341,7 +341,7 @@ def run_ours(args):
     avg_ms = dom["ms"] / max(dom["timed"], 1)
     bytes_per = dom["bytes"] / max(dom["timed"], 1)
     achieved = bytes_per / (avg_ms / 1e3) / 1e9 if dom["timed"] else None
-    tr = traffic_record(kname)
+    tr = traffic_record(kname, kind)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
