@@ -222,3 +222,71 @@ def generalisation_error(UPsi_val: np.ndarray, Psi_val: np.ndarray, gates, pairs
     """Normalised generalisation error c_val / c_train - 1 (Section 3)."""
     c_val = sample_cost(UPsi_val, Psi_val, gates, pairs, n)
     return c_val / c_train - 1.0
+
+
+# ------------------------------------------- double-and-restart (Sec. 3, App. A)
+
+@dataclasses.dataclass
+class RestartResult:
+    gates: np.ndarray          # (L, 4, 4) of the returned start
+    cost: float                # its training cost
+    validation_cost: float     # its validation cost (NaN when M reached 2^n)
+    converged: bool
+    best_start: int
+    training_states: int       # M of the last attempt
+    attempts: int
+    sweeps: int                # over all attempts
+
+
+def instantiate_restarting(U: np.ndarray, training_states, validation_states, init_gates: np.ndarray,
+                           pairs, n: int, tol: float, max_sweeps: int, M0: int,
+                           overtrain_ratio: float, min_sweeps: int = 0) -> RestartResult:
+    """QFactor-Sample with the on-the-fly generalisation check (Sec. 3 and
+    Appendix A): multistart sweeps on M training states; after every sweep
+    (from min_sweeps on) the start with the lowest training cost c_train is
+    evaluated on M validation states (c_val).  When c_val / c_train - 1 >
+    overtrain_ratio the attempt halts, M doubles (up to 2^n), new training and
+    validation states are drawn, every start keeps its gates, and the run
+    restarts.  Success needs c_train <= tol and c_val <= (1 + overtrain_ratio)
+    c_train; at M = 2^n the check is skipped.  max_sweeps bounds each attempt.
+
+    training_states(M, attempt) and validation_states(M, attempt) return
+    the N x M states of an attempt."""
+    N = 1 << n
+    G = np.array(init_gates, dtype=np.complex128, copy=True)
+    S = G.shape[0]
+    M, attempt, total = M0, 0, 0
+    while True:
+        Psi = training_states(M, attempt)
+        UPsi = U @ Psi
+        check = M < N
+        if check:
+            Psi_v = validation_states(M, attempt)
+            UPsi_v = U @ Psi_v
+        costs = np.full(S, np.inf)
+        overtrained, done, cv = False, False, float("nan")
+        s = 0
+        while s < max_sweeps and not done:
+            s += 1
+            for i in range(S):
+                r = sweep(UPsi, Psi, G[i], pairs, n)
+                G[i] = r.gates
+                costs[i] = r.cost
+            b = int(np.argmin(costs))
+            converged_now = costs[b] <= tol
+            if check and s >= min_sweeps:
+                cv = sample_cost(UPsi_v, Psi_v, G[b], pairs, n)
+                if cv / costs[b] - 1.0 > overtrain_ratio:
+                    overtrained, done = True, True
+            if converged_now:
+                done = True
+        total += s
+        b = int(np.argmin(costs))
+        if check and not overtrained:
+            cv = sample_cost(UPsi_v, Psi_v, G[b], pairs, n)
+        if overtrained and 2 * M <= N:
+            M, attempt = 2 * M, attempt + 1
+            continue
+        conv = bool(costs[b] <= tol and not overtrained)
+        return RestartResult(G[b].copy(), float(costs[b]), float(cv) if check else float("nan"), conv, b, M,
+                             attempt + 1, total)

@@ -124,6 +124,14 @@ def sample_states(seed: int, n: int, M: int, stream: int = STREAM_SAMPLES) -> np
     return positive_qr_q(g)
 
 
+def attempt_seed(seed: int, attempt: int) -> int:
+    """Seed of the training and validation states of a double-and-restart
+    attempt (attempt 0 uses the run seed itself)."""
+    if attempt == 0:
+        return int(seed) & 0xFFFFFFFFFFFFFFFF
+    return (int(seed) ^ (attempt * 0x9E3779B97F4A7C15)) & 0xFFFFFFFFFFFFFFFF
+
+
 def haar_gates(seed: int, stream: int, count: int, first_gate: int = 0) -> np.ndarray:
     """`count` Haar-random U(4) matrices, gate i drawn from counters 16*i..16*i+15."""
     z = complex_normals(seed, stream, 16 * first_gate, 16 * count).reshape(count, 4, 4)

@@ -394,3 +394,44 @@ def test_unbroken_copy_passes():
     m = _Broken(_dagger=lambda g: g.conj().T)
     for pin in [check_env_definition, check_sweep_objectives, check_single_gate_closed_form]:
         assert pin(m)
+
+
+# ------------------------------------------------------ double-and-restart
+
+def _restart_inputs(name):
+    p = w.chain_n3(target_seed=1) if name == "chain_n3" else None
+    tr = lambda M, a: w.sample_states(w.attempt_seed(p.seed, a), p.n, M)
+    va = lambda M, a: w.sample_states(w.attempt_seed(p.seed, a), p.n, M, stream=w.STREAM_VALIDATION)
+    return p, tr, va
+
+
+def test_restart_without_overtraining_is_the_plain_run():
+    """With an overtrain ratio no run can exceed, the outer loop is one
+    attempt identical to the fixed-M instantiation."""
+    p, tr, va = _restart_inputs("chain_n3")
+    G0 = w.initial_gates(p.seed, 2, p.L)
+    r = o.instantiate_restarting(p.U, tr, va, G0, p.pairs, p.n, 1e-10, 60, 4, 1e300)
+    plain = o.instantiate(p.U, tr(4, 0), G0, p.pairs, p.n, 1e-10, 60)
+    assert r.attempts == 1 and r.training_states == 4
+    assert r.sweeps == plain.sweeps and r.best_start == plain.best_start
+    assert abs(r.cost - plain.cost) < 1e-15
+    assert np.max(np.abs(r.gates - plain.gates)) < 1e-15
+
+
+def test_restart_doubles_until_the_target_generalises():
+    """chain_n3 stalls at M = 4 (sample-cost plateau ~3e-4); the outer loop
+    detects the gap between validation and training cost, doubles M and
+    converges, and the returned gates generalise: the full-unitary cost
+    (Eq. 1, all 2^n states) is below the bound dist_tol (1 + otr)."""
+    p, tr, va = _restart_inputs("chain_n3")
+    G0 = w.initial_gates(p.seed, 1, p.L)
+    otr = 0.1
+    r = o.instantiate_restarting(p.U, tr, va, G0, p.pairs, p.n, 1e-10, 200, 2, otr)
+    assert r.converged and r.cost <= 1e-10
+    assert r.training_states > 2 and r.training_states <= 8
+    assert r.training_states & (r.training_states - 1) == 0
+    assert r.attempts == int(np.log2(r.training_states)) - 1 + 1
+    if r.training_states < 8:
+        assert r.validation_cost <= (1 + otr) * r.cost
+    # generalisation to all states: ||U - C||_F^2 / N is the M = N sample cost
+    assert o.full_cost(p.U, r.gates, p.pairs, p.n) < 1e-10 * (1 + otr) * 10
