@@ -270,9 +270,14 @@ def run_ours(args):
                        torch.from_numpy(np.ascontiguousarray(p.init_gates())).to(dev)))
     out = torch.zeros((L, 4, 4), dtype=torch.complex128, device=dev)
     prm = qfs.default_params(M=M, multistarts=S, max_sweeps=first.max_sweeps, dist_tol=first.tol,
-                             precision=prec, start_groups=args.start_groups)
+                             precision=prec, start_groups=args.start_groups,
+                             restart_doubling=1 if args.restart_doubling else 0)
 
     def step(i):
+        if args.restart_doubling:
+            # double-and-restart draws its training states itself (host target)
+            prm.seed = probs[i].seed
+            return ctx.instantiate(n, first.pairs, probs[i].U, prm)
         U, Psi, G0 = dev_in[i]
         return ctx.instantiate_dev(n, first.pairs, U, Psi, G0, prm, out)
 
@@ -347,11 +352,14 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64" if prec == 1 else "f64",
         "data": "synthetic (seeded Haar-random targets of the stated structure)",
-        "config": {"workload": WORKLOADS[kind][2], "n": n, "gates": L, "M": M, "multistarts": S,
+        "config": {"workload": WORKLOADS[kind][2] + (", double-and-restart of M (overtrain ratio 0.1)"
+                                                     if args.restart_doubling else ""),
+                   "n": n, "gates": L, "M": M, "multistarts": S,
                    "tol": first.tol, "max_sweeps": first.max_sweeps, "parallelism": f"{world} independent ranks",
                    "l2": "inputs larger than L2 (B list 512 MiB per target), no flush"},
         "converged": int(conv_all), "instantiations": args.steps * world,
         "sweeps_per_instantiation": float(np.mean(sweeps)),
+        "training_states": [int(r.training_states) for r in results],
         "roofline": {"bound": "hbm", "kernel": kdesc,
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None,
@@ -609,6 +617,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--batch-problems", type=int, default=4096)
+    ap.add_argument("--restart-doubling", action="store_true",
+                    help="the paper's double-and-restart of the training states (host targets)")
     ap.add_argument("--learned-train", type=int, default=1 << 20)
     ap.add_argument("--learned-eval", type=int, default=65536)
     ap.add_argument("--learned-epochs", type=int, default=40)

@@ -79,6 +79,15 @@ typedef struct {
   double dist_tol;           /* stop when a start's cost <= dist_tol */
   double diff_tol_r;         /* plateau: relative improvement threshold */
   double beta;               /* update damping, 0 <= beta < 1 (0 = full update) */
+  int32_t restart_doubling;  /* 1: double-and-restart (Sec. 3, App. A): after every sweep from
+                                min_sweeps on, the start with the lowest training cost is also
+                                evaluated on M fresh validation states; when c_val / c_train - 1 >
+                                overtrain_ratio the run halts, M doubles (up to 2^n), new training
+                                and validation states are drawn, every start keeps its gates and
+                                the run restarts (max_sweeps per attempt).  Success needs
+                                c_train <= dist_tol and c_val <= (1 + overtrain_ratio) c_train.
+                                Needs library-drawn training states (qfs_instantiate). */
+  double overtrain_ratio;    /* overtrain_ratio of the generalisation check */
 } qfs_params;
 
 typedef struct {
@@ -87,13 +96,17 @@ typedef struct {
   int32_t converged;   /* 1 if cost <= dist_tol */
   int32_t best_start;  /* index of the returned start */
   int32_t fp64_sweeps; /* QFS_MIXED: FP64 refinement sweeps run */
+  int32_t training_states; /* M of the (last) attempt */
 } qfs_result;
 
 /* Fill *p with defaults: M = 2, multistarts = 16, max_sweeps = 10000,
  * min_sweeps = 6, plateau_window = 0, precision = QFS_FP64,
  * refine_sweeps_max = 50, start_groups = 0, seed = 0, dist_tol = 1e-8,
- * diff_tol_r = 1e-5, beta = 0 (the paper's suggested values, with plateau
- * detection off). */
+ * diff_tol_r = 1e-5, beta = 0, restart_doubling = 0, overtrain_ratio = 0.1
+ * (the paper's suggested values, with plateau detection and
+ * double-and-restart off).  With restart_doubling, attempt a > 0 draws its
+ * training states (stream 1) and validation states (stream 5) from seed
+ * XOR (a * 0x9E3779B97F4A7C15); attempt 0 validates with stream 5 of seed. */
 void qfs_default_params(qfs_params* p);
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a

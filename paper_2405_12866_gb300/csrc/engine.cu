@@ -23,6 +23,7 @@
 
 namespace qfs {
 void generate_samples(uint64_t seed, int n, int M, std::complex<double>* out);
+void generate_states(uint64_t seed, uint32_t stream, int n, int M, std::complex<double>* out);
 void generate_gates(uint64_t seed, int count, std::complex<double>* out);
 }  // namespace qfs
 
@@ -228,6 +229,10 @@ struct Run {
   double2* phi64r = nullptr;
   double* partials64r = nullptr;
   double* cost64r = nullptr;
+  // Validation states and U times them (double-and-restart), FP64.
+  bool validate = false;
+  double2* psi_val64 = nullptr;
+  double2* phil_val64 = nullptr;
   int stream_b = 0;
   int stream_b64 = 0;
   // Dataflow sweep: step table (device), control words, partial sums.
@@ -286,11 +291,15 @@ size_t carve(Run& R, char* base, bool need_U, bool need_envs) {
   // environment partials are floats, and one start's residual slots would
   // overlap another start's environment slots while that start still sweeps.
   R.df_resid = (double*)take(sizeof(double) * 32 * (size_t)R.S * std::max(R.df_max_nchunk, 1));
-  if (R.prec == QFS_MIXED) {
+  if (R.prec == QFS_MIXED || R.validate) {
     R.B64r = (double2*)take((size_t)std::max(R.L - 1, 2) * state64);
     R.phi64r = (double2*)take(state64);
     R.partials64r = (double*)take((size_t)R.nblk64_max * 32 * sizeof(double));
     R.cost64r = (double*)take(sizeof(double) * 2);
+  }
+  if (R.validate) {
+    R.psi_val64 = (double2*)take(state64);
+    R.phil_val64 = (double2*)take(state64);
   }
   return off;
 }
@@ -472,7 +481,8 @@ void df_build(const qfs_ctx* ctx, const Run& R, Real r, const void* psi, const v
 }
 
 int prepare(qfs_ctx* ctx, Run& R, const qfs_circuit* c, int M, int S, int prec, double beta,
-            bool need_U, bool need_envs, int groups = 1) {
+            bool need_U, bool need_envs, int groups = 1, bool validate = false) {
+  R.validate = validate;
   R.n = c->n;
   R.L = c->L;
   R.M = M;
@@ -732,11 +742,15 @@ int df_sweep(qfs_ctx* ctx, Run& R, Real r, const void* psi, const void* phil, do
   return QFS_OK;
 }
 
-// FP64 sample cost of start s's master gates: (1/M) ||Phi_L - C Psi||^2.
-int check64(qfs_ctx* ctx, Run& R, int s, double* out) {
+// FP64 sample cost of start s's master gates on states psi with
+// phil = U psi: (1/M) ||phil - C psi||^2 (the training states by default).
+int check64(qfs_ctx* ctx, Run& R, int s, double* out, const double2* psi = nullptr,
+            const double2* phil = nullptr) {
   cudaStream_t st = ctx->stream;
   const double2* g = R.g64 + (size_t)s * R.L * 16;
-  const void* in = R.psi64;
+  if (!psi) psi = R.psi64;
+  if (!phil) phil = R.phil64;
+  const void* in = psi;
   for (int k = 1; k <= R.L; ++k) {
     const Geom gm = make_geom(R.n, R.M, R.pairs[2 * (k - 1)], R.pairs[2 * (k - 1) + 1]);
     double2* out_buf = R.B64r + (size_t)(k & 1) * R.sN;
@@ -747,7 +761,7 @@ int check64(qfs_ctx* ctx, Run& R, int s, double* out) {
   const BwdGeom bg = make_bwd_geom(R.n, R.M, R.pairs[0], R.pairs[1], R.pairs[0], R.pairs[1]);
   {
     ProfScope ps(ctx, QFS_PROF_CHECK, 2.0 * R.sN * sizeof(double2));
-    launch_backward(R64, 1, bg, R.sh64, 1, in, 0, R.phil64, 0, nullptr, nullptr, 16, R.partials64r,
+    launch_backward(R64, 1, bg, R.sh64, 1, in, 0, phil, 0, nullptr, nullptr, 16, R.partials64r,
                     0, nullptr, st);
   }
   {
@@ -856,6 +870,8 @@ struct Outcome {
   int converged = 0;
   int fp64_sweeps = 0;
   std::vector<double> start_costs;
+  bool overtrained = false;  // the validation check halted the run (double-and-restart)
+  double c_val = std::numeric_limits<double>::quiet_NaN();
 };
 
 // The multistart run.  Starts sweep in lock step; the run stops at the first
@@ -925,6 +941,23 @@ int run_multistart(qfs_ctx* ctx, Run& R, const qfs_params* p, Outcome& out) {
       for (int s = 0; s < S; ++s)
         if (!std::isnan(c64[s])) c[s] = c64[s];
     }
+    if (R.validate && (done || sweeps >= p->min_sweeps)) {
+      // Generalisation check (Sec. 3): the start with the lowest training
+      // cost, evaluated in FP64 on the validation states.
+      int b = -1;
+      for (int s = 0; s < S; ++s)
+        if (act[s] && (b < 0 || c[s] < c[b])) b = s;
+      if (b >= 0) {
+        double cv = 0.0;
+        TRY(check64(ctx, R, b, &cv, R.psi_val64, R.phil_val64));
+        out.c_val = cv;
+        const double gen = c[b] > 0.0 ? cv / c[b] - 1.0 : (cv > 0.0 ? std::numeric_limits<double>::infinity() : 0.0);
+        if (gen > p->overtrain_ratio) {
+          out.overtrained = true;
+          done = true;
+        }
+      }
+    }
     if (!done && p->plateau_window > 0) {
       bool changed = false;
       for (int s = 0; s < S; ++s) {
@@ -958,7 +991,7 @@ int run_multistart(qfs_ctx* ctx, Run& R, const qfs_params* p, Outcome& out) {
   out.best = best;
   out.cost = cost;
   out.sweeps = sweeps;
-  out.converged = cost <= tol;
+  out.converged = cost <= tol && !out.overtrained;
   out.fp64_sweeps = fp64_sweeps;
   out.start_costs = prev;
   out.start_costs[best] = cost;
@@ -973,6 +1006,78 @@ int ctx_check(const qfs_ctx* ctx) {
 int set_device(qfs_ctx* ctx) {
   CK(cudaSetDevice(ctx->device));
   return QFS_OK;
+}
+
+// Seed of attempt a's training and validation states (attempt 0: the seed).
+uint64_t attempt_seed(uint64_t seed, int a) { return a == 0 ? seed : seed ^ ((uint64_t)a * 0x9E3779B97F4A7C15ULL); }
+
+// Double-and-restart (Sec. 3, App. A): multistart runs on M training
+// states with the validation check; when it halts a run, M doubles (up to
+// 2^n), fresh states are drawn, every start keeps its gates, and the run
+// restarts.
+int instantiate_restarting(qfs_ctx* ctx, const qfs_circuit* c, const double* target, bool target_dev,
+                           const double* gates0, bool gates_dev, uint64_t seed, const qfs_params* p,
+                           double* gates_out, bool out_dev, qfs_result* result, double* start_costs) {
+  cudaStream_t st = ctx->stream;
+  const int S = p->multistarts, L = c->L, n = c->n;
+  const long long N = 1LL << n;
+  int groups = p->start_groups;
+  if (groups <= 0) groups = S >= 8 ? 2 : 1;
+  // Every start's gates, carried from attempt to attempt (host).
+  std::vector<std::complex<double>> G((size_t)S * L * 16);
+  if (gates0) {
+    CK(cudaMemcpy(G.data(), gates0, G.size() * sizeof(double2), gates_dev ? cudaMemcpyDeviceToHost
+                                                                           : cudaMemcpyHostToHost));
+  } else {
+    generate_gates(seed, S * L, G.data());
+  }
+  int M = p->M, total = 0, fp64 = 0;
+  for (int attempt = 0;; ++attempt) {
+    const bool validate = M < N;
+    Run R;
+    TRY(prepare(ctx, R, c, M, S, p->precision, p->beta, !target_dev, false, groups, validate));
+    if (target_dev) {
+      R.U = reinterpret_cast<const double2*>(target);
+    } else {
+      CK(cudaMemcpyAsync(R.U_copy, target, (size_t)R.N * R.N * sizeof(double2), cudaMemcpyHostToDevice, st));
+      R.U = R.U_copy;
+    }
+    const uint64_t sa = attempt_seed(seed, attempt);
+    std::vector<std::complex<double>> h((size_t)R.sN);
+    generate_states(sa, 1u, n, M, h.data());
+    CK(cudaMemcpyAsync(R.psi64, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    if (validate) {
+      generate_states(sa, 5u, n, M, h.data());
+      CK(cudaMemcpyAsync(R.psi_val64, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+      launch_gemm_upsi(R.U, R.psi_val64, R.phil_val64, (int)R.N, M, st);
+      ctx->prof.launches[QFS_PROF_GEMM] += 1;
+      CK(cudaStreamSynchronize(st));
+    }
+    CK(cudaMemcpyAsync(R.g64, G.data(), G.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+    TRY(setup_inputs(ctx, R));
+    Outcome o;
+    TRY(run_multistart(ctx, R, p, o));
+    total += o.sweeps;
+    fp64 += o.fp64_sweeps;
+    CK(cudaMemcpyAsync(G.data(), R.g64, G.size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (o.overtrained && 2LL * M <= N) {
+      M *= 2;
+      continue;
+    }
+    CK(cudaMemcpyAsync(gates_out, G.data() + (size_t)o.best * L * 16, (size_t)L * 16 * sizeof(double2),
+                       out_dev ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, st));
+    CK(cudaStreamSynchronize(st));
+    result->cost = o.cost;
+    result->sweeps = total;
+    result->converged = o.converged;
+    result->best_start = o.best;
+    result->fp64_sweeps = fp64;
+    result->training_states = M;
+    if (start_costs) std::copy(o.start_costs.begin(), o.start_costs.end(), start_costs);
+    return QFS_OK;
+  }
 }
 
 int instantiate_common(qfs_ctx* ctx, const qfs_circuit* c, const double* target, bool target_dev,
@@ -990,8 +1095,12 @@ int instantiate_common(qfs_ctx* ctx, const qfs_circuit* c, const double* target,
   if (p->precision == QFS_MIXED && p->refine_sweeps_max < 0)
     return fail(QFS_EINVAL, "refine_sweeps_max must be >= 0");
   if (p->start_groups < 0) return fail(QFS_EINVAL, "start_groups = %d: need >= 0", p->start_groups);
+  if (p->restart_doubling && (samples || !(p->overtrain_ratio >= 0.0)))
+    return fail(QFS_EINVAL, "restart_doubling needs library-drawn training states and overtrain_ratio >= 0");
   TRY(ctx_check(ctx));
   TRY(set_device(ctx));
+  if (p->restart_doubling) return instantiate_restarting(ctx, c, target, target_dev, gates0, gates_dev, seed, p,
+                                                         gates_out, out_dev, result, start_costs);
   Run R;
   int groups = p->start_groups;
   if (groups <= 0) groups = p->multistarts >= 8 ? 2 : 1;
@@ -1032,6 +1141,7 @@ int instantiate_common(qfs_ctx* ctx, const qfs_circuit* c, const double* target,
   result->converged = o.converged;
   result->best_start = o.best;
   result->fp64_sweeps = o.fp64_sweeps;
+  result->training_states = R.M;
   if (start_costs) std::copy(o.start_costs.begin(), o.start_costs.end(), start_costs);
   return QFS_OK;
 }
@@ -1051,6 +1161,8 @@ void qfs_default_params(qfs_params* p) {
   p->precision = QFS_FP64;
   p->refine_sweeps_max = 50;
   p->start_groups = 0;
+  p->restart_doubling = 0;
+  p->overtrain_ratio = 0.1;
   p->seed = 0;
   p->dist_tol = 1e-8;
   p->diff_tol_r = 1e-5;
@@ -1676,6 +1788,7 @@ int batch_common(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls, 
     results[i].converged = rc[i] <= p->dist_tol;
     results[i].best_start = rb[i];
     results[i].fp64_sweeps = rr[i];
+    results[i].training_states = probs[i].M;
   }
   return QFS_OK;
 }

@@ -69,10 +69,14 @@ void positive_q(std::complex<double>* a, int rows, int cols) {
   }
 }
 
-void generate_samples(uint64_t seed, int n, int M, std::complex<double>* out) {
+void generate_states(uint64_t seed, uint32_t stream, int n, int M, std::complex<double>* out) {
   const size_t N = (size_t)1 << n;
-  for (size_t i = 0; i < N * (size_t)M; ++i) out[i] = complex_normal(seed, 1u, i);
+  for (size_t i = 0; i < N * (size_t)M; ++i) out[i] = complex_normal(seed, stream, i);
   positive_q(out, (int)N, M);
+}
+
+void generate_samples(uint64_t seed, int n, int M, std::complex<double>* out) {
+  generate_states(seed, 1u, n, M, out);
 }
 
 void generate_gates(uint64_t seed, int count, std::complex<double>* out) {

@@ -58,12 +58,13 @@ class Params(C.Structure):
                 ("min_sweeps", C.c_int32), ("plateau_window", C.c_int32),
                 ("precision", C.c_int32), ("refine_sweeps_max", C.c_int32),
                 ("start_groups", C.c_int32), ("seed", C.c_uint64), ("dist_tol", C.c_double),
-                ("diff_tol_r", C.c_double), ("beta", C.c_double)]
+                ("diff_tol_r", C.c_double), ("beta", C.c_double), ("restart_doubling", C.c_int32),
+                ("overtrain_ratio", C.c_double)]
 
 
 class Result(C.Structure):
     _fields_ = [("cost", C.c_double), ("sweeps", C.c_int32), ("converged", C.c_int32),
-                ("best_start", C.c_int32), ("fp64_sweeps", C.c_int32)]
+                ("best_start", C.c_int32), ("fp64_sweeps", C.c_int32), ("training_states", C.c_int32)]
 
 
 _lib = None
@@ -178,6 +179,7 @@ class InstantiateOutput:
     best_start: int
     fp64_sweeps: int
     start_costs: np.ndarray
+    training_states: int = 0
 
 
 def generate_inputs(seed: int, n: int, M: int, S: int, L: int):
@@ -235,7 +237,7 @@ class Context:
                                             C.byref(params), out.ctypes.data, C.byref(res),
                                             costs.ctypes.data))
         return InstantiateOutput(out, res.cost, res.sweeps, bool(res.converged), res.best_start,
-                                 res.fp64_sweeps, costs)
+                                 res.fp64_sweeps, costs, res.training_states)
 
     def instantiate_dev(self, n, pairs, target, samples, init_gates, params: Params, out):
         """Device (torch complex128 CUDA) tensors in and out."""
@@ -250,7 +252,7 @@ class Context:
                                          init_gates.data_ptr(), C.byref(params), out.data_ptr(),
                                          C.byref(res), costs.ctypes.data))
         return InstantiateOutput(out, res.cost, res.sweeps, bool(res.converged), res.best_start,
-                                 res.fp64_sweeps, costs)
+                                 res.fp64_sweeps, costs, res.training_states)
 
     def sweep_once(self, n, pairs, target, samples, gates, precision=QFS_FP64, beta=0.0,
                    want_envs=True):
@@ -294,7 +296,7 @@ class Context:
         for i in range(P):
             gates.append(out[offs[i]:offs[i + 1]].reshape(Ls[i], 4, 4))
         info = [dict(cost=r.cost, sweeps=r.sweeps, converged=bool(r.converged), best_start=r.best_start,
-                     fp64_sweeps=r.fp64_sweeps) for r in res]
+                     fp64_sweeps=r.fp64_sweeps, training_states=r.training_states) for r in res]
         return gates, info
 
     def instantiate_batch_uniform(self, n, pairs, targets, params: Params, init_gates=None):
@@ -316,7 +318,8 @@ class Context:
                                            t.ctypes.data, None, ig.ctypes.data if ig is not None else None,
                                            C.byref(params), out.ctypes.data, res))
         r = np.frombuffer(res, dtype=np.dtype([("cost", "f8"), ("sweeps", "i4"), ("converged", "i4"),
-                                                ("best_start", "i4"), ("fp64_sweeps", "i4")]), count=P)
+                                                ("best_start", "i4"), ("fp64_sweeps", "i4"),
+                                                ("training_states", "i4")], align=True), count=P)
         return out, r["cost"].copy(), r["sweeps"].copy(), r["converged"].astype(bool), r["best_start"].copy()
 
     def instantiate_batch_dev(self, ns, Ls, pairs, targets, samples, init_gates, params: Params, out):

@@ -39,6 +39,7 @@ def test_default_params(lib):
     p = qfs.default_params()
     assert (p.M, p.multistarts, p.max_sweeps, p.min_sweeps) == (2, 16, 10000, 6)
     assert p.dist_tol == 1e-8 and p.beta == 0.0 and p.precision == qfs.QFS_FP64
+    assert p.restart_doubling == 0 and p.overtrain_ratio == 0.1
 
 
 def _call_instantiate(n, pairs, params, target=None):
