@@ -324,7 +324,13 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
-        e2e_res = [ctx.instantiate(n, first.pairs, U_h, prm, Ps_h, G_h) for (U_h, Ps_h, G_h) in hin]
+        if args.restart_doubling:
+            e2e_res = []
+            for i, (U_h, Ps_h, G_h) in enumerate(hin):
+                prm.seed = probs[(args.warmup + i) % n_steps].seed
+                e2e_res.append(ctx.instantiate(n, first.pairs, U_h, prm))
+        else:
+            e2e_res = [ctx.instantiate(n, first.pairs, U_h, prm, Ps_h, G_h) for (U_h, Ps_h, G_h) in hin]
         torch.cuda.synchronize(dev)
         t_e2e = time.perf_counter() - t0
         conv_e2e = sum(r.converged for r in e2e_res)
