@@ -399,6 +399,20 @@ def profile_case(args):
     from paper_2405_12866_gb300 import build as qbuild
     from paper_2405_12866_gb300 import qfs
     qbuild.build()
+    if args.workload == "uneven_blocks":
+        # One batched launch over the 4096 uneven problems (8 starts each).
+        from paper_2405_12866_gb300 import workloads as w
+        import torch
+        probs = w.uneven_blocks(P=args.batch_problems, seed=4, S=8)
+        ns, Ls, pairs, tg, sm, ig = _pack_batch(probs, 8)
+        dev = torch.device("cuda", 0)
+        prm = qfs.default_params(M=0, multistarts=8, max_sweeps=500, dist_tol=1e-8, refine_sweeps_max=20)
+        with qfs.Context(0) as ctx:
+            out = torch.zeros(int(Ls.sum()) * 16, dtype=torch.complex128, device=dev)
+            info = ctx.instantiate_batch_dev(ns, Ls, pairs, torch.from_numpy(tg).to(dev), torch.from_numpy(sm).to(dev),
+                                             torch.from_numpy(ig).to(dev), prm, out)
+        print(json.dumps({"profile_case": "uneven_blocks", "converged": int(sum(r["converged"] for r in info))}))
+        return 0
     if args.workload == "learned":
         # One loss-and-gradient pass of the warm-start network on a batch of
         # 4096 targets: the training GEMMs of one step.
@@ -447,6 +461,9 @@ def run_ours_batch(args):
         batches.append((ns, Ls, pairs, torch.from_numpy(tg).to(dev), torch.from_numpy(sm).to(dev),
                         torch.from_numpy(ig).to(dev), probs, (tg, sm, ig)))
     prm = qfs.default_params(M=0, multistarts=S, max_sweeps=500, dist_tol=1e-8, refine_sweeps_max=20)
+    if args.plateau:
+        # the paper's suggested plateau detection (App. A): window 5, diff_tol_r 1e-5, min_iter 6
+        prm.plateau_window, prm.diff_tol_r, prm.min_sweeps = 5, 1e-5, 6
     outs = [torch.zeros(int(b[1].sum()) * 16, dtype=torch.complex128, device=dev) for b in batches]
 
     def step(i):
@@ -491,7 +508,9 @@ def run_ours_batch(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "c64+f64", "data": "synthetic (seeded Haar-random targets of the stated structures)",
-        "config": {"workload": WORKLOADS["uneven_blocks"][2], "problems_per_step": P, "multistarts": S,
+        "config": {"workload": WORKLOADS["uneven_blocks"][2] + (", plateau detection (window 5, diff_tol_r 1e-5)"
+                                                                if args.plateau else ""),
+                   "problems_per_step": P, "multistarts": S,
                    "tol": 1e-8, "max_sweeps": 500, "l2": "working set on chip; no flush"},
         "converged": int(conv), "instantiations": P * args.steps,
         "roofline": {"bound": "alu", "kernel": "k_batch_sweep (persistent)", "achieved": achieved,
@@ -623,6 +642,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--batch-problems", type=int, default=4096)
+    ap.add_argument("--plateau", action="store_true",
+                    help="batched form: the paper's plateau detection (window 5, diff_tol_r 1e-5, min_iter 6)")
     ap.add_argument("--restart-doubling", action="store_true",
                     help="the paper's double-and-restart of the training states (host targets)")
     ap.add_argument("--learned-train", type=int, default=1 << 20)

@@ -227,7 +227,9 @@ int qfs_gate_update(qfs_ctx* ctx, int32_t count, const double* envs, const doubl
  * and init_gates (host, multistarts x L_i x 16 per problem, concatenated)
  * may be NULL: then problem i draws them as qfs_generate_inputs does with
  * seed p->seed + i.  Every start sweeps in complex64 (FP32 polar update)
- * until its residual cost is <= p->dist_tol or p->max_sweeps; the problem's
+ * until its residual cost is <= p->dist_tol, p->max_sweeps, or a plateau
+ * (p->plateau_window > 0: no relative improvement > p->diff_tol_r over that
+ * many sweeps once p->min_sweeps have run, as in qfs_instantiate); the problem's
  * answer is the lowest-cost start among those that converged at its
  * earliest converged sweep (the lock-step rule of qfs_instantiate), made
  * unitary in FP64, checked in FP64 and refined with up to

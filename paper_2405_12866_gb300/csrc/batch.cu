@@ -106,24 +106,28 @@ __device__ double2 warp_env(const T2* Bs, const T2* Ph, int n, int M, int qa, in
 
 // New gate from E (E[c][r] in lane 4c + r): the polar factor of E^dagger.
 template <typename T2>
-__device__ void warp_update(double2 e, T2* g, double2* sm);
+__device__ void warp_update(double2 e, T2* g, double2* sm, float2* v);
 
+// v: the gate's right singular vectors from its previous update (the Jacobi
+// start; identity at the first sweep), updated in place.
 template <>
-__device__ void warp_update<float2>(double2 e, float2* g, double2* sm) {
+__device__ void warp_update<float2>(double2 e, float2* g, double2* sm, float2* v) {
   const int lane = threadIdx.x & 31;
   const int l16 = lane & 15, r = l16 & 3, c = l16 >> 2;
   const float2 a32{(float)e.x, -(float)e.y};  // A[r][c] = conj(E[c][r])
   float2 q;
-  if (!warp_polar4_f32(a32, &q)) {
+  if (!warp_polar4_f32_warm(a32, v, &q)) {
     const double2 p = warp_polar4(double2{e.x, -e.y}, double2{r == c ? 1.0 : 0.0, 0.0}, sm, nullptr);
     q = float2{(float)p.x, (float)p.y};
+    if (lane < 16) v[l16] = float2{r == c ? 1.f : 0.f, 0.f};  // restart from the identity
   }
   if (lane < 16) g[4 * r + c] = q;
   __syncwarp();
 }
 
 template <>
-__device__ void warp_update<double2>(double2 e, double2* g, double2* sm) {
+__device__ void warp_update<double2>(double2 e, double2* g, double2* sm, float2* v) {
+  (void)v;
   const int lane = threadIdx.x & 31;
   const int l16 = lane & 15, r = l16 & 3, c = l16 >> 2;
   double2 p;
@@ -157,7 +161,7 @@ __device__ double warp_residual(T2* Ph, const T2* g1, const T2* psi, int n, int 
 // (new gate).  Returns the residual cost of the swept gates.
 template <typename T, typename T2>
 __device__ double warp_sweep(T2* Bs, T2* Ph, T2* G, const T2* psi, const T2* phil, const int* pairs,
-                             int n, int M, int L, double2* sm) {
+                             int n, int M, int L, double2* sm, float2* V = nullptr) {
   const int lane = threadIdx.x & 31;
   const int E = M << n;
   for (int i = lane; i < E; i += 32) Bs[i] = psi[i];
@@ -168,7 +172,7 @@ __device__ double warp_sweep(T2* Bs, T2* Ph, T2* G, const T2* psi, const T2* phi
   for (int k = L; k >= 1; --k) {
     const int qa = pairs[2 * (k - 1)], qb = pairs[2 * (k - 1) + 1];
     const double2 e = warp_env<T, T2>(Bs, Ph, n, M, qa, qb);
-    warp_update<T2>(e, G + 16 * (k - 1), sm);
+    warp_update<T2>(e, G + 16 * (k - 1), sm, V ? V + 16 * (k - 1) : nullptr);
     if (k > 1) {
       warp_apply<T2>(Bs, G + 16 * (k - 2), n, M, pairs[2 * (k - 2)], pairs[2 * (k - 2) + 1], true);
       warp_apply<T2>(Ph, G + 16 * (k - 1), n, M, qa, qb, true);
@@ -211,10 +215,11 @@ __global__ void k_batch_sweep(BatchArgs a) {
   __shared__ double2 sm_polar[kBatchMaxWarps][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int E = a.max_elems;
-  float2* base = reinterpret_cast<float2*>(dsm) + (size_t)warp * (2 * E + 16 * a.max_L);
+  float2* base = reinterpret_cast<float2*>(dsm) + (size_t)warp * (2 * E + 32 * a.max_L);
   float2* Bs = base;
   float2* Ph = base + E;
   float2* G = base + 2 * E;
+  float2* V = G + 16 * a.max_L;  // per gate: right singular vectors of its last update
   const int total = a.P * a.S;
   while (true) {
     int item = 0;
@@ -228,23 +233,32 @@ __global__ void k_batch_sweep(BatchArgs a) {
     for (int i = lane; i < 16 * pr.L; i += 32) {
       const double2 g = a.init_gates[goff + i];
       G[i] = float2{(float)g.x, (float)g.y};
+      const int e = i & 15;
+      V[i] = float2{(e & 3) == (e >> 2) ? 1.f : 0.f, 0.f};
     }
     __syncwarp();
     const float2* psi = a.psi32 + pr.state_off;
     const float2* phil = a.phil32 + pr.state_off;
-    int conv = INT_MAX, sweeps = 0;
-    double cost = 4.0;
+    int conv = INT_MAX, sweeps = 0, stall = 0;
+    double cost = 4.0, prev = -1.0;
     for (int sw = 1; sw <= a.max_sweeps; ++sw) {
       // A start that has not converged by its problem's earliest converged
       // sweep can no longer be selected.
       if (sw > *(volatile int*)(a.s_star + p)) break;
-      cost = warp_sweep<float, float2>(Bs, Ph, G, psi, phil, pairs, pr.n, pr.M, pr.L, sm_polar[warp]);
+      cost = warp_sweep<float, float2>(Bs, Ph, G, psi, phil, pairs, pr.n, pr.M, pr.L, sm_polar[warp], V);
       sweeps = sw;
       if (cost <= a.tol) {
         conv = sw;
         if (lane == 0) atomicMin(a.s_star + p, sw);
         break;
       }
+      // Plateau (App. A): no relative improvement > diff_tol_r for
+      // plateau_window sweeps in a row stops this start.
+      if (a.plateau_window > 0 && prev >= 0.0) {
+        stall = fabs(prev) - fabs(cost) > a.diff_tol_r * fabs(cost) ? 0 : stall + 1;
+        if (stall >= a.plateau_window && sw >= a.min_sweeps) break;
+      }
+      prev = cost;
     }
     const size_t ri = (size_t)p * a.S + s;
     if (lane == 0) {
@@ -337,7 +351,7 @@ void launch_batch_prep(const BatchArgs& a, cudaStream_t st) {
 }
 
 size_t batch_sweep_smem(int warps, int max_elems, int max_L) {
-  return (size_t)warps * (2 * max_elems + 16 * max_L) * sizeof(float2);
+  return (size_t)warps * (2 * max_elems + 32 * max_L) * sizeof(float2);
 }
 
 int batch_sweep_blocks_per_sm(int warps, size_t smem) {

@@ -1707,6 +1707,9 @@ int batch_common(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls, 
   a.order = reinterpret_cast<int*>(w + o_order);
   a.max_sweeps = p->max_sweeps;
   a.tol = p->dist_tol;
+  a.plateau_window = p->plateau_window;
+  a.diff_tol_r = p->diff_tol_r;
+  a.min_sweeps = p->min_sweeps;
   a.max_elems = max_elems;
   a.max_L = max_L;
   a.gates_out = reinterpret_cast<double2*>(w + o_gout);

@@ -221,6 +221,9 @@ struct BatchArgs {
   const int* order;       // problem indices, largest work first
   int max_sweeps;
   double tol;
+  int plateau_window;     // > 0: a start stops after this many sweeps without relative
+  double diff_tol_r;      //   improvement > diff_tol_r (App. A), once min_sweeps have run
+  int min_sweeps;
   int max_elems, max_L;   // largest N*M and L in the batch (shared-memory slices)
   double2* gates_out;     // selected gates, FP64 (L x 16 per problem)
   double* res_cost;

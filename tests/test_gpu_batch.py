@@ -74,3 +74,32 @@ def test_batch_seeded_draws(ctx):
     g_exp, i_exp = ctx.instantiate_batch([(p.n, p.pairs, p.U) for p in probs], prm, samples, inits)
     for a, b in zip(g_seed, g_exp):
         assert np.max(np.abs(a - b)) < 1e-12
+
+
+def test_batch_plateau_stops_stuck_starts_early():
+    """With the paper's plateau detection (App. A) the starts of problems
+    that do not converge stop early; converging problems still converge."""
+    import torch
+    from paper_2405_12866_gb300 import build, qfs
+    from paper_2405_12866_gb300 import workloads as w
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    build.build()
+    probs = w.uneven_blocks(P=512, seed=9, S=8)
+    ctx = qfs.Context(0)
+    args = [(pr.n, pr.pairs, pr.U) for pr in probs]
+    samples = [pr.samples() for pr in probs]
+    inits = [pr.init_gates()[:8] for pr in probs]
+    base = qfs.default_params(M=0, multistarts=8, max_sweeps=300, dist_tol=1e-8, refine_sweeps_max=20)
+    plat = qfs.default_params(M=0, multistarts=8, max_sweeps=300, dist_tol=1e-8, refine_sweeps_max=20,
+                              plateau_window=5, diff_tol_r=1e-5, min_sweeps=6)
+    _, i0 = ctx.instantiate_batch(args, base, samples, inits)
+    _, i1 = ctx.instantiate_batch(args, plat, samples, inits)
+    c0 = sum(r["converged"] for r in i0)
+    c1 = sum(r["converged"] for r in i1)
+    stuck0 = [r["sweeps"] for r in i0 if not r["converged"]]
+    stuck1 = [r["sweeps"] for r in i1 if not r["converged"]]
+    assert c1 >= 0.98 * c0
+    if stuck0 and stuck1:
+        assert np.mean(stuck1) < np.mean(stuck0)
+    ctx.close()
