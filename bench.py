@@ -44,6 +44,7 @@ WORKLOADS = {
     "chain_n3": ("chain_n3", 0, "n=3 chain of 4 gates, M=4, 1 start, FP64, tol 1e-10"),
     "uneven_blocks": ("uneven_blocks", 1, "4096 problems, n uniform in {3,4,5}, 2-10 nearest-neighbour gates, "
                       "M=2^(n-1), 8 starts, complex64 sweeps + FP64 check/refine, one persistent launch"),
+    "qf_vs_qfs": ("qf_vs_qfs", 0, "full-unitary QFactor vs QFactor-Sample with double-and-restart, n = 3..10"),
     "learned": ("learned", 1, "learned warm start: 4-qubit 6-gate structure, MLP 256-3x1024-192 trained on "
                 "method-generated pairs; 65536 fresh targets, predicted start then 8 random starts as fallback"),
 }
@@ -632,6 +633,61 @@ def run_ours_learned(args):
     return 0
 
 
+def run_qf_vs_qfs(args):
+    """Full-unitary QFactor (M = 2^n) against QFactor-Sample with the paper's
+    double-and-restart (M from 2, overtrain ratio 0.1), on the same kernels,
+    the same targets and the same initial gates: time per instantiation for
+    n = 3..args.qf_max_n, brick walls of 4 half-layers (FP64, 8 starts).
+    The paper's ratios (QF-J over QFS-J on A100) are context only."""
+    import torch
+    from paper_2405_12866_gb300 import build as qbuild
+    from paper_2405_12866_gb300 import qfs
+    from paper_2405_12866_gb300 import workloads as w
+    qbuild.build()
+    ctx = qfs.Context(0)
+    rows = []
+    S, sweeps, tol = 8, 500, 1e-8
+    for n in range(3, args.qf_max_n + 1):
+        pairs = w.brick_pairs(n, 4)
+        times = {"qf": [], "qfs": []}
+        conv = {"qf": 0, "qfs": 0}
+        ms = []
+        for t in range(args.steps + args.warmup):
+            p = w.make_problem(f"qf_{n}", n, pairs, 1 << n, S, 7000 + 100 * n + t, 9000 + 100 * n + t, tol, sweeps)
+            for kind in ("qf", "qfs"):
+                if kind == "qf":
+                    prm = qfs.default_params(M=1 << n, multistarts=S, max_sweeps=sweeps, dist_tol=tol, seed=p.seed)
+                else:
+                    prm = qfs.default_params(M=2, multistarts=S, max_sweeps=sweeps, dist_tol=tol, seed=p.seed,
+                                             restart_doubling=1, overtrain_ratio=0.1)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = ctx.instantiate(n, pairs, p.U, prm)
+                dt = time.perf_counter() - t0
+                if t >= args.warmup:
+                    times[kind].append(dt)
+                    conv[kind] += int(r.converged)
+                    if kind == "qfs":
+                        ms.append(int(r.training_states))
+        tq, ts = float(np.mean(times["qf"])), float(np.mean(times["qfs"]))
+        rows.append({"n": n, "gates": len(pairs), "qf_s": tq, "qfs_s": ts, "ratio": tq / ts,
+                     "qf_converged": conv["qf"], "qfs_converged": conv["qfs"], "of": args.steps,
+                     "qfs_final_M": ms})
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    big = [r["ratio"] for r in rows if r["n"] > 8]
+    line = {"metric": "QF/QFS instantiation-time ratio (same kernels)", "value": float(np.exp(np.mean(np.log(
+        [r["ratio"] for r in rows])))), "unit": "x (geometric mean over n)", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (Haar-random brick-wall targets)",
+        "config": {"workload": "QF (M = 2^n) vs QFS (double-and-restart from M = 2), brick walls of 4 half-layers, "
+                               "n = 3..%d, 8 starts, tol 1e-8" % args.qf_max_n},
+        "ratio_above_8_qubits": float(np.exp(np.mean(np.log(big)))) if big else None,
+        "rows": rows, "paper_context": "QF-J / QFS-J on A100: 17.7x average, 69x above 8 qubits (Sec. 4)"}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -646,6 +702,7 @@ def main():
                     help="batched form: the paper's plateau detection (window 5, diff_tol_r 1e-5, min_iter 6)")
     ap.add_argument("--restart-doubling", action="store_true",
                     help="the paper's double-and-restart of the training states (host targets)")
+    ap.add_argument("--qf-max-n", type=int, default=10)
     ap.add_argument("--learned-train", type=int, default=1 << 20)
     ap.add_argument("--learned-eval", type=int, default=65536)
     ap.add_argument("--learned-epochs", type=int, default=40)
@@ -664,6 +721,8 @@ def main():
         return run_ours_batch(args)
     if args.workload == "learned":
         return run_ours_learned(args)
+    if args.workload == "qf_vs_qfs":
+        return run_qf_vs_qfs(args)
     return run_ours(args)
 
 
