@@ -45,6 +45,8 @@ WORKLOADS = {
     "uneven_blocks": ("uneven_blocks", 1, "4096 problems, n uniform in {3,4,5}, 2-10 nearest-neighbour gates, "
                       "M=2^(n-1), 8 starts, complex64 sweeps + FP64 check/refine, one persistent launch"),
     "qf_vs_qfs": ("qf_vs_qfs", 0, "full-unitary QFactor vs QFactor-Sample with double-and-restart, n = 3..10"),
+    "states_ablation": ("states_ablation", 0, "Haar vs computational-basis training states (Appendix D): "
+                        "smallest M that generalises and double-and-restart, brick walls n = 6, 8, 10"),
     "learned": ("learned", 1, "learned warm start: 4-qubit 6-gate structure, MLP 256-3x1024-192 trained on "
                 "method-generated pairs; 65536 fresh targets, predicted start then 8 random starts as fallback"),
 }
@@ -688,6 +690,83 @@ def run_qf_vs_qfs(args):
     return 0
 
 
+def run_states_ablation(args):
+    """Training-state distribution (Appendix D): Haar states against
+    distinct computational-basis states as training data, on the same
+    kernels, targets and initial gates.  For brick walls of 4 half-layers
+    (n = 6, 8, 10; FP64, 8 starts, tol 1e-8) and args.steps targets each:
+    (a) fixed M = 2, 4, ..., 2^n: how many results generalise, i.e. converge
+    and have a full-unitary cost ||U - C||_F^2 / N (Eq. 1 per state,
+    evaluated on the host from the returned gates) within tol (1 + otr);
+    M_gen of a target = the smallest M whose result generalises; (b) double-and-restart
+    from M = 2 with validation states of the same distribution: the final M,
+    whether the returned gates generalise, time per instantiation."""
+    import torch
+    from paper_2405_12866_gb300 import build as qbuild
+    from paper_2405_12866_gb300 import qfs
+    from paper_2405_12866_gb300 import workloads as w
+    qbuild.build()
+    ctx = qfs.Context(0)
+    S, sweeps, tol, otr, T = 8, 500, 1e-8, 0.1, max(1, args.steps)
+    names = {qfs.QFS_STATES_HAAR: "haar", qfs.QFS_STATES_BASIS: "basis"}
+    rows = []
+    for n in args.ablation_n:
+        pairs = w.brick_pairs(n, 4)
+        N = 1 << n
+        probs = [w.make_problem(f"abl_{n}", n, pairs, 2, S, 5000 + 100 * n + t, 6000 + 100 * n + t, tol, sweeps)
+                 for t in range(T)]
+
+        def generalises(p, gates):
+            C = w.target_unitary(gates, pairs, n)
+            return float(np.sum(np.abs(p.U - C) ** 2) / N)
+
+        row = {"n": n, "gates": len(pairs), "targets": T}
+        for dist, name in names.items():
+            fixed, m_gen = {}, [None] * T
+            M = 2
+            while M <= N and any(m is None for m in m_gen):
+                ok = conv = 0
+                for t, p in enumerate(probs):
+                    prm = qfs.default_params(M=M, multistarts=S, max_sweeps=sweeps, dist_tol=tol, seed=p.seed,
+                                             training_distribution=dist)
+                    r = ctx.instantiate(n, pairs, p.U, prm)
+                    conv += int(r.converged)
+                    good = r.converged and generalises(p, r.gates) <= tol * (1 + otr)
+                    ok += int(good)
+                    if good and m_gen[t] is None:
+                        m_gen[t] = M
+                fixed[M] = {"converged": conv, "generalised": ok}
+                M *= 2
+            final_m, gen, times = [], 0, []
+            for t, p in enumerate(probs):
+                prm = qfs.default_params(M=2, multistarts=S, max_sweeps=sweeps, dist_tol=tol, seed=p.seed,
+                                         restart_doubling=1, overtrain_ratio=otr, training_distribution=dist)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = ctx.instantiate(n, pairs, p.U, prm)
+                times.append(time.perf_counter() - t0)
+                final_m.append(int(r.training_states))
+                gen += int(r.converged and generalises(p, r.gates) <= tol * (1 + otr))
+            row[name] = {"M_gen": m_gen, "fixed_M": fixed, "restart_final_M": final_m,
+                         "restart_generalised": gen, "restart_s": float(np.mean(times))}
+        print(json.dumps(row), file=sys.stderr, flush=True)
+        rows.append(row)
+    ratios = [b / h for r in rows for b, h in zip(r["basis"]["M_gen"], r["haar"]["M_gen"]) if b and h]
+    line = {"metric": "training data needed to generalise, computational-basis / Haar states (per-target M_gen ratio)",
+            "value": float(np.exp(np.mean(np.log(ratios)))) if ratios else None,
+            "unit": "x (geometric mean over targets)", "n_gpus": 1, "steps": T, "warmup": 0,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (Haar-random brick-wall targets)",
+            "config": {"workload": "Haar vs computational-basis training states, brick walls of 4 half-layers, "
+                                   "n = %s, 8 starts, tol 1e-8, overtrain ratio 0.1, %d targets per n"
+                                   % (",".join(map(str, args.ablation_n)), T)},
+            "rows": rows,
+            "paper_context": "Appendix D: computational-basis training needs much more data than Haar states"}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -703,6 +782,7 @@ def main():
     ap.add_argument("--restart-doubling", action="store_true",
                     help="the paper's double-and-restart of the training states (host targets)")
     ap.add_argument("--qf-max-n", type=int, default=10)
+    ap.add_argument("--ablation-n", type=int, nargs="+", default=[6, 8, 10])
     ap.add_argument("--learned-train", type=int, default=1 << 20)
     ap.add_argument("--learned-eval", type=int, default=65536)
     ap.add_argument("--learned-epochs", type=int, default=40)
@@ -723,6 +803,8 @@ def main():
         return run_ours_learned(args)
     if args.workload == "qf_vs_qfs":
         return run_qf_vs_qfs(args)
+    if args.workload == "states_ablation":
+        return run_states_ablation(args)
     return run_ours(args)
 
 

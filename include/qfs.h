@@ -88,6 +88,10 @@ typedef struct {
                                 c_train <= dist_tol and c_val <= (1 + overtrain_ratio) c_train.
                                 Needs library-drawn training states (qfs_instantiate). */
   double overtrain_ratio;    /* overtrain_ratio of the generalisation check */
+  int32_t training_distribution; /* distribution of library-drawn training and validation states
+                                    (Appendix D): QFS_STATES_HAAR (columns of a Haar-random
+                                    unitary) or QFS_STATES_BASIS (distinct computational-basis
+                                    states, uniform without replacement) */
 } qfs_params;
 
 typedef struct {
@@ -99,11 +103,14 @@ typedef struct {
   int32_t training_states; /* M of the (last) attempt */
 } qfs_result;
 
+#define QFS_STATES_HAAR 0
+#define QFS_STATES_BASIS 1
+
 /* Fill *p with defaults: M = 2, multistarts = 16, max_sweeps = 10000,
  * min_sweeps = 6, plateau_window = 0, precision = QFS_FP64,
  * refine_sweeps_max = 50, start_groups = 0, seed = 0, dist_tol = 1e-8,
- * diff_tol_r = 1e-5, beta = 0, restart_doubling = 0, overtrain_ratio = 0.1
- * (the paper's suggested values, with plateau detection and
+ * diff_tol_r = 1e-5, beta = 0, restart_doubling = 0, overtrain_ratio = 0.1,
+ * training_distribution = QFS_STATES_HAAR (the paper's suggested values, with plateau detection and
  * double-and-restart off).  With restart_doubling, attempt a > 0 draws its
  * training states (stream 1) and validation states (stream 5) from seed
  * XOR (a * 0x9E3779B97F4A7C15); attempt 0 validates with stream 5 of seed. */
@@ -171,6 +178,18 @@ int qfs_dataflow_trace_read(qfs_ctx* ctx, uint64_t* out, int64_t capacity, int32
  * S x L x 16 (either may be NULL). */
 int qfs_generate_inputs(uint64_t seed, int32_t n, int32_t M, int32_t S, int32_t L,
                         double* samples_out, double* gates_out);
+
+/* The library's draw of M states of either training distribution (host
+ * only, no GPU), as qfs_instantiate makes it for training_distribution =
+ * distribution: QFS_STATES_HAAR as in qfs_generate_inputs on the given
+ * stream; QFS_STATES_BASIS the computational-basis states e_{p_0} ..
+ * e_{p_{M-1}}, p the first M entries of a partial Fisher-Yates shuffle of
+ * 0..N-1 whose step j swaps positions j and j + floor(w_j (N - j) / 2^32),
+ * w_j = word 0 of Philox block (j, stream) under key = seed.  Streams: 1 =
+ * training states, 5 = validation states.  out: host N x M complex128,
+ * row-major.  QFS_EINVAL for n, M or distribution out of range. */
+int qfs_generate_states(uint64_t seed, int32_t distribution, uint32_t stream, int32_t n, int32_t M,
+                        double* out);
 
 /* Instantiate `target` (host, N x N) on `circuit`: draws samples and
  * initial gates from p->seed, runs the multistart sweeps and writes the

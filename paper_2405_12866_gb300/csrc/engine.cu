@@ -24,6 +24,7 @@
 namespace qfs {
 void generate_samples(uint64_t seed, int n, int M, std::complex<double>* out);
 void generate_states(uint64_t seed, uint32_t stream, int n, int M, std::complex<double>* out);
+void draw_states(int kind, uint64_t seed, uint32_t stream, int n, int M, std::complex<double>* out);
 void generate_gates(uint64_t seed, int count, std::complex<double>* out);
 }  // namespace qfs
 
@@ -1044,11 +1045,11 @@ int instantiate_restarting(qfs_ctx* ctx, const qfs_circuit* c, const double* tar
     }
     const uint64_t sa = attempt_seed(seed, attempt);
     std::vector<std::complex<double>> h((size_t)R.sN);
-    generate_states(sa, 1u, n, M, h.data());
+    draw_states(p->training_distribution, sa, 1u, n, M, h.data());
     CK(cudaMemcpyAsync(R.psi64, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
     if (validate) {
-      generate_states(sa, 5u, n, M, h.data());
+      draw_states(p->training_distribution, sa, 5u, n, M, h.data());
       CK(cudaMemcpyAsync(R.psi_val64, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
       launch_gemm_upsi(R.U, R.psi_val64, R.phil_val64, (int)R.N, M, st);
       ctx->prof.launches[QFS_PROF_GEMM] += 1;
@@ -1095,6 +1096,9 @@ int instantiate_common(qfs_ctx* ctx, const qfs_circuit* c, const double* target,
   if (p->precision == QFS_MIXED && p->refine_sweeps_max < 0)
     return fail(QFS_EINVAL, "refine_sweeps_max must be >= 0");
   if (p->start_groups < 0) return fail(QFS_EINVAL, "start_groups = %d: need >= 0", p->start_groups);
+  if (p->training_distribution != QFS_STATES_HAAR && p->training_distribution != QFS_STATES_BASIS)
+    return fail(QFS_EINVAL, "training_distribution = %d: need QFS_STATES_HAAR or QFS_STATES_BASIS",
+                p->training_distribution);
   if (p->restart_doubling && (samples || !(p->overtrain_ratio >= 0.0)))
     return fail(QFS_EINVAL, "restart_doubling needs library-drawn training states and overtrain_ratio >= 0");
   TRY(ctx_check(ctx));
@@ -1118,7 +1122,7 @@ int instantiate_common(qfs_ctx* ctx, const qfs_circuit* c, const double* target,
                        samples_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
   } else {
     std::vector<std::complex<double>> h((size_t)R.sN);
-    generate_samples(seed, R.n, R.M, h.data());
+    draw_states(p->training_distribution, seed, 1u, R.n, R.M, h.data());
     CK(cudaMemcpyAsync(R.psi64, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
   }
@@ -1163,6 +1167,7 @@ void qfs_default_params(qfs_params* p) {
   p->start_groups = 0;
   p->restart_doubling = 0;
   p->overtrain_ratio = 0.1;
+  p->training_distribution = QFS_STATES_HAAR;
   p->seed = 0;
   p->dist_tol = 1e-8;
   p->diff_tol_r = 1e-5;
@@ -1330,6 +1335,18 @@ int qfs_generate_inputs(uint64_t seed, int32_t n, int32_t M, int32_t S, int32_t 
     if (S < 1 || L < 1) return fail(QFS_EINVAL, "S = %d, L = %d: need >= 1", S, L);
     qfs::generate_gates(seed, S * L, reinterpret_cast<std::complex<double>*>(gates_out));
   }
+  return QFS_OK;
+}
+
+int qfs_generate_states(uint64_t seed, int32_t distribution, uint32_t stream, int32_t n, int32_t M,
+                        double* out) {
+  g_err.clear();
+  if (n < 2 || n > QFS_MAX_QUBITS) return fail(QFS_EINVAL, "n = %d out of [2, %d]", n, QFS_MAX_QUBITS);
+  if (M < 1 || (long long)M > (1LL << n)) return fail(QFS_EINVAL, "M = %d out of [1, 2^n]", M);
+  if (distribution != QFS_STATES_HAAR && distribution != QFS_STATES_BASIS)
+    return fail(QFS_EINVAL, "distribution = %d: need QFS_STATES_HAAR or QFS_STATES_BASIS", distribution);
+  if (!out) return fail(QFS_EINVAL, "out is NULL");
+  qfs::draw_states(distribution, seed, stream, n, M, reinterpret_cast<std::complex<double>*>(out));
   return QFS_OK;
 }
 
@@ -1639,6 +1656,9 @@ int batch_common(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls, 
   if (p->max_sweeps < 1) return fail(QFS_EINVAL, "max_sweeps = %d: need >= 1", p->max_sweeps);
   if (!(p->dist_tol >= 0.0)) return fail(QFS_EINVAL, "dist_tol = %g", p->dist_tol);
   if (p->beta != 0.0) return fail(QFS_EUNSUPPORTED, "the batched form runs beta = 0 only");
+  if (p->training_distribution != QFS_STATES_HAAR && p->training_distribution != QFS_STATES_BASIS)
+    return fail(QFS_EINVAL, "training_distribution = %d: need QFS_STATES_HAAR or QFS_STATES_BASIS",
+                p->training_distribution);
   std::vector<BatchProblem> probs(P);
   long long pair_off = 0, state_off = 0, target_off = 0, gate_off = 0, gout_off = 0;
   int max_elems = 0, max_L = 0;
@@ -1731,7 +1751,8 @@ int batch_common(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls, 
   } else {
     hs.resize(state_off);
     host_parallel_for(P, [&](int i) {
-      generate_samples(p->seed + (uint64_t)i, probs[i].n, probs[i].M, hs.data() + probs[i].state_off);
+      draw_states(p->training_distribution, p->seed + (uint64_t)i, 1u, probs[i].n, probs[i].M,
+                  hs.data() + probs[i].state_off);
     });
     CK(cudaMemcpyAsync(w + o_psi64, hs.data(), sizeof(double2) * state_off, cudaMemcpyHostToDevice, st));
   }

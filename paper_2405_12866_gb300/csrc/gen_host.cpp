@@ -8,6 +8,7 @@
 // normal.  The Q factor (positive real R diagonal) of a complex Gaussian
 // matrix is Haar distributed (Mezzadri 2007); the training states are such
 // columns, as the paper's Appendix A describes them.
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstdint>
@@ -73,6 +74,34 @@ void generate_states(uint64_t seed, uint32_t stream, int n, int M, std::complex<
   const size_t N = (size_t)1 << n;
   for (size_t i = 0; i < N * (size_t)M; ++i) out[i] = complex_normal(seed, stream, i);
   positive_q(out, (int)N, M);
+}
+
+// M distinct computational-basis states, uniform without replacement: a
+// partial Fisher-Yates shuffle of 0..N-1 in which step j swaps position j
+// with j + floor(w_j (N - j) / 2^32), w_j = word 0 of Philox block j of
+// (seed, stream).  Column j of out (N x M, row-major) is e_{perm[j]}.
+void generate_basis_states(uint64_t seed, uint32_t stream, int n, int M, std::complex<double>* out) {
+  const size_t N = (size_t)1 << n;
+  std::vector<uint32_t> perm(N);
+  for (size_t i = 0; i < N; ++i) perm[i] = (uint32_t)i;
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  for (int j = 0; j < M; ++j) {
+    const uint32_t ctr[4] = {(uint32_t)j, 0u, stream, 0u};
+    uint32_t x[4];
+    philox4x32_10(ctr, key, x);
+    const size_t r = (size_t)j + (size_t)(((uint64_t)x[0] * (uint64_t)(N - (size_t)j)) >> 32);
+    const uint32_t t = perm[j];
+    perm[j] = perm[r];
+    perm[r] = t;
+  }
+  std::fill(out, out + N * (size_t)M, std::complex<double>(0.0, 0.0));
+  for (int j = 0; j < M; ++j) out[(size_t)perm[j] * M + j] = 1.0;
+}
+
+// States of distribution kind (0: Haar, 1: computational basis).
+void draw_states(int kind, uint64_t seed, uint32_t stream, int n, int M, std::complex<double>* out) {
+  if (kind == 1) generate_basis_states(seed, stream, n, M, out);
+  else generate_states(seed, stream, n, M, out);
 }
 
 void generate_samples(uint64_t seed, int n, int M, std::complex<double>* out) {

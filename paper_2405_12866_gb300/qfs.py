@@ -27,11 +27,13 @@ QFS_EUNSUPPORTED = -5
 QFS_ENONFINITE = -6
 QFS_FP64 = 0
 QFS_MIXED = 1
+QFS_STATES_HAAR = 0
+QFS_STATES_BASIS = 1
 
 # Every function the header declares; the CPU tests check the library exports them.
 EXPORTS = [
     "qfs_default_params", "qfs_create", "qfs_destroy", "qfs_last_error", "qfs_device_sms",
-    "qfs_generate_inputs", "qfs_instantiate", "qfs_instantiate_ex", "qfs_instantiate_dev",
+    "qfs_generate_inputs", "qfs_generate_states", "qfs_instantiate", "qfs_instantiate_ex", "qfs_instantiate_dev",
     "qfs_sweep_once", "qfs_gate_update", "qfs_profile_enable", "qfs_profile_reset",
     "qfs_profile_read", "qfs_sweep_once_noalloc", "qfs_instantiate_batch",
     "qfs_instantiate_batch_dev", "qfs_gemm_bf16_dev", "qfs_ws_create", "qfs_ws_destroy", "qfs_ws_params",
@@ -59,7 +61,7 @@ class Params(C.Structure):
                 ("precision", C.c_int32), ("refine_sweeps_max", C.c_int32),
                 ("start_groups", C.c_int32), ("seed", C.c_uint64), ("dist_tol", C.c_double),
                 ("diff_tol_r", C.c_double), ("beta", C.c_double), ("restart_doubling", C.c_int32),
-                ("overtrain_ratio", C.c_double)]
+                ("overtrain_ratio", C.c_double), ("training_distribution", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -89,6 +91,7 @@ def lib():
     L.qfs_last_error.restype = C.c_char_p
     L.qfs_device_sms.argtypes = [_P]
     L.qfs_generate_inputs.argtypes = [C.c_uint64, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P, _P]
+    L.qfs_generate_states.argtypes = [C.c_uint64, C.c_int32, C.c_uint32, C.c_int32, C.c_int32, _P]
     L.qfs_instantiate.argtypes = [_P, C.POINTER(Circuit), _P, C.POINTER(Params), _P,
                                   C.POINTER(Result), _P]
     L.qfs_instantiate_ex.argtypes = [_P, C.POINTER(Circuit), _P, _P, _P, C.POINTER(Params), _P,
@@ -188,6 +191,15 @@ def generate_inputs(seed: int, n: int, M: int, S: int, L: int):
     gates = np.zeros((S, L, 4, 4), dtype=np.complex128)
     _check(lib().qfs_generate_inputs(seed, n, M, S, L, samples.ctypes.data, gates.ctypes.data))
     return samples, gates
+
+
+def generate_states(seed: int, distribution: int, stream: int, n: int, M: int) -> np.ndarray:
+    """The library's own draw of M states (N x M) of either training
+    distribution (QFS_STATES_HAAR or QFS_STATES_BASIS) on a stream
+    (1 = training, 5 = validation)."""
+    out = np.zeros((1 << n, M), dtype=np.complex128)
+    _check(lib().qfs_generate_states(seed, distribution, stream, n, M, out.ctypes.data))
+    return out
 
 
 class Context:

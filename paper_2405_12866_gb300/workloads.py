@@ -124,6 +124,45 @@ def sample_states(seed: int, n: int, M: int, stream: int = STREAM_SAMPLES) -> np
     return positive_qr_q(g)
 
 
+def basis_indices(seed: int, n: int, M: int, stream: int = STREAM_SAMPLES) -> np.ndarray:
+    """M distinct computational-basis indices, uniform without replacement:
+    a partial Fisher-Yates shuffle of 0..N-1 in which step j swaps position
+    j with position j + floor(w_j (N - j) / 2^32), w_j = word 0 of Philox
+    block j of (seed, stream)."""
+    N = 1 << n
+    if not (1 <= M <= N):
+        raise ValueError(f"need 1 <= M <= 2^n, got M={M}, n={n}")
+    w = _blocks(seed, stream, 0, M)[:, 0].astype(np.uint64)
+    perm = np.arange(N, dtype=np.int64)
+    for j in range(M):
+        r = j + int((w[j] * np.uint64(N - j)) >> np.uint64(32))
+        perm[j], perm[r] = perm[r], perm[j]
+    return perm[:M].copy()
+
+
+def basis_states(seed: int, n: int, M: int, stream: int = STREAM_SAMPLES) -> np.ndarray:
+    """M distinct computational-basis states (columns e_i, i from
+    basis_indices) as an N x M complex128 matrix: the alternative training
+    distribution of the paper's Appendix D."""
+    idx = basis_indices(seed, n, M, stream)
+    out = np.zeros((1 << n, M), dtype=np.complex128)
+    out[idx, np.arange(M)] = 1.0
+    return out
+
+
+STATES_HAAR = 0
+STATES_BASIS = 1
+
+
+def training_states(kind: int, seed: int, n: int, M: int, stream: int = STREAM_SAMPLES) -> np.ndarray:
+    """States of either distribution (STATES_HAAR or STATES_BASIS)."""
+    if kind == STATES_HAAR:
+        return sample_states(seed, n, M, stream)
+    if kind == STATES_BASIS:
+        return basis_states(seed, n, M, stream)
+    raise ValueError(f"unknown state distribution {kind}")
+
+
 def attempt_seed(seed: int, attempt: int) -> int:
     """Seed of the training and validation states of a double-and-restart
     attempt (attempt 0 uses the run seed itself)."""

@@ -40,6 +40,7 @@ def test_default_params(lib):
     assert (p.M, p.multistarts, p.max_sweeps, p.min_sweeps) == (2, 16, 10000, 6)
     assert p.dist_tol == 1e-8 and p.beta == 0.0 and p.precision == qfs.QFS_FP64
     assert p.restart_doubling == 0 and p.overtrain_ratio == 0.1
+    assert p.training_distribution == qfs.QFS_STATES_HAAR
 
 
 def _call_instantiate(n, pairs, params, target=None):
@@ -70,6 +71,7 @@ def test_circuit_validation(lib, n, pairs, frag):
     (dict(M=0), "M = 0"), (dict(M=9), "M = 9"), (dict(multistarts=0), "multistarts"),
     (dict(max_sweeps=0), "max_sweeps"), (dict(precision=7), "precision"),
     (dict(beta=1.0), "beta"), (dict(beta=-0.1), "beta"), (dict(dist_tol=-1.0), "dist_tol"),
+    (dict(training_distribution=2), "training_distribution"),
 ])
 def test_param_validation(lib, kw, frag):
     code, msg = _call_instantiate(3, [(0, 1), (1, 2)], qfs.default_params(**{"M": 4, **kw}))
@@ -98,3 +100,20 @@ def test_library_draws_match_generator(lib, n, M, S, L, seed):
     assert np.allclose(samples, w.sample_states(seed, n, M), atol=1e-12)
     assert np.allclose(gates, w.initial_gates(seed, S, L), atol=1e-12)
     assert np.allclose(samples.conj().T @ samples, np.eye(M), atol=1e-13)
+
+
+@pytest.mark.parametrize("n,M,seed,stream", [(2, 4, 0, 1), (3, 5, 9, 5), (6, 17, 2**40 + 3, 1), (10, 64, 31, 5)])
+def test_library_state_draws_match_generator(lib, n, M, seed, stream):
+    """Both training distributions (Appendix D): the library's draw equals
+    the seeded generator's, bit for bit."""
+    haar = qfs.generate_states(seed, qfs.QFS_STATES_HAAR, stream, n, M)
+    assert np.allclose(haar, w.sample_states(seed, n, M, stream), atol=1e-12)
+    basis = qfs.generate_states(seed, qfs.QFS_STATES_BASIS, stream, n, M)
+    assert np.array_equal(basis, w.basis_states(seed, n, M, stream))
+
+
+def test_state_draw_validation(lib):
+    out = np.zeros((8, 2), np.complex128)
+    for args, frag in [((0, 2, 1, 3, 2), "distribution"), ((0, 1, 1, 3, 9), "M = 9"), ((0, 1, 1, 1, 1), "n = 1")]:
+        assert lib.qfs_generate_states(*args, out.ctypes.data) == qfs.QFS_EINVAL
+        assert frag in lib.qfs_last_error().decode()

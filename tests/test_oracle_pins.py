@@ -435,3 +435,77 @@ def test_restart_doubles_until_the_target_generalises():
         assert r.validation_cost <= (1 + otr) * r.cost
     # generalisation to all states: ||U - C||_F^2 / N is the M = N sample cost
     assert o.full_cost(p.U, r.gates, p.pairs, p.n) / (1 << p.n) <= 1e-10 * (1 + otr)
+
+
+# ------------------------------------ training-state distribution (Appendix D)
+
+def test_basis_draw_is_distinct_and_uniform():
+    """The computational-basis draw gives M distinct unit vectors, and every
+    M-subset is equally likely (partial Fisher-Yates), checked by counting
+    over seeds: N = 4, M = 2 has 6 unordered pairs, each 1/6."""
+    P = w.basis_states(5, 5, 32)
+    assert np.array_equal(P.conj().T @ P, np.eye(32))
+    assert np.array_equal(np.sort(w.basis_indices(5, 5, 32)), np.arange(32))
+    counts = {}
+    T = 6000
+    for seed in range(T):
+        key = tuple(sorted(w.basis_indices(seed, 2, 2)))
+        counts[key] = counts.get(key, 0) + 1
+    assert len(counts) == 6
+    chi2 = sum((c - T / 6) ** 2 / (T / 6) for c in counts.values())
+    assert chi2 < 20.5  # 5 degrees of freedom, p ~ 0.001
+
+
+def test_all_basis_states_give_the_full_cost():
+    """With all N computational-basis states (in any order) the sample cost
+    (residual form) equals the full cost of Eq. (1) divided by N."""
+    p = w.chain_n3(target_seed=4)
+    G = w.initial_gates(9, 1, p.L)[0]
+    Psi = w.basis_states(3, p.n, 1 << p.n)
+    c = o.sample_cost(p.U @ Psi, Psi, G, p.pairs, p.n)
+    assert abs(c - o.full_cost(p.U, G, p.pairs, p.n) / (1 << p.n)) < 1e-13
+
+
+def test_basis_states_blind_to_a_phase_on_unset_qubit():
+    """Appendix D's example: a phase diag(1, e^{i alpha}) on qubit 0 before
+    the circuit acts trivially on every basis state whose qubit 0 is |0>, so
+    a training set of such states cannot tell alpha from alpha'; one Haar
+    state can."""
+    n = 3
+    pairs = [(0, 1), (1, 2), (0, 1)]
+    rest = w.haar_gates(3, w.STREAM_TARGET_GATES, 2)
+
+    def circuit(alpha):
+        ph = np.diag([1, 1, np.exp(1j * alpha), np.exp(1j * alpha)])  # on (0, 1): local index 2*b0 + b1
+        return np.stack([ph, rest[0], rest[1]])
+
+    U = w.target_unitary(circuit(0.7), pairs, n)
+    zero_q0 = np.zeros((8, 4), np.complex128)
+    zero_q0[[0, 1, 2, 3], [0, 1, 2, 3]] = 1.0  # rows 0..3: bit 2 (qubit 0) is 0
+    assert o.sample_cost(U @ zero_q0, zero_q0, circuit(2.1), pairs, n) < 1e-28
+    haar = w.sample_states(1, n, 1)
+    assert o.sample_cost(U @ haar, haar, circuit(2.1), pairs, n) > 1e-3
+
+
+def test_basis_states_need_more_data_than_haar_states():
+    """Appendix D, numerically (seeded): on n = 6 brick-wall circuits of 10
+    gates, M = 16 Haar training states give results that generalise (full
+    cost / N within dist_tol (1 + otr)) while M = 16 computational-basis
+    states fit the training set as well but do not generalise; at M = 32
+    both do."""
+    n, tol, otr = 6, 1e-8, 0.1
+    pairs = w.brick_pairs(n, 4)
+    gen = {w.STATES_HAAR: {}, w.STATES_BASIS: {}}
+    for dist in gen:
+        for M in (16, 32):
+            ok = 0
+            for t in range(4):
+                U = w.target_unitary(w.haar_gates(1000 + t, w.STREAM_TARGET_GATES, len(pairs)), pairs, n)
+                Psi = w.training_states(dist, 77 + t, n, M)
+                r = o.instantiate(U, Psi, w.initial_gates(77 + t, 4, len(pairs)), pairs, n, tol, 300)
+                if dist == w.STATES_BASIS:
+                    assert r.cost <= tol  # the training set is fitted
+                ok += o.full_cost(U, r.gates, pairs, n) / (1 << n) <= tol * (1 + otr)
+            gen[dist][M] = ok
+    assert gen[w.STATES_HAAR][16] >= 3 and gen[w.STATES_BASIS][16] == 0
+    assert gen[w.STATES_HAAR][32] == 4 and gen[w.STATES_BASIS][32] == 4
