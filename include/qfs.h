@@ -237,6 +237,16 @@ int qfs_sweep_once(qfs_ctx* ctx, const qfs_circuit* circuit, const double* targe
 int qfs_gate_update(qfs_ctx* ctx, int32_t count, const double* envs, const double* gates_old,
                     double beta, double* gates_out);
 
+/* Phi_L = U Psi, the A tensor of Section 3 (the product every instantiation
+ * starts from), on device buffers: target_dev N x N and samples_dev N x M
+ * complex128 row-major, out_dev N x M (N = 2^n).  precision = QFS_FP64:
+ * FP64 arithmetic.  QFS_MIXED: FP32 pair arithmetic (each FP64 operand
+ * split into two floats, exact products through FMA, error-tracked sums),
+ * about 48 significant bits, the product the mixed-precision runs use.
+ * Synchronous; uses the context's workspace.  QFS_EINVAL for bad sizes. */
+int qfs_target_product_dev(qfs_ctx* ctx, int32_t n, int32_t M, const double* target_dev,
+                           const double* samples_dev, int32_t precision, double* out_dev);
+
 /* Batched instantiation of P small problems (e.g. thousands of uneven 3-5
  * qubit partition blocks) in one persistent launch.  Problem i has ns[i] qubits
  * (2..6) and Ls[i] gates (1..32); pairs (host) holds 2*Ls[i] qubit indices

@@ -95,6 +95,7 @@ struct qfs_ctx {
   bool fuse_update = true;  // gate update inside the backward launch (QFS_FUSE_UPDATE=0: separate)
   bool tma = false;         // shared-memory-staged backward steps (QFS_TMA=1); register kernels by default
   bool dataflow = true;     // whole sweeps as one cooperative persistent launch (QFS_DATAFLOW=0: per-step launches)
+  bool upsi_fp64 = false;   // mixed runs: U Psi in FP64 instead of FP32 pair arithmetic (QFS_UPSI_FP64=1)
   unsigned long long* df_trace = nullptr;  // device buffer for step time stamps (qfs_dataflow_trace_*)
   size_t df_trace_n = 0;
   int df_trace_steps = 0, df_trace_S = 0;  // shape of the last traced sweep
@@ -529,7 +530,26 @@ int prepare(qfs_ctx* ctx, Run& R, const qfs_circuit* c, int M, int S, int prec, 
   return QFS_OK;
 }
 
-// Phi_L = U Psi in FP64, complex64 copies for the mixed sweeps, gate copies.
+// Phi_L = U Psi (Sec. 3, the A tensor).  QFS_FP64 runs take the FP64
+// product; mixed runs the FP32 pair-arithmetic product (about 48 bits, far
+// below what the FP64 cost check at dist_tol resolves), with the B list,
+// not in use before the first sweep, as its scratch.  Returns the launches.
+int target_product(qfs_ctx* ctx, Run& R, const double2* psi, double2* out) {
+  cudaStream_t st = ctx->stream;
+  const size_t bbytes = (size_t)std::max(R.L - 1, 1) * R.S * R.sN * elem_bytes(R.prec == QFS_MIXED ? R32 : R64);
+  const size_t split_bytes = align_up((size_t)R.sN * sizeof(float4));
+  if (R.prec == QFS_MIXED && !ctx->upsi_fp64 && bbytes >= 2 * split_bytes) {
+    const int splits = upsi_pair_splits((int)R.N, R.M, ctx->num_sms, bbytes - split_bytes);
+    float4* ps = reinterpret_cast<float4*>(R.B);
+    double2* scratch = reinterpret_cast<double2*>(static_cast<char*>(R.B) + split_bytes);
+    launch_gemm_upsi_pair(R.U, psi, out, (int)R.N, R.M, ps, scratch, splits, ctx->num_sms, st);
+    return splits > 1 ? 3 : 2;
+  }
+  launch_gemm_upsi(R.U, psi, out, (int)R.N, R.M, st);
+  return 1;
+}
+
+// Phi_L = U Psi, complex64 copies for the mixed sweeps, gate copies.
 int setup_inputs(qfs_ctx* ctx, Run& R) {
   cudaStream_t st = ctx->stream;
   CK(cudaMemsetAsync(R.flag, 0, sizeof(int) * 4, st));
@@ -548,7 +568,7 @@ int setup_inputs(qfs_ctx* ctx, Run& R) {
   }
   {
     ProfScope ps(ctx, QFS_PROF_GEMM, 8.0 * R.N * R.N * R.M);  // flops, not bytes
-    launch_gemm_upsi(R.U, R.psi64, R.phil64, (int)R.N, R.M, st);
+    ctx->prof.launches[QFS_PROF_GEMM] += target_product(ctx, R, R.psi64, R.phil64) - 1;
   }
   if (R.prec == QFS_MIXED) {
     ProfScope ps(ctx, QFS_PROF_OTHER, 0.0);
@@ -1051,8 +1071,7 @@ int instantiate_restarting(qfs_ctx* ctx, const qfs_circuit* c, const double* tar
     if (validate) {
       draw_states(p->training_distribution, sa, 5u, n, M, h.data());
       CK(cudaMemcpyAsync(R.psi_val64, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
-      launch_gemm_upsi(R.U, R.psi_val64, R.phil_val64, (int)R.N, M, st);
-      ctx->prof.launches[QFS_PROF_GEMM] += 1;
+      ctx->prof.launches[QFS_PROF_GEMM] += target_product(ctx, R, R.psi_val64, R.phil_val64);
       CK(cudaStreamSynchronize(st));
     }
     CK(cudaMemcpyAsync(R.g64, G.data(), G.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
@@ -1190,6 +1209,7 @@ int qfs_create(qfs_ctx** out, int device, void* cuda_stream) {
   if (const char* f = std::getenv("QFS_FUSE_UPDATE")) ctx->fuse_update = std::atoi(f) != 0;
   if (const char* f = std::getenv("QFS_TMA")) ctx->tma = std::atoi(f) != 0;
   if (const char* f = std::getenv("QFS_DATAFLOW")) ctx->dataflow = std::atoi(f) != 0;
+  if (const char* f = std::getenv("QFS_UPSI_FP64")) ctx->upsi_fp64 = std::atoi(f) != 0;
   if (const char* f = std::getenv("QFS_DF_ITEM_KB")) ctx->df_item_bytes = std::max(16, std::atoi(f)) * 1024.0;
   if (const char* f = std::getenv("QFS_DF_ITEMS_PER_CTA")) ctx->df_items_per_cta = std::max(0.25, std::atof(f));
   if (const char* f = std::getenv("QFS_DF_ITEMS_PER_CTA_FWD"))
@@ -1438,6 +1458,37 @@ int qfs_gate_update(qfs_ctx* ctx, int32_t count, const double* envs, const doubl
   launch_gate_update_batch(count, dE, gates_old ? dG : nullptr, beta, dO, st);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(gates_out, dO, bytes, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return QFS_OK;
+}
+
+int qfs_target_product_dev(qfs_ctx* ctx, int32_t n, int32_t M, const double* target_dev,
+                           const double* samples_dev, int32_t precision, double* out_dev) {
+  g_err.clear();
+  if (n < 2 || n > QFS_MAX_QUBITS) return fail(QFS_EINVAL, "n = %d out of [2, %d]", n, QFS_MAX_QUBITS);
+  if (M < 1 || (long long)M > (1LL << n)) return fail(QFS_EINVAL, "M = %d out of [1, 2^n]", M);
+  if (precision != QFS_FP64 && precision != QFS_MIXED)
+    return fail(QFS_EINVAL, "precision = %d: need QFS_FP64 or QFS_MIXED", precision);
+  if (!target_dev || !samples_dev || !out_dev) return fail(QFS_EINVAL, "target, samples and out must be given");
+  TRY(ctx_check(ctx));
+  TRY(set_device(ctx));
+  const int N = 1 << n;
+  const double2* U = reinterpret_cast<const double2*>(target_dev);
+  const double2* P = reinterpret_cast<const double2*>(samples_dev);
+  double2* O = reinterpret_cast<double2*>(out_dev);
+  cudaStream_t st = ctx->stream;
+  if (precision == QFS_FP64) {
+    ctx->prof.launches[QFS_PROF_GEMM] += 1;
+    launch_gemm_upsi(U, P, O, N, M, st);
+  } else {
+    const size_t split_bytes = align_up((size_t)N * M * sizeof(float4));
+    const int splits = upsi_pair_splits(N, M, ctx->num_sms, (size_t)16 * N * M * sizeof(double2));
+    TRY(ensure_ws(ctx, split_bytes + align_up((size_t)splits * N * M * sizeof(double2))));
+    ctx->prof.launches[QFS_PROF_GEMM] += splits > 1 ? 3 : 2;
+    launch_gemm_upsi_pair(U, P, O, N, M, reinterpret_cast<float4*>(ctx->ws),
+                          reinterpret_cast<double2*>(ctx->ws + split_bytes), splits, ctx->num_sms, st);
+  }
+  CK(cudaGetLastError());
   CK(cudaStreamSynchronize(st));
   return QFS_OK;
 }

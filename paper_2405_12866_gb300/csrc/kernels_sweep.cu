@@ -667,6 +667,171 @@ void launch_gemm_upsi(const double2* U, const double2* Psi, double2* out, int N,
   k_gemm_upsi<<<grid, dim3(32, 8), 0, st>>>(U, Psi, out, N, M);
 }
 
+// ------------------------------------------- U * Psi in FP32 pair arithmetic
+//
+// The same product to FP64-class accuracy on the FP32 pipe, which issues 64x
+// the FP64 rate on this GPU.  Every FP64 operand x is split into two floats,
+// x = x_h + x_l (x_h = fl32(x), x_l = fl32(x - x_h)), and every real product
+// u psi is formed as u_h psi_h exactly (Dekker's product through an FMA: the
+// rounded product plus its exact error) plus the cross terms u_h psi_l and
+// u_l psi_h (u_l psi_l, below 2^-48 relative, is dropped).  The rounded
+// products enter a float accumulator S through Knuth's two-sum, whose exact
+// rounding error goes, with the small terms, into a second float s (the
+// pair is renormalised every 32 terms).  A pair carries about 48 bits: the
+// result is within ~2^-44 of the exact sum in the worst case at K = 4096.
+//
+// Work: tiles of 16 rows x 32 columns x one K slab; four warps, warp w owns
+// rows 4w..4w+3 of its tile, lane c column c.  Slab partials (as doubles)
+// go to a scratch buffer and a second kernel adds them in FP64.
+
+__global__ void k_split_psi(const double2* __restrict__ psi, float4* __restrict__ out, long long count) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = psi[i];
+    const float hx = __double2float_rn(v.x), hy = __double2float_rn(v.y);
+    out[i] = float4{hx, hy, __double2float_rn(v.x - (double)hx), __double2float_rn(v.y - (double)hy)};
+  }
+}
+
+namespace {
+// The _rn intrinsics keep every rounding where it is written: the compiler
+// never contracts them into an FMA, which would void the error identities.
+__device__ __forceinline__ void pair_add(float& S, float& s, float p) {
+  const float t = __fadd_rn(S, p);
+  const float bp = __fsub_rn(t, S);
+  s = __fadd_rn(s, __fadd_rn(__fsub_rn(S, __fsub_rn(t, bp)), __fsub_rn(p, bp)));
+  S = t;
+}
+__device__ __forceinline__ void pair_norm(float& S, float& s) {
+  const float t = __fadd_rn(S, s);
+  const float bp = __fsub_rn(t, S);
+  s = __fadd_rn(__fsub_rn(S, __fsub_rn(t, bp)), __fsub_rn(s, bp));
+  S = t;
+}
+// acc (Sr, sr, Si, si) += u * p, u = (hr, hi, lr, li) likewise p.
+__device__ __forceinline__ void pair_cmac(float4& acc, const float4 u, const float4 p) {
+  const float a = __fmul_rn(u.x, p.x), b = __fmul_rn(-u.y, p.y), c = __fmul_rn(u.x, p.y), d = __fmul_rn(u.y, p.x);
+  const float ea = fmaf(u.x, p.x, -a), eb = fmaf(-u.y, p.y, -b);
+  const float ec = fmaf(u.x, p.y, -c), ed = fmaf(u.y, p.x, -d);
+  const float smr = fmaf(u.x, p.z, fmaf(u.z, p.x, fmaf(-u.y, p.w, fmaf(-u.w, p.y, ea + eb))));
+  const float smi = fmaf(u.x, p.w, fmaf(u.z, p.y, fmaf(u.y, p.z, fmaf(u.w, p.x, ec + ed))));
+  pair_add(acc.x, acc.y, a);
+  pair_add(acc.x, acc.y, b);
+  acc.y = __fadd_rn(acc.y, smr);
+  pair_add(acc.z, acc.w, c);
+  pair_add(acc.z, acc.w, d);
+  acc.w = __fadd_rn(acc.w, smi);
+}
+}  // namespace
+
+constexpr int kPairRows = 16, kPairCols = 32, kPairK = 32;
+
+__global__ void __launch_bounds__(128) k_gemm_upsi_pair(const double2* __restrict__ U, const float4* __restrict__ P,
+                                                        double2* __restrict__ part, int N, int M, int slab,
+                                                        int row_tiles, int col_tiles, int splits) {
+  __shared__ float4 Us[kPairRows][kPairK + 1];
+  __shared__ float4 Ps[kPairK][kPairCols];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long tiles = (long long)row_tiles * col_tiles * splits;
+  for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int sp = (int)(t % splits);
+    const long long rc = t / splits;
+    const int ct = (int)(rc % col_tiles), rt = (int)(rc / col_tiles);
+    const int row0 = rt * kPairRows, col = ct * kPairCols + lane;
+    const int k0 = sp * slab, k1 = min(N, k0 + slab);
+    float4 acc[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) acc[r] = float4{0.f, 0.f, 0.f, 0.f};
+    for (int kc = k0; kc < k1; kc += kPairK) {
+      // U chunk: 16 rows x 32 k, split on the way into shared memory.
+#pragma unroll
+      for (int i = 0; i < (kPairRows * kPairK) / 128; ++i) {
+        const int e = i * 128 + threadIdx.x;
+        const int r = e / kPairK, k = e % kPairK;
+        const int row = row0 + r, kk = kc + k;
+        float4 v{0.f, 0.f, 0.f, 0.f};
+        if (row < N && kk < k1) {
+          const double2 x = U[(long long)row * N + kk];
+          const float hx = __double2float_rn(x.x), hy = __double2float_rn(x.y);
+          v = float4{hx, hy, __double2float_rn(x.x - (double)hx), __double2float_rn(x.y - (double)hy)};
+        }
+        Us[r][k] = v;
+      }
+#pragma unroll
+      for (int i = 0; i < (kPairK * kPairCols) / 128; ++i) {
+        const int e = i * 128 + threadIdx.x;
+        const int k = e / kPairCols, c = e % kPairCols;
+        const int kk = kc + k, cc = ct * kPairCols + c;
+        Ps[k][c] = (kk < k1 && cc < M) ? P[(long long)kk * M + cc] : float4{0.f, 0.f, 0.f, 0.f};
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int k = 0; k < kPairK; ++k) {
+        const float4 p = Ps[k][lane];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) pair_cmac(acc[r], Us[4 * warp + r][k], p);
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        pair_norm(acc[r].x, acc[r].y);
+        pair_norm(acc[r].z, acc[r].w);
+      }
+      __syncthreads();
+    }
+    if (col < M) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int row = row0 + 4 * warp + r;
+        if (row < N)
+          part[((long long)sp * N + row) * M + col] =
+              double2{(double)acc[r].x + (double)acc[r].y, (double)acc[r].z + (double)acc[r].w};
+      }
+    }
+  }
+}
+
+__global__ void k_sum_slabs(const double2* __restrict__ part, double2* __restrict__ out, long long count,
+                            int splits) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    double2 a = part[i];
+    for (int s = 1; s < splits; ++s) {
+      const double2 b = part[(long long)s * count + i];
+      a.x += b.x;
+      a.y += b.y;
+    }
+    out[i] = a;
+  }
+}
+
+int upsi_pair_splits(int N, int M, int num_sms, size_t scratch_bytes) {
+  const long long base = (long long)((N + kPairRows - 1) / kPairRows) * ((M + kPairCols - 1) / kPairCols);
+  const long long want_tiles = 12LL * std::max(num_sms, 1);
+  int splits = (int)std::min<long long>(16, std::max<long long>(1, (want_tiles + base - 1) / base));
+  // Each slab is a whole number of K chunks; the scratch holds every slab.
+  while (splits > 1 && ((size_t)splits * N * M * sizeof(double2) > scratch_bytes || N / splits < kPairK)) --splits;
+  return splits;
+}
+
+void launch_gemm_upsi_pair(const double2* U, const double2* Psi, double2* out, int N, int M, float4* psi_split,
+                           double2* scratch, int splits, int num_sms, cudaStream_t st) {
+  const long long count = (long long)N * M;
+  k_split_psi<<<(unsigned)std::min<long long>((count + 255) / 256, 4096), 256, 0, st>>>(Psi, psi_split, count);
+  int slab = (N + splits - 1) / splits;
+  slab = (slab + kPairK - 1) / kPairK * kPairK;
+  const int row_tiles = (N + kPairRows - 1) / kPairRows, col_tiles = (M + kPairCols - 1) / kPairCols;
+  const long long tiles = (long long)row_tiles * col_tiles * splits;
+  static int per_sm = 0;  // resident CTAs per SM: the grid is one full wave
+  if (per_sm == 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gemm_upsi_pair, 128, 0) != cudaSuccess)
+    per_sm = 4;
+  const long long grid = std::min<long long>(tiles, (long long)std::max(per_sm, 1) * std::max(num_sms, 1));
+  double2* dst = splits == 1 ? out : scratch;
+  k_gemm_upsi_pair<<<(unsigned)grid, 128, 0, st>>>(U, psi_split, dst, N, M, slab, row_tiles, col_tiles, splits);
+  if (splits > 1)
+    k_sum_slabs<<<(unsigned)std::min<long long>((count + 255) / 256, 4096), 256, 0, st>>>(scratch, out, count,
+                                                                                             splits);
+}
+
 __global__ void k_cast(const double2* in, float2* out, long long count) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
        i += (long long)gridDim.x * blockDim.x) {

@@ -182,6 +182,13 @@ void launch_gate_update_batch(int count, const double2* envs, const double2* g_o
 void launch_gemm_upsi(const double2* U, const double2* Psi, double2* out, int N, int M,
                       cudaStream_t st);
 
+// U Psi in FP32 pair arithmetic (FP64-class accuracy, about 48 bits).
+// psi_split: N x M float4 scratch; scratch: splits x N x M double2 (unused
+// when splits == 1).  upsi_pair_splits picks the number of K slabs that
+// fills num_sms and fits scratch_bytes.
+int upsi_pair_splits(int N, int M, int num_sms, size_t scratch_bytes);
+void launch_gemm_upsi_pair(const double2* U, const double2* Psi, double2* out, int N, int M, float4* psi_split,
+                           double2* scratch, int splits, int num_sms, cudaStream_t st);
 void launch_cast_c128_to_c64(const double2* in, float2* out, long long count, cudaStream_t st);
 
 // flag[0] |= 1 when any of the `count` doubles is NaN or infinite.

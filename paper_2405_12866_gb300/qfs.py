@@ -38,7 +38,7 @@ EXPORTS = [
     "qfs_profile_read", "qfs_sweep_once_noalloc", "qfs_instantiate_batch",
     "qfs_instantiate_batch_dev", "qfs_gemm_bf16_dev", "qfs_ws_create", "qfs_ws_destroy", "qfs_ws_params",
     "qfs_ws_loss_grad", "qfs_ws_train", "qfs_ws_predict",
-    "qfs_dataflow_trace_enable", "qfs_dataflow_trace_read",
+    "qfs_dataflow_trace_enable", "qfs_dataflow_trace_read", "qfs_target_product_dev",
 ]
 (PROF_BACKWARD, PROF_FORWARD, PROF_UPDATE, PROF_GEMM, PROF_RESIDUAL, PROF_CHECK, PROF_OTHER, PROF_BATCH,
  PROF_MLP, PROF_DATAFLOW) = range(10)
@@ -101,6 +101,7 @@ def lib():
     L.qfs_sweep_once.argtypes = [_P, C.POINTER(Circuit), _P, _P, C.c_int32, C.c_int32, _P,
                                  C.c_int32, C.c_double, _P, _P, _P]
     L.qfs_gate_update.argtypes = [_P, C.c_int32, _P, _P, C.c_double, _P]
+    L.qfs_target_product_dev.argtypes = [_P, C.c_int32, C.c_int32, _P, _P, C.c_int32, _P]
     L.qfs_instantiate_batch.argtypes = [_P, C.c_int32, _P, _P, _P, _P, _P, _P, C.POINTER(Params), _P, _P]
     L.qfs_instantiate_batch_dev.argtypes = [_P, C.c_int32, _P, _P, _P, _P, _P, _P, C.POINTER(Params), _P, _P]
     L.qfs_gemm_bf16_dev.argtypes = [_P, C.c_int32, C.c_int32, C.c_int32, _P, C.c_int32, _P, C.c_int32, _P, _P,
@@ -265,6 +266,20 @@ class Context:
                                          C.byref(res), costs.ctypes.data))
         return InstantiateOutput(out, res.cost, res.sweeps, bool(res.converged), res.best_start,
                                  res.fp64_sweeps, costs, res.training_states)
+
+    def target_product(self, n, target, samples, precision=QFS_FP64, out=None):
+        """Phi_L = U Psi on device (torch complex128 CUDA) tensors."""
+        M = samples.shape[1]
+        for name, t in (("target", target), ("samples", samples)):
+            if not (t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.complex128"):
+                raise ValueError(f"{name} must be a contiguous complex128 CUDA tensor")
+        if out is None:
+            import torch
+            out = torch.empty((1 << n, M), dtype=torch.complex128, device=samples.device)
+        _wait_torch(target, samples, out)
+        _check(lib().qfs_target_product_dev(self._h, n, M, target.data_ptr(), samples.data_ptr(), precision,
+                                            out.data_ptr()))
+        return out
 
     def sweep_once(self, n, pairs, target, samples, gates, precision=QFS_FP64, beta=0.0,
                    want_envs=True):
