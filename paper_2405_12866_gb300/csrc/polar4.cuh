@@ -299,6 +299,18 @@ __device__ __forceinline__ float2 skew_correction(float2 k32, float2 v, float si
   return float2{0.5f * (om.x - omt.x), 0.5f * (om.y + omt.y)};  // exactly skew-Hermitian
 }
 
+// True when every column pair of X (lanes 0..15) has |gamma|^2 <= 1e-13
+// alpha beta, from the Gram matrix X^H X in one product: cheaper than a
+// sweep that finds nothing to rotate.
+__device__ __forceinline__ bool jacobi32_converged(float2 x) {
+  const int lane = threadIdx.x & 31;
+  const int l16 = lane & 15, row = l16 & 3, col = l16 >> 2;
+  const float2 g = mm_ah(x, x, row, col);  // G[row][col] = <x_row, x_col>
+  const float dr = __shfl_sync(FULL, g.x, 5 * row), dc = __shfl_sync(FULL, g.x, 5 * col);
+  const bool ok = row == col || (g.x * g.x + g.y * g.y) <= 1e-13f * dr * dc;
+  return __all_sync(FULL, ok);
+}
+
 // FP32 one-sided Jacobi sweeps on X (lanes 0..15, X[r][c] at 4c + r) with
 // the accumulated right rotations V in lanes 16..31, until every column pair
 // has |gamma|^2 <= 1e-13 alpha beta (FP32 accuracy) or 12 sweeps.
@@ -306,6 +318,7 @@ __device__ __forceinline__ float2 jacobi32_sweeps(float2 x) {
   const int lane = threadIdx.x & 31;
   const int l16 = lane & 15, col = l16 >> 2;
   const int c = col;
+  if (jacobi32_converged(x)) return x;  // a warm start that is already orthogonal
   for (int sweep = 0; sweep < 12; ++sweep) {
     int rotated = 0;
 #pragma unroll
@@ -348,9 +361,39 @@ __device__ __forceinline__ float2 jacobi32_sweeps(float2 x) {
         x = float2{sn * y.x + cs * tx, sn * y.y + cs * ty};
       }
     }
-    if (!__any_sync(FULL, rotated)) break;
+    if (!__any_sync(FULL, rotated) || jacobi32_converged(x)) break;
   }
   return x;
+}
+
+// exp(Omega) to third order for a small skew-Hermitian Omega (lanes 0..15,
+// FP32; big = max_ij |Re| + |Im| of its entries), as the FP64 entry of lane
+// l16.  The first-order term enters exactly (FP32 -> FP64 is exact), so X
+// keeps Omega's exact skew-Hermitian structure; the O(|Omega|^2) terms are
+// summed in FP32 (relative error 6e-8).  Omega^2 is skipped below 1e-8 and
+// Omega^3 below 2e-6 (their norms are then under 1e-15 and 1e-16).
+__device__ __forceinline__ double2 exp_skew3(float2 om, float big, int row, int col) {
+  float2 hot{0.f, 0.f};
+  if (big >= 1e-8f) {
+    const float2 om2 = mm(om, om, row, col);
+    hot = float2{0.5f * om2.x, 0.5f * om2.y};
+    if (big >= 2e-6f) {
+      const float2 om3 = mm(om2, om, row, col);
+      hot.x = fmaf(om3.x, 1.f / 6.f, hot.x);
+      hot.y = fmaf(om3.y, 1.f / 6.f, hot.y);
+    }
+  }
+  return double2{(row == col ? 1.0 : 0.0) + ((double)om.x + (double)hot.x), (double)om.y + (double)hot.y};
+}
+
+// max over lanes 0..15 of |Re| + |Im| (every lane gets it).
+__device__ __forceinline__ float max_abs16(float2 v) {
+  float big = fabsf(v.x) + fabsf(v.y);
+  big = fmaxf(big, __shfl_xor_sync(FULL, big, 1));
+  big = fmaxf(big, __shfl_xor_sync(FULL, big, 2));
+  big = fmaxf(big, __shfl_xor_sync(FULL, big, 4));
+  big = fmaxf(big, __shfl_xor_sync(FULL, big, 8));
+  return big;
 }
 
 // POLISH = 2 (FP64 sweeps): two polish steps, accurate to FP64 rounding.
@@ -437,22 +480,12 @@ __device__ __forceinline__ bool warp_polar4_fast(double2 a, double2 v0, double2*
   for (int it = 0; it < POLISH; ++it) {
     const double2 bm = mm64_ah(q, as, row, col, act);
     const double2 bt = shfl2(bm, 4 * row + col);  // B[col][row]
-    const float2 k32{(float)(0.5 * (bm.x - bt.x)), (float)(0.5 * (bm.y + bt.y))};
+    const float2 k32{0.5f * (float)(bm.x - bt.x), 0.5f * (float)(bm.y + bt.y)};
     const float2 om = skew_correction(k32, v, sig, row, col);
-    if (it == 0) {
-      float big = fabsf(om.x) + fabsf(om.y);
-      big = fmaxf(big, __shfl_xor_sync(FULL, big, 1));
-      big = fmaxf(big, __shfl_xor_sync(FULL, big, 2));
-      big = fmaxf(big, __shfl_xor_sync(FULL, big, 4));
-      big = fmaxf(big, __shfl_xor_sync(FULL, big, 8));
-      if (!(big < 1e-3f)) return false;
-    }
-    // exp(Omega) to third order (|Omega|^4 < 1e-20 after the first step).
-    const float2 om2 = mm(om, om, row, col);
-    const float2 om3 = mm(om2, om, row, col);
-    const double2 ecorr{(row == col ? 1.0 : 0.0) + (double)om.x + 0.5 * (double)om2.x + (double)om3.x / 6.0,
-                        (double)om.y + 0.5 * (double)om2.y + (double)om3.y / 6.0};
-    q = mm64(q, ecorr, row, col, act);
+    const float big = max_abs16(om);
+    if (it == 0 && !(big < 1e-3f)) return false;
+    // exp(Omega) to third order (|Omega|^4 < 1e-12 after the first check).
+    q = mm64(q, exp_skew3(om, big, row, col), row, col, act);
   }
   *p_out = q;
   if (v_out && lane < 16) v_out[l16] = double2{(double)v.x, (double)v.y};

@@ -619,22 +619,12 @@ __device__ void df_update(const UpdateArgs& ua, int s, DfShared<T>& sh, double v
       if (warp == 0) {
         const double2 bm = u.T[l16];
         const double2 bt = u.T[4 * row + col];  // B[col][row]
-        const float2 k32{(float)(0.5 * (bm.x - bt.x)), (float)(0.5 * (bm.y + bt.y))};
+        const float2 k32{0.5f * (float)(bm.x - bt.x), 0.5f * (float)(bm.y + bt.y)};
         const float2 om = skew_correction(k32, u.V[l16], u.sig[l16], row, col);
-        int good = 1;
-        if (it == 0) {
-          float big = fabsf(om.x) + fabsf(om.y);
-          big = fmaxf(big, __shfl_xor_sync(FULL, big, 1));
-          big = fmaxf(big, __shfl_xor_sync(FULL, big, 2));
-          big = fmaxf(big, __shfl_xor_sync(FULL, big, 4));
-          big = fmaxf(big, __shfl_xor_sync(FULL, big, 8));
-          good = big < 1e-3f ? 1 : 0;
-        }
-        const float2 om2 = mm(om, om, row, col);
-        const float2 om3 = mm(om2, om, row, col);
-        if (lane < 16)
-          u.X[l16] = double2{(row == col ? 1.0 : 0.0) + (double)om.x + 0.5 * (double)om2.x + (double)om3.x / 6.0,
-                             (double)om.y + 0.5 * (double)om2.y + (double)om3.y / 6.0};
+        const float big = max_abs16(om);
+        const int good = it > 0 || big < 1e-3f ? 1 : 0;
+        const double2 xc = exp_skew3(om, big, row, col);
+        if (lane < 16) u.X[l16] = xc;
         if (lane == 0) u.ok = good;
       }
       __syncthreads();
