@@ -95,6 +95,7 @@ struct qfs_ctx {
   bool fuse_update = true;  // gate update inside the backward launch (QFS_FUSE_UPDATE=0: separate)
   bool tma = false;         // shared-memory-staged backward steps (QFS_TMA=1); register kernels by default
   bool dataflow = true;     // whole sweeps as one cooperative persistent launch (QFS_DATAFLOW=0: per-step launches)
+  bool df_fwd2 = true;      // forward gates on four distinct qubits two per step (QFS_DF_FWD2=0: one per step)
   bool upsi_fp64 = false;   // mixed runs: U Psi in FP64 instead of FP32 pair arithmetic (QFS_UPSI_FP64=1)
   unsigned long long* df_trace = nullptr;  // device buffer for step time stamps (qfs_dataflow_trace_*)
   size_t df_trace_n = 0;
@@ -393,22 +394,42 @@ void df_build(const qfs_ctx* ctx, const Run& R, Real r, const void* psi, const v
   // that a start's chunks finish sooner and its update starts earlier.
   auto chunk_it = [&](DfStep& st, double bytes_per_unit) {
     const double step_bytes = bytes_per_unit * st.units * S;
-    const double per_cta = st.kind == DF_FWD ? ctx->df_items_per_cta_fwd : ctx->df_items_per_cta;
+    const bool fwd = st.kind == DF_FWD || st.kind == DF_FWD2;
+    const double per_cta = fwd ? ctx->df_items_per_cta_fwd : ctx->df_items_per_cta;
     const double target = std::min(ctx->df_item_bytes, std::max(16.0 * 1024.0, step_bytes / (per_cta * resident)));
     df_chunking(st, bytes_per_unit, target);
     *bytes += step_bytes;
   };
-  for (int k = 1; k <= L - 1; ++k) {
+  // Forward: gates k and k+1 on four distinct qubits go in one step (B_k is
+  // then written but not read back), others one at a time.
+  for (int k = 1; k <= L - 1;) {
     DfStep st{};
-    st.kind = DF_FWD;
-    st.fg = make_geom(n, M, R.pairs[2 * (k - 1)], R.pairs[2 * (k - 1) + 1]);
     st.in = k == 1 ? psi : B_ptr(k - 1);
     st.in_stride = k == 1 ? 0 : sN;
     st.out = B_ptr(k);
     st.gate = gate_ptr(k - 1);
     st.gate_stride = gstride;
-    st.units = (1 << (n - 2)) * (M / vec);
-    chunk_it(st, 4.0 * vec * es * 2.0);
+    const int a1 = R.pairs[2 * (k - 1)], b1 = R.pairs[2 * (k - 1) + 1];
+    bool two = ctx->df_fwd2 && k + 1 <= L - 1;
+    if (two) {
+      const int a2 = R.pairs[2 * k], b2 = R.pairs[2 * k + 1];
+      two = a2 != a1 && a2 != b1 && b2 != a1 && b2 != b1;
+      if (two) st.bg = make_bwd_geom(n, M, a1, b1, a2, b2);
+    }
+    if (two) {
+      st.kind = DF_FWD2;
+      st.out2 = B_ptr(k + 1);
+      st.gate2 = gate_ptr(k);
+      st.units = (1 << (n - 4)) * (M / vec);
+      chunk_it(st, 16.0 * vec * es * 3.0);
+      k += 2;
+    } else {
+      st.kind = DF_FWD;
+      st.fg = make_geom(n, M, a1, b1);
+      st.units = (1 << (n - 2)) * (M / vec);
+      chunk_it(st, 4.0 * vec * es * 2.0);
+      k += 1;
+    }
     steps.push_back(st);
   }
   for (int k = L; k >= 1; --k) {
@@ -1210,6 +1231,7 @@ int qfs_create(qfs_ctx** out, int device, void* cuda_stream) {
   if (const char* f = std::getenv("QFS_TMA")) ctx->tma = std::atoi(f) != 0;
   if (const char* f = std::getenv("QFS_DATAFLOW")) ctx->dataflow = std::atoi(f) != 0;
   if (const char* f = std::getenv("QFS_UPSI_FP64")) ctx->upsi_fp64 = std::atoi(f) != 0;
+  if (const char* f = std::getenv("QFS_DF_FWD2")) ctx->df_fwd2 = std::atoi(f) != 0;
   if (const char* f = std::getenv("QFS_DF_ITEM_KB")) ctx->df_item_bytes = std::max(16, std::atoi(f)) * 1024.0;
   if (const char* f = std::getenv("QFS_DF_ITEMS_PER_CTA")) ctx->df_items_per_cta = std::max(0.25, std::atof(f));
   if (const char* f = std::getenv("QFS_DF_ITEMS_PER_CTA_FWD"))

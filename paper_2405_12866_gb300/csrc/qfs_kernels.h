@@ -84,6 +84,7 @@ enum DfKind {
   DF_BWD3_10 = 6,
   DF_BWD3_01 = 7,
   DF_RESID = 8,    // residual cost (1/M) sum |g_1^dagger Phi_1 - Psi|^2
+  DF_FWD2 = 9,     // B_k = g_k B_{k-1} and B_{k+1} = g_{k+1} B_k, gates on four distinct qubits
 };
 struct DfStep {
   int kind;
@@ -91,6 +92,8 @@ struct DfStep {
   long long item0;                      // first work item of this step
   const void* in; long long in_stride;  // forward input / backward B_{k-1} / residual Psi
   void* out;                            // forward output B_k (start stride fg.sN)
+  void* out2;                           // DF_FWD2: B_{k+1} (start stride bg.sN)
+  const void* gate2;                    // DF_FWD2: gate k+1 (start stride gate_stride)
   const void* phi_in; long long phi_in_stride;
   void* phi_out;                        // start stride bg.sN; null: not stored
   const void* gate; long long gate_stride;  // gate applied (null: none)

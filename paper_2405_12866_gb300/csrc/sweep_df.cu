@@ -98,6 +98,7 @@ struct DfUpd {
 template <typename T>
 struct DfShared {
   typename C2<T>::t gs[16];
+  typename C2<T>::t gs2[16];  // the second gate of a two-gate forward step
   double red[kDfMaxWarps][32];
   double2 polar[32];
   DfUpd u;
@@ -218,6 +219,133 @@ constexpr int kDfStages = 3;
 template <typename T>
 __host__ __device__ constexpr int df_stage_bytes() {
   return kDfStages * 8 * df_threads<T>() * 16;
+}
+
+// Two forward steps in one pass over 16-row units (gates k and k+1 on four
+// distinct qubits; geometry bg with gate k's pair on local bits 3, 2 and
+// gate k+1's on local bits 1, 0): B_k = g_k B_{k-1} and B_{k+1} = g_{k+1}
+// B_k, both stored, B_k never read back.  Four lanes share a unit: lane
+// quarter qx holds the four rows of one value of gate k+1's bits and applies
+// g_k to them; g_{k+1} then mixes the four quarters through shuffles.  Rows
+// are staged by cp.async into the thread's own slots (kDfFwd2Stages - 1
+// rounds in flight).
+constexpr int kDfFwd2Stages = 4;
+template <typename T, int VEC>
+__device__ void df_forward2(const DfStep& st, int s, int c, DfShared<T>& sh, uint4* stage) {
+  using T2 = typename C2<T>::t;
+  static_assert(sizeof(T2) * VEC == 16, "one 16-byte slot per row");
+  static_assert(kDfFwd2Stages * 4 <= kDfStages * 8, "forward stages fit the stage buffer");
+  constexpr int NT = df_threads<T>();
+  constexpr int NW = NT / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int qx = lane >> 3, v = lane & 7;
+  if (threadIdx.x < 16)
+    sh.gs[threadIdx.x] = __ldcg(reinterpret_cast<const T2*>(st.gate) + s * st.gate_stride + threadIdx.x);
+  else if (threadIdx.x < 32)
+    sh.gs2[threadIdx.x - 16] =
+        __ldcg(reinterpret_cast<const T2*>(st.gate2) + s * st.gate_stride + (threadIdx.x - 16));
+  __syncthreads();
+  T2 g1[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) g1[i] = sh.gs[i];
+  T2 g2[4];  // row qx of g_{k+1}
+#pragma unroll
+  for (int m = 0; m < 4; ++m) g2[m] = sh.gs2[4 * qx + m];
+  const T2* X = reinterpret_cast<const T2*>(st.in) + s * st.in_stride;
+  T2* Y1 = reinterpret_cast<T2*>(st.out) + s * st.bg.sN;
+  T2* Y2 = reinterpret_cast<T2*>(st.out2) + s * st.bg.sN;
+  const uint32_t M = (uint32_t)st.bg.M;
+  const uint32_t d0 = (1u << st.bg.pos[0]) * M, d1 = (1u << st.bg.pos[1]) * M;
+  const uint32_t d2 = (1u << st.bg.pos[2]) * M, d3 = (1u << st.bg.pos[3]) * M;
+  const uint32_t xoff = ((qx >> 1) ? d1 : 0u) + ((qx & 1) ? d0 : 0u);
+  const uint32_t joff[4] = {0u, d2, d3, d3 + d2};  // j = 2 bit(local 3) + bit(local 2): gate k's index
+  const int MV = st.bg.M / VEC;
+  const int u0 = c * st.chunk, u1 = min(u0 + st.chunk, st.units);
+  constexpr int per_round = 8 * NW;
+  const int rounds = (u1 - u0 + per_round - 1) / per_round;
+  auto unit_off = [&](int u) {
+    const int r = u / MV, jv = u - r * MV;
+    uint32_t base = (uint32_t)r;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int p = st.bg.ins[i];
+      base = ((base >> p) << (p + 1)) | (base & ((1u << p) - 1u));
+    }
+    return base * M + (uint32_t)jv * VEC + xoff;
+  };
+  auto issue = [&](int rd) {
+    const int u = u0 + rd * per_round + warp * 8 + v;
+    if (rd < rounds && u < u1) {
+      uint4* slot = stage + (size_t)((rd % kDfFwd2Stages) * 4) * NT + threadIdx.x;
+      const uint32_t o = unit_off(u);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) cp_async16(slot + (size_t)j * NT, X + o + joff[j]);
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int rd = 0; rd < kDfFwd2Stages - 1; ++rd) issue(rd);
+  for (int rd = 0; rd < rounds; ++rd) {
+    issue(rd + kDfFwd2Stages - 1);
+    cp_async_wait<kDfFwd2Stages - 1>();
+    const int u = u0 + rd * per_round + warp * 8 + v;
+    const bool valid = u < u1;  // (all four lanes of a unit agree)
+    T2 b[4][VEC];
+    {
+      const uint4* slot = stage + (size_t)((rd % kDfFwd2Stages) * 4) * NT + threadIdx.x;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        uint4 w4 = valid ? slot[(size_t)j * NT] : make_uint4(0u, 0u, 0u, 0u);
+        const T2* e = reinterpret_cast<const T2*>(&w4);
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) b[j][q] = e[q];
+      }
+    }
+    const uint32_t o = valid ? unit_off(u) : 0u;
+    T2 y[4][VEC];
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) {
+        T2 acc = cmul(g1[4 * x], b[0][q]);
+#pragma unroll
+        for (int xp = 1; xp < 4; ++xp) {
+          const T2 t = cmul(g1[4 * x + xp], b[xp][q]);
+          acc.x += t.x;
+          acc.y += t.y;
+        }
+        y[x][q] = acc;
+      }
+    if (valid) {
+#pragma unroll
+      for (int x = 0; x < 4; ++x) stg<T, VEC>(Y1 + o + joff[x], y[x]);
+    }
+    // z = g_{k+1} y over the quarters, summed in the order of the one-gate
+    // forward step (quarter 0 first); quarter xp sits xor 8 (qx ^ xp) away.
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      T2 z[VEC];
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) {
+        T2 w[4];
+#pragma unroll
+        for (int xp = 0; xp < 4; ++xp) {
+          w[xp].x = __shfl_xor_sync(FULL, y[x][q].x, 8 * (qx ^ xp));
+          w[xp].y = __shfl_xor_sync(FULL, y[x][q].y, 8 * (qx ^ xp));
+        }
+        T2 acc = cmul(g2[0], w[0]);
+#pragma unroll
+        for (int xp = 1; xp < 4; ++xp) {
+          const T2 t = cmul(g2[xp], w[xp]);
+          acc.x += t.x;
+          acc.y += t.y;
+        }
+        z[q] = acc;
+      }
+      if (valid) stg<T, VEC>(Y2 + o + joff[x], z);
+    }
+  }
+  cp_async_wait<0>();
 }
 
 // Backward step on 16-row units (gate k+1 and gate k on four distinct
@@ -671,6 +799,7 @@ __device__ void df_process(const DfStep& st, int s, int c, DfShared<T>& sh, void
   double* part64 = resid + ((long long)s * stride + c) * 32;
   switch (st.kind) {
     case DF_FWD: df_forward<T, V2>(st, s, c, sh); break;
+    case DF_FWD2: df_forward2<T, V2>(st, s, c, sh, stage); break;
     case DF_BWD4: df_backward_q4<T, V2>(st, s, c, sh, part, stage); break;
     case DF_BWD2_10: df_backward_gen<T, V2, 0, 2, 1, 0>(st, s, c, sh, part); break;
     case DF_BWD2_01: df_backward_gen<T, V2, 0, 2, 0, 1>(st, s, c, sh, part); break;
@@ -748,7 +877,7 @@ __global__ void __launch_bounds__(df_threads<T>(), 1) k_sweep_df(DfArgs a) {
     if (sh.flag) {
       unsigned long long* tr = a.trace ? a.trace + ((long long)i * a.S + s) * 4 : nullptr;
       if (tr && threadIdx.x == 0) tr[1] = globaltimer_ns();
-      if (act && st.kind != DF_FWD) {
+      if (act && st.kind != DF_FWD && st.kind != DF_FWD2) {
         __threadfence();
         if (st.kind == DF_RESID) {
           if (warp == 0) {
