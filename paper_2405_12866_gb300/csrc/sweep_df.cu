@@ -907,7 +907,10 @@ __global__ void __launch_bounds__(df_threads<T>(), 1) k_sweep_df(DfArgs a) {
 #pragma unroll
             for (int w = 0; w < NW; ++w) v += sh.red[w][lane];
           }
-          df_update<T, sizeof(T) == 4 ? 1 : 2>(st.upd, s, sh, v);
+          // complex64 sweeps: the polar factor to FP32 accuracy, the
+          // accuracy of their environments (no skew-Hermitian correction);
+          // FP64 sweeps: polar to FP64 rounding (two corrections).
+          df_update<T, sizeof(T) == 4 ? 0 : 2>(st.upd, s, sh, v);
         }
       }
       __syncthreads();
