@@ -20,6 +20,23 @@ template <> struct C2<double> { using t = double2; };
 template <typename T2> __device__ __forceinline__ T2 cmul(T2 a, T2 b) {
   return T2{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }
+// acc + a * b as four FMAs (two per component, no rounded product in between).
+__device__ __forceinline__ float fmat(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmat(double a, double b, double c) { return fma(a, b, c); }
+template <typename T2> __device__ __forceinline__ T2 cfma(T2 a, T2 b, T2 acc) {
+  acc.x = fmat(a.x, b.x, acc.x);
+  acc.x = fmat(-a.y, b.y, acc.x);
+  acc.y = fmat(a.x, b.y, acc.y);
+  acc.y = fmat(a.y, b.x, acc.y);
+  return acc;
+}
+// acc (re, im) + b * conj(p) as four FMAs.
+template <typename T, typename T2> __device__ __forceinline__ void cfma_conj(T& re, T& im, T2 b, T2 p) {
+  re = fmat(b.x, p.x, re);
+  re = fmat(b.y, p.y, re);
+  im = fmat(b.y, p.x, im);
+  im = fmat(-b.x, p.y, im);
+}
 // conj(a) * b
 template <typename T2> __device__ __forceinline__ T2 cmulc(T2 a, T2 b) {
   return T2{a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x};

@@ -160,11 +160,7 @@ __device__ void df_forward(const DfStep& st, int s, int c, DfShared<T>& sh) {
       for (int q = 0; q < VEC; ++q) {
         T2 acc = cmul(gr[4 * x], v[0][q]);
 #pragma unroll
-        for (int xp = 1; xp < 4; ++xp) {
-          const T2 t = cmul(gr[4 * x + xp], v[xp][q]);
-          acc.x += t.x;
-          acc.y += t.y;
-        }
+        for (int xp = 1; xp < 4; ++xp) acc = cfma(gr[4 * x + xp], v[xp][q], acc);
         o[q] = acc;
       }
       stg<T, VEC>(Y + off[x], o);
@@ -309,11 +305,7 @@ __device__ void df_forward2(const DfStep& st, int s, int c, DfShared<T>& sh, uin
       for (int q = 0; q < VEC; ++q) {
         T2 acc = cmul(g1[4 * x], b[0][q]);
 #pragma unroll
-        for (int xp = 1; xp < 4; ++xp) {
-          const T2 t = cmul(g1[4 * x + xp], b[xp][q]);
-          acc.x += t.x;
-          acc.y += t.y;
-        }
+        for (int xp = 1; xp < 4; ++xp) acc = cfma(g1[4 * x + xp], b[xp][q], acc);
         y[x][q] = acc;
       }
     if (valid) {
@@ -335,11 +327,7 @@ __device__ void df_forward2(const DfStep& st, int s, int c, DfShared<T>& sh, uin
         }
         T2 acc = cmul(g2[0], w[0]);
 #pragma unroll
-        for (int xp = 1; xp < 4; ++xp) {
-          const T2 t = cmul(g2[xp], w[xp]);
-          acc.x += t.x;
-          acc.y += t.y;
-        }
+        for (int xp = 1; xp < 4; ++xp) acc = cfma(g2[xp], w[xp], acc);
         z[q] = acc;
       }
       if (valid) stg<T, VEC>(Y2 + o + joff[x], z);
@@ -435,11 +423,7 @@ __device__ void df_backward_q4(const DfStep& st, int s, int c, DfShared<T>& sh, 
         for (int q = 0; q < VEC; ++q) {
           T2 t = cmul(gd[4 * y], ph[0][q]);
 #pragma unroll
-          for (int j = 1; j < 4; ++j) {
-            const T2 w = cmul(gd[4 * y + j], ph[j][q]);
-            t.x += w.x;
-            t.y += w.y;
-          }
+          for (int j = 1; j < 4; ++j) t = cfma(gd[4 * y + j], ph[j][q], t);
           nw[y][q] = t;
         }
 #pragma unroll
@@ -462,9 +446,7 @@ __device__ void df_backward_q4(const DfStep& st, int s, int c, DfShared<T>& sh, 
             pp.x = __shfl_xor_sync(FULL, pp.x, 8 * m);
             pp.y = __shfl_xor_sync(FULL, pp.y, 8 * m);
           }
-          const T2 bb = b[j][q];
-          acc[2 * m] += bb.x * pp.x + bb.y * pp.y;
-          acc[2 * m + 1] += bb.y * pp.x - bb.x * pp.y;
+          cfma_conj(acc[2 * m], acc[2 * m + 1], b[j][q], pp);
         }
     }
   }
@@ -558,11 +540,7 @@ __device__ void df_backward_gen(const DfStep& st, int s, int c, DfShared<T>& sh,
           for (int q = 0; q < VEC; ++q) {
             T2 a2 = cmul(gd(y, 0), ph[(0 << (U - 2)) | t0][q]);
 #pragma unroll
-            for (int yp = 1; yp < 4; ++yp) {
-              const T2 w = cmul(gd(y, yp), ph[(yp << (U - 2)) | t0][q]);
-              a2.x += w.x;
-              a2.y += w.y;
-            }
+            for (int yp = 1; yp < 4; ++yp) a2 = cfma(gd(y, yp), ph[(yp << (U - 2)) | t0][q], a2);
             nw[y][q] = a2;
           }
 #pragma unroll
@@ -589,9 +567,7 @@ __device__ void df_backward_gen(const DfStep& st, int s, int c, DfShared<T>& sh,
             const int ty = rest | ((y >> 1) << EA) | ((y & 1) << EB);
 #pragma unroll
             for (int q = 0; q < VEC; ++q) {
-              const T2 bb = b[x][q], pp = ph[ty][q];
-              acc[2 * (4 * x + y)] += bb.x * pp.x + bb.y * pp.y;
-              acc[2 * (4 * x + y) + 1] += bb.y * pp.x - bb.x * pp.y;
+              cfma_conj(acc[2 * (4 * x + y)], acc[2 * (4 * x + y) + 1], b[x][q], ph[ty][q]);
             }
           }
       }
@@ -603,7 +579,7 @@ __device__ void df_backward_gen(const DfStep& st, int s, int c, DfShared<T>& sh,
 #pragma unroll
         for (int q = 0; q < VEC; ++q) {
           const T dx = ph[t][q].x - b[q].x, dy = ph[t][q].y - b[q].y;
-          acc[0] += dx * dx + dy * dy;
+          acc[0] = fmat(dx, dx, fmat(dy, dy, acc[0]));
         }
       }
     }
