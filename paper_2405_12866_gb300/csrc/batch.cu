@@ -60,8 +60,7 @@ __device__ void warp_apply(T2* X, const T2* g, int n, int M, int qa, int qb, boo
 #pragma unroll
       for (int x = 0; x < 4; ++x) {
         const T2 gg = dag ? T2{g[4 * x + y].x, -g[4 * x + y].y} : g[4 * y + x];
-        t.x += gg.x * v[x].x - gg.y * v[x].y;
-        t.y += gg.x * v[x].y + gg.y * v[x].x;
+        t = cfma(gg, v[x], t);
       }
       X[off[y]] = t;
     }
@@ -95,8 +94,7 @@ __device__ double2 warp_env(const T2* Bs, const T2* Ph, int n, int M, int qa, in
     for (int x = 0; x < 4; ++x)
 #pragma unroll
       for (int y = 0; y < 4; ++y) {
-        acc[2 * (4 * x + y)] += b[x].x * p[y].x + b[x].y * p[y].y;
-        acc[2 * (4 * x + y) + 1] += b[x].y * p[y].x - b[x].x * p[y].y;
+        cfma_conj(acc[2 * (4 * x + y)], acc[2 * (4 * x + y) + 1], b[x], p[y]);
       }
   }
   const double v = (double)warp_reduce_scatter32<T>(acc, lane);

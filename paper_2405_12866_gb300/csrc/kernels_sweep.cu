@@ -128,11 +128,7 @@ __global__ void k_forward(FwdArgs a) {
       for (int q = 0; q < VEC; ++q) {
         T2 acc = cmul(gr[4 * x], v[0][q]);
 #pragma unroll
-        for (int xp = 1; xp < 4; ++xp) {
-          const T2 t = cmul(gr[4 * x + xp], v[xp][q]);
-          acc.x += t.x;
-          acc.y += t.y;
-        }
+        for (int xp = 1; xp < 4; ++xp) acc = cfma(gr[4 * x + xp], v[xp][q], acc);
         o[q] = acc;
       }
       st<T, VEC>(Y + off[x], o);
@@ -276,11 +272,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (U == 4 ? 3 : 4) : 2) k_
           for (int q = 0; q < VEC; ++q) {
             T2 acc2 = cmul(gd(y, 0), ph[(0 << (U - 2)) | t0][q]);
 #pragma unroll
-            for (int yp = 1; yp < 4; ++yp) {
-              const T2 w = cmul(gd(y, yp), ph[(yp << (U - 2)) | t0][q]);
-              acc2.x += w.x;
-              acc2.y += w.y;
-            }
+            for (int yp = 1; yp < 4; ++yp) acc2 = cfma(gd(y, yp), ph[(yp << (U - 2)) | t0][q], acc2);
             nw[y][q] = acc2;
           }
 #pragma unroll
@@ -312,8 +304,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (U == 4 ? 3 : 4) : 2) k_
 #pragma unroll
             for (int q = 0; q < VEC; ++q) {
               const T2 bb = b[x][q], pp = ph[ty][q];
-              acc[2 * (4 * x + y)] += bb.x * pp.x + bb.y * pp.y;
-              acc[2 * (4 * x + y) + 1] += bb.y * pp.x - bb.x * pp.y;
+              cfma_conj(acc[2 * (4 * x + y)], acc[2 * (4 * x + y) + 1], bb, pp);
             }
           }
       }
@@ -325,7 +316,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (U == 4 ? 3 : 4) : 2) k_
 #pragma unroll
         for (int q = 0; q < VEC; ++q) {
           const T dx = ph[t][q].x - b[q].x, dy = ph[t][q].y - b[q].y;
-          acc[0] += dx * dx + dy * dy;
+          acc[0] = fmat(dx, dx, fmat(dy, dy, acc[0]));
         }
       }
     }
@@ -471,11 +462,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2) k_backward_q4(Bwd
         for (int q = 0; q < VEC; ++q) {
           T2 t = cmul(gd[4 * y], ph[0][q]);
 #pragma unroll
-          for (int j = 1; j < 4; ++j) {
-            const T2 w = cmul(gd[4 * y + j], ph[j][q]);
-            t.x += w.x;
-            t.y += w.y;
-          }
+          for (int j = 1; j < 4; ++j) t = cfma(gd[4 * y + j], ph[j][q], t);
           nw[y][q] = t;
         }
 #pragma unroll
@@ -499,8 +486,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2) k_backward_q4(Bwd
             pp.y = __shfl_xor_sync(FULL, pp.y, 8 * m);
           }
           const T2 bb = b[j][q];
-          acc[2 * m] += bb.x * pp.x + bb.y * pp.y;
-          acc[2 * m + 1] += bb.y * pp.x - bb.x * pp.y;
+          cfma_conj(acc[2 * m], acc[2 * m + 1], bb, pp);
         }
     }
   }

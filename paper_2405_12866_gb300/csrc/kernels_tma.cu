@@ -231,8 +231,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_backward_tma(TmaBwdArgs ta) {
           for (int x = 0; x < 4; ++x)
 #pragma unroll
             for (int y = 0; y < 4; ++y) {
-              acc[2 * (4 * x + y)] += bx[x].x * py[y].x + bx[x].y * py[y].y;
-              acc[2 * (4 * x + y) + 1] += bx[x].y * py[y].x - bx[x].x * py[y].y;
+              cfma_conj(acc[2 * (4 * x + y)], acc[2 * (4 * x + y) + 1], bx[x], py[y]);
             }
         }
       }
@@ -398,8 +397,7 @@ __global__ void __launch_bounds__(128, 1) k_backward_cpa(TmaBwdArgs ta) {
         for (int x = 0; x < 4; ++x)
 #pragma unroll
           for (int y = 0; y < 4; ++y) {
-            acc[2 * (4 * x + y)] += bx[x].x * py[y].x + bx[x].y * py[y].y;
-            acc[2 * (4 * x + y) + 1] += bx[x].y * py[y].x - bx[x].x * py[y].y;
+            cfma_conj(acc[2 * (4 * x + y)], acc[2 * (4 * x + y) + 1], bx[x], py[y]);
           }
       }
     }
