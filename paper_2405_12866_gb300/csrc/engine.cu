@@ -197,6 +197,12 @@ void prof_harvest(qfs_ctx* ctx) {
   ctx->prof.pending.clear();
 }
 
+// Sweeps queued per host round trip while no per-sweep host decision
+// (plateau, validation) is needed: a launch behind a sweep that met the
+// tolerance returns at once (device stop flag), so the run ends at the same
+// sweep as with one launch per round trip.
+constexpr int kSweepBatch = 4;
+
 // Device buffers of one run, carved from the context's workspace.
 struct Run {
   int n = 0, L = 0, M = 0, S = 0;
@@ -222,6 +228,7 @@ struct Run {
   double2* vprev = nullptr;  // right singular vectors of each gate's last update
   double* partials = nullptr;
   double* costs = nullptr;
+  double* cost_rows = nullptr;   // kSweepBatch x S: the costs of each sweep of a batch
   int* active = nullptr;
   int* flag = nullptr;
   unsigned* counters = nullptr;  // S + 1 "last block done" counters (fused update)
@@ -282,6 +289,7 @@ size_t carve(Run& R, char* base, bool need_U, bool need_envs) {
   R.vprev = (double2*)take((size_t)R.S * R.L * 16 * sizeof(double2));
   R.partials = (double*)take((size_t)R.S * R.nblk_max * 32 * sizeof(double));
   R.costs = (double*)take((size_t)R.S * sizeof(double));
+  R.cost_rows = (double*)take((size_t)kSweepBatch * R.S * sizeof(double));
   R.active = (int*)take((size_t)R.S * sizeof(int));
   R.counters = (unsigned*)take((size_t)(R.S + 1) * sizeof(unsigned));
   R.flag = (int*)take(sizeof(int) * 4);
@@ -547,7 +555,7 @@ int prepare(qfs_ctx* ctx, Run& R, const qfs_circuit* c, int M, int S, int prec, 
   const size_t blist = (size_t)std::max(R.L - 1, 1) * S * R.sN * elem_bytes(prec == QFS_MIXED ? R32 : R64);
   R.stream_b = blist > ctx->l2_bytes / 2;
   R.stream_b64 = (size_t)std::max(R.L - 1, 1) * R.sN * sizeof(double2) > ctx->l2_bytes / 2;
-  TRY(ensure_pinned(ctx, (size_t)S + 8));
+  TRY(ensure_pinned(ctx, (size_t)kSweepBatch * S + 8));
   return QFS_OK;
 }
 
@@ -736,7 +744,7 @@ void sweep(qfs_ctx* ctx, Run& R, Real r, const Slice& sl, double2* g64, float2* 
 // sweep() up to the order of the reduction sums).  The step table is built
 // and uploaded once per (precision, outputs) and reused by later sweeps.
 int df_sweep(qfs_ctx* ctx, Run& R, Real r, const void* psi, const void* phil, double2* envs, const int* active,
-             double2* vprev, cudaStream_t st) {
+             double2* vprev, cudaStream_t st, int* stop = nullptr, double stop_tol = 0.0) {
   const void* key[4] = {psi, envs, active, vprev};
   if (R.df_key_r != (int)r || std::memcmp(key, R.df_key, sizeof(key)) != 0) {
     std::vector<DfStep> steps;
@@ -771,6 +779,8 @@ int df_sweep(qfs_ctx* ctx, Run& R, Real r, const void* psi, const void* phil, do
   a.part_stride = R.df_max_nchunk;
   a.resid_cost = R.costs;
   a.inv_M = 1.0 / R.M;
+  a.stop = stop;
+  a.stop_tol = stop_tol;
   const size_t nstep_stamps = (size_t)R.df_nsteps * R.S * 4;
   a.trace = ctx->df_trace && ctx->df_trace_n >= nstep_stamps ? ctx->df_trace : nullptr;
   a.item_trace = a.trace && ctx->df_trace_n >= nstep_stamps + (size_t)R.df_items * 4 ? a.trace + nstep_stamps : nullptr;
@@ -831,6 +841,34 @@ int read_costs(qfs_ctx* ctx, const double* dev, int S, std::vector<double>& out,
     if (e) return fail(QFS_ETIMEOUT, "a bounded device wait ran out (error word %d)", e);
   }
   return QFS_OK;
+}
+
+// The cost rows of a batch of B sweeps and the error word, without folding
+// the profile (the caller first drops the launches that found the stop flag).
+int read_rows(qfs_ctx* ctx, const double* dev, int S, int B, std::vector<std::vector<double>>& rows,
+              const int* err) {
+  CK(cudaMemcpyAsync(ctx->h_pinned, dev, sizeof(double) * S * B, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->h_pinned + (size_t)S * B, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  rows.assign(B, std::vector<double>());
+  for (int b = 0; b < B; ++b) rows[b].assign(ctx->h_pinned + (size_t)b * S, ctx->h_pinned + (size_t)(b + 1) * S);
+  int e;
+  std::memcpy(&e, ctx->h_pinned + (size_t)S * B, sizeof(int));
+  if (e) return fail(QFS_ETIMEOUT, "a bounded device wait ran out (error word %d)", e);
+  return QFS_OK;
+}
+
+// Forget the last k dataflow launches of the profile (launches that
+// returned at once on the stop flag did no work).
+void prof_drop_dataflow(qfs_ctx* ctx, int k) {
+  ctx->prof.launches[QFS_PROF_DATAFLOW] -= k;
+  for (int i = (int)ctx->prof.pending.size() - 1; i >= 0 && k > 0; --i) {
+    if (ctx->prof.pending[i].id != QFS_PROF_DATAFLOW) continue;
+    ctx->prof.pool.push_back(ctx->prof.pending[i].a);
+    ctx->prof.pool.push_back(ctx->prof.pending[i].b);
+    ctx->prof.pending.erase(ctx->prof.pending.begin() + i);
+    --k;
+  }
 }
 
 int ensure_group_streams(qfs_ctx* ctx, int groups) {
@@ -937,16 +975,52 @@ int run_multistart(qfs_ctx* ctx, Run& R, const qfs_params* p, Outcome& out) {
   SweepGraph graph;
   const bool df = df_usable(ctx, R, rs);
   if (!df) TRY(capture_sweep(ctx, R, rs, psi, phil, graph));
+  // Without plateau detection or validation the host decides nothing until
+  // some start meets the tolerance, so sweeps go out in batches.
+  const bool batch = df && p->plateau_window == 0 && !R.validate;
+  int* stop = R.flag + 2;
+  std::vector<std::vector<double>> rows;
+  int row = 0, nrows = 0;
   while (!done && sweeps < p->max_sweeps) {
     ++sweeps;
-    if (df) {
-      TRY(df_sweep(ctx, R, rs, psi, phil, nullptr, R.active, R.vprev, st));
-    } else {
-      CK(cudaGraphLaunch(graph.exec, st));
-      for (int i = 0; i < QFS_PROF_KINDS; ++i) ctx->prof.launches[i] += graph.launches[i];
+    if (row == nrows) {  // launch the next batch (or single sweep)
+      const int B = batch ? std::min(kSweepBatch, p->max_sweeps - sweeps + 1) : 1;
+      if (df && B > 1) {
+        CK(cudaMemsetAsync(stop, 0, sizeof(int), st));
+        for (int b = 0; b < B; ++b) {
+          TRY(df_sweep(ctx, R, rs, psi, phil, nullptr, R.active, R.vprev, st, stop, tol));
+          CK(cudaMemcpyAsync(R.cost_rows + (size_t)b * S, R.costs, sizeof(double) * S, cudaMemcpyDeviceToDevice,
+                             st));
+        }
+        TRY(read_rows(ctx, R.cost_rows, S, B, rows, R.err));
+        // The sweep whose cost met the tolerance ends the batch; the
+        // launches behind it returned at once.
+        nrows = B;
+        for (int b = 0; b < B; ++b) {
+          bool met = false;
+          for (int s = 0; s < S; ++s) met |= act[s] && rows[b][s] <= tol;
+          if (met) {
+            nrows = b + 1;
+            break;
+          }
+        }
+        prof_drop_dataflow(ctx, B - nrows);
+        prof_harvest(ctx);
+      } else {
+        if (df) {
+          TRY(df_sweep(ctx, R, rs, psi, phil, nullptr, R.active, R.vprev, st));
+        } else {
+          CK(cudaGraphLaunch(graph.exec, st));
+          for (int i = 0; i < QFS_PROF_KINDS; ++i) ctx->prof.launches[i] += graph.launches[i];
+        }
+        rows.assign(1, std::vector<double>());
+        TRY(read_costs(ctx, R.costs, S, rows[0], R.err));
+        if (ctx->prof.on && !df) prof_harvest_graph(ctx);
+        nrows = 1;
+      }
+      row = 0;
     }
-    TRY(read_costs(ctx, R.costs, S, c, R.err));
-    if (ctx->prof.on && !df) prof_harvest_graph(ctx);
+    c = rows[row++];
     for (int s = 0; s < S; ++s)
       if (!act[s]) c[s] = prev[s];
     if (R.prec == QFS_FP64) {

@@ -113,6 +113,8 @@ struct DfArgs {
   double* resid_partials;               // S x part_stride x 32, residual step only
   int part_stride;                      // slots per start: the most chunks of any step
   double* resid_cost; double inv_M;     // residual step output
+  int* stop;                            // nullable: set when an active start's cost <= stop_tol; a launch
+  double stop_tol;                      //   that finds it set returns at once (batched sweeps)
   unsigned long long* item_trace;       // nullable: per work item (dequeued, ready, processed, CTA)
   unsigned long long* trace;            // nullable: per (step, start) 4 global-timer stamps (first
                                         // chunk started, last chunk done, partials summed, published)

@@ -799,6 +799,8 @@ __global__ void __launch_bounds__(df_threads<T>(), 1) k_sweep_df(DfArgs a) {
   // Thread 0 takes the next item when the CTA is free (a reservation held
   // while the current item runs would delay that item by a whole item).
   // A CTA's items increase, so the step search resumes where it stopped.
+  // A sweep queued behind one that met the tolerance does nothing.
+  if (a.stop != nullptr && ld_volatile_i32(a.stop)) return;
   int i = 0;
   for (;;) {
     if (threadIdx.x == 0) {
@@ -862,7 +864,10 @@ __global__ void __launch_bounds__(df_threads<T>(), 1) k_sweep_df(DfArgs a) {
             for (int b = lane; b < st.nchunk; b += 32) t += __ldcg(pp + (long long)b * 32);
 #pragma unroll
             for (int m = 16; m >= 1; m >>= 1) t += __shfl_xor_sync(FULL, t, m);
-            if (lane == 0) a.resid_cost[s] = t * a.inv_M;
+            if (lane == 0) {
+              a.resid_cost[s] = t * a.inv_M;
+              if (a.stop != nullptr && t * a.inv_M <= a.stop_tol) atomicExch(a.stop, 1);
+            }
           }
         } else {
           // Sum the chunk partials with all warps (warp w takes chunks w,
@@ -887,6 +892,9 @@ __global__ void __launch_bounds__(df_threads<T>(), 1) k_sweep_df(DfArgs a) {
           // accuracy of their environments (no skew-Hermitian correction);
           // FP64 sweeps: polar to FP64 rounding (two corrections).
           df_update<T, sizeof(T) == 4 ? 0 : 2>(st.upd, s, sh, v);
+          if (a.stop != nullptr && st.upd.cost_out != nullptr && threadIdx.x == 0 &&
+              st.upd.cost_out[s] <= a.stop_tol)
+            atomicExch(a.stop, 1);
         }
       }
       __syncthreads();
