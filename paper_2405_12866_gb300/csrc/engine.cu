@@ -248,6 +248,9 @@ struct Run {
   // Dataflow sweep: step table (device), control words, partial sums.
   DfStep* df_steps = nullptr;
   unsigned* df_ctrl = nullptr;
+  size_t df_ctrl_cap = 0;
+  int df_slot = 0;              // control slot of the next sweep
+  bool df_slot_zero = false;    // that slot is known to be zero (the previous sweep cleared it)
   double* df_partials = nullptr;
   double* df_resid = nullptr;
   int df_cap = 0;           // steps the table holds
@@ -296,7 +299,8 @@ size_t carve(Run& R, char* base, bool need_U, bool need_envs) {
   R.err = R.flag ? R.flag + 1 : nullptr;
   R.envs = need_envs ? (double2*)take((size_t)R.S * R.L * 16 * sizeof(double2)) : nullptr;
   R.df_steps = (DfStep*)take((size_t)std::max(R.df_cap, 1) * sizeof(DfStep));
-  R.df_ctrl = (unsigned*)take(sizeof(unsigned) * (1 + ((size_t)R.df_cap + 1) * R.S));
+  R.df_ctrl_cap = 1 + ((size_t)R.df_cap + 1) * R.S;
+  R.df_ctrl = (unsigned*)take(sizeof(unsigned) * 2 * R.df_ctrl_cap);  // two slots: this sweep's, the next's
   R.df_partials = (double*)take(sizeof(double) * 32 * (size_t)R.S * std::max(R.df_max_nchunk, 1));
   // The residual pass keeps its double partials apart: in complex64 the
   // environment partials are floats, and one start's residual slots would
@@ -744,7 +748,8 @@ void sweep(qfs_ctx* ctx, Run& R, Real r, const Slice& sl, double2* g64, float2* 
 // sweep() up to the order of the reduction sums).  The step table is built
 // and uploaded once per (precision, outputs) and reused by later sweeps.
 int df_sweep(qfs_ctx* ctx, Run& R, Real r, const void* psi, const void* phil, double2* envs, const int* active,
-             double2* vprev, cudaStream_t st, int* stop = nullptr, double stop_tol = 0.0) {
+             double2* vprev, cudaStream_t st, int* stop = nullptr, double stop_tol = 0.0,
+             double* cost_row = nullptr) {
   const void* key[4] = {psi, envs, active, vprev};
   if (R.df_key_r != (int)r || std::memcmp(key, R.df_key, sizeof(key)) != 0) {
     std::vector<DfStep> steps;
@@ -762,17 +767,23 @@ int df_sweep(qfs_ctx* ctx, Run& R, Real r, const void* psi, const void* phil, do
     std::memcpy(R.df_key, key, sizeof(key));
     R.df_key_r = (int)r;
   }
-  const size_t nctrl = 1 + ((size_t)R.df_nsteps + 1) * R.S;
-  CK(cudaMemsetAsync(R.df_ctrl, 0, sizeof(unsigned) * nctrl, st));
+  // Control words (queue, chunk counts, published steps) alternate between
+  // two slots; each sweep clears the slot of the next one at its entry.
+  unsigned* ctrl = R.df_ctrl + (size_t)R.df_slot * R.df_ctrl_cap;
+  unsigned* next = R.df_ctrl + (size_t)(R.df_slot ^ 1) * R.df_ctrl_cap;
+  if (!R.df_slot_zero) CK(cudaMemsetAsync(ctrl, 0, sizeof(unsigned) * R.df_ctrl_cap, st));
   DfArgs a{};
   a.steps = R.df_steps;
   a.nsteps = R.df_nsteps;
   a.S = R.S;
   a.total_items = R.df_items;
   a.active = active;
-  a.queue = R.df_ctrl;
-  a.chunk_cnt = R.df_ctrl + 1;
-  a.done = R.df_ctrl + 1 + (size_t)R.df_nsteps * R.S;
+  a.queue = ctrl;
+  a.chunk_cnt = ctrl + 1;
+  a.done = ctrl + 1 + (size_t)R.df_nsteps * R.S;
+  a.zero_next = next;
+  a.zero_count = (int)R.df_ctrl_cap;
+  a.cost_row = cost_row;
   a.err = R.err;
   a.partials = R.df_partials;
   a.resid_partials = R.df_resid;
@@ -790,7 +801,10 @@ int df_sweep(qfs_ctx* ctx, Run& R, Real r, const void* psi, const void* phil, do
     ctx->df_trace_items = a.item_trace ? R.df_items : 0;
   }
   ProfScope ps(ctx, QFS_PROF_DATAFLOW, R.df_bytes, st);
+  R.df_slot_zero = false;
   CK(launch_sweep_df(r, a, ctx->num_sms, st));
+  R.df_slot ^= 1;
+  R.df_slot_zero = true;
   return QFS_OK;
 }
 
@@ -987,11 +1001,9 @@ int run_multistart(qfs_ctx* ctx, Run& R, const qfs_params* p, Outcome& out) {
       const int B = batch ? std::min(kSweepBatch, p->max_sweeps - sweeps + 1) : 1;
       if (df && B > 1) {
         CK(cudaMemsetAsync(stop, 0, sizeof(int), st));
-        for (int b = 0; b < B; ++b) {
-          TRY(df_sweep(ctx, R, rs, psi, phil, nullptr, R.active, R.vprev, st, stop, tol));
-          CK(cudaMemcpyAsync(R.cost_rows + (size_t)b * S, R.costs, sizeof(double) * S, cudaMemcpyDeviceToDevice,
-                             st));
-        }
+        for (int b = 0; b < B; ++b)
+          TRY(df_sweep(ctx, R, rs, psi, phil, nullptr, R.active, R.vprev, st, stop, tol,
+                       R.cost_rows + (size_t)b * S));
         TRY(read_rows(ctx, R.cost_rows, S, B, rows, R.err));
         // The sweep whose cost met the tolerance ends the batch; the
         // launches behind it returned at once.

@@ -113,6 +113,8 @@ struct DfArgs {
   double* resid_partials;               // S x part_stride x 32, residual step only
   int part_stride;                      // slots per start: the most chunks of any step
   double* resid_cost; double inv_M;     // residual step output
+  double* cost_row;                     // nullable: this sweep's costs are also written here
+  unsigned* zero_next; int zero_count;  // nullable: the next sweep's control words, zeroed at entry
   int* stop;                            // nullable: set when an active start's cost <= stop_tol; a launch
   double stop_tol;                      //   that finds it set returns at once (batched sweeps)
   unsigned long long* item_trace;       // nullable: per work item (dequeued, ready, processed, CTA)

@@ -799,6 +799,10 @@ __global__ void __launch_bounds__(df_threads<T>(), 1) k_sweep_df(DfArgs a) {
   // Thread 0 takes the next item when the CTA is free (a reservation held
   // while the current item runs would delay that item by a whole item).
   // A CTA's items increase, so the step search resumes where it stopped.
+  // The next sweep's control words (a slot this sweep does not use).
+  if (a.zero_next != nullptr)
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < a.zero_count; k += gridDim.x * blockDim.x)
+      a.zero_next[k] = 0u;
   // A sweep queued behind one that met the tolerance does nothing.
   if (a.stop != nullptr && ld_volatile_i32(a.stop)) return;
   int i = 0;
@@ -866,6 +870,7 @@ __global__ void __launch_bounds__(df_threads<T>(), 1) k_sweep_df(DfArgs a) {
             for (int m = 16; m >= 1; m >>= 1) t += __shfl_xor_sync(FULL, t, m);
             if (lane == 0) {
               a.resid_cost[s] = t * a.inv_M;
+              if (a.cost_row != nullptr) a.cost_row[s] = t * a.inv_M;
               if (a.stop != nullptr && t * a.inv_M <= a.stop_tol) atomicExch(a.stop, 1);
             }
           }
@@ -892,9 +897,11 @@ __global__ void __launch_bounds__(df_threads<T>(), 1) k_sweep_df(DfArgs a) {
           // accuracy of their environments (no skew-Hermitian correction);
           // FP64 sweeps: polar to FP64 rounding (two corrections).
           df_update<T, sizeof(T) == 4 ? 0 : 2>(st.upd, s, sh, v);
-          if (a.stop != nullptr && st.upd.cost_out != nullptr && threadIdx.x == 0 &&
-              st.upd.cost_out[s] <= a.stop_tol)
-            atomicExch(a.stop, 1);
+          if (st.upd.cost_out != nullptr && threadIdx.x == 0) {
+            const double cost = st.upd.cost_out[s];
+            if (a.cost_row != nullptr) a.cost_row[s] = cost;
+            if (a.stop != nullptr && cost <= a.stop_tol) atomicExch(a.stop, 1);
+          }
         }
       }
       __syncthreads();
