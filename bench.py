@@ -261,17 +261,22 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     ctx = qfs.Context(local, stream.cuda_stream)
 
-    # Inputs for every step, generated on the host and made resident before timing.
+    # Inputs for every step, generated on the host and made resident before
+    # timing.  With --targets-per-call T > 1 a step is one call that
+    # instantiates T targets together (their starts share the sweep launches).
+    TPC = 1 if args.restart_doubling else max(1, args.targets_per_call)
     n_steps = args.warmup + args.steps
     from paper_2405_12866_gb300.ranks import combine, target_seeds
-    probs = [_problem(kind, seed) for seed in target_seeds(rank, n_steps)]
+    probs = [_problem(kind, seed) for seed in target_seeds(rank, n_steps * TPC)]
     first = probs[0]
     L, S, M, n = first.L, first.S, first.M, first.n
     dev_in = []
-    for p in probs:
-        dev_in.append((torch.from_numpy(p.U).to(dev), torch.from_numpy(p.samples()).to(dev),
-                       torch.from_numpy(np.ascontiguousarray(p.init_gates())).to(dev)))
-    out = torch.zeros((L, 4, 4), dtype=torch.complex128, device=dev)
+    for i in range(n_steps):
+        grp = probs[i * TPC:(i + 1) * TPC]
+        dev_in.append((torch.from_numpy(np.stack([p.U for p in grp])).to(dev),
+                       torch.from_numpy(np.stack([p.samples() for p in grp])).to(dev),
+                       torch.from_numpy(np.ascontiguousarray(np.stack([p.init_gates() for p in grp]))).to(dev)))
+    out = torch.zeros((TPC, L, 4, 4), dtype=torch.complex128, device=dev)
     prm = qfs.default_params(M=M, multistarts=S, max_sweeps=first.max_sweeps, dist_tol=first.tol,
                              precision=prec, start_groups=args.start_groups,
                              restart_doubling=1 if args.restart_doubling else 0)
@@ -280,9 +285,11 @@ def run_ours(args):
         if args.restart_doubling:
             # double-and-restart draws its training states itself (host target)
             prm.seed = probs[i].seed
-            return ctx.instantiate(n, first.pairs, probs[i].U, prm)
+            return [ctx.instantiate(n, first.pairs, probs[i].U, prm)]
         U, Psi, G0 = dev_in[i]
-        return ctx.instantiate_dev(n, first.pairs, U, Psi, G0, prm, out)
+        if TPC == 1:
+            return [ctx.instantiate_dev(n, first.pairs, U[0], Psi[0], G0[0], prm, out[0])]
+        return ctx.instantiate_many_dev(n, first.pairs, U, Psi, G0, prm, out)
 
     for i in range(args.warmup):
         step(i)
@@ -296,7 +303,7 @@ def run_ours(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(dev)
     e0.record(stream)
-    results = [step(args.warmup + i) for i in range(args.steps)]
+    results = [r for i in range(args.steps) for r in step(args.warmup + i)]
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ctx.profile(False)
@@ -318,10 +325,10 @@ def run_ours(args):
     if args.e2e_steps > 0:
         hin = []
         for i in range(args.e2e_steps):
-            p = probs[(args.warmup + i) % n_steps]
-            U_h = torch.from_numpy(p.U).pin_memory().numpy()
-            Ps_h = torch.from_numpy(p.samples()).pin_memory().numpy()
-            G_h = torch.from_numpy(np.ascontiguousarray(p.init_gates())).pin_memory().numpy()
+            grp = [probs[((args.warmup + i) % n_steps) * TPC + t] for t in range(TPC)]
+            U_h = torch.from_numpy(np.stack([p.U for p in grp])).pin_memory().numpy()
+            Ps_h = torch.from_numpy(np.stack([p.samples() for p in grp])).pin_memory().numpy()
+            G_h = torch.from_numpy(np.ascontiguousarray(np.stack([p.init_gates() for p in grp]))).pin_memory().numpy()
             hin.append((U_h, Ps_h, G_h))
         torch.cuda.synchronize(dev)
         if world > 1:
@@ -331,17 +338,20 @@ def run_ours(args):
             e2e_res = []
             for i, (U_h, Ps_h, G_h) in enumerate(hin):
                 prm.seed = probs[(args.warmup + i) % n_steps].seed
-                e2e_res.append(ctx.instantiate(n, first.pairs, U_h, prm))
+                e2e_res.append(ctx.instantiate(n, first.pairs, U_h[0], prm))
+        elif TPC == 1:
+            e2e_res = [ctx.instantiate(n, first.pairs, U_h[0], prm, Ps_h[0], G_h[0]) for (U_h, Ps_h, G_h) in hin]
         else:
-            e2e_res = [ctx.instantiate(n, first.pairs, U_h, prm, Ps_h, G_h) for (U_h, Ps_h, G_h) in hin]
+            e2e_res = [r for (U_h, Ps_h, G_h) in hin
+                       for r in ctx.instantiate_many(n, first.pairs, U_h, prm, Ps_h, G_h)]
         torch.cuda.synchronize(dev)
         t_e2e = time.perf_counter() - t0
         conv_e2e = sum(r.converged for r in e2e_res)
         (t_e2e,), (conv_e2e,) = combine([t_e2e], [conv_e2e], dev)
         N = 1 << n
         e2e = {"value": conv_e2e / t_e2e, "unit": UNIT,
-               "h2d_bytes_per_step": 16 * (N * N + N * M + S * L * 16),
-               "d2h_bytes_per_step": 16 * L * 16 + 8 * S, "steps": args.e2e_steps}
+               "h2d_bytes_per_step": TPC * 16 * (N * N + N * M + S * L * 16),
+               "d2h_bytes_per_step": TPC * (16 * L * 16 + 8 * S), "steps": args.e2e_steps}
 
     peak, peak_src = peaks()
     # The dominant kernel: the dataflow sweep (one launch per sweep of all
@@ -365,8 +375,9 @@ def run_ours(args):
                                                      if args.restart_doubling else ""),
                    "n": n, "gates": L, "M": M, "multistarts": S,
                    "tol": first.tol, "max_sweeps": first.max_sweeps, "parallelism": f"{world} independent ranks",
+                   "targets_per_call": TPC,
                    "l2": "inputs larger than L2 (B list 512 MiB per target), no flush"},
-        "converged": int(conv_all), "instantiations": args.steps * world,
+        "converged": int(conv_all), "instantiations": args.steps * world * TPC,
         "sweeps_per_instantiation": float(np.mean(sweeps)),
         "training_states": [int(r.training_states) for r in results],
         "roofline": {"bound": "hbm", "kernel": kdesc,
@@ -384,7 +395,7 @@ def run_ours(args):
         cores = os.cpu_count()
         with ctx_mp.Pool(cores) as pool:
             line["cpu_baseline"] = oracle_sample(kind, 0, float(np.mean(sweeps)),
-                                                 conv_all / (args.steps * world), pool=pool, cores=cores)
+                                                 conv_all / (args.steps * world * TPC), pool=pool, cores=cores)
         line["cpu_baseline"].pop("seconds_per_sweep_all_starts", None)
         line["cpu_baseline"].pop("seconds_precompute", None)
     if rank == 0:
@@ -775,6 +786,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="brick_n12")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--targets-per-call", type=int, default=1,
+                    help="instantiate this many targets per call, their starts sweeping together")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--batch-problems", type=int, default=4096)
     ap.add_argument("--plateau", action="store_true",

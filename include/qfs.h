@@ -92,6 +92,8 @@ typedef struct {
                                     (Appendix D): QFS_STATES_HAAR (columns of a Haar-random
                                     unitary) or QFS_STATES_BASIS (distinct computational-basis
                                     states, uniform without replacement) */
+  int32_t concurrent_targets;    /* qfs_instantiate_many: target slots swept together (0 = 4); a slot
+                                    whose target finishes takes the next one */
 } qfs_params;
 
 typedef struct {
@@ -215,6 +217,27 @@ int qfs_instantiate_dev(qfs_ctx* ctx, const qfs_circuit* circuit, const double* 
                         const double* samples_dev, const double* init_gates_dev,
                         const qfs_params* p, double* gates_out_dev, qfs_result* result,
                         double* start_costs);
+
+/* T independent instantiations of one circuit structure in one call: every
+ * target's starts sweep together in the same dataflow launches, so the
+ * per-start dependency chain of one target is hidden behind the work of the
+ * others (throughput mode).  Each target follows exactly the rules of
+ * qfs_instantiate (its own first converged sweep, its own selection) and
+ * gets the result it would get alone: a target's work items and sums do not
+ * depend on the other targets.  Arrays are target-major: targets T x N x N,
+ * samples T x N x M and init_gates T x multistarts x L x 16 (either may be
+ * NULL on the host entry: target t then draws from p->seed + t), gates_out
+ * T x L x 16, results[T], start_costs T x multistarts (may be NULL).
+ * QFS_EUNSUPPORTED with restart_doubling, without a cooperative launch, or
+ * for odd M in QFS_MIXED. */
+int qfs_instantiate_many(qfs_ctx* ctx, const qfs_circuit* circuit, int32_t T, const double* targets,
+                         const double* samples, const double* init_gates, const qfs_params* p,
+                         double* gates_out, qfs_result* results, double* start_costs);
+/* As qfs_instantiate_many with targets, samples, init_gates and gates_out in
+ * device memory (samples and init_gates required). */
+int qfs_instantiate_many_dev(qfs_ctx* ctx, const qfs_circuit* circuit, int32_t T, const double* targets_dev,
+                             const double* samples_dev, const double* init_gates_dev, const qfs_params* p,
+                             double* gates_out_dev, qfs_result* results, double* start_costs);
 
 /* Exactly one sweep (Section 3) for S starts, for parity checks: from
  * gates_in (host, S x L x 16) with target (host N x N) and samples (host

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <complex>
 #include <cstdarg>
@@ -206,6 +207,9 @@ constexpr int kSweepBatch = 4;
 // Device buffers of one run, carved from the context's workspace.
 struct Run {
   int n = 0, L = 0, M = 0, S = 0;
+  int T = 1, spt = 1;      // target slots swept together and starts per slot (S = T * spt); start s
+                           // belongs to slot s / spt, and U, Psi, Phi_L hold one copy per slot
+  std::vector<const double2*> Uslot;  // the target of each slot (N x N, device)
   long long N = 0, sN = 0;
   std::vector<int> pairs;
   int prec = QFS_FP64;
@@ -278,12 +282,12 @@ size_t carve(Run& R, char* base, bool need_U, bool need_envs) {
   const Real rs = R.prec == QFS_MIXED ? R32 : R64;
   const size_t es = elem_bytes(rs);
   const size_t state64 = (size_t)R.sN * sizeof(double2);
-  R.U_copy = need_U ? (double2*)take((size_t)R.N * R.N * sizeof(double2)) : nullptr;
-  R.psi64 = (double2*)take(state64);
-  R.phil64 = (double2*)take(state64);
+  R.U_copy = need_U ? (double2*)take((size_t)R.T * R.N * R.N * sizeof(double2)) : nullptr;
+  R.psi64 = (double2*)take(R.T * state64);
+  R.phil64 = (double2*)take(R.T * state64);
   if (R.prec == QFS_MIXED) {
-    R.psi32 = (float2*)take((size_t)R.sN * sizeof(float2));
-    R.phil32 = (float2*)take((size_t)R.sN * sizeof(float2));
+    R.psi32 = (float2*)take((size_t)R.T * R.sN * sizeof(float2));
+    R.phil32 = (float2*)take((size_t)R.T * R.sN * sizeof(float2));
   }
   R.B = take((size_t)std::max(R.L - 1, 1) * R.S * R.sN * es);
   R.phi = take((size_t)R.S * R.sN * es);
@@ -404,13 +408,15 @@ void df_build(const qfs_ctx* ctx, const Run& R, Real r, const void* psi, const v
   // Items per CTA and step: forward steps have no update on the chain, so
   // fewer, larger items pay off; backward steps keep more, smaller items so
   // that a start's chunks finish sooner and its update starts earlier.
+  // Chunks are sized from one target's starts, so a start's items (and its
+  // sums) are the same whether it sweeps alone or beside other targets.
   auto chunk_it = [&](DfStep& st, double bytes_per_unit) {
-    const double step_bytes = bytes_per_unit * st.units * S;
+    const double step_bytes = bytes_per_unit * st.units * R.spt;
     const bool fwd = st.kind == DF_FWD || st.kind == DF_FWD2;
     const double per_cta = fwd ? ctx->df_items_per_cta_fwd : ctx->df_items_per_cta;
     const double target = std::min(ctx->df_item_bytes, std::max(16.0 * 1024.0, step_bytes / (per_cta * resident)));
     df_chunking(st, bytes_per_unit, target);
-    *bytes += step_bytes;
+    *bytes += bytes_per_unit * st.units * S;
   };
   // Forward: gates k and k+1 on four distinct qubits go in one step (B_k is
   // then written but not read back), others one at a time.
@@ -418,6 +424,7 @@ void df_build(const qfs_ctx* ctx, const Run& R, Real r, const void* psi, const v
     DfStep st{};
     st.in = k == 1 ? psi : B_ptr(k - 1);
     st.in_stride = k == 1 ? 0 : sN;
+    st.in_gstride = k == 1 ? sN : 0;
     st.out = B_ptr(k);
     st.gate = gate_ptr(k - 1);
     st.gate_stride = gstride;
@@ -450,14 +457,17 @@ void df_build(const qfs_ctx* ctx, const Run& R, Real r, const void* psi, const v
     int ua = qa, ub = qb;
     st.in = k == 1 ? psi : B_ptr(k - 1);
     st.in_stride = k == 1 ? 0 : sN;
+    st.in_gstride = k == 1 ? sN : 0;
     if (k == L) {
       st.phi_in = phil;
       st.phi_in_stride = 0;
+      st.phi_in_gstride = sN;
       st.phi_out = nullptr;
       st.gate = nullptr;
     } else {
       st.phi_in = k == L - 1 ? phil : R.phi;
       st.phi_in_stride = k == L - 1 ? 0 : sN;
+      st.phi_in_gstride = k == L - 1 ? sN : 0;
       st.phi_out = R.phi;
       st.gate = gate_ptr(k);
       ua = R.pairs[2 * k];
@@ -498,8 +508,10 @@ void df_build(const qfs_ctx* ctx, const Run& R, Real r, const void* psi, const v
     st.kind = DF_RESID;
     st.in = psi;
     st.in_stride = 0;
+    st.in_gstride = sN;
     st.phi_in = L == 1 ? phil : R.phi;
     st.phi_in_stride = L == 1 ? 0 : sN;
+    st.phi_in_gstride = L == 1 ? sN : 0;
     st.phi_out = nullptr;
     st.gate = gate_ptr(0);
     st.gate_stride = gstride;
@@ -510,17 +522,21 @@ void df_build(const qfs_ctx* ctx, const Run& R, Real r, const void* psi, const v
   }
   long long item = 0;
   for (DfStep& st : steps) {
+    st.spt = std::max(R.spt, 1);
     st.item0 = item;
     item += (long long)S * st.nchunk;
   }
 }
 
-int prepare(qfs_ctx* ctx, Run& R, const qfs_circuit* c, int M, int S, int prec, double beta,
-            bool need_U, bool need_envs, int groups = 1, bool validate = false) {
+int prepare(qfs_ctx* ctx, Run& R, const qfs_circuit* c, int M, int S_target, int prec, double beta,
+            bool need_U, bool need_envs, int groups = 1, bool validate = false, int T = 1) {
   R.validate = validate;
   R.n = c->n;
   R.L = c->L;
   R.M = M;
+  R.T = T;
+  R.spt = S_target;
+  const int S = T * S_target;
   R.S = S;
   R.N = 1LL << c->n;
   R.sN = (long long)M << c->n;
@@ -567,7 +583,7 @@ int prepare(qfs_ctx* ctx, Run& R, const qfs_circuit* c, int M, int S, int prec, 
 // product; mixed runs the FP32 pair-arithmetic product (about 48 bits, far
 // below what the FP64 cost check at dist_tol resolves), with the B list,
 // not in use before the first sweep, as its scratch.  Returns the launches.
-int target_product(qfs_ctx* ctx, Run& R, const double2* psi, double2* out) {
+int target_product(qfs_ctx* ctx, Run& R, const double2* U, const double2* psi, double2* out) {
   cudaStream_t st = ctx->stream;
   const size_t bbytes = (size_t)std::max(R.L - 1, 1) * R.S * R.sN * elem_bytes(R.prec == QFS_MIXED ? R32 : R64);
   const size_t split_bytes = align_up((size_t)R.sN * sizeof(float4));
@@ -575,52 +591,65 @@ int target_product(qfs_ctx* ctx, Run& R, const double2* psi, double2* out) {
     const int splits = upsi_pair_splits((int)R.N, R.M, ctx->num_sms, bbytes - split_bytes);
     float4* ps = reinterpret_cast<float4*>(R.B);
     double2* scratch = reinterpret_cast<double2*>(static_cast<char*>(R.B) + split_bytes);
-    launch_gemm_upsi_pair(R.U, psi, out, (int)R.N, R.M, ps, scratch, splits, ctx->num_sms, st);
+    launch_gemm_upsi_pair(U, psi, out, (int)R.N, R.M, ps, scratch, splits, ctx->num_sms, st);
     return splits > 1 ? 3 : 2;
   }
-  launch_gemm_upsi(R.U, psi, out, (int)R.N, R.M, st);
+  launch_gemm_upsi(U, psi, out, (int)R.N, R.M, st);
   return 1;
 }
 
 // Phi_L = U Psi, complex64 copies for the mixed sweeps, gate copies.
-int setup_inputs(qfs_ctx* ctx, Run& R) {
+// Inputs of slot t, whose target U (R.Uslot[t]), training states
+// (R.psi64 + t sN) and initial gates (its starts' rows of R.g64) are in
+// place: input checks, Phi_L = U Psi, the complex64 copies, the warm starts
+// and the slot's starts active.
+int setup_slot(qfs_ctx* ctx, Run& R, int t) {
   cudaStream_t st = ctx->stream;
-  CK(cudaMemsetAsync(R.flag, 0, sizeof(int) * 4, st));
-  CK(cudaMemsetAsync(R.counters, 0, sizeof(unsigned) * (R.S + 1), st));
+  const size_t so = (size_t)t * R.sN, go = (size_t)t * R.spt * R.L * 16;
+  CK(cudaMemsetAsync(R.flag, 0, sizeof(int), st));
   {
     ProfScope ps(ctx, QFS_PROF_OTHER, 0.0);
-    launch_nonfinite_check(reinterpret_cast<const double*>(R.U), 2 * R.N * R.N, R.flag, st);
+    launch_nonfinite_check(reinterpret_cast<const double*>(R.Uslot[t]), 2 * R.N * R.N, R.flag, st);
   }
   {
     ProfScope ps(ctx, QFS_PROF_OTHER, 0.0);
-    launch_nonfinite_check(reinterpret_cast<const double*>(R.psi64), 2 * R.sN, R.flag, st);
+    launch_nonfinite_check(reinterpret_cast<const double*>(R.psi64 + so), 2 * R.sN, R.flag, st);
   }
   {
     ProfScope ps(ctx, QFS_PROF_OTHER, 0.0);
-    launch_nonfinite_check(reinterpret_cast<const double*>(R.g64), 2LL * R.S * R.L * 16, R.flag, st);
+    launch_nonfinite_check(reinterpret_cast<const double*>(R.g64 + go), 2LL * R.spt * R.L * 16, R.flag, st);
   }
   {
     ProfScope ps(ctx, QFS_PROF_GEMM, 8.0 * R.N * R.N * R.M);  // flops, not bytes
-    ctx->prof.launches[QFS_PROF_GEMM] += target_product(ctx, R, R.psi64, R.phil64) - 1;
+    ctx->prof.launches[QFS_PROF_GEMM] += target_product(ctx, R, R.Uslot[t], R.psi64 + so, R.phil64 + so) - 1;
   }
   if (R.prec == QFS_MIXED) {
     ProfScope ps(ctx, QFS_PROF_OTHER, 0.0);
-    launch_cast_c128_to_c64(R.psi64, R.psi32, R.sN, st);
-    launch_cast_c128_to_c64(R.phil64, R.phil32, R.sN, st);
-    launch_cast_c128_to_c64(R.g64, R.g32, (long long)R.S * R.L * 16, st);
+    launch_cast_c128_to_c64(R.psi64 + so, R.psi32 + so, R.sN, st);
+    launch_cast_c128_to_c64(R.phil64 + so, R.phil32 + so, R.sN, st);
+    launch_cast_c128_to_c64(R.g64 + go, R.g32 + go, (long long)R.spt * R.L * 16, st);
     ctx->prof.launches[QFS_PROF_OTHER] += 2;
   }
-  std::vector<int> ones(R.S, 1);
-  CK(cudaMemcpyAsync(R.active, ones.data(), sizeof(int) * R.S, cudaMemcpyHostToDevice, st));
+  std::vector<int> ones(R.spt, 1);
+  CK(cudaMemcpyAsync(R.active + (size_t)t * R.spt, ones.data(), sizeof(int) * R.spt, cudaMemcpyHostToDevice, st));
   {
     ProfScope ps(ctx, QFS_PROF_OTHER, 0.0);
-    launch_set_identity4(R.vprev, (long long)R.S * R.L, st);
+    launch_set_identity4(R.vprev + go, (long long)R.spt * R.L, st);
   }
   int flag = 0;
   CK(cudaMemcpyAsync(&flag, R.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   prof_harvest(ctx);
   if (flag) return fail(QFS_ENONFINITE, "NaN or Inf in the target, samples or initial gates");
+  return QFS_OK;
+}
+
+int setup_inputs(qfs_ctx* ctx, Run& R) {
+  cudaStream_t st = ctx->stream;
+  CK(cudaMemsetAsync(R.flag, 0, sizeof(int) * 4, st));
+  CK(cudaMemsetAsync(R.counters, 0, sizeof(unsigned) * (R.S + 1), st));
+  if ((int)R.Uslot.size() != R.T) R.Uslot.assign(R.T, R.U);
+  for (int t = 0; t < R.T; ++t) TRY(setup_slot(ctx, R, t));
   return QFS_OK;
 }
 
@@ -814,8 +843,8 @@ int check64(qfs_ctx* ctx, Run& R, int s, double* out, const double2* psi = nullp
             const double2* phil = nullptr) {
   cudaStream_t st = ctx->stream;
   const double2* g = R.g64 + (size_t)s * R.L * 16;
-  if (!psi) psi = R.psi64;
-  if (!phil) phil = R.phil64;
+  if (!psi) psi = R.psi64 + (size_t)(s / R.spt) * R.sN;
+  if (!phil) phil = R.phil64 + (size_t)(s / R.spt) * R.sN;
   const void* in = psi;
   for (int k = 1; k <= R.L; ++k) {
     const Geom gm = make_geom(R.n, R.M, R.pairs[2 * (k - 1)], R.pairs[2 * (k - 1) + 1]);
@@ -973,19 +1002,32 @@ struct Outcome {
 // start of that sweep (lowest index on ties).  With plateau_window > 0 a
 // start stops once its cost failed plateau_window times in a row to improve
 // by diff_tol_r relative to the newer cost (Appendix A) after min_sweeps.
-int run_multistart(qfs_ctx* ctx, Run& R, const qfs_params* p, Outcome& out) {
+// The multistart run of every slot.  A slot's starts sweep in lock step with
+// every other slot's; the slot's target is finished at the first sweep after
+// which one of its starts has cost <= tol (FP64-confirmed), when all its
+// starts stopped on a plateau, when the validation check halts it, or after
+// max_sweeps of its own sweeps.  finish(slot, outcome) then receives the
+// lowest-cost start (lowest index on ties) and returns true when it loaded a
+// new target into the slot (its starts begin afresh) or false to leave the
+// slot idle.  The run ends when every slot is idle.
+int run_multistart(qfs_ctx* ctx, Run& R, const qfs_params* p,
+                   const std::function<int(int, const Outcome&, bool&)>& finish) {
   cudaStream_t st = ctx->stream;
-  const int S = R.S;
+  const int S = R.S, T = R.T, spt = R.spt;
   const double tol = p->dist_tol;
-  std::vector<double> c, prev(S, std::numeric_limits<double>::infinity());
+  const double inf = std::numeric_limits<double>::infinity(), nan = std::numeric_limits<double>::quiet_NaN();
+  std::vector<double> c, prev(S, inf);
   std::vector<int> stall(S, 0), act(S, 1);
-  std::vector<double> c64(S, std::numeric_limits<double>::quiet_NaN());
+  std::vector<double> c64(S, nan);
   const Real rs = R.prec == QFS_MIXED ? R32 : R64;
   const void* psi = rs == R32 ? (const void*)R.psi32 : (const void*)R.psi64;
   const void* phil = rs == R32 ? (const void*)R.phil32 : (const void*)R.phil64;
-  int sweeps = 0;
-  bool done = false;
-  int fp64_sweeps = 0;
+  // Per slot: busy (a target is sweeping), its sweeps, FP64 refinement
+  // sweeps, validation outcome.
+  std::vector<char> busy(T, 1);
+  std::vector<int> tsweeps(T, 0), tfp64(T, 0);
+  std::vector<Outcome> cur(T);
+  int left = T;
   SweepGraph graph;
   const bool df = df_usable(ctx, R, rs);
   if (!df) TRY(capture_sweep(ctx, R, rs, psi, phil, graph));
@@ -995,10 +1037,12 @@ int run_multistart(qfs_ctx* ctx, Run& R, const qfs_params* p, Outcome& out) {
   int* stop = R.flag + 2;
   std::vector<std::vector<double>> rows;
   int row = 0, nrows = 0;
-  while (!done && sweeps < p->max_sweeps) {
-    ++sweeps;
+  while (left > 0) {
     if (row == nrows) {  // launch the next batch (or single sweep)
-      const int B = batch ? std::min(kSweepBatch, p->max_sweeps - sweeps + 1) : 1;
+      int room = p->max_sweeps;
+      for (int t = 0; t < T; ++t)
+        if (busy[t]) room = std::min(room, p->max_sweeps - tsweeps[t]);
+      const int B = batch ? std::max(1, std::min(kSweepBatch, room)) : 1;
       if (df && B > 1) {
         CK(cudaMemsetAsync(stop, 0, sizeof(int), st));
         for (int b = 0; b < B; ++b)
@@ -1033,97 +1077,142 @@ int run_multistart(qfs_ctx* ctx, Run& R, const qfs_params* p, Outcome& out) {
       row = 0;
     }
     c = rows[row++];
+    for (int t = 0; t < T; ++t)
+      if (busy[t]) ++tsweeps[t];
     for (int s = 0; s < S; ++s)
       if (!act[s]) c[s] = prev[s];
-    if (R.prec == QFS_FP64) {
-      for (int s = 0; s < S; ++s)
-        if (act[s] && c[s] <= tol) done = true;
-    } else {
+    std::vector<char> fin(T, 0);  // slots whose target finishes at this sweep
+    for (int t = 0; t < T; ++t) {
+      if (!busy[t]) continue;
+      const int s0 = t * spt, s1 = s0 + spt;
+      if (R.prec == QFS_FP64) {
+        for (int s = s0; s < s1; ++s)
+          if (act[s] && c[s] <= tol) fin[t] = 1;
+        continue;
+      }
       // Candidates by their complex64 cost; each is confirmed in FP64.
       std::vector<int> cand;
-      for (int s = 0; s < S; ++s)
+      for (int s = s0; s < s1; ++s)
         if (act[s] && c[s] <= tol) cand.push_back(s);
       for (int s : cand) {
         TRY(check64(ctx, R, s, &c64[s]));
-        if (c64[s] <= tol) done = true;
+        if (c64[s] <= tol) fin[t] = 1;
       }
-      if (!done) {
+      if (!fin[t]) {
         // complex64 reached tol but FP64 did not: refine that start in FP64.
         for (int s : cand) {
-          for (int it = 0; it < p->refine_sweeps_max && !done; ++it) {
+          const size_t toff = (size_t)t * R.sN;
+          for (int it = 0; it < p->refine_sweeps_max && !fin[t]; ++it) {
             sweep(ctx, R, R64, Slice{0, 1, 1, ctx->stream}, R.g64 + (size_t)s * R.L * 16,
-                  R.g32 + (size_t)s * R.L * 16, R.psi64, R.phil64, R.B64r, R.phi64r, R.partials64r,
+                  R.g32 + (size_t)s * R.L * 16, R.psi64 + toff, R.phil64 + toff, R.B64r, R.phi64r, R.partials64r,
                   R.nblk64_max, R.cost64r, nullptr, nullptr, R.stream_b64, R.vprev + (size_t)s * R.L * 16,
                   R.counters + R.S);
-            ++fp64_sweeps;
+            ++tfp64[t];
             std::vector<double> cr;
             TRY(read_costs(ctx, R.cost64r, 1, cr));
             if (cr[0] <= tol) {
               TRY(check64(ctx, R, s, &c64[s]));
-              if (c64[s] <= tol) done = true;
+              if (c64[s] <= tol) fin[t] = 1;
             }
           }
-          if (done) break;
+          if (fin[t]) break;
         }
       }
-      for (int s = 0; s < S; ++s)
+      for (int s = s0; s < s1; ++s)
         if (!std::isnan(c64[s])) c[s] = c64[s];
     }
-    if (R.validate && (done || sweeps >= p->min_sweeps)) {
+    if (R.validate && busy[0] && (fin[0] || tsweeps[0] >= p->min_sweeps)) {
       // Generalisation check (Sec. 3): the start with the lowest training
-      // cost, evaluated in FP64 on the validation states.
+      // cost, evaluated in FP64 on the validation states (one target).
       int b = -1;
       for (int s = 0; s < S; ++s)
         if (act[s] && (b < 0 || c[s] < c[b])) b = s;
       if (b >= 0) {
         double cv = 0.0;
         TRY(check64(ctx, R, b, &cv, R.psi_val64, R.phil_val64));
-        out.c_val = cv;
-        const double gen = c[b] > 0.0 ? cv / c[b] - 1.0 : (cv > 0.0 ? std::numeric_limits<double>::infinity() : 0.0);
+        cur[0].c_val = cv;
+        const double gen = c[b] > 0.0 ? cv / c[b] - 1.0 : (cv > 0.0 ? inf : 0.0);
         if (gen > p->overtrain_ratio) {
-          out.overtrained = true;
-          done = true;
+          cur[0].overtrained = true;
+          fin[0] = 1;
         }
       }
     }
-    if (!done && p->plateau_window > 0) {
-      bool changed = false;
+    bool act_changed = false;
+    if (p->plateau_window > 0) {
       for (int s = 0; s < S; ++s) {
-        if (!act[s]) continue;
+        const int t = s / spt;
+        if (!act[s] || !busy[t] || fin[t]) continue;
         if (std::isfinite(prev[s])) {
           const bool improved = std::fabs(prev[s]) - std::fabs(c[s]) > p->diff_tol_r * std::fabs(c[s]);
           stall[s] = improved ? 0 : stall[s] + 1;
-          if (stall[s] >= p->plateau_window && sweeps >= p->min_sweeps) {
+          if (stall[s] >= p->plateau_window && tsweeps[t] >= p->min_sweeps) {
             act[s] = 0;
-            changed = true;
+            act_changed = true;
           }
         }
       }
-      if (changed) {
+      for (int t = 0; t < T; ++t) {
+        if (!busy[t] || fin[t]) continue;
         bool any = false;
-        for (int s = 0; s < S; ++s) any |= act[s] != 0;
-        if (!any) done = true;
-        CK(cudaMemcpyAsync(R.active, act.data(), sizeof(int) * S, cudaMemcpyHostToDevice, st));
+        for (int s = t * spt; s < (t + 1) * spt; ++s) any |= act[s] != 0;
+        if (!any) fin[t] = 1;
       }
     }
+    for (int t = 0; t < T; ++t)
+      if (busy[t] && !fin[t] && tsweeps[t] >= p->max_sweeps) fin[t] = 1;
     prev = c;
+    for (int t = 0; t < T; ++t) {
+      if (!fin[t]) continue;
+      // Selection: lowest cost (FP64-confirmed where available), lowest
+      // index on ties.
+      Outcome& out = cur[t];
+      const int s0 = t * spt;
+      int best = s0;
+      for (int s = s0 + 1; s < s0 + spt; ++s)
+        if (prev[s] < prev[best]) best = s;
+      double cost = prev[best];
+      if (R.prec == QFS_MIXED) TRY(check64(ctx, R, best, &cost));
+      out.best = best - s0;
+      out.cost = cost;
+      out.sweeps = tsweeps[t];
+      out.converged = cost <= tol && !out.overtrained;
+      out.fp64_sweeps = tfp64[t];
+      out.start_costs.assign(prev.begin() + s0, prev.begin() + s0 + spt);
+      out.start_costs[best - s0] = cost;
+      bool refilled = false;
+      TRY(finish(t, out, refilled));
+      for (int s = s0; s < s0 + spt; ++s) {
+        prev[s] = inf;
+        stall[s] = 0;
+        c64[s] = nan;
+        if ((act[s] != 0) != refilled) act_changed = true;
+        act[s] = refilled ? 1 : 0;
+      }
+      cur[t] = Outcome();
+      tsweeps[t] = 0;
+      tfp64[t] = 0;
+      if (!refilled) {
+        busy[t] = 0;
+        --left;
+      }
+    }
+    if (act_changed && left > 0)
+      CK(cudaMemcpyAsync(R.active, act.data(), sizeof(int) * S, cudaMemcpyHostToDevice, st));
     if (R.prec == QFS_MIXED)
-      std::fill(c64.begin(), c64.end(), std::numeric_limits<double>::quiet_NaN());
+      for (int s = 0; s < S; ++s)
+        if (!std::isnan(c64[s])) c64[s] = nan;
   }
-  // Selection: lowest cost (FP64-confirmed where available), lowest index on ties.
-  int best = 0;
-  for (int s = 1; s < S; ++s)
-    if (prev[s] < prev[best]) best = s;
-  double cost = prev[best];
-  if (R.prec == QFS_MIXED) TRY(check64(ctx, R, best, &cost));
-  out.best = best;
-  out.cost = cost;
-  out.sweeps = sweeps;
-  out.converged = cost <= tol && !out.overtrained;
-  out.fp64_sweeps = fp64_sweeps;
-  out.start_costs = prev;
-  out.start_costs[best] = cost;
   return QFS_OK;
+}
+
+// One target (slot 0): run and report its outcome.
+int run_multistart(qfs_ctx* ctx, Run& R, const qfs_params* p, Outcome& out) {
+  return run_multistart(ctx, R, p, [&](int, const Outcome& o, bool& refilled) {
+    out = o;
+    refilled = false;
+    return (int)QFS_OK;
+  });
 }
 
 int ctx_check(const qfs_ctx* ctx) {
@@ -1178,7 +1267,7 @@ int instantiate_restarting(qfs_ctx* ctx, const qfs_circuit* c, const double* tar
     if (validate) {
       draw_states(p->training_distribution, sa, 5u, n, M, h.data());
       CK(cudaMemcpyAsync(R.psi_val64, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
-      ctx->prof.launches[QFS_PROF_GEMM] += target_product(ctx, R, R.psi_val64, R.phil_val64);
+      ctx->prof.launches[QFS_PROF_GEMM] += target_product(ctx, R, R.U, R.psi_val64, R.phil_val64);
       CK(cudaStreamSynchronize(st));
     }
     CK(cudaMemcpyAsync(R.g64, G.data(), G.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
@@ -1207,10 +1296,15 @@ int instantiate_restarting(qfs_ctx* ctx, const qfs_circuit* c, const double* tar
   }
 }
 
+// T targets of one structure swept together (several targets per dataflow
+// launch; T = 1: one instantiation).  Arrays are target-major: targets
+// T x N x N, samples T x N x M, initial gates T x multistarts x L x 16,
+// gates_out T x L x 16, result[T], start_costs T x multistarts.  Drawn
+// inputs of target t come from seed + t.
 int instantiate_common(qfs_ctx* ctx, const qfs_circuit* c, const double* target, bool target_dev,
                        const double* samples, bool samples_dev, const double* gates0,
                        bool gates_dev, uint64_t seed, const qfs_params* p, double* gates_out,
-                       bool out_dev, qfs_result* result, double* start_costs) {
+                       bool out_dev, qfs_result* result, double* start_costs, int T = 1) {
   TRY(check_circuit(c));
   if (!p) return fail(QFS_EINVAL, "params is NULL");
   if (!target) return fail(QFS_EINVAL, "target is NULL");
@@ -1227,6 +1321,12 @@ int instantiate_common(qfs_ctx* ctx, const qfs_circuit* c, const double* target,
                 p->training_distribution);
   if (p->restart_doubling && (samples || !(p->overtrain_ratio >= 0.0)))
     return fail(QFS_EINVAL, "restart_doubling needs library-drawn training states and overtrain_ratio >= 0");
+  if (T < 1) return fail(QFS_EINVAL, "T = %d: need >= 1 targets", T);
+  if (p->concurrent_targets < 0) return fail(QFS_EINVAL, "concurrent_targets = %d: need >= 0", p->concurrent_targets);
+  if (T > 1 && p->restart_doubling)
+    return fail(QFS_EUNSUPPORTED, "double-and-restart takes one target per call");
+  if ((long long)T * p->multistarts > 65535)
+    return fail(QFS_EUNSUPPORTED, "T x multistarts = %lld > 65535", (long long)T * p->multistarts);
   TRY(ctx_check(ctx));
   TRY(set_device(ctx));
   if (p->restart_doubling) return instantiate_restarting(ctx, c, target, target_dev, gates0, gates_dev, seed, p,
@@ -1234,45 +1334,73 @@ int instantiate_common(qfs_ctx* ctx, const qfs_circuit* c, const double* target,
   Run R;
   int groups = p->start_groups;
   if (groups <= 0) groups = p->multistarts >= 8 ? 2 : 1;
-  TRY(prepare(ctx, R, c, p->M, p->multistarts, p->precision, p->beta, !target_dev, false, groups));
+  // Targets sweep in `slots` concurrent slots; a slot whose target finishes
+  // takes the next target (continuous batching).
+  const int slots = T == 1 ? 1 : std::max(1, std::min(T, p->concurrent_targets > 0 ? p->concurrent_targets : 4));
+  TRY(prepare(ctx, R, c, p->M, p->multistarts, p->precision, p->beta, !target_dev, false, groups, false, slots));
+  if (slots > 1 && !df_usable(ctx, R, p->precision == QFS_MIXED ? R32 : R64))
+    return fail(QFS_EUNSUPPORTED, "several targets per call need the dataflow sweep (cooperative launch%s)",
+                p->precision == QFS_MIXED ? ", even M" : "");
   cudaStream_t st = ctx->stream;
-  const size_t gbytes = (size_t)R.S * R.L * 16 * sizeof(double2);
-  if (target_dev) {
-    R.U = reinterpret_cast<const double2*>(target);
-  } else {
-    CK(cudaMemcpyAsync(R.U_copy, target, (size_t)R.N * R.N * sizeof(double2), cudaMemcpyHostToDevice, st));
-    R.U = R.U_copy;
-  }
-  if (samples) {
-    CK(cudaMemcpyAsync(R.psi64, samples, (size_t)R.sN * sizeof(double2),
-                       samples_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-  } else {
-    std::vector<std::complex<double>> h((size_t)R.sN);
-    draw_states(p->training_distribution, seed, 1u, R.n, R.M, h.data());
-    CK(cudaMemcpyAsync(R.psi64, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
-    CK(cudaStreamSynchronize(st));
-  }
-  if (gates0) {
-    CK(cudaMemcpyAsync(R.g64, gates0, gbytes, gates_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-  } else {
-    std::vector<std::complex<double>> h((size_t)R.S * R.L * 16);
-    generate_gates(seed, R.S * R.L, h.data());
-    CK(cudaMemcpyAsync(R.g64, h.data(), gbytes, cudaMemcpyHostToDevice, st));
-    CK(cudaStreamSynchronize(st));
-  }
+  const size_t NN = (size_t)R.N * R.N, gsz = (size_t)R.spt * R.L * 16;
+  R.Uslot.assign(slots, nullptr);
+  std::vector<int> slot_target(slots, -1);
+  // Target i's inputs into slot t.
+  auto load = [&](int t, int i) -> int {
+    if (target_dev) {
+      R.Uslot[t] = reinterpret_cast<const double2*>(target) + (size_t)i * NN;
+    } else {
+      CK(cudaMemcpyAsync(R.U_copy + (size_t)t * NN, target + (size_t)i * NN * 2, NN * sizeof(double2),
+                         cudaMemcpyHostToDevice, st));
+      R.Uslot[t] = R.U_copy + (size_t)t * NN;
+    }
+    if (samples) {
+      CK(cudaMemcpyAsync(R.psi64 + (size_t)t * R.sN, samples + (size_t)i * R.sN * 2, (size_t)R.sN * sizeof(double2),
+                         samples_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    } else {
+      std::vector<std::complex<double>> h((size_t)R.sN);
+      draw_states(p->training_distribution, seed + (uint64_t)i, 1u, R.n, R.M, h.data());
+      CK(cudaMemcpyAsync(R.psi64 + (size_t)t * R.sN, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice,
+                         st));
+      CK(cudaStreamSynchronize(st));
+    }
+    if (gates0) {
+      CK(cudaMemcpyAsync(R.g64 + (size_t)t * gsz, gates0 + (size_t)i * gsz * 2, gsz * sizeof(double2),
+                         gates_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    } else {
+      std::vector<std::complex<double>> h(gsz);
+      generate_gates(seed + (uint64_t)i, R.spt * R.L, h.data());
+      CK(cudaMemcpyAsync(R.g64 + (size_t)t * gsz, h.data(), gsz * sizeof(double2), cudaMemcpyHostToDevice, st));
+      CK(cudaStreamSynchronize(st));
+    }
+    slot_target[t] = i;
+    return QFS_OK;
+  };
+  for (int t = 0; t < slots; ++t) TRY(load(t, t));
   TRY(setup_inputs(ctx, R));
-  Outcome o;
-  TRY(run_multistart(ctx, R, p, o));
-  CK(cudaMemcpyAsync(gates_out, R.g64 + (size_t)o.best * R.L * 16, (size_t)R.L * 16 * sizeof(double2),
-                     out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  result->cost = o.cost;
-  result->sweeps = o.sweeps;
-  result->converged = o.converged;
-  result->best_start = o.best;
-  result->fp64_sweeps = o.fp64_sweeps;
-  result->training_states = R.M;
-  if (start_costs) std::copy(o.start_costs.begin(), o.start_costs.end(), start_costs);
+  int next = slots;
+  auto finish = [&](int t, const Outcome& o, bool& refilled) -> int {
+    const int i = slot_target[t];
+    CK(cudaMemcpyAsync(gates_out + (size_t)i * R.L * 32, R.g64 + ((size_t)t * R.spt + o.best) * R.L * 16,
+                       (size_t)R.L * 16 * sizeof(double2), out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       st));
+    CK(cudaStreamSynchronize(st));
+    qfs_result& r = result[i];
+    r.cost = o.cost;
+    r.sweeps = o.sweeps;
+    r.converged = o.converged;
+    r.best_start = o.best;
+    r.fp64_sweeps = o.fp64_sweeps;
+    r.training_states = R.M;
+    if (start_costs) std::copy(o.start_costs.begin(), o.start_costs.end(), start_costs + (size_t)i * R.spt);
+    refilled = next < T;
+    if (refilled) {
+      TRY(load(t, next++));
+      TRY(setup_slot(ctx, R, t));
+    }
+    return QFS_OK;
+  };
+  TRY(run_multistart(ctx, R, p, finish));
   return QFS_OK;
 }
 
@@ -1294,6 +1422,7 @@ void qfs_default_params(qfs_params* p) {
   p->restart_doubling = 0;
   p->overtrain_ratio = 0.1;
   p->training_distribution = QFS_STATES_HAAR;
+  p->concurrent_targets = 0;
   p->seed = 0;
   p->dist_tol = 1e-8;
   p->diff_tol_r = 1e-5;
@@ -1503,6 +1632,23 @@ int qfs_instantiate_dev(qfs_ctx* ctx, const qfs_circuit* circuit, const double* 
   if (!samples_dev || !init_gates_dev) return fail(QFS_EINVAL, "samples and init_gates must be given");
   return instantiate_common(ctx, circuit, target_dev, true, samples_dev, true, init_gates_dev, true,
                             0, p, gates_out_dev, true, result, start_costs);
+}
+
+int qfs_instantiate_many(qfs_ctx* ctx, const qfs_circuit* circuit, int32_t T, const double* targets,
+                         const double* samples, const double* init_gates, const qfs_params* p,
+                         double* gates_out, qfs_result* results, double* start_costs) {
+  g_err.clear();
+  return instantiate_common(ctx, circuit, targets, false, samples, false, init_gates, false, p ? p->seed : 0, p,
+                            gates_out, false, results, start_costs, T);
+}
+
+int qfs_instantiate_many_dev(qfs_ctx* ctx, const qfs_circuit* circuit, int32_t T, const double* targets_dev,
+                             const double* samples_dev, const double* init_gates_dev, const qfs_params* p,
+                             double* gates_out_dev, qfs_result* results, double* start_costs) {
+  g_err.clear();
+  if (!samples_dev || !init_gates_dev) return fail(QFS_EINVAL, "samples and init_gates must be given");
+  return instantiate_common(ctx, circuit, targets_dev, true, samples_dev, true, init_gates_dev, true, 0, p,
+                            gates_out_dev, true, results, start_costs, T);
 }
 
 int qfs_sweep_once(qfs_ctx* ctx, const qfs_circuit* circuit, const double* target,

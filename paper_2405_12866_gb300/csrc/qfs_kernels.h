@@ -91,6 +91,9 @@ struct DfStep {
   int units, chunk, nchunk;             // units per start, units per chunk, chunks per start
   long long item0;                      // first work item of this step
   const void* in; long long in_stride;  // forward input / backward B_{k-1} / residual Psi
+  long long in_gstride;                 // per target (start s belongs to target s / spt): Psi of each target
+  long long phi_in_gstride;             // per target: Phi_L = U Psi of each target
+  int spt;                              // starts per target (targets swept together share one launch)
   void* out;                            // forward output B_k (start stride fg.sN)
   void* out2;                           // DF_FWD2: B_{k+1} (start stride bg.sN)
   const void* gate2;                    // DF_FWD2: gate k+1 (start stride gate_stride)

@@ -121,6 +121,18 @@ __device__ __forceinline__ void block_partials32(double mine, DfShared<T>& sh, P
   }
 }
 
+// Start s's input and Phi input: per-start stride, plus a per-target stride
+// for the arrays one per target (Psi, U Psi) when several targets share the
+// launch (start s belongs to target s / spt).
+template <typename T2>
+__device__ __forceinline__ const T2* df_in(const DfStep& st, int s) {
+  return reinterpret_cast<const T2*>(st.in) + s * st.in_stride + (long long)(s / st.spt) * st.in_gstride;
+}
+template <typename T2>
+__device__ __forceinline__ const T2* df_phi_in(const DfStep& st, int s) {
+  return reinterpret_cast<const T2*>(st.phi_in) + s * st.phi_in_stride + (long long)(s / st.spt) * st.phi_in_gstride;
+}
+
 // Gate of this start (16 complex) into shared memory.
 template <typename T>
 __device__ __forceinline__ void load_gate(const DfStep& st, int s, DfShared<T>& sh) {
@@ -139,7 +151,7 @@ __device__ void df_forward(const DfStep& st, int s, int c, DfShared<T>& sh) {
   T2 gr[16];
 #pragma unroll
   for (int i = 0; i < 16; ++i) gr[i] = sh.gs[i];
-  const T2* X = reinterpret_cast<const T2*>(st.in) + s * st.in_stride;
+  const T2* X = df_in<T2>(st, s);
   T2* Y = reinterpret_cast<T2*>(st.out) + s * st.fg.sN;
   const int MV = st.fg.M / VEC;
   const int u0 = c * st.chunk, u1 = min(u0 + st.chunk, st.units);
@@ -247,7 +259,7 @@ __device__ void df_forward2(const DfStep& st, int s, int c, DfShared<T>& sh, uin
   T2 g2[4];  // row qx of g_{k+1}
 #pragma unroll
   for (int m = 0; m < 4; ++m) g2[m] = sh.gs2[4 * qx + m];
-  const T2* X = reinterpret_cast<const T2*>(st.in) + s * st.in_stride;
+  const T2* X = df_in<T2>(st, s);
   T2* Y1 = reinterpret_cast<T2*>(st.out) + s * st.bg.sN;
   T2* Y2 = reinterpret_cast<T2*>(st.out2) + s * st.bg.sN;
   const uint32_t M = (uint32_t)st.bg.M;
@@ -356,8 +368,8 @@ __device__ void df_backward_q4(const DfStep& st, int s, int c, DfShared<T>& sh, 
       const T2 t = sh.gs[4 * j + y];
       gd[4 * y + j] = T2{t.x, -t.y};
     }
-  const T2* B = reinterpret_cast<const T2*>(st.in) + s * st.in_stride;
-  const T2* P = reinterpret_cast<const T2*>(st.phi_in) + s * st.phi_in_stride;
+  const T2* B = df_in<T2>(st, s);
+  const T2* P = df_phi_in<T2>(st, s);
   T2* Po = reinterpret_cast<T2*>(st.phi_out) + s * st.bg.sN;
   const uint32_t M = (uint32_t)st.bg.M;
   const uint32_t d0 = (1u << st.bg.pos[0]) * M, d1 = (1u << st.bg.pos[1]) * M;
@@ -499,8 +511,8 @@ __device__ void df_backward_gen(const DfStep& st, int s, int c, DfShared<T>& sh,
     const T2 t = sh.gs[4 * yp + y];
     return T2{t.x, -t.y};
   };
-  const T2* B = reinterpret_cast<const T2*>(st.in) + s * st.in_stride;
-  const T2* P = reinterpret_cast<const T2*>(st.phi_in) + s * st.phi_in_stride;
+  const T2* B = df_in<T2>(st, s);
+  const T2* P = df_phi_in<T2>(st, s);
   T2* Po = st.phi_out ? reinterpret_cast<T2*>(st.phi_out) + s * st.bg.sN : nullptr;
   const uint32_t M = (uint32_t)st.bg.M;
   uint32_t dpos[U];

@@ -33,7 +33,8 @@ QFS_STATES_BASIS = 1
 # Every function the header declares; the CPU tests check the library exports them.
 EXPORTS = [
     "qfs_default_params", "qfs_create", "qfs_destroy", "qfs_last_error", "qfs_device_sms",
-    "qfs_generate_inputs", "qfs_generate_states", "qfs_instantiate", "qfs_instantiate_ex", "qfs_instantiate_dev",
+    "qfs_generate_inputs", "qfs_generate_states", "qfs_instantiate", "qfs_instantiate_many",
+    "qfs_instantiate_many_dev", "qfs_instantiate_ex", "qfs_instantiate_dev",
     "qfs_sweep_once", "qfs_gate_update", "qfs_profile_enable", "qfs_profile_reset",
     "qfs_profile_read", "qfs_sweep_once_noalloc", "qfs_instantiate_batch",
     "qfs_instantiate_batch_dev", "qfs_gemm_bf16_dev", "qfs_ws_create", "qfs_ws_destroy", "qfs_ws_params",
@@ -61,7 +62,8 @@ class Params(C.Structure):
                 ("precision", C.c_int32), ("refine_sweeps_max", C.c_int32),
                 ("start_groups", C.c_int32), ("seed", C.c_uint64), ("dist_tol", C.c_double),
                 ("diff_tol_r", C.c_double), ("beta", C.c_double), ("restart_doubling", C.c_int32),
-                ("overtrain_ratio", C.c_double), ("training_distribution", C.c_int32)]
+                ("overtrain_ratio", C.c_double), ("training_distribution", C.c_int32),
+                ("concurrent_targets", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -98,6 +100,10 @@ def lib():
                                      C.POINTER(Result), _P]
     L.qfs_instantiate_dev.argtypes = [_P, C.POINTER(Circuit), _P, _P, _P, C.POINTER(Params), _P,
                                       C.POINTER(Result), _P]
+    L.qfs_instantiate_many.argtypes = [_P, C.POINTER(Circuit), C.c_int32, _P, _P, _P, C.POINTER(Params), _P,
+                                       C.POINTER(Result), _P]
+    L.qfs_instantiate_many_dev.argtypes = [_P, C.POINTER(Circuit), C.c_int32, _P, _P, _P, C.POINTER(Params), _P,
+                                           C.POINTER(Result), _P]
     L.qfs_sweep_once.argtypes = [_P, C.POINTER(Circuit), _P, _P, C.c_int32, C.c_int32, _P,
                                  C.c_int32, C.c_double, _P, _P, _P]
     L.qfs_gate_update.argtypes = [_P, C.c_int32, _P, _P, C.c_double, _P]
@@ -251,6 +257,45 @@ class Context:
                                             costs.ctypes.data))
         return InstantiateOutput(out, res.cost, res.sweeps, bool(res.converged), res.best_start,
                                  res.fp64_sweeps, costs, res.training_states)
+
+    def instantiate_many(self, n, pairs, targets, params: Params, samples=None, init_gates=None):
+        """T targets (T, N, N) host arrays in one call; samples (T, N, M) and
+        init_gates (T, S, L, 4, 4) or None (target t draws from seed + t).
+        Returns a list of InstantiateOutput."""
+        cir = _CircuitArg(n, pairs)
+        N = 1 << n
+        targets = np.ascontiguousarray(np.asarray(targets, dtype=np.complex128))
+        T = targets.shape[0]
+        targets = _host_c128(targets, (T, N, N))
+        S, L = params.multistarts, cir.c.L
+        sm = None if samples is None else _host_c128(samples, (T, N, params.M))
+        ig = None if init_gates is None else _host_c128(init_gates, (T, S, L, 4, 4))
+        out = np.zeros((T, L, 4, 4), dtype=np.complex128)
+        res = (Result * T)()
+        costs = np.zeros((T, S), dtype=np.float64)
+        _check(lib().qfs_instantiate_many(self._h, C.byref(cir.c), T, targets.ctypes.data,
+                                          None if sm is None else sm.ctypes.data,
+                                          None if ig is None else ig.ctypes.data, C.byref(params),
+                                          out.ctypes.data, res, costs.ctypes.data))
+        return [InstantiateOutput(out[t], res[t].cost, res[t].sweeps, bool(res[t].converged), res[t].best_start,
+                                  res[t].fp64_sweeps, costs[t], res[t].training_states) for t in range(T)]
+
+    def instantiate_many_dev(self, n, pairs, targets, samples, init_gates, params: Params, out):
+        """Device (torch complex128 CUDA) tensors: targets (T, N, N), samples
+        (T, N, M), init_gates (T, S, L, 4, 4), out (T, L, 4, 4)."""
+        cir = _CircuitArg(n, pairs)
+        for name, t in (("targets", targets), ("samples", samples), ("init_gates", init_gates), ("out", out)):
+            if not (t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.complex128"):
+                raise ValueError(f"{name} must be a contiguous complex128 CUDA tensor")
+        T = targets.shape[0]
+        res = (Result * T)()
+        costs = np.zeros((T, params.multistarts), dtype=np.float64)
+        _wait_torch(targets, samples, init_gates, out)
+        _check(lib().qfs_instantiate_many_dev(self._h, C.byref(cir.c), T, targets.data_ptr(), samples.data_ptr(),
+                                              init_gates.data_ptr(), C.byref(params), out.data_ptr(), res,
+                                              costs.ctypes.data))
+        return [InstantiateOutput(out[t], res[t].cost, res[t].sweeps, bool(res[t].converged), res[t].best_start,
+                                  res[t].fp64_sweeps, costs[t], res[t].training_states) for t in range(T)]
 
     def instantiate_dev(self, n, pairs, target, samples, init_gates, params: Params, out):
         """Device (torch complex128 CUDA) tensors in and out."""
