@@ -279,7 +279,7 @@ def run_ours(args):
     out = torch.zeros((TPC, L, 4, 4), dtype=torch.complex128, device=dev)
     prm = qfs.default_params(M=M, multistarts=S, max_sweeps=first.max_sweeps, dist_tol=first.tol,
                              precision=prec, start_groups=args.start_groups,
-                             restart_doubling=1 if args.restart_doubling else 0)
+                             restart_doubling=1 if args.restart_doubling else 0, concurrent_targets=args.slots)
 
     def step(i):
         if args.restart_doubling:
@@ -788,6 +788,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--targets-per-call", type=int, default=1,
                     help="instantiate this many targets per call, their starts sweeping together")
+    ap.add_argument("--slots", type=int, default=0,
+                    help="targets sweeping concurrently within a call (0: the library's choice)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--batch-problems", type=int, default=4096)
     ap.add_argument("--plateau", action="store_true",
