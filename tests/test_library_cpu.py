@@ -117,3 +117,23 @@ def test_state_draw_validation(lib):
     for args, frag in [((0, 2, 1, 3, 2), "distribution"), ((0, 1, 1, 3, 9), "M = 9"), ((0, 1, 1, 1, 1), "n = 1")]:
         assert lib.qfs_generate_states(*args, out.ctypes.data) == qfs.QFS_EINVAL
         assert frag in lib.qfs_last_error().decode()
+
+
+@pytest.mark.parametrize("T,kw,code,frag", [
+    (0, {}, "EINVAL", "T = 0"),
+    (2, dict(concurrent_targets=-1), "EINVAL", "concurrent_targets"),
+    (2, dict(restart_doubling=1), "EUNSUPPORTED", "one target per call"),
+])
+def test_many_targets_validation(lib, T, kw, code, frag):
+    """qfs_instantiate_many checks its arguments on the host, before any
+    device work (no context is needed to reach these errors)."""
+    n, pairs = 3, [(0, 1), (1, 2)]
+    cir = qfs._CircuitArg(n, pairs)
+    prm = qfs.default_params(M=4, multistarts=2, **kw)
+    tg = np.zeros((max(T, 1), 8, 8), np.complex128)
+    out = np.zeros((max(T, 1), 2, 4, 4), np.complex128)
+    res = (qfs.Result * max(T, 1))()
+    rc = lib.qfs_instantiate_many(None, C.byref(cir.c), T, tg.ctypes.data, None, None, C.byref(prm),
+                                  out.ctypes.data, res, None)
+    assert rc == getattr(qfs, "QFS_" + code)
+    assert frag in lib.qfs_last_error().decode()
