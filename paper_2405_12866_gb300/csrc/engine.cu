@@ -494,7 +494,9 @@ void df_build(const qfs_ctx* ctx, const Run& R, Real r, const void* psi, const v
     u.g_stride = gstride;
     u.g32 = R.g32 ? R.g32 + (size_t)(k - 1) * 16 : nullptr;
     u.beta = R.beta;
-    u.cost_out = (k == 1 && r == R64) ? R.costs : nullptr;
+    // Gate 1's update leaves 2 - (2/M) Re Tr(g_1 E_1): the cost of FP64
+    // sweeps, and the estimate that lets complex64 sweeps skip the residual.
+    u.cost_out = k == 1 ? R.costs : nullptr;
     u.inv_M = 1.0 / M;
     u.env_out = envs ? envs + (size_t)(k - 1) * 16 : nullptr;
     u.env_stride = gstride;
@@ -778,7 +780,7 @@ void sweep(qfs_ctx* ctx, Run& R, Real r, const Slice& sl, double2* g64, float2* 
 // and uploaded once per (precision, outputs) and reused by later sweeps.
 int df_sweep(qfs_ctx* ctx, Run& R, Real r, const void* psi, const void* phil, double2* envs, const int* active,
              double2* vprev, cudaStream_t st, int* stop = nullptr, double stop_tol = 0.0,
-             double* cost_row = nullptr) {
+             double* cost_row = nullptr, double resid_skip = 0.0) {
   const void* key[4] = {psi, envs, active, vprev};
   if (R.df_key_r != (int)r || std::memcmp(key, R.df_key, sizeof(key)) != 0) {
     std::vector<DfStep> steps;
@@ -821,6 +823,8 @@ int df_sweep(qfs_ctx* ctx, Run& R, Real r, const void* psi, const void* phil, do
   a.inv_M = 1.0 / R.M;
   a.stop = stop;
   a.stop_tol = stop_tol;
+  a.stop_from_update = r == R64 ? 1 : 0;
+  a.resid_skip = r == R32 ? resid_skip : 0.0;
   const size_t nstep_stamps = (size_t)R.df_nsteps * R.S * 4;
   a.trace = ctx->df_trace && ctx->df_trace_n >= nstep_stamps ? ctx->df_trace : nullptr;
   a.item_trace = a.trace && ctx->df_trace_n >= nstep_stamps + (size_t)R.df_items * 4 ? a.trace + nstep_stamps : nullptr;
@@ -1035,6 +1039,10 @@ int run_multistart(qfs_ctx* ctx, Run& R, const qfs_params* p,
   // some start meets the tolerance, so sweeps go out in batches.
   const bool batch = df && p->plateau_window == 0 && !R.validate;
   int* stop = R.flag + 2;
+  // Complex64 sweeps skip the residual pass of starts whose update-time
+  // estimate (error ~1e-7) is far above tol; plateau detection needs every
+  // sweep's residual, so it keeps them all.
+  const double skip = p->plateau_window == 0 ? std::max(1e3 * tol, 1e-5) : 0.0;
   std::vector<std::vector<double>> rows;
   int row = 0, nrows = 0;
   while (left > 0) {
@@ -1047,7 +1055,7 @@ int run_multistart(qfs_ctx* ctx, Run& R, const qfs_params* p,
         CK(cudaMemsetAsync(stop, 0, sizeof(int), st));
         for (int b = 0; b < B; ++b)
           TRY(df_sweep(ctx, R, rs, psi, phil, nullptr, R.active, R.vprev, st, stop, tol,
-                       R.cost_rows + (size_t)b * S));
+                       R.cost_rows + (size_t)b * S, skip));
         TRY(read_rows(ctx, R.cost_rows, S, B, rows, R.err));
         // The sweep whose cost met the tolerance ends the batch; the
         // launches behind it returned at once.
@@ -1064,7 +1072,7 @@ int run_multistart(qfs_ctx* ctx, Run& R, const qfs_params* p,
         prof_harvest(ctx);
       } else {
         if (df) {
-          TRY(df_sweep(ctx, R, rs, psi, phil, nullptr, R.active, R.vprev, st));
+          TRY(df_sweep(ctx, R, rs, psi, phil, nullptr, R.active, R.vprev, st, nullptr, 0.0, nullptr, skip));
         } else {
           CK(cudaGraphLaunch(graph.exec, st));
           for (int i = 0; i < QFS_PROF_KINDS; ++i) ctx->prof.launches[i] += graph.launches[i];

@@ -118,6 +118,9 @@ struct DfArgs {
   double* resid_cost; double inv_M;     // residual step output
   double* cost_row;                     // nullable: this sweep's costs are also written here
   unsigned* zero_next; int zero_count;  // nullable: the next sweep's control words, zeroed at entry
+  double resid_skip;                    // > 0: a start whose update-time cost estimate exceeds it skips the
+                                        //   residual pass (the estimate stands as its cost)
+  int stop_from_update;                 // the update's cost (FP64 sweeps) may set the stop flag
   int* stop;                            // nullable: set when an active start's cost <= stop_tol; a launch
   double stop_tol;                      //   that finds it set returns at once (batched sweeps)
   unsigned long long* item_trace;       // nullable: per work item (dequeued, ready, processed, CTA)

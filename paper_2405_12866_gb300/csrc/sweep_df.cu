@@ -855,7 +855,11 @@ __global__ void __launch_bounds__(df_threads<T>(), 1) k_sweep_df(DfArgs a) {
     }
     __syncthreads();
     if (!sh.flag) return;
-    const bool act = a.active == nullptr || a.active[s] != 0;
+    // The residual pass of a start whose cost estimate from the gate-1
+    // update is far above the tolerance is skipped: it could not decide
+    // anything (the estimate, accurate to ~1e-7 absolute, stands).
+    const bool act = (a.active == nullptr || a.active[s] != 0) &&
+                     !(st.kind == DF_RESID && a.resid_skip > 0.0 && __ldcg(a.resid_cost + s) > a.resid_skip);
     if (a.trace && threadIdx.x == 0 && c == 0) a.trace[((long long)i * a.S + s) * 4] = globaltimer_ns();
     if (itr && threadIdx.x == 0) itr[1] = globaltimer_ns();
     if (act) df_process<T>(st, s, c, sh, a.partials, a.resid_partials, a.part_stride, df_stage);
@@ -912,7 +916,7 @@ __global__ void __launch_bounds__(df_threads<T>(), 1) k_sweep_df(DfArgs a) {
           if (st.upd.cost_out != nullptr && threadIdx.x == 0) {
             const double cost = st.upd.cost_out[s];
             if (a.cost_row != nullptr) a.cost_row[s] = cost;
-            if (a.stop != nullptr && cost <= a.stop_tol) atomicExch(a.stop, 1);
+            if (a.stop != nullptr && a.stop_from_update && cost <= a.stop_tol) atomicExch(a.stop, 1);
           }
         }
       }
