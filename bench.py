@@ -75,7 +75,9 @@ class Clocks:
     def __init__(self, device_index: int):
         self.dev = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+        import tempfile
+        self.path = os.environ.get("QFS_CLOCKS_CSV",
+                                   os.path.join(tempfile.gettempdir(), f"qfs_clocks_rank{device_index}.csv"))
 
     def start(self):
         try:
