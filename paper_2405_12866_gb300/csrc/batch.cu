@@ -142,15 +142,20 @@ __device__ double warp_residual(T2* Ph, const T2* g1, const T2* psi, int n, int 
   warp_apply<T2>(Ph, g1, n, M, qa, qb, true);
   const int lane = threadIdx.x & 31;
   const int E = M << n;
-  double acc = 0.0;
+  // A sum of squares in the sweep's own precision: no cancellation, so its
+  // relative error stays ~1e-6 even for the largest states, far below what
+  // the FP64 check at dist_tol needs (FP64 on this GPU would cost a
+  // 64-cycle warp instruction per operation).
+  T acc = T(0);
   for (int i = lane; i < E; i += 32) {
     const T2 p = Ph[i], q = psi[i];
-    const double dx = (double)p.x - (double)q.x, dy = (double)p.y - (double)q.y;
-    acc += dx * dx + dy * dy;
+    const T dx = p.x - q.x, dy = p.y - q.y;
+    acc = fmat(dx, dx, fmat(dy, dy, acc));
   }
+  double v = (double)acc;
 #pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
-  return acc / M;
+  for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v / M;
 }
 
 // One sweep of one start (Section 3): forward to B_{L-1} with the current
