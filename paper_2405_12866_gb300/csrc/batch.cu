@@ -44,6 +44,14 @@ __device__ void warp_apply(T2* X, const T2* g, int n, int M, int qa, int qb, boo
   const int pa = n - 1 - qa, pb = n - 1 - qb;
   const int lo = min(pa, pb), hi = max(pa, pb);
   const int groups = (1 << (n - 2)) * M;
+  // The operator in registers (the state writes below could alias it for
+  // the compiler): gg[4y + x] = (g or g^dagger)[y][x].
+  T2 gg[16];
+#pragma unroll
+  for (int y = 0; y < 4; ++y)
+#pragma unroll
+    for (int x = 0; x < 4; ++x) gg[4 * y + x] = dag ? T2{g[4 * x + y].x, -g[4 * x + y].y} : g[4 * y + x];
+  __syncwarp();
   for (int w = lane; w < groups; w += 32) {
     const int r = w / M, j = w - r * M;
     const uint32_t base = ins2((uint32_t)r, lo, hi);
@@ -58,10 +66,7 @@ __device__ void warp_apply(T2* X, const T2* g, int n, int M, int qa, int qb, boo
     for (int y = 0; y < 4; ++y) {
       T2 t{0, 0};
 #pragma unroll
-      for (int x = 0; x < 4; ++x) {
-        const T2 gg = dag ? T2{g[4 * x + y].x, -g[4 * x + y].y} : g[4 * y + x];
-        t = cfma(gg, v[x], t);
-      }
+      for (int x = 0; x < 4; ++x) t = cfma(gg[4 * y + x], v[x], t);
       X[off[y]] = t;
     }
   }
@@ -72,7 +77,7 @@ __device__ void warp_apply(T2* X, const T2* g, int n, int M, int qa, int qb, boo
 // lane l16 < 16 holds the complex entry E[c][r] with l16 = 4c + r, the
 // layout the polar routines take (as A[r][c] after conjugation).
 template <typename T, typename T2>
-__device__ double2 warp_env(const T2* Bs, const T2* Ph, int n, int M, int qa, int qb) {
+__device__ T2 warp_env(const T2* Bs, const T2* Ph, int n, int M, int qa, int qb) {
   const int lane = threadIdx.x & 31;
   const int pa = n - 1 - qa, pb = n - 1 - qb;
   const int lo = min(pa, pb), hi = max(pa, pb);
@@ -97,25 +102,26 @@ __device__ double2 warp_env(const T2* Bs, const T2* Ph, int n, int M, int qa, in
         cfma_conj(acc[2 * (4 * x + y)], acc[2 * (4 * x + y) + 1], b[x], p[y]);
       }
   }
-  const double v = (double)warp_reduce_scatter32<T>(acc, lane);
+  const T v = warp_reduce_scatter32<T>(acc, lane);
   const int l16 = lane & 15;
-  return double2{__shfl_sync(FULL, v, 2 * l16), __shfl_sync(FULL, v, 2 * l16 + 1)};
+  return T2{__shfl_sync(FULL, v, 2 * l16), __shfl_sync(FULL, v, 2 * l16 + 1)};
 }
 
 // New gate from E (E[c][r] in lane 4c + r): the polar factor of E^dagger.
 template <typename T2>
-__device__ void warp_update(double2 e, T2* g, double2* sm, float2* v);
+__device__ void warp_update(T2 e, T2* g, double2* sm, float2* v);
 
 // v: the gate's right singular vectors from its previous update (the Jacobi
 // start; identity at the first sweep), updated in place.
 template <>
-__device__ void warp_update<float2>(double2 e, float2* g, double2* sm, float2* v) {
+__device__ void warp_update<float2>(float2 e, float2* g, double2* sm, float2* v) {
   const int lane = threadIdx.x & 31;
   const int l16 = lane & 15, r = l16 & 3, c = l16 >> 2;
-  const float2 a32{(float)e.x, -(float)e.y};  // A[r][c] = conj(E[c][r])
+  const float2 a32{e.x, -e.y};  // A[r][c] = conj(E[c][r])
   float2 q;
   if (!warp_polar4_f32_warm(a32, v, &q)) {
-    const double2 p = warp_polar4(double2{e.x, -e.y}, double2{r == c ? 1.0 : 0.0, 0.0}, sm, nullptr);
+    const double2 p =
+        warp_polar4(double2{(double)e.x, -(double)e.y}, double2{r == c ? 1.0 : 0.0, 0.0}, sm, nullptr);
     q = float2{(float)p.x, (float)p.y};
     if (lane < 16) v[l16] = float2{r == c ? 1.f : 0.f, 0.f};  // restart from the identity
   }
@@ -174,7 +180,7 @@ __device__ double warp_sweep(T2* Bs, T2* Ph, T2* G, const T2* psi, const T2* phi
   __syncwarp();
   for (int k = L; k >= 1; --k) {
     const int qa = pairs[2 * (k - 1)], qb = pairs[2 * (k - 1) + 1];
-    const double2 e = warp_env<T, T2>(Bs, Ph, n, M, qa, qb);
+    const T2 e = warp_env<T, T2>(Bs, Ph, n, M, qa, qb);
     warp_update<T2>(e, G + 16 * (k - 1), sm, V ? V + 16 * (k - 1) : nullptr);
     if (k > 1) {
       warp_apply<T2>(Bs, G + 16 * (k - 2), n, M, pairs[2 * (k - 2)], pairs[2 * (k - 2) + 1], true);
