@@ -573,6 +573,9 @@ def run_ours_learned(args):
     t0 = time.perf_counter()
     Ttr = learned.make_targets(11, ntrain, workers=workers)
     Tev = learned.make_targets(12, neval, workers=workers)
+    # Pinned host memory for the targets the timed steps upload (the
+    # end-to-end contract: host inputs from pinned memory).
+    Tev = torch.from_numpy(np.ascontiguousarray(Tev)).pin_memory().numpy()
     t_targets = time.perf_counter() - t0
     ls = learned.method_labels(ctx, Ttr, workers=workers)
     ws = qfs.WarmStart(ctx, seed=3, batch_cap=4096)

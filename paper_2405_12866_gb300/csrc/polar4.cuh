@@ -314,10 +314,13 @@ __device__ __forceinline__ bool jacobi32_converged(float2 x) {
 // FP32 one-sided Jacobi sweeps on X (lanes 0..15, X[r][c] at 4c + r) with
 // the accumulated right rotations V in lanes 16..31, until every column pair
 // has |gamma|^2 <= 1e-13 alpha beta (FP32 accuracy) or 12 sweeps.
-__device__ __forceinline__ float2 jacobi32_sweeps(float2 x) {
+// *rotated_out (optional): whether any rotation was applied.
+__device__ __forceinline__ float2 jacobi32_sweeps(float2 x, bool* rotated_out = nullptr) {
   const int lane = threadIdx.x & 31;
   const int l16 = lane & 15, col = l16 >> 2;
   const int c = col;
+  bool any = false;
+  if (rotated_out) *rotated_out = false;
   if (jacobi32_converged(x)) return x;  // a warm start that is already orthogonal
   for (int sweep = 0; sweep < 12; ++sweep) {
     int rotated = 0;
@@ -361,8 +364,11 @@ __device__ __forceinline__ float2 jacobi32_sweeps(float2 x) {
         x = float2{sn * y.x + cs * tx, sn * y.y + cs * ty};
       }
     }
-    if (!__any_sync(FULL, rotated) || jacobi32_converged(x)) break;
+    const bool r = __any_sync(FULL, rotated) != 0;
+    any |= r;
+    if (!r || jacobi32_converged(x)) break;
   }
+  if (rotated_out) *rotated_out = any;
   return x;
 }
 
@@ -544,7 +550,8 @@ __device__ __forceinline__ bool warp_polar4_f32_warm(float2 a, float2* v_io, flo
     }
     x = isV ? v0 : acc;
   }
-  x = jacobi32_sweeps(x);
+  bool rotated = false;
+  x = jacobi32_sweeps(x, &rotated);
   float2 w = shfl_c(x, l16);
   float2 v = shfl_c(x, 16 + l16);
   float nrm = w.x * w.x + w.y * w.y;
@@ -562,11 +569,13 @@ __device__ __forceinline__ bool warp_polar4_f32_warm(float2 a, float2* v_io, flo
   const float2 gq = mm_ah(q, q, row, col);
   const float2 t{(row == col ? 1.5f : 0.f) - 0.5f * gq.x, -0.5f * gq.y};
   *q_out = mm(q, t, row, col);
-  const float2 gv = mm_ah(v, v, row, col);
-  const float2 tv{(row == col ? 1.5f : 0.f) - 0.5f * gv.x, -0.5f * gv.y};
-  v = mm(v, tv, row, col);
-  __syncwarp();
-  if (lane < 16) v_io[l16] = v;
+  if (rotated) {  // an unrotated V is the stored one: nothing to renormalise
+    const float2 gv = mm_ah(v, v, row, col);
+    const float2 tv{(row == col ? 1.5f : 0.f) - 0.5f * gv.x, -0.5f * gv.y};
+    v = mm(v, tv, row, col);
+    __syncwarp();
+    if (lane < 16) v_io[l16] = v;
+  }
   __syncwarp();
   return true;
 }
