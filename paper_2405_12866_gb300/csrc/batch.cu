@@ -144,7 +144,7 @@ __device__ void warp_update<double2>(double2 e, double2* g, double2* sm, float2*
 // (1/M) sum |g_1^dagger Phi_1 - Psi|^2 after the sweep (Phi_1 in Ph, which
 // is overwritten).
 template <typename T, typename T2>
-__device__ double warp_residual(T2* Ph, const T2* g1, const T2* psi, int n, int M, int qa, int qb) {
+__device__ T warp_residual(T2* Ph, const T2* g1, const T2* psi, int n, int M, int qa, int qb) {
   warp_apply<T2>(Ph, g1, n, M, qa, qb, true);
   const int lane = threadIdx.x & 31;
   const int E = M << n;
@@ -158,10 +158,10 @@ __device__ double warp_residual(T2* Ph, const T2* g1, const T2* psi, int n, int 
     const T dx = p.x - q.x, dy = p.y - q.y;
     acc = fmat(dx, dx, fmat(dy, dy, acc));
   }
-  double v = (double)acc;
 #pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-  return v / M;
+  for (int o = 16; o >= 1; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+  if constexpr (sizeof(T) == 4) return acc * (1.f / (float)M);
+  else return acc / M;
 }
 
 // One sweep of one start (Section 3): forward to B_{L-1} with the current
@@ -169,7 +169,7 @@ __device__ double warp_residual(T2* Ph, const T2* g1, const T2* psi, int n, int 
 // B_{k-2} = g_{k-1}^dagger B_{k-1} (old gate), Phi_{k-1} = g_k^dagger Phi_k
 // (new gate).  Returns the residual cost of the swept gates.
 template <typename T, typename T2>
-__device__ double warp_sweep(T2* Bs, T2* Ph, T2* G, const T2* psi, const T2* phil, const int* pairs,
+__device__ T warp_sweep(T2* Bs, T2* Ph, T2* G, const T2* psi, const T2* phil, const int* pairs,
                              int n, int M, int L, double2* sm, float2* V = nullptr) {
   const int lane = threadIdx.x & 31;
   const int E = M << n;
@@ -249,22 +249,25 @@ __global__ void k_batch_sweep(BatchArgs a) {
     const float2* psi = a.psi32 + pr.state_off;
     const float2* phil = a.phil32 + pr.state_off;
     int conv = INT_MAX, sweeps = 0, stall = 0;
-    double cost = 4.0, prev = -1.0;
+    // The sweep's cost and the plateau test stay in FP32 (the FP64 pipe
+    // costs 64 cycles per warp instruction); only the tolerance test is FP64.
+    float cost = 4.f, prev = -1.f;
+    const float dtr = (float)a.diff_tol_r;
     for (int sw = 1; sw <= a.max_sweeps; ++sw) {
       // A start that has not converged by its problem's earliest converged
       // sweep can no longer be selected.
       if (sw > *(volatile int*)(a.s_star + p)) break;
       cost = warp_sweep<float, float2>(Bs, Ph, G, psi, phil, pairs, pr.n, pr.M, pr.L, sm_polar[warp], V);
       sweeps = sw;
-      if (cost <= a.tol) {
+      if ((double)cost <= a.tol) {
         conv = sw;
         if (lane == 0) atomicMin(a.s_star + p, sw);
         break;
       }
       // Plateau (App. A): no relative improvement > diff_tol_r for
       // plateau_window sweeps in a row stops this start.
-      if (a.plateau_window > 0 && prev >= 0.0) {
-        stall = fabs(prev) - fabs(cost) > a.diff_tol_r * fabs(cost) ? 0 : stall + 1;
+      if (a.plateau_window > 0 && prev >= 0.f) {
+        stall = fabsf(prev) - fabsf(cost) > dtr * fabsf(cost) ? 0 : stall + 1;
         if (stall >= a.plateau_window && sw >= a.min_sweeps) break;
       }
       prev = cost;
@@ -272,7 +275,7 @@ __global__ void k_batch_sweep(BatchArgs a) {
     const size_t ri = (size_t)p * a.S + s;
     if (lane == 0) {
       a.conv_sweep[ri] = conv;
-      a.final_cost[ri] = cost;
+      a.final_cost[ri] = (double)cost;
       a.sweeps_run[ri] = sweeps;
     }
     for (int i = lane; i < 16 * pr.L; i += 32) a.gates32[goff + i] = G[i];
