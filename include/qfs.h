@@ -112,8 +112,8 @@ typedef struct {
  * min_sweeps = 6, plateau_window = 0, precision = QFS_FP64,
  * refine_sweeps_max = 50, start_groups = 0, seed = 0, dist_tol = 1e-8,
  * diff_tol_r = 1e-5, beta = 0, restart_doubling = 0, overtrain_ratio = 0.1,
- * training_distribution = QFS_STATES_HAAR (the paper's suggested values, with plateau detection and
- * double-and-restart off).  With restart_doubling, attempt a > 0 draws its
+ * training_distribution = QFS_STATES_HAAR, concurrent_targets = 0 (the paper's
+ * suggested values, with plateau detection and double-and-restart off).  With restart_doubling, attempt a > 0 draws its
  * training states (stream 1) and validation states (stream 5) from seed
  * XOR (a * 0x9E3779B97F4A7C15); attempt 0 validates with stream 5 of seed. */
 void qfs_default_params(qfs_params* p);

@@ -40,7 +40,7 @@ def test_default_params(lib):
     assert (p.M, p.multistarts, p.max_sweeps, p.min_sweeps) == (2, 16, 10000, 6)
     assert p.dist_tol == 1e-8 and p.beta == 0.0 and p.precision == qfs.QFS_FP64
     assert p.restart_doubling == 0 and p.overtrain_ratio == 0.1
-    assert p.training_distribution == qfs.QFS_STATES_HAAR
+    assert p.training_distribution == qfs.QFS_STATES_HAAR and p.concurrent_targets == 0
 
 
 def _call_instantiate(n, pairs, params, target=None):
