@@ -49,8 +49,7 @@ __device__ __forceinline__ double2 warp_polar4(double2 a, double2 v0, double2* s
     for (int k = 0; k < 4; ++k) {
       const double2 ak = shfl2(a, 4 * k + r);
       const double2 vk = shfl2(v0, 16 + 4 * c + k);
-      acc.x += ak.x * vk.x - ak.y * vk.y;
-      acc.y += ak.x * vk.y + ak.y * vk.x;
+      acc = cfma(ak, vk, acc);
     }
     x = isV ? v0 : acc;
   }
@@ -220,11 +219,7 @@ template <typename T2>
 __device__ __forceinline__ T2 mm(T2 a, T2 b, int row, int col) {
   T2 acc{0, 0};
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const T2 ak = shfl_c(a, 4 * k + row), bk = shfl_c(b, 4 * col + k);
-    acc.x += ak.x * bk.x - ak.y * bk.y;
-    acc.y += ak.x * bk.y + ak.y * bk.x;
-  }
+  for (int k = 0; k < 4; ++k) acc = cfma(shfl_c(a, 4 * k + row), shfl_c(b, 4 * col + k), acc);
   return acc;
 }
 template <typename T2>
@@ -233,8 +228,7 @@ __device__ __forceinline__ T2 mm_ah(T2 a, T2 b, int row, int col) {
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const T2 ak = shfl_c(a, 4 * row + k), bk = shfl_c(b, 4 * col + k);  // conj(A[k][row]) B[k][col]
-    acc.x += ak.x * bk.x + ak.y * bk.y;
-    acc.y += ak.x * bk.y - ak.y * bk.x;
+    acc = cfma(T2{ak.x, -ak.y}, bk, acc);
   }
   return acc;
 }
@@ -244,8 +238,7 @@ __device__ __forceinline__ T2 mm_bh(T2 a, T2 b, int row, int col) {
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const T2 ak = shfl_c(a, 4 * k + row), bk = shfl_c(b, 4 * k + col);  // A[row][k] conj(B[col][k])
-    acc.x += ak.x * bk.x + ak.y * bk.y;
-    acc.y += ak.y * bk.x - ak.x * bk.y;
+    acc = cfma(ak, T2{bk.x, -bk.y}, acc);
   }
   return acc;
 }
@@ -448,8 +441,7 @@ __device__ __forceinline__ bool warp_polar4_fast(double2 a, double2 v0, double2*
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const float2 ak = shfl_c(a32, 4 * k + row), vk = shfl_c(v032, 16 + 4 * col + k);
-      acc.x += ak.x * vk.x - ak.y * vk.y;
-      acc.y += ak.x * vk.y + ak.y * vk.x;
+      acc = cfma(ak, vk, acc);
     }
     x = isV ? v032 : acc;
   }
@@ -545,8 +537,7 @@ __device__ __forceinline__ bool warp_polar4_f32_warm(float2 a, float2* v_io, flo
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const float2 ak = shfl_c(a, 4 * k + row), vk = shfl_c(v0, 4 * col + k);
-      acc.x += ak.x * vk.x - ak.y * vk.y;
-      acc.y += ak.x * vk.y + ak.y * vk.x;
+      acc = cfma(ak, vk, acc);
     }
     x = isV ? v0 : acc;
   }

@@ -660,8 +660,7 @@ __device__ __forceinline__ bool df_polar_begin(double2 a, double2 v0, DfUpd& u) 
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const float2 ak = shfl_c(a32, 4 * k + row), vk = shfl_c(v032, 16 + 4 * col + k);
-      acc.x += ak.x * vk.x - ak.y * vk.y;
-      acc.y += ak.x * vk.y + ak.y * vk.x;
+      acc = cfma(ak, vk, acc);
     }
     x = isV ? v032 : acc;
   }
