@@ -1333,8 +1333,12 @@ int instantiate_common(qfs_ctx* ctx, const qfs_circuit* c, const double* target,
   if (p->concurrent_targets < 0) return fail(QFS_EINVAL, "concurrent_targets = %d: need >= 0", p->concurrent_targets);
   if (T > 1 && p->restart_doubling)
     return fail(QFS_EUNSUPPORTED, "double-and-restart takes one target per call");
-  if ((long long)T * p->multistarts > 65535)
-    return fail(QFS_EUNSUPPORTED, "T x multistarts = %lld > 65535", (long long)T * p->multistarts);
+  // Targets sweep in `slots` concurrent slots; a slot whose target finishes
+  // takes the next target (continuous batching).
+  const int slots = T == 1 ? 1 : std::max(1, std::min(T, p->concurrent_targets > 0 ? p->concurrent_targets : 4));
+  if ((long long)slots * p->multistarts > 65535)
+    return fail(QFS_EUNSUPPORTED, "concurrent targets x multistarts = %lld > 65535",
+                (long long)slots * p->multistarts);
   TRY(ctx_check(ctx));
   TRY(set_device(ctx));
   if (p->restart_doubling) return instantiate_restarting(ctx, c, target, target_dev, gates0, gates_dev, seed, p,
@@ -1342,9 +1346,6 @@ int instantiate_common(qfs_ctx* ctx, const qfs_circuit* c, const double* target,
   Run R;
   int groups = p->start_groups;
   if (groups <= 0) groups = p->multistarts >= 8 ? 2 : 1;
-  // Targets sweep in `slots` concurrent slots; a slot whose target finishes
-  // takes the next target (continuous batching).
-  const int slots = T == 1 ? 1 : std::max(1, std::min(T, p->concurrent_targets > 0 ? p->concurrent_targets : 4));
   TRY(prepare(ctx, R, c, p->M, p->multistarts, p->precision, p->beta, !target_dev, false, groups, false, slots));
   if (slots > 1 && !df_usable(ctx, R, p->precision == QFS_MIXED ? R32 : R64))
     return fail(QFS_EUNSUPPORTED, "several targets per call need the dataflow sweep (cooperative launch%s)",
