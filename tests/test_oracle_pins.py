@@ -509,3 +509,16 @@ def test_basis_states_need_more_data_than_haar_states():
             gen[dist][M] = ok
     assert gen[w.STATES_HAAR][16] >= 3 and gen[w.STATES_BASIS][16] == 0
     assert gen[w.STATES_HAAR][32] == 4 and gen[w.STATES_BASIS][32] == 4
+
+
+def test_generalisation_error_against_the_full_cost():
+    """With every computational-basis state as the validation set, the
+    validation cost is the full cost of Eq. (1) per state, so the normalised
+    generalisation error c_val / c_train - 1 follows from Eq. (1) alone."""
+    p = w.chain_n3(target_seed=6)
+    G = w.initial_gates(4, 1, p.L)[0]
+    Pv = w.basis_states(2, p.n, 1 << p.n)
+    c_train = 0.25
+    want = o.full_cost(p.U, G, p.pairs, p.n) / (1 << p.n) / c_train - 1.0
+    got = o.generalisation_error(p.U @ Pv, Pv, G, p.pairs, p.n, c_train)
+    assert abs(got - want) < 1e-12 * max(1.0, abs(want))
