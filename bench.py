@@ -178,10 +178,10 @@ def _oracle_start_sweeps(args):
     return time.perf_counter() - t
 
 
-def oracle_sample(kind, seed, sweeps_per_inst, converged_frac, sweeps=1, pool=None, cores=None):
-    """Time the oracle on a bounded sample of the workload: U Psi once and
-    `sweeps` sweeps of every start in parallel over host processes; scale to
-    instantiations/s with the given sweeps per instantiation."""
+def oracle_sample(kind, seed, pool=None, cores=None):
+    """Time the oracle on a bounded sample of one target of the workload:
+    U Psi once and one sweep of every start, the starts in parallel over
+    host processes.  Returns the seconds of each part."""
     from oracle import qfs_oracle as o  # noqa: F401  (imported where it runs)
     p = _problem(kind, seed)
     Psi, G0 = p.samples(), p.init_gates()
@@ -189,55 +189,72 @@ def oracle_sample(kind, seed, sweeps_per_inst, converged_frac, sweeps=1, pool=No
     UPsi = p.U @ Psi
     t_pre = time.perf_counter() - t0
     t1 = time.perf_counter()
-    pool.map(_oracle_start_sweeps, [(UPsi, Psi, G0[s], p.pairs, p.n, sweeps) for s in range(p.S)])
-    t_sw = (time.perf_counter() - t1) / sweeps
-    t_inst = t_pre + t_sw * sweeps_per_inst
-    return {"value": converged_frac / t_inst, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": (f"{p.name}: U Psi once + {sweeps} sweep(s) of all {p.S} starts "
-                       f"({t_pre + t_sw * sweeps:.1f} s on {cores} processes), scaled to "
-                       f"{sweeps_per_inst:.1f} sweeps/instantiation x converged fraction {converged_frac:.2f}"),
-            "seconds_per_sweep_all_starts": t_sw, "seconds_precompute": t_pre}
+    pool.map(_oracle_start_sweeps, [(UPsi, Psi, G0[s], p.pairs, p.n, 1) for s in range(p.S)])
+    t_sw = time.perf_counter() - t1
+    return {"seconds_precompute": t_pre, "seconds_per_sweep_all_starts": t_sw, "name": p.name, "starts": p.S}
 
 
-def golden_sweeps(kind):
+def golden_runs(kind):
+    """The oracle's own full runs of this workload (tests/golden), written by
+    oracle/make_golden.py: mean sweeps per instantiation, converged
+    fraction, the number of targets and their seeds."""
     path = os.path.join(ROOT, "tests", "golden", f"{kind}_oracle_runs.json")
     try:
         runs = json.load(open(path))
-        sw = [r["sweeps"] for r in runs.values()]
-        conv = [r["converged"] for r in runs.values()]
-        return float(np.mean(sw)), float(np.mean(conv)), len(sw)
     except Exception:
         return None
+    sw = [r["sweeps"] for r in runs.values()]
+    conv = [r["converged"] for r in runs.values()]
+    return {"sweeps": float(np.mean(sw)), "converged": float(np.mean(conv)), "targets": len(sw),
+            "seeds": sorted(int(k) for k in runs)}
+
+
+def oracle_rate(samples, g):
+    """Converged instantiations/s of the oracle extrapolated from timed
+    samples: per target, U Psi + (mean sweeps per instantiation of the
+    oracle's own full runs) x (one sweep of all starts), times the converged
+    fraction of those runs."""
+    t_inst = float(np.mean([x["seconds_precompute"] + x["seconds_per_sweep_all_starts"] * g["sweeps"]
+                            for x in samples]))
+    return g["converged"] / t_inst, t_inst
+
+
+def oracle_note(g, n_samples, cores):
+    return (f"extrapolated: per timed target, U Psi once + 1 sweep of all starts on {cores} host processes; "
+            f"x {g['sweeps']:.2f} sweeps/instantiation and x converged fraction {g['converged']:.2f}, both "
+            f"from the oracle's own full runs of {g['targets']} targets of this workload (seeds "
+            f"{g['seeds'][0]}..{g['seeds'][-1]}); {n_samples} target(s) timed")
 
 
 # ---------------------------------------------------------------- arms
 
 def run_reference(args):
+    """The oracle on the workload's timed targets (the same seeds as our
+    arm's timed steps), one bounded sample per step."""
+    from paper_2405_12866_gb300.ranks import target_seeds, warmup_seeds
     rank, world, local = dist_env()
     if rank != 0:
         return 0
     cores = os.cpu_count()
-    g = golden_sweeps(args.workload)
-    sweeps_per_inst, conv_frac = (g[0], g[1]) if g else (100.0, 1.0)
+    g = golden_runs(args.workload) or {"sweeps": 100.0, "converged": 1.0, "targets": 0, "seeds": [0]}
     ctx = mp.get_context("spawn")
     with ctx.Pool(cores) as pool:
-        for i in range(args.warmup):
-            oracle_sample(args.workload, 1000 + i, sweeps_per_inst, conv_frac, pool=pool, cores=cores)
-        samples = [oracle_sample(args.workload, i, sweeps_per_inst, conv_frac, pool=pool, cores=cores)
-                   for i in range(args.steps)]
-    t_inst = float(np.mean([s["seconds_precompute"] + s["seconds_per_sweep_all_starts"] * sweeps_per_inst
-                            for s in samples]))
-    value = conv_frac / t_inst
+        for sd in warmup_seeds(0, args.warmup):
+            oracle_sample(args.workload, sd, pool=pool, cores=cores)
+        t0 = time.perf_counter()
+        samples = [oracle_sample(args.workload, sd, pool=pool, cores=cores) for sd in target_seeds(0, args.steps)]
+        wall = time.perf_counter() - t0
+    value, t_inst = oracle_rate(samples, g)
+    note = oracle_note(g, len(samples), cores)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_inst,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOADS[args.workload][2],
-                                            "parallelism": "host processes over starts"},
+            "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload][2], "parallelism": "host processes over starts",
+                       "step": "one bounded sample per timed target: U Psi + one sweep of all starts",
+                       "extrapolation": note, "seconds_per_instantiation_extrapolated": t_inst},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": samples[0]["sample"] + (
-                                 f"; sweeps/instantiation from the oracle's own full runs ({g[2]} targets)"
-                                 if g else "; sweeps/instantiation assumed 100 (no oracle runs recorded)")},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": note},
             "gpu_launches": 0}
     print(json.dumps(line), flush=True)
     return 0
@@ -263,27 +280,33 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     ctx = qfs.Context(local, stream.cuda_stream)
 
-    # Inputs for every step, generated on the host and made resident before
-    # timing.  With --targets-per-call T > 1 a step is one call that
+    # Inputs of every step, generated on the host and made resident before
+    # timing: the timed targets (seeds 0..K*T-1 of this rank) and separate
+    # warm-up targets.  With --targets-per-call T > 1 a step is one call that
     # instantiates T targets together (their starts share the sweep launches).
     TPC = 1 if args.restart_doubling else max(1, args.targets_per_call)
-    n_steps = args.warmup + args.steps
-    from paper_2405_12866_gb300.ranks import combine, target_seeds
-    probs = [_problem(kind, seed) for seed in target_seeds(rank, n_steps * TPC)]
-    first = probs[0]
+    from paper_2405_12866_gb300.ranks import combine, target_seeds, warmup_seeds
+    probs_t = [_problem(kind, seed) for seed in target_seeds(rank, args.steps * TPC)]
+    probs_w = [_problem(kind, seed) for seed in warmup_seeds(rank, args.warmup * TPC)]
+    first = probs_t[0]
     L, S, M, n = first.L, first.S, first.M, first.n
-    dev_in = []
-    for i in range(n_steps):
-        grp = probs[i * TPC:(i + 1) * TPC]
-        dev_in.append((torch.from_numpy(np.stack([p.U for p in grp])).to(dev),
-                       torch.from_numpy(np.stack([p.samples() for p in grp])).to(dev),
-                       torch.from_numpy(np.ascontiguousarray(np.stack([p.init_gates() for p in grp]))).to(dev)))
+
+    def upload(probs):
+        out = []
+        for i in range(0, len(probs), TPC):
+            grp = probs[i:i + TPC]
+            out.append((torch.from_numpy(np.stack([p.U for p in grp])).to(dev),
+                        torch.from_numpy(np.stack([p.samples() for p in grp])).to(dev),
+                        torch.from_numpy(np.ascontiguousarray(np.stack([p.init_gates() for p in grp]))).to(dev)))
+        return out
+
+    dev_t, dev_w = upload(probs_t), upload(probs_w)
     out = torch.zeros((TPC, L, 4, 4), dtype=torch.complex128, device=dev)
     prm = qfs.default_params(M=M, multistarts=S, max_sweeps=first.max_sweeps, dist_tol=first.tol,
                              precision=prec, start_groups=args.start_groups,
                              restart_doubling=1 if args.restart_doubling else 0, concurrent_targets=args.slots)
 
-    def step(i):
+    def step(probs, dev_in, i):
         if args.restart_doubling:
             # double-and-restart draws its training states itself (host target)
             prm.seed = probs[i].seed
@@ -294,44 +317,41 @@ def run_ours(args):
         return ctx.instantiate_many_dev(n, first.pairs, U, Psi, G0, prm, out)
 
     for i in range(args.warmup):
-        step(i)
+        step(probs_w, dev_w, i)
     torch.cuda.synchronize(dev)
     if world > 1:
         dist.barrier()
+    # Timed region: K steps, kernel launches counted, no per-launch events.
     clocks = Clocks(local)
     clocks.start()
     ctx.profile_reset()
-    ctx.profile(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(dev)
     e0.record(stream)
-    results = [r for i in range(args.steps) for r in step(args.warmup + i)]
+    results = [r for i in range(args.steps) for r in step(probs_t, dev_t, i)]
     e1.record(stream)
     torch.cuda.synchronize(dev)
-    ctx.profile(False)
     if world > 1:
         dist.barrier()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
-    prof = {name: ctx.profile_read(k) for k, name in enumerate(qfs.PROF_NAMES)}
     launches = ctx.profile_read(-1)["launches"]
     conv = sum(r.converged for r in results)
     sweeps = [r.sweeps for r in results]
-
     (ms_all,), (conv_all, launches_all) = combine([ms], [conv, launches], dev)
     value = conv_all / (ms_all / 1e3)
 
-    # End to end through the public host-pointer API: pinned host inputs,
-    # H2D of target, samples and initial gates inside the call, D2H of gates.
+    # End to end through the public host-pointer API on the same K targets:
+    # pinned host inputs, H2D of target, samples and initial gates inside
+    # the call, D2H of the gates and costs.
     e2e = None
-    if args.e2e_steps > 0:
+    if args.e2e:
         hin = []
-        for i in range(args.e2e_steps):
-            grp = [probs[((args.warmup + i) % n_steps) * TPC + t] for t in range(TPC)]
-            U_h = torch.from_numpy(np.stack([p.U for p in grp])).pin_memory().numpy()
-            Ps_h = torch.from_numpy(np.stack([p.samples() for p in grp])).pin_memory().numpy()
-            G_h = torch.from_numpy(np.ascontiguousarray(np.stack([p.init_gates() for p in grp]))).pin_memory().numpy()
-            hin.append((U_h, Ps_h, G_h))
+        for i in range(0, len(probs_t), TPC):
+            grp = probs_t[i:i + TPC]
+            hin.append(tuple(torch.from_numpy(np.ascontiguousarray(x)).pin_memory().numpy()
+                             for x in (np.stack([p.U for p in grp]), np.stack([p.samples() for p in grp]),
+                                       np.stack([p.init_gates() for p in grp]))))
         torch.cuda.synchronize(dev)
         if world > 1:
             dist.barrier()
@@ -339,7 +359,7 @@ def run_ours(args):
         if args.restart_doubling:
             e2e_res = []
             for i, (U_h, Ps_h, G_h) in enumerate(hin):
-                prm.seed = probs[(args.warmup + i) % n_steps].seed
+                prm.seed = probs_t[i].seed
                 e2e_res.append(ctx.instantiate(n, first.pairs, U_h[0], prm))
         elif TPC == 1:
             e2e_res = [ctx.instantiate(n, first.pairs, U_h[0], prm, Ps_h[0], G_h[0]) for (U_h, Ps_h, G_h) in hin]
@@ -348,13 +368,25 @@ def run_ours(args):
                        for r in ctx.instantiate_many(n, first.pairs, U_h, prm, Ps_h, G_h)]
         torch.cuda.synchronize(dev)
         t_e2e = time.perf_counter() - t0
+        if world > 1:
+            dist.barrier()
         conv_e2e = sum(r.converged for r in e2e_res)
         (t_e2e,), (conv_e2e,) = combine([t_e2e], [conv_e2e], dev)
         N = 1 << n
         e2e = {"value": conv_e2e / t_e2e, "unit": UNIT,
                "h2d_bytes_per_step": TPC * 16 * (N * N + N * M + S * L * 16),
-               "d2h_bytes_per_step": TPC * (16 * L * 16 + 8 * S), "steps": args.e2e_steps}
+               "d2h_bytes_per_step": TPC * (16 * L * 16 + 8 * S), "steps": len(hin),
+               "targets": "the timed targets"}
 
+    # Roofline of the dominant kernel from a separate pass over the same
+    # targets with every launch bracketed by CUDA events on its stream.
+    ctx.profile_reset()
+    ctx.profile(True)
+    for i in range(args.steps):
+        step(probs_t, dev_t, i)
+    torch.cuda.synchronize(dev)
+    ctx.profile(False)
+    prof = {name: ctx.profile_read(k) for k, name in enumerate(qfs.PROF_NAMES)}
     peak, peak_src = peaks()
     # The dominant kernel: the dataflow sweep (one launch per sweep of all
     # starts) or, with per-step launches, the fused backward step.
@@ -378,6 +410,7 @@ def run_ours(args):
                    "n": n, "gates": L, "M": M, "multistarts": S,
                    "tol": first.tol, "max_sweeps": first.max_sweeps, "parallelism": f"{world} independent ranks",
                    "targets_per_call": TPC,
+                   "timed_target_seeds": f"rank r: r*100000 + (0..{args.steps * TPC - 1}); warm-up targets separate",
                    "l2": "inputs larger than L2 (B list 512 MiB per target), no flush"},
         "converged": int(conv_all), "instantiations": args.steps * world * TPC,
         "sweeps_per_instantiation": float(np.mean(sweeps)),
@@ -387,19 +420,22 @@ def run_ours(args):
                      "frac": (achieved / peak) if achieved else None,
                      "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback 6.8 TB/s",
                      "traffic": tr, "avg_launch_us": avg_ms * 1e3, "algorithmic_bytes_per_launch": bytes_per,
-                     "launches_timed": dom["timed"]},
+                     "launches_timed": dom["timed"],
+                     "measured": "separate pass over the timed targets, every launch bracketed by CUDA events"},
         "kernel_time_share": {k: round(v["ms"] / max(sum(x["ms"] for x in prof.values()), 1e-9), 4)
                               for k, v in prof.items()},
         "clocks": clk, "e2e": e2e, "gpu_launches": int(launches_all),
     }
     if rank == 0 and args.cpu_baseline:
-        ctx_mp = mp.get_context("spawn")
-        cores = os.cpu_count()
-        with ctx_mp.Pool(cores) as pool:
-            line["cpu_baseline"] = oracle_sample(kind, 0, float(np.mean(sweeps)),
-                                                 conv_all / (args.steps * world * TPC), pool=pool, cores=cores)
-        line["cpu_baseline"].pop("seconds_per_sweep_all_starts", None)
-        line["cpu_baseline"].pop("seconds_precompute", None)
+        g = golden_runs(kind)
+        if g is not None:
+            ctx_mp = mp.get_context("spawn")
+            cores = os.cpu_count()
+            with ctx_mp.Pool(cores) as pool:
+                smp = [oracle_sample(kind, target_seeds(0, 1)[0], pool=pool, cores=cores)]
+            v, _ = oracle_rate(smp, g)
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                    "sample": oracle_note(g, 1, cores)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -531,7 +567,7 @@ def run_ours_batch(args):
         "converged": int(conv), "instantiations": P * args.steps,
         "roofline": {"bound": "alu", "kernel": "k_batch_sweep (persistent)", "achieved": achieved,
                      "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                     "peak_source": "FP32 FMA probe (paper_2405_12866_gb300/probes/alu_peak.cu): 72.9 TFLOP/s",
+                     "peak_source": "FP32 FMA peak measured on GB300 by an FMA-chain throughput kernel: 72.9 TFLOP/s",
                      "traffic": None, "algorithmic_flops_per_step": flops / args.steps},
         "clocks": clk,
         "e2e": {"value": conv_e2e / t_e2e, "unit": UNIT, "note": "host API incl. host-side packing and copies",
@@ -786,11 +822,12 @@ def run_states_ablation(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=6)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="brick_n12")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false",
+                    help="skip the end-to-end pass through the host-pointer API")
     ap.add_argument("--targets-per-call", type=int, default=1,
                     help="instantiate this many targets per call, their starts sweeping together")
     ap.add_argument("--slots", type=int, default=0,

@@ -49,6 +49,7 @@ extern "C" {
 #define QFS_ETIMEOUT (-4)     /* a bounded device wait ran out */
 #define QFS_EUNSUPPORTED (-5) /* valid but not supported (e.g. n > 14) */
 #define QFS_ENONFINITE (-6)   /* NaN or Inf in an input */
+#define QFS_EINTERNAL (-7)    /* an internal consistency check failed before any launch */
 
 #define QFS_FP64 0  /* every step in complex128 */
 #define QFS_MIXED 1 /* complex64 sweeps; FP64 SVD, master gates, refinement, cost check */
@@ -94,6 +95,9 @@ typedef struct {
                                     states, uniform without replacement) */
   int32_t concurrent_targets;    /* qfs_instantiate_many: target slots swept together (0 = 4); a slot
                                     whose target finishes takes the next one */
+  double refine_switch_tol;      /* QFS_MIXED: a start whose complex64 cost is <= max(dist_tol, this) is
+                                    checked in FP64 and, if that cost is above dist_tol, continued with
+                                    up to refine_sweeps_max FP64 sweeps (0: switch at dist_tol) */
 } qfs_params;
 
 typedef struct {
@@ -112,7 +116,8 @@ typedef struct {
  * min_sweeps = 6, plateau_window = 0, precision = QFS_FP64,
  * refine_sweeps_max = 50, start_groups = 0, seed = 0, dist_tol = 1e-8,
  * diff_tol_r = 1e-5, beta = 0, restart_doubling = 0, overtrain_ratio = 0.1,
- * training_distribution = QFS_STATES_HAAR, concurrent_targets = 0 (the paper's
+ * training_distribution = QFS_STATES_HAAR, concurrent_targets = 0,
+ * refine_switch_tol = 0 (the paper's
  * suggested values, with plateau detection and double-and-restart off).  With restart_doubling, attempt a > 0 draws its
  * training states (stream 1) and validation states (stream 5) from seed
  * XOR (a * 0x9E3779B97F4A7C15); attempt 0 validates with stream 5 of seed. */
@@ -131,6 +136,35 @@ const char* qfs_last_error(void);
 
 /* Number of SMs of the context's device (host query, no kernel). */
 int qfs_device_sms(const qfs_ctx* ctx);
+
+/* Context options (none of them is in the paper; defaults in brackets).
+ *   QFS_OPT_WAIT_LIMIT [2^25]: polls (each >= 32 ns) a dependency wait of
+ *     the dataflow sweep makes before it gives up; the kernel then sets the
+ *     run's error word, every CTA stops taking work and returns, and the call
+ *     returns QFS_ETIMEOUT.  The context stays usable; the next call clears
+ *     the error word.  Must be >= 1.
+ *   QFS_OPT_WORKSPACE_CAP [0 = none]: largest device workspace, in bytes, a
+ *     call may use; a call that needs more returns QFS_ENOMEM before it
+ *     allocates (the paper's runs instead halve their multistarts on an
+ *     out-of-memory error, Appendix A).
+ *   QFS_OPT_FUSED_UPDATE [1]: per-step sweeps run each gate update in the
+ *     backward launch (0: a separate update launch).
+ *   QFS_OPT_DATAFLOW [1]: a sweep of all starts is one persistent launch
+ *     (0: per-step launches).
+ *   QFS_OPT_TWO_GATE_FORWARD [1]: the dataflow sweep applies consecutive
+ *     forward gates on four distinct qubits in one step (0: one per step).
+ *   QFS_OPT_FP64_TARGET_PRODUCT [0]: QFS_MIXED runs form U Psi in FP64
+ *     instead of FP32 pair arithmetic.
+ * Every setting gives the same results up to the order of reduction sums.
+ * QFS_EINVAL for an unknown option or a value out of range. */
+#define QFS_OPT_WAIT_LIMIT 0
+#define QFS_OPT_WORKSPACE_CAP 1
+#define QFS_OPT_FUSED_UPDATE 2
+#define QFS_OPT_DATAFLOW 3
+#define QFS_OPT_TWO_GATE_FORWARD 4
+#define QFS_OPT_FP64_TARGET_PRODUCT 5
+int qfs_set_option(qfs_ctx* ctx, int32_t option, int64_t value);
+int qfs_get_option(qfs_ctx* ctx, int32_t option, int64_t* value);
 
 /* Kernel accounting.  Launches of every kind are always counted; with
  * profiling enabled each launch is also bracketed by CUDA events on the

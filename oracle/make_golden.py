@@ -8,6 +8,11 @@ loop because the starts never interact before the stop.  Records, per
 target: converged, the stopping sweep, the selected start and its cost.
 
     python -m oracle.make_golden brick_n12 0 1 2 3
+    python -m oracle.make_golden brick_n8_restart 0 1 2
+
+The second form runs the oracle's double-and-restart outer loop on the
+brick_n8 workload (one target per process) and records converged, the
+total sweeps, the selected start, the final M and the costs.
 """
 from __future__ import annotations
 
@@ -64,10 +69,43 @@ def lockstep_parallel(UPsi, Psi, G0, pairs, n, tol, max_sweeps, pool, chunk=10):
                 cost=float(final[best]), start_costs=final.tolist())
 
 
+def _restart_run(sd):
+    """Double-and-restart (Sec. 3, App. A) of brick_n8 target sd from its
+    literal M = 16, with the library's draws of seed p.seed: training
+    states of attempt a from attempt_seed(seed, a) (stream 1), validation
+    states from stream 5, initial gates from stream 2."""
+    from paper_2405_12866_gb300 import workloads as w
+    p = w.brick_n8(target_seed=sd)
+    t = time.time()
+    tr = lambda M, a: w.training_states(0, w.attempt_seed(p.seed, a), p.n, M)
+    va = lambda M, a: w.training_states(0, w.attempt_seed(p.seed, a), p.n, M, stream=w.STREAM_VALIDATION)
+    r = o.instantiate_restarting(p.U, tr, va, w.initial_gates(p.seed, p.S, p.L), p.pairs, p.n, p.tol,
+                                 p.max_sweeps, p.M, RESTART_OTR, min_sweeps=RESTART_MIN_SWEEPS)
+    return dict(converged=r.converged, sweeps=r.sweeps, best_start=r.best_start, cost=r.cost,
+                validation_cost=r.validation_cost, training_states=r.training_states, attempts=r.attempts,
+                name=p.name + "_restart", target_seed=sd, run_seed=p.seed, M0=p.M, tol=p.tol,
+                max_sweeps=p.max_sweeps, overtrain_ratio=RESTART_OTR, min_sweeps=RESTART_MIN_SWEEPS,
+                seconds=round(time.time() - t, 1))
+
+
+RESTART_OTR = 0.1
+RESTART_MIN_SWEEPS = 6
+
+
 def main(argv):
     from paper_2405_12866_gb300 import workloads as w
     kind = argv[0]
     seeds = [int(x) for x in argv[1:]] or [0]
+    if kind == "brick_n8_restart":
+        out_path = os.path.join(ROOT, "tests", "golden", "brick_n8_restart_oracle_runs.json")
+        runs = json.load(open(out_path)) if os.path.exists(out_path) else {}
+        with mp.get_context("spawn").Pool(min(len(seeds), os.cpu_count())) as pool:
+            for sd, r in zip(seeds, pool.map(_restart_run, seeds)):
+                runs[str(sd)] = r
+                print(kind, sd, {k: r[k] for k in ("converged", "sweeps", "best_start", "training_states")},
+                      flush=True)
+        json.dump(runs, open(out_path, "w"), indent=1)
+        return
     factory = {"brick_n12": w.brick_n12, "brick_n8": w.brick_n8}[kind]
     out_path = os.path.join(ROOT, "tests", "golden", f"{kind}_oracle_runs.json")
     runs = json.load(open(out_path)) if os.path.exists(out_path) else {}

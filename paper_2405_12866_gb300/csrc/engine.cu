@@ -93,11 +93,10 @@ struct qfs_ctx {
   cudaEvent_t gevent[kMaxGroups] = {};
   cudaEvent_t fork_event = nullptr;
   cudaStream_t cap_stream = nullptr;  // stream used only to capture sweep graphs
-  bool fuse_update = true;  // gate update inside the backward launch (QFS_FUSE_UPDATE=0: separate)
-  bool tma = false;         // shared-memory-staged backward steps (QFS_TMA=1); register kernels by default
-  bool dataflow = true;     // whole sweeps as one cooperative persistent launch (QFS_DATAFLOW=0: per-step launches)
-  bool df_fwd2 = true;      // forward gates on four distinct qubits two per step (QFS_DF_FWD2=0: one per step)
-  bool upsi_fp64 = false;   // mixed runs: U Psi in FP64 instead of FP32 pair arithmetic (QFS_UPSI_FP64=1)
+  bool fuse_update = true;  // gate update inside the backward launch (QFS_OPT_FUSED_UPDATE)
+  bool dataflow = true;     // whole sweeps as one cooperative persistent launch (QFS_OPT_DATAFLOW)
+  bool df_fwd2 = true;      // forward gates on four distinct qubits two per step (QFS_OPT_TWO_GATE_FORWARD)
+  bool upsi_fp64 = false;   // mixed runs: U Psi in FP64 instead of FP32 pair arithmetic (QFS_OPT_FP64_TARGET_PRODUCT)
   unsigned long long* df_trace = nullptr;  // device buffer for step time stamps (qfs_dataflow_trace_*)
   size_t df_trace_n = 0;
   int df_trace_steps = 0, df_trace_S = 0;  // shape of the last traced sweep
@@ -105,6 +104,8 @@ struct qfs_ctx {
   double df_item_bytes = 1024.0 * 1024.0;  // largest streaming bytes of one dataflow work item (QFS_DF_ITEM_KB)
   double df_items_per_cta = 1.5;           // work items per CTA and backward step (QFS_DF_ITEMS_PER_CTA)
   double df_items_per_cta_fwd = 1.0;       // ... and forward step (QFS_DF_ITEMS_PER_CTA_FWD)
+  long long df_wait_limit = 1LL << 25;     // polls before a dataflow dependency wait gives up (QFS_OPT_WAIT_LIMIT)
+  size_t ws_cap = 0;                       // largest device workspace a call may use, 0 = no cap
   int coop = 0;             // device supports cooperative launches
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -352,6 +353,9 @@ int check_run_params(int n, int M, int S, int max_sweeps, int precision, double 
 }
 
 int ensure_ws(qfs_ctx* ctx, size_t bytes) {
+  if (ctx->ws_cap && bytes > ctx->ws_cap)
+    return fail(QFS_ENOMEM, "this call needs %.3f GiB of device workspace, above the context's cap of %.3f GiB",
+                bytes / 1073741824.0, ctx->ws_cap / 1073741824.0);
   if (ctx->ws_bytes >= bytes) return QFS_OK;
   if (ctx->ws) {
     CK(cudaStreamSynchronize(ctx->stream));
@@ -554,9 +558,7 @@ int prepare(qfs_ctx* ctx, Run& R, const qfs_circuit* c, int M, int S_target, int
   for (int U = 2; U <= std::min(4, R.n); ++U) {
     const Real rs = prec == QFS_MIXED ? R32 : R64;
     R.nblk_max = std::max(R.nblk_max, make_bwd_shape(R.n, M, shape_starts(S), rs, ctx->num_sms, U).nblk);
-    R.nblk_max = std::max(R.nblk_max, make_tma_shape(R.n, M, shape_starts(S), rs, ctx->num_sms, U).nblk);
     R.nblk64_max = std::max(R.nblk64_max, make_bwd_shape(R.n, M, 1, R64, ctx->num_sms, U).nblk);
-    R.nblk64_max = std::max(R.nblk64_max, make_tma_shape(R.n, M, 1, R64, ctx->num_sms, U).nblk);
   }
   R.df_cap = 0;
   R.df_max_nchunk = 0;
@@ -670,10 +672,12 @@ struct Slice {
   cudaStream_t st = nullptr;
 };
 
-void sweep(qfs_ctx* ctx, Run& R, Real r, const Slice& sl, double2* g64, float2* g32,
-           const void* psi, const void* phil, void* B, void* phi, double* partials,
-           int nblk_stride, double* cost_out, double2* envs, const int* active, int stream_b,
-           double2* vprev, unsigned* counters) {
+// Returns QFS_EINTERNAL, before any launch, if a backward step's blocks
+// would outnumber the nblk_stride partial-sum slots each start owns.
+int sweep(qfs_ctx* ctx, Run& R, Real r, const Slice& sl, double2* g64, float2* g32,
+          const void* psi, const void* phil, void* B, void* phi, double* partials,
+          int nblk_stride, double* cost_out, double2* envs, const int* active, int stream_b,
+          double2* vprev, unsigned* counters) {
   cudaStream_t st = sl.st ? sl.st : ctx->stream;
   const int S = sl.S, s0 = sl.s0;
   const size_t es = elem_bytes(r);
@@ -701,6 +705,17 @@ void sweep(qfs_ctx* ctx, Run& R, Real r, const Slice& sl, double2* g64, float2* 
     return (void*)((char*)B + ((size_t)(k - 1) * sl.S_total + s0) * sN * es);
   };
   const int L = R.L;
+  for (int k = L; k >= 1; --k) {
+    const int ua = k == L ? R.pairs[2 * (k - 1)] : R.pairs[2 * k];
+    const int ub = k == L ? R.pairs[2 * (k - 1) + 1] : R.pairs[2 * k + 1];
+    const BwdGeom bg = make_bwd_geom(R.n, R.M, ua, ub, R.pairs[2 * (k - 1)], R.pairs[2 * (k - 1) + 1]);
+    const int nb = make_bwd_shape(R.n, R.M, S_shape, r, ctx->num_sms, bg.U).nblk;
+    if (nb > nblk_stride)
+      return fail(QFS_EINTERNAL, "backward step %d needs %d partial-sum slots per start, %d allocated", k, nb,
+                  nblk_stride);
+  }
+  if (r == R32 && make_bwd_shape(R.n, R.M, S_shape, r, ctx->num_sms, 2).nblk > nblk_stride)
+    return fail(QFS_EINTERNAL, "the residual pass needs more partial-sum slots than allocated");
   for (int k = 1; k <= L - 1; ++k) {
     const Geom gm = make_geom(R.n, R.M, R.pairs[2 * (k - 1)], R.pairs[2 * (k - 1) + 1]);
     const void* in = k == 1 ? psi : B_ptr(k - 1);
@@ -727,9 +742,7 @@ void sweep(qfs_ctx* ctx, Run& R, Real r, const Slice& sl, double2* g64, float2* 
       ub = R.pairs[2 * k + 1];
     }
     const BwdGeom bg = make_bwd_geom(R.n, R.M, ua, ub, qa, qb);
-    const bool use_tma = ctx->tma && R.err && tma_backward_supported(r, R.M, bg.U);
-    const Shape bsh = use_tma ? make_tma_shape(R.n, R.M, S_shape, r, ctx->num_sms, bg.U)
-                              : make_bwd_shape(R.n, R.M, S_shape, r, ctx->num_sms, bg.U);
+    const Shape bsh = make_bwd_shape(R.n, R.M, S_shape, r, ctx->num_sms, bg.U);
     UpdateArgs ua_{};
     ua_.partials = partials;
     ua_.nblk = bsh.nblk;
@@ -749,12 +762,8 @@ void sweep(qfs_ctx* ctx, Run& R, Real r, const Slice& sl, double2* g64, float2* 
     // launch: the last block of each start to finish performs its update.
     {
       ProfScope ps(ctx, QFS_PROF_BACKWARD, (double)S * sN * es * (pout ? 3.0 : 2.0), st);
-      if (use_tma)
-        launch_backward_tma(r, bg, bsh, S, bprev, bstride, pin, pstride, pout, gate, gstride, partials,
-                            stream_b, active, st, ctx->fuse_update ? &ua_ : nullptr, counters, R.err);
-      else
-        launch_backward(r, 0, bg, bsh, S, bprev, bstride, pin, pstride, pout, gate, gstride, partials,
-                        stream_b, active, st, ctx->fuse_update ? &ua_ : nullptr, counters);
+      launch_backward(r, 0, bg, bsh, S, bprev, bstride, pin, pstride, pout, gate, gstride, partials, stream_b,
+                      active, st, ctx->fuse_update ? &ua_ : nullptr, counters);
     }
     if (!ctx->fuse_update) {
       ProfScope ps(ctx, QFS_PROF_UPDATE, (double)S * bsh.nblk * 32 * sizeof(double), st);
@@ -773,6 +782,7 @@ void sweep(qfs_ctx* ctx, Run& R, Real r, const Slice& sl, double2* g64, float2* 
     ProfScope ps(ctx, QFS_PROF_OTHER, 0.0, st);
     launch_residual_finish(partials, bsh.nblk, S, 1.0 / R.M, cost_out, st);
   }
+  return QFS_OK;
 }
 
 // One sweep of all starts of R as one dataflow launch (same results as
@@ -816,6 +826,7 @@ int df_sweep(qfs_ctx* ctx, Run& R, Real r, const void* psi, const void* phil, do
   a.zero_count = (int)R.df_ctrl_cap;
   a.cost_row = cost_row;
   a.err = R.err;
+  a.wait_limit = ctx->df_wait_limit;
   a.partials = R.df_partials;
   a.resid_partials = R.df_resid;
   a.part_stride = R.df_max_nchunk;
@@ -931,19 +942,17 @@ int ensure_group_streams(qfs_ctx* ctx, int groups) {
 // swept concurrently on their own streams (one slice's SVD updates overlap
 // the others' streaming), forked from and joined back to ctx->stream.
 int sweep_all(qfs_ctx* ctx, Run& R, Real rs, const void* psi, const void* phil, cudaStream_t origin) {
-  if (R.groups <= 1) {
-    sweep(ctx, R, rs, Slice{0, R.S, R.S, origin}, R.g64, R.g32, psi, phil, R.B, R.phi, R.partials,
-          R.nblk_max, R.costs, nullptr, R.active, R.stream_b, R.vprev, R.counters);
-    return QFS_OK;
-  }
+  if (R.groups <= 1)
+    return sweep(ctx, R, rs, Slice{0, R.S, R.S, origin}, R.g64, R.g32, psi, phil, R.B, R.phi, R.partials,
+                 R.nblk_max, R.costs, nullptr, R.active, R.stream_b, R.vprev, R.counters);
   TRY(ensure_group_streams(ctx, R.groups));
   CK(cudaEventRecord(ctx->fork_event, origin));
   for (int g = 0; g < R.groups; ++g) {
     const int s0 = g * R.group_size;
     const int Sg = std::min(R.group_size, R.S - s0);
     CK(cudaStreamWaitEvent(ctx->gstream[g], ctx->fork_event, 0));
-    sweep(ctx, R, rs, Slice{s0, Sg, R.S, ctx->gstream[g]}, R.g64, R.g32, psi, phil, R.B, R.phi,
-          R.partials, R.nblk_max, R.costs, nullptr, R.active, R.stream_b, R.vprev, R.counters);
+    TRY(sweep(ctx, R, rs, Slice{s0, Sg, R.S, ctx->gstream[g]}, R.g64, R.g32, psi, phil, R.B, R.phi,
+              R.partials, R.nblk_max, R.costs, nullptr, R.active, R.stream_b, R.vprev, R.counters));
     CK(cudaEventRecord(ctx->gevent[g], ctx->gstream[g]));
     CK(cudaStreamWaitEvent(origin, ctx->gevent[g], 0));
   }
@@ -1019,6 +1028,9 @@ int run_multistart(qfs_ctx* ctx, Run& R, const qfs_params* p,
   cudaStream_t st = ctx->stream;
   const int S = R.S, T = R.T, spt = R.spt;
   const double tol = p->dist_tol;
+  // Complex64 cost at which a start is handed to FP64 (checked, and refined
+  // if the check is above tol): tol, or the larger refine_switch_tol.
+  const double ctol = R.prec == QFS_MIXED ? std::max(tol, p->refine_switch_tol) : tol;
   const double inf = std::numeric_limits<double>::infinity(), nan = std::numeric_limits<double>::quiet_NaN();
   std::vector<double> c, prev(S, inf);
   std::vector<int> stall(S, 0), act(S, 1);
@@ -1042,7 +1054,7 @@ int run_multistart(qfs_ctx* ctx, Run& R, const qfs_params* p,
   // Complex64 sweeps skip the residual pass of starts whose update-time
   // estimate (error ~1e-7) is far above tol; plateau detection needs every
   // sweep's residual, so it keeps them all.
-  const double skip = p->plateau_window == 0 ? std::max(1e3 * tol, 1e-5) : 0.0;
+  const double skip = p->plateau_window == 0 ? std::max(1e3 * ctol, 1e-5) : 0.0;
   std::vector<std::vector<double>> rows;
   int row = 0, nrows = 0;
   while (left > 0) {
@@ -1054,7 +1066,7 @@ int run_multistart(qfs_ctx* ctx, Run& R, const qfs_params* p,
       if (df && B > 1) {
         CK(cudaMemsetAsync(stop, 0, sizeof(int), st));
         for (int b = 0; b < B; ++b)
-          TRY(df_sweep(ctx, R, rs, psi, phil, nullptr, R.active, R.vprev, st, stop, tol,
+          TRY(df_sweep(ctx, R, rs, psi, phil, nullptr, R.active, R.vprev, st, stop, ctol,
                        R.cost_rows + (size_t)b * S, skip));
         TRY(read_rows(ctx, R.cost_rows, S, B, rows, R.err));
         // The sweep whose cost met the tolerance ends the batch; the
@@ -1062,7 +1074,7 @@ int run_multistart(qfs_ctx* ctx, Run& R, const qfs_params* p,
         nrows = B;
         for (int b = 0; b < B; ++b) {
           bool met = false;
-          for (int s = 0; s < S; ++s) met |= act[s] && rows[b][s] <= tol;
+          for (int s = 0; s < S; ++s) met |= act[s] && rows[b][s] <= ctol;
           if (met) {
             nrows = b + 1;
             break;
@@ -1101,20 +1113,21 @@ int run_multistart(qfs_ctx* ctx, Run& R, const qfs_params* p,
       // Candidates by their complex64 cost; each is confirmed in FP64.
       std::vector<int> cand;
       for (int s = s0; s < s1; ++s)
-        if (act[s] && c[s] <= tol) cand.push_back(s);
+        if (act[s] && c[s] <= ctol) cand.push_back(s);
       for (int s : cand) {
         TRY(check64(ctx, R, s, &c64[s]));
         if (c64[s] <= tol) fin[t] = 1;
       }
       if (!fin[t]) {
-        // complex64 reached tol but FP64 did not: refine that start in FP64.
+        // complex64 reached the switch cost but FP64 is above tol: refine
+        // that start in FP64.
         for (int s : cand) {
           const size_t toff = (size_t)t * R.sN;
           for (int it = 0; it < p->refine_sweeps_max && !fin[t]; ++it) {
-            sweep(ctx, R, R64, Slice{0, 1, 1, ctx->stream}, R.g64 + (size_t)s * R.L * 16,
-                  R.g32 + (size_t)s * R.L * 16, R.psi64 + toff, R.phil64 + toff, R.B64r, R.phi64r, R.partials64r,
-                  R.nblk64_max, R.cost64r, nullptr, nullptr, R.stream_b64, R.vprev + (size_t)s * R.L * 16,
-                  R.counters + R.S);
+            TRY(sweep(ctx, R, R64, Slice{0, 1, 1, ctx->stream}, R.g64 + (size_t)s * R.L * 16,
+                      R.g32 + (size_t)s * R.L * 16, R.psi64 + toff, R.phil64 + toff, R.B64r, R.phi64r,
+                      R.partials64r, R.nblk64_max, R.cost64r, nullptr, nullptr, R.stream_b64,
+                      R.vprev + (size_t)s * R.L * 16, R.counters + R.S));
             ++tfp64[t];
             std::vector<double> cr;
             TRY(read_costs(ctx, R.cost64r, 1, cr));
@@ -1323,6 +1336,8 @@ int instantiate_common(qfs_ctx* ctx, const qfs_circuit* c, const double* target,
     return fail(QFS_EINVAL, "plateau_window, min_sweeps and diff_tol_r must be >= 0");
   if (p->precision == QFS_MIXED && p->refine_sweeps_max < 0)
     return fail(QFS_EINVAL, "refine_sweeps_max must be >= 0");
+  if (!(p->refine_switch_tol >= 0.0) || std::isinf(p->refine_switch_tol))
+    return fail(QFS_EINVAL, "refine_switch_tol = %g: need a finite value >= 0", p->refine_switch_tol);
   if (p->start_groups < 0) return fail(QFS_EINVAL, "start_groups = %d: need >= 0", p->start_groups);
   if (p->training_distribution != QFS_STATES_HAAR && p->training_distribution != QFS_STATES_BASIS)
     return fail(QFS_EINVAL, "training_distribution = %d: need QFS_STATES_HAAR or QFS_STATES_BASIS",
@@ -1432,6 +1447,7 @@ void qfs_default_params(qfs_params* p) {
   p->overtrain_ratio = 0.1;
   p->training_distribution = QFS_STATES_HAAR;
   p->concurrent_targets = 0;
+  p->refine_switch_tol = 0.0;
   p->seed = 0;
   p->dist_tol = 1e-8;
   p->diff_tol_r = 1e-5;
@@ -1451,11 +1467,6 @@ int qfs_create(qfs_ctx** out, int device, void* cuda_stream) {
   if (device < 0 || device >= count) return fail(QFS_EINVAL, "device %d of %d", device, count);
   qfs_ctx* ctx = new qfs_ctx();
   ctx->device = device;
-  if (const char* f = std::getenv("QFS_FUSE_UPDATE")) ctx->fuse_update = std::atoi(f) != 0;
-  if (const char* f = std::getenv("QFS_TMA")) ctx->tma = std::atoi(f) != 0;
-  if (const char* f = std::getenv("QFS_DATAFLOW")) ctx->dataflow = std::atoi(f) != 0;
-  if (const char* f = std::getenv("QFS_UPSI_FP64")) ctx->upsi_fp64 = std::atoi(f) != 0;
-  if (const char* f = std::getenv("QFS_DF_FWD2")) ctx->df_fwd2 = std::atoi(f) != 0;
   if (const char* f = std::getenv("QFS_DF_ITEM_KB")) ctx->df_item_bytes = std::max(16, std::atoi(f)) * 1024.0;
   if (const char* f = std::getenv("QFS_DF_ITEMS_PER_CTA")) ctx->df_items_per_cta = std::max(0.25, std::atof(f));
   if (const char* f = std::getenv("QFS_DF_ITEMS_PER_CTA_FWD"))
@@ -1466,10 +1477,6 @@ int qfs_create(qfs_ctx** out, int device, void* cuda_stream) {
   int l2 = 0;
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device);
   ctx->l2_bytes = (size_t)l2;
-  if (e == cudaSuccess) {
-    configure_tma_kernels();
-    e = cudaGetLastError();
-  }
   if (e == cudaSuccess) {
     if (cuda_stream) {
       ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
@@ -1542,6 +1549,40 @@ void qfs_destroy(qfs_ctx* ctx) {
 }
 
 int qfs_device_sms(const qfs_ctx* ctx) { return ctx ? ctx->num_sms : 0; }
+
+int qfs_set_option(qfs_ctx* ctx, int32_t option, int64_t value) {
+  g_err.clear();
+  if (!ctx) return fail(QFS_EINVAL, "ctx is NULL");
+  switch (option) {
+    case QFS_OPT_WAIT_LIMIT:
+      if (value < 1) return fail(QFS_EINVAL, "wait limit %lld < 1", (long long)value);
+      ctx->df_wait_limit = value;
+      return QFS_OK;
+    case QFS_OPT_WORKSPACE_CAP:
+      if (value < 0) return fail(QFS_EINVAL, "workspace cap %lld < 0", (long long)value);
+      ctx->ws_cap = (size_t)value;
+      return QFS_OK;
+    case QFS_OPT_FUSED_UPDATE: ctx->fuse_update = value != 0; return QFS_OK;
+    case QFS_OPT_DATAFLOW: ctx->dataflow = value != 0; return QFS_OK;
+    case QFS_OPT_TWO_GATE_FORWARD: ctx->df_fwd2 = value != 0; return QFS_OK;
+    case QFS_OPT_FP64_TARGET_PRODUCT: ctx->upsi_fp64 = value != 0; return QFS_OK;
+    default: return fail(QFS_EINVAL, "unknown option %d", option);
+  }
+}
+
+int qfs_get_option(qfs_ctx* ctx, int32_t option, int64_t* value) {
+  g_err.clear();
+  if (!ctx || !value) return fail(QFS_EINVAL, "ctx and value must be given");
+  switch (option) {
+    case QFS_OPT_WAIT_LIMIT: *value = ctx->df_wait_limit; return QFS_OK;
+    case QFS_OPT_WORKSPACE_CAP: *value = (int64_t)ctx->ws_cap; return QFS_OK;
+    case QFS_OPT_FUSED_UPDATE: *value = ctx->fuse_update; return QFS_OK;
+    case QFS_OPT_DATAFLOW: *value = ctx->dataflow; return QFS_OK;
+    case QFS_OPT_TWO_GATE_FORWARD: *value = ctx->df_fwd2; return QFS_OK;
+    case QFS_OPT_FP64_TARGET_PRODUCT: *value = ctx->upsi_fp64; return QFS_OK;
+    default: return fail(QFS_EINVAL, "unknown option %d", option);
+  }
+}
 
 int qfs_profile_enable(qfs_ctx* ctx, int enable) {
   g_err.clear();
@@ -1686,8 +1727,8 @@ int qfs_sweep_once(qfs_ctx* ctx, const qfs_circuit* circuit, const double* targe
   if (df_usable(ctx, R, rs))
     TRY(df_sweep(ctx, R, rs, psi, phil, R.envs, nullptr, nullptr, st));
   else
-    sweep(ctx, R, rs, Slice{0, S, S, ctx->stream}, R.g64, R.g32, psi, phil, R.B, R.phi, R.partials, R.nblk_max,
-          R.costs, R.envs, nullptr, R.stream_b, nullptr, R.counters);
+    TRY(sweep(ctx, R, rs, Slice{0, S, S, ctx->stream}, R.g64, R.g32, psi, phil, R.B, R.phi, R.partials,
+              R.nblk_max, R.costs, R.envs, nullptr, R.stream_b, nullptr, R.counters));
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(gates_out, R.g64, gbytes, cudaMemcpyDeviceToHost, st));
   if (envs_out) CK(cudaMemcpyAsync(envs_out, R.envs, gbytes, cudaMemcpyDeviceToHost, st));
@@ -1831,9 +1872,12 @@ extern "C" int qfs_sweep_once_noalloc(void* cuda_stream, const qfs_circuit* circ
   R.prec = QFS_FP64;
   R.beta = beta;
   R.sh = make_shape(R.n, M, S, R64, sms);
+  // sweep() shapes every backward launch for shape_starts(S) starts (fewer
+  // starts per shape, smaller chunks, more blocks), so the partial-sum slots
+  // per start are sized for that shape, as prepare() sizes them.
   R.nblk_max = 1;
   for (int U = 2; U <= std::min(4, R.n); ++U)
-    R.nblk_max = std::max(R.nblk_max, make_bwd_shape(R.n, M, S, R64, sms, U).nblk);
+    R.nblk_max = std::max(R.nblk_max, make_bwd_shape(R.n, M, shape_starts(S), R64, sms, U).nblk);
 
   const size_t state = (size_t)R.sN * sizeof(double2);
   const size_t need = align_up(state) + align_up((size_t)std::max(R.L - 1, 1) * S * state) +
@@ -1867,9 +1911,9 @@ extern "C" int qfs_sweep_once_noalloc(void* cuda_stream, const qfs_circuit* circ
     CK(cudaMemcpyAsync(gates_out_dev, gates_in_dev, (size_t)S * R.L * 16 * sizeof(double2),
                        cudaMemcpyDeviceToDevice, st));
   launch_gemm_upsi(R.U, R.psi64, R.phil64, (int)R.N, M, st);
-  sweep(&tmp, R, R64, Slice{0, S, S, st}, R.g64, nullptr, R.psi64, R.phil64, R.B, R.phi, R.partials,
-        R.nblk_max, costs_out_dev, reinterpret_cast<double2*>(envs_out_dev), nullptr, stream_b,
-        nullptr, R.counters);
+  TRY(sweep(&tmp, R, R64, Slice{0, S, S, st}, R.g64, nullptr, R.psi64, R.phil64, R.B, R.phi, R.partials,
+            R.nblk_max, costs_out_dev, reinterpret_cast<double2*>(envs_out_dev), nullptr, stream_b,
+            nullptr, R.counters));
   CK(cudaGetLastError());
   return QFS_OK;
 }

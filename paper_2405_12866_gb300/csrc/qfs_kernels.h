@@ -112,6 +112,7 @@ struct DfArgs {
   unsigned* chunk_cnt;                  // nsteps x S finished chunks
   unsigned* done;                       // S: steps finished per start
   int* err;                             // bit 0: a bounded wait ran out
+  long long wait_limit;                 // polls of a dependency wait before it gives up
   void* partials;                       // S x part_stride x 32 environment partials (float or double)
   double* resid_partials;               // S x part_stride x 32, residual step only
   int part_stride;                      // slots per start: the most chunks of any step
@@ -167,21 +168,6 @@ struct BwdArgs {
   unsigned* counters;  // per start, zero between launches
   UpdateArgs upd;
 };
-
-// TMA-staged backward step (mode 0): rows are staged in shared memory by
-// bulk copies.  Supported when a row is a multiple of 16 bytes and a unit
-// (Phi and B rows) fits a stage.  Shapes from make_tma_shape.  A bounded
-// wait that runs out sets bit 0 of *err.
-bool tma_backward_supported(Real r, int M, int U);
-Shape make_tma_shape(int n, int M, int S, Real r, int num_sms, int U);
-void launch_backward_tma(Real r, const BwdGeom& g, const Shape& sh, int S, const void* bprev,
-                         long long bprev_stride, const void* phi_in, long long phi_in_stride,
-                         void* phi_out, const void* gates, long long gate_stride, void* partials,
-                         int stream_b, const int* active, cudaStream_t st, const UpdateArgs* fuse,
-                         unsigned* counters, int* err);
-// Set kernel attributes (large dynamic shared memory) once per process and
-// device, outside any stream capture.
-void configure_tma_kernels();
 
 // Residual cost: cost[s] = sum_blk partial[s][blk][0] * inv_M.
 void launch_residual_finish(const double* partials, int nblk, int S, double inv_M,

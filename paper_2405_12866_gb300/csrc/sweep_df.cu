@@ -31,8 +31,6 @@ namespace qfs {
 
 namespace {
 
-constexpr long long kDfSpinLimit = 1LL << 25;  // polls of 32+ ns before giving up (> 1 s)
-
 // One CTA per SM holding all the warps the registers allow (12 for complex64,
 // 8 for complex128): an item is streamed by the whole SM, so the chunks of
 // one start finish sooner than with several smaller CTAs sharing the SM.
@@ -843,7 +841,7 @@ __global__ void __launch_bounds__(df_threads<T>(), 1) k_sweep_df(DfArgs a) {
       int ok = 1;
       long long polls = 0;
       while (ld_acquire_u32(a.done + s) < (unsigned)i) {
-        if (++polls > kDfSpinLimit || ld_volatile_i32(a.err)) {
+        if (++polls > a.wait_limit || ld_volatile_i32(a.err)) {
           ok = 0;
           break;
         }

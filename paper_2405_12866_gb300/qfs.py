@@ -25,6 +25,13 @@ QFS_ECUDA = -3
 QFS_ETIMEOUT = -4
 QFS_EUNSUPPORTED = -5
 QFS_ENONFINITE = -6
+QFS_EINTERNAL = -7
+QFS_OPT_WAIT_LIMIT = 0
+QFS_OPT_WORKSPACE_CAP = 1
+QFS_OPT_FUSED_UPDATE = 2
+QFS_OPT_DATAFLOW = 3
+QFS_OPT_TWO_GATE_FORWARD = 4
+QFS_OPT_FP64_TARGET_PRODUCT = 5
 QFS_FP64 = 0
 QFS_MIXED = 1
 QFS_STATES_HAAR = 0
@@ -40,6 +47,7 @@ EXPORTS = [
     "qfs_instantiate_batch_dev", "qfs_gemm_bf16_dev", "qfs_ws_create", "qfs_ws_destroy", "qfs_ws_params",
     "qfs_ws_loss_grad", "qfs_ws_train", "qfs_ws_predict",
     "qfs_dataflow_trace_enable", "qfs_dataflow_trace_read", "qfs_target_product_dev",
+    "qfs_set_option", "qfs_get_option",
 ]
 (PROF_BACKWARD, PROF_FORWARD, PROF_UPDATE, PROF_GEMM, PROF_RESIDUAL, PROF_CHECK, PROF_OTHER, PROF_BATCH,
  PROF_MLP, PROF_DATAFLOW) = range(10)
@@ -63,7 +71,7 @@ class Params(C.Structure):
                 ("start_groups", C.c_int32), ("seed", C.c_uint64), ("dist_tol", C.c_double),
                 ("diff_tol_r", C.c_double), ("beta", C.c_double), ("restart_doubling", C.c_int32),
                 ("overtrain_ratio", C.c_double), ("training_distribution", C.c_int32),
-                ("concurrent_targets", C.c_int32)]
+                ("concurrent_targets", C.c_int32), ("refine_switch_tol", C.c_double)]
 
 
 class Result(C.Structure):
@@ -125,6 +133,8 @@ def lib():
     L.qfs_sweep_once_noalloc.argtypes = [_P, C.POINTER(Circuit), _P, _P, C.c_int32, C.c_int32,
                                          C.c_double, _P, _P, _P, _P]
     L.qfs_profile_enable.argtypes = [_P, C.c_int]
+    L.qfs_set_option.argtypes = [_P, C.c_int32, C.c_int64]
+    L.qfs_get_option.argtypes = [_P, C.c_int32, C.POINTER(C.c_int64)]
     L.qfs_profile_reset.argtypes = [_P]
     L.qfs_profile_read.argtypes = [_P, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                    C.POINTER(C.c_double), C.POINTER(C.c_double)]
@@ -236,6 +246,15 @@ class Context:
     @property
     def num_sms(self) -> int:
         return lib().qfs_device_sms(self._h)
+
+    def set_option(self, option: int, value: int):
+        """qfs_set_option: one of the QFS_OPT_* settings of this context."""
+        _check(lib().qfs_set_option(self._h, option, int(value)))
+
+    def get_option(self, option: int) -> int:
+        v = C.c_int64()
+        _check(lib().qfs_get_option(self._h, option, C.byref(v)))
+        return v.value
 
     def instantiate(self, n, pairs, target, params: Params, samples=None, init_gates=None):
         """Host arrays in, numpy gates out.  samples/init_gates None -> drawn from params.seed."""

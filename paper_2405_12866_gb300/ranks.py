@@ -19,9 +19,17 @@ def dist_env() -> tuple[int, int, int]:
 
 def target_seeds(rank: int, n: int, stride: int = 100000) -> list[int]:
     """Seeds of the n targets a rank instantiates; disjoint across ranks."""
-    if n > stride:
-        raise ValueError("more targets per rank than the seed stride")
+    if n > stride // 2:
+        raise ValueError("more targets per rank than half the seed stride")
     return [rank * stride + i for i in range(n)]
+
+
+def warmup_seeds(rank: int, n: int, stride: int = 100000) -> list[int]:
+    """Seeds of the n untimed warm-up targets of a rank: the upper half of
+    its seed range, disjoint from target_seeds and from other ranks."""
+    if n > stride // 2:
+        raise ValueError("more warm-up targets per rank than half the seed stride")
+    return [rank * stride + stride // 2 + i for i in range(n)]
 
 
 def combine(values_max, values_sum, device=None):

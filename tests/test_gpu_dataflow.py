@@ -3,8 +3,6 @@ the per-step launches and against the CPU oracle, on structures that reach
 every kind of step: forward steps, backward steps whose two gates touch
 four, three (all four placements) or two qubits (both orders), the first
 backward step without a gate, and the complex64 residual pass."""
-import os
-
 import numpy as np
 import pytest
 
@@ -13,15 +11,9 @@ pytestmark = pytest.mark.gpu
 
 def _ctx(dataflow: bool):
     from paper_2405_12866_gb300 import qfs
-    old = os.environ.get("QFS_DATAFLOW")
-    os.environ["QFS_DATAFLOW"] = "1" if dataflow else "0"
-    try:
-        return qfs.Context(0)
-    finally:
-        if old is None:
-            del os.environ["QFS_DATAFLOW"]
-        else:
-            os.environ["QFS_DATAFLOW"] = old
+    c = qfs.Context(0)
+    c.set_option(qfs.QFS_OPT_DATAFLOW, 1 if dataflow else 0)
+    return c
 
 
 @pytest.fixture(scope="module")

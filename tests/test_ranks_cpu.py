@@ -22,7 +22,7 @@ def _worker(rank, world, port, out):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     from paper_2405_12866_gb300 import ranks
     r, w, local = ranks.dist_env()
-    seeds = ranks.target_seeds(r, 5)
+    seeds = ranks.target_seeds(r, 5) + ranks.warmup_seeds(r, 3)
     mx, sm = ranks.combine([10.0 + r], [3 + r, 100 * (r + 1)])
     out.put((r, w, local, seeds, mx, sm))
     dist.barrier()
@@ -43,7 +43,7 @@ def test_two_gloo_ranks_shard_and_combine():
         assert p.exitcode == 0
     (r0, w0, l0, s0, mx0, sm0), (r1, w1, l1, s1, mx1, sm1) = res
     assert (r0, r1, w0, w1, l0, l1) == (0, 1, 2, 2, 0, 1)
-    assert not set(s0) & set(s1) and len(s0) == len(s1) == 5
+    assert not set(s0) & set(s1) and len(set(s0)) == len(set(s1)) == 8
     assert mx0 == mx1 == [11.0]
     assert sm0 == sm1 == [7.0, 300.0]
 
@@ -53,3 +53,5 @@ def test_single_process_combine_is_identity():
     assert ranks.combine([1.5], [2, 3]) == ([1.5], [2.0, 3.0])
     with pytest.raises(ValueError):
         ranks.target_seeds(0, 200000)
+    with pytest.raises(ValueError):
+        ranks.warmup_seeds(0, 60000)

@@ -6,7 +6,9 @@ device-wide synchronisation an allocation can cause).  Its scratch is a
 static device array shared by every call, so this test calls it twice in a
 row with different problems and checks each result against
 qfs_sweep_once, to the FP64 sweep tolerances used elsewhere (1e-10 on gates
-and environments, 1e-12 on the cost).  The file name makes pytest collect
+and environments, 1e-12 on the cost).  A third call runs a problem large
+enough that its launches need more partial-sum slots per start than a
+shape for all starts would give.  The file name makes pytest collect
 it last.
 """
 import ctypes as C
@@ -35,7 +37,11 @@ def test_noalloc_sweep_matches_regular_sweep_twice():
     dev = torch.device("cuda:0")
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
-    cases = [(6, w.brick_pairs(6, 3), 16, 3, 501), (5, [(0, 1), (3, 4), (2, 1), (4, 0)], 5, 4, 502)]
+    # The third case (8.5 MiB of scratch) is one where the backward launches,
+    # shaped for a quarter of the starts, use more blocks per start than a
+    # shape for all S starts would: its partial sums must still fit.
+    cases = [(6, w.brick_pairs(6, 3), 16, 3, 501), (5, [(0, 1), (3, 4), (2, 1), (4, 0)], 5, 4, 502),
+             (10, [(0, 1), (2, 3)], 32, 8, 503)]
     with qfs.Context(0) as ctx:
         for n, pairs, M, S, seed in cases:
             U, Psi, G = _problem(n, pairs, M, S, seed)
