@@ -51,8 +51,13 @@ def forward(params, X, round_bf16=False):
     return H, cache
 
 
-def loss_and_grads(params, X, T, n_out, round_bf16=False):
-    """Mean squared error over the first n_out outputs and its gradients."""
+def loss_and_grads(params, X, T, n_out, round_bf16=False, magnitudes=False):
+    """Mean squared error over the first n_out outputs and its gradients.
+
+    With magnitudes=True it also returns, per layer, the sums of the
+    absolute values of the terms that make up each gradient entry
+    (|g|^T |H| for the weights, sum |g| for the biases): the scale against
+    which a rounding difference in one of those terms is measured."""
     Y, cache = forward(params, X, round_bf16)
     B = X.shape[0]
     D = np.zeros_like(Y)
@@ -60,6 +65,7 @@ def loss_and_grads(params, X, T, n_out, round_bf16=False):
     loss = float(np.sum(D ** 2) / (B * n_out))
     dY = 2.0 * D / (B * n_out)
     grads = [None] * len(params)
+    mags = [None] * len(params)
     g = dY                      # gradient w.r.t. this layer's pre-activation
     for li in range(len(params) - 1, -1, -1):
         W, b = params[li]
@@ -69,5 +75,9 @@ def loss_and_grads(params, X, T, n_out, round_bf16=False):
         g16 = bf16(g) if round_bf16 else g     # operand of the weight and input GEMMs
         Wr = bf16(W) if round_bf16 else W
         grads[li] = (g16.T @ H, g.sum(axis=0))
+        if magnitudes:
+            mags[li] = (np.abs(g16).T @ np.abs(H), np.abs(g).sum(axis=0))
         g = g16 @ Wr
+    if magnitudes:
+        return loss, grads, mags
     return loss, grads

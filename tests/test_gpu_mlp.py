@@ -87,12 +87,28 @@ def test_warm_start_gradients_match_oracle(ctx):
     phif = w.sample_states(seed ^ 0x5EEDF1C5, 4, 8)
     F = 4.0 * np.einsum("tij,jk->tik", U, phif)
     X = np.stack([F.real, F.imag], axis=-1).reshape(200, 256)
-    want_loss, want = mo.loss_and_grads(params, X, labels, 192, round_bf16=True)
+    want_loss, want, mags = mo.loss_and_grads(params, X, labels, 192, round_bf16=True, magnitudes=True)
     assert abs(loss - want_loss) < 1e-3 * want_loss
     got = qfs.WarmStart.unflatten(g.astype(np.float64))
-    for (gw, gb), (ww, wb) in zip(got, want):
-        assert np.linalg.norm(gw - ww) < 3e-2 * np.linalg.norm(ww) + 1e-12
-        assert np.linalg.norm(gb - wb) < 3e-2 * np.linalg.norm(wb) + 1e-12
+    # Element by element.  Both sides round the same tensors to bf16 at the
+    # same points; an FP32-computed value that lies within its FP32 error of
+    # a bf16 rounding boundary can round the other way, which moves that one
+    # term of a sum by at most one bf16 step (2^-7 of its size, relative;
+    # bf16 keeps 8 significant bits).  Each entry may therefore differ by
+    # 2^-7 of the summed magnitude of its terms (|g|^T |H| for weights,
+    # sum |g| for biases, from the oracle), which also covers the FP32
+    # accumulation error; nothing else.  A wrong row, column or slice moves
+    # entries by their own size, far outside this bound.
+    for li, ((gw, gb), (ww, wb), (mw, mb)) in enumerate(zip(got, want, mags)):
+        for name, a, b, m in (("W", gw, ww, mw), ("b", gb, wb, mb)):
+            bound = 2.0 ** -7 * m + 1e-6 * np.max(m)
+            bad = np.abs(a - b) > bound
+            assert not np.any(bad), (f"layer {li} {name}: {int(bad.sum())} of {bad.size} entries outside the "
+                                     f"bf16 rounding bound; worst excess "
+                                     f"{float(np.max((np.abs(a - b) - bound) / np.maximum(m, 1e-30)))}")
+        # and most entries agree far more closely than the bound
+        rel = np.abs(gw - ww) / np.maximum(mw, 1e-30)
+        assert np.median(rel) < 1e-4, (li, float(np.median(rel)))
     model.close()
 
 

@@ -257,6 +257,28 @@ def test_plateau_stops_run():
     assert all(not (abs(last[j - 1]) - abs(last[j]) > 1e-3 * abs(last[j])) for j in range(1, 6))
 
 
+def test_plateau_window_length_is_exact():
+    """One gate on three qubits: the gate's environment does not depend on
+    the gate itself, so the first update already is the exact minimiser and
+    every later sweep returns the same gate and the same cost, bit for bit
+    (Eq. 2 is the optimum of the single-gate cost).  The cost never improves
+    after sweep 1, so a window of w sweeps without improvement ends the run
+    at sweep w + 1, or at min_sweeps if that is later (Appendix A)."""
+    n, pairs = 3, [(0, 1)]
+    # a target the single gate cannot reach: two gates on (0, 1), (1, 2)
+    U = w.target_unitary(w.haar_gates(141, w.STREAM_TARGET_GATES, 2), [(0, 1), (1, 2)], n)
+    Psi, G0 = w.sample_states(142, n, 8), w.initial_gates(143, 2, 1)
+    base = o.instantiate(U, Psi, G0, pairs, n, 0.0, 8)
+    assert base.cost > 1e-3
+    assert np.all(base.cost_trace[1:] == base.cost_trace[0])
+    for win in range(1, 7):
+        r = o.instantiate(U, Psi, G0, pairs, n, 0.0, 100, plateau_window=win, diff_tol_r=1e-12, min_sweeps=0)
+        assert r.sweeps == win + 1, (win, r.sweeps)
+        r = o.instantiate(U, Psi, G0, pairs, n, 0.0, 100, plateau_window=win, diff_tol_r=1e-12,
+                          min_sweeps=win + 4)
+        assert r.sweeps == win + 4, (win, r.sweeps)
+
+
 def test_target_generator_matches_kron():
     n = 5
     pairs = [(0, 1), (3, 4), (1, 2), (2, 3)]
