@@ -574,6 +574,9 @@ def run_ours_batch(args):
                 "h2d_bytes_per_step": int(sum(x.nbytes for x in hin)), "d2h_bytes_per_step": int(b[1].sum()) * 256},
         "gpu_launches": int(launches),
     }
+    tuned, trials = ctx.batch_schedules()
+    line["config"]["schedules"] = {f"n{t['n']}_L{t['L']}": f"G{t['G']}w{t['warps']}" for t in tuned}
+    print(json.dumps({"batch_trials": trials}), file=sys.stderr, flush=True)
     if args.cpu_baseline:
         t0 = time.perf_counter()
         n_sample = 0
@@ -642,7 +645,7 @@ def run_ours_learned(args):
     secs = sum(s.seconds for s in stats)
     conv = sum(s.converged for s in stats)
     value = conv / secs
-    rand = learned.two_stage(ctx, Tev, first_rand, seed=7000, name="random first start")
+    rand = learned.two_stage(ctx, Tev, first_rand, ws=ws, seed=7000, name="random first start")
     base = learned.multistart(ctx, Tev, S=8, seed=7000, name="8 random starts")
     # The plain FP64 GPU path (one problem per call, 8 starts) on a sample.
     nfp = min(64, neval)

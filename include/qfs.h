@@ -322,9 +322,14 @@ int qfs_target_product_dev(qfs_ctx* ctx, int32_t n, int32_t M, const double* tar
  * p->refine_sweeps_max FP64 sweeps if the check is above tol.  gates_out
  * (host) receives L_i x 16 complex per problem, concatenated; results
  * (host) one qfs_result per problem (fp64_sweeps = refinement sweeps).
- * The warps per block of the persistent kernel are tuned on the first call
- * for a given (largest N*M, largest L) and cached.  beta must be 0;
- * multistarts 1..64. */
+ * Problems are grouped in classes (n, L, M); for each class an autotuner
+ * times the launch shapes that fit (G = 4, 8, 16 or 32 lanes per start, i.e.
+ * 8, 4, 2 or 1 starts of a problem per warp, and 2, 4 or 8 warps per block)
+ * on a few sweeps of that class's problems the first time the context sees
+ * the class, and keeps the fastest; the batch then runs as one captured
+ * graph with one persistent launch per shape, replayed by later calls of the
+ * same shape.  Results do not depend on the shapes chosen beyond the order of
+ * FP32 sums.  beta must be 0; multistarts 1..64. */
 int qfs_instantiate_batch(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls,
                           const int32_t* pairs, const double* targets, const double* samples,
                           const double* init_gates, const qfs_params* p, double* gates_out,
@@ -336,6 +341,30 @@ int qfs_instantiate_batch_dev(qfs_ctx* ctx, int32_t P, const int32_t* ns, const 
                               const int32_t* pairs, const double* targets_dev,
                               const double* samples_dev, const double* init_gates_dev,
                               const qfs_params* p, double* gates_out_dev, qfs_result* results);
+
+/* The batched form's autotuner state on this context (a measurement aid;
+ * the paper has no counterpart).  tuned (host, cap x 6 int32, may be NULL):
+ * per problem class, n, L, M, multistarts, the chosen lanes per start G and
+ * warps per block; *n_tuned: the classes tuned so far.  trials (cap x 6,
+ * may be NULL) and trial_ns (cap doubles, may be NULL): every timed trial
+ * (n, L, M, multistarts, G, warps) and its time per start-sweep in ns;
+ * *n_trials: the trials so far.  At most cap rows are written. */
+int qfs_batch_schedules(qfs_ctx* ctx, int32_t cap, int32_t* tuned, int32_t* n_tuned, int32_t* trials,
+                        double* trial_ns, int32_t* n_trials);
+
+/* Exactly one complex64 sweep of the batched form for every start of P
+ * problems (parity checks): inputs as qfs_instantiate_batch (host; samples
+ * N_i x M_i with M_i = M if M > 0 (capped at N_i) else N_i / 2, gates_in S x
+ * L_i x 16 per problem, concatenated), lanes_per_start = 4, 8, 16 or 32
+ * forces that launch shape for every class (0: the tuned shapes).  Every
+ * start runs one sweep from its gates_in with the Jacobi started from the
+ * identity; gates_out (host, same layout as gates_in, complex128 values of
+ * the complex64 gates) and costs_out (host, P x S, may be NULL) receive the
+ * swept gates and each start's complex64 residual cost
+ * (1/M) sum_j ||U psi_j - C psi_j||^2. */
+int qfs_batch_sweep_once(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls, const int32_t* pairs,
+                         const double* targets, const double* samples, int32_t M, int32_t S,
+                         const double* gates_in, int32_t lanes_per_start, double* gates_out, double* costs_out);
 
 /* BF16 GEMM on the tcgen05 tensor cores (the learned warm start's layers):
  * C = A B^T (+ bias, optional GELU), A (M x K, leading dimension lda) and B
@@ -382,6 +411,23 @@ int qfs_ws_loss_grad(qfs_ws* ws, int32_t count, const double* targets, const dou
 int qfs_ws_train(qfs_ws* ws, int32_t count, const double* targets, const double* labels, int32_t epochs,
                  int32_t batch, double lr, double lr_final, uint64_t shuffle_seed, double* epoch_loss);
 int qfs_ws_predict(qfs_ws* ws, int32_t count, const double* targets, double* gates_out);
+
+/* The learned warm start as an instantiation policy for P targets of the
+ * learned structure (host, P x 16 x 16): the first start of target i is the
+ * network's prediction projected onto U(4) (or first_gates, host P x 6 x 16,
+ * when given: the same policy with other first starts), run alone in the
+ * batched form for at most first_sweeps sweeps (training states drawn from
+ * p->seed + i); every target left unconverged falls back to
+ * p->multistarts random starts and p->max_sweeps sweeps, with training
+ * states and starts drawn from p->seed + 2^30 + i.  The prediction stays on
+ * the device.  gates_out (host, P x 6 x 16) and results[P] receive each
+ * target's answer (best_start 0: the first start; j + 1: fallback start j;
+ * sweeps: both stages).  stats (host, 4 int64, may be NULL): targets the
+ * first start converged, its start-sweeps, the fallback's start-sweeps,
+ * targets that fell back.  p->M = 0 takes N / 2 = 8 training states. */
+int qfs_ws_instantiate(qfs_ws* ws, int32_t P, const double* targets, const double* first_gates,
+                       const qfs_params* p, int32_t first_sweeps, double* gates_out, qfs_result* results,
+                       int64_t* stats);
 
 /* One FP64 sweep (as qfs_sweep_once with QFS_FP64) that allocates no
  * memory, for callers that cannot call cudaMalloc: code running inside a

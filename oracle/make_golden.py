@@ -9,10 +9,13 @@ target: converged, the stopping sweep, the selected start and its cost.
 
     python -m oracle.make_golden brick_n12 0 1 2 3
     python -m oracle.make_golden brick_n8_restart 0 1 2
+    python -m oracle.make_golden uneven_blocks 512
 
 The second form runs the oracle's double-and-restart outer loop on the
 brick_n8 workload (one target per process) and records converged, the
-total sweeps, the selected start, the final M and the costs.
+total sweeps, the selected start, the final M and the costs.  The third
+runs the oracle's multistart instantiation on the first P problems of the
+batched workload (one problem per process).
 """
 from __future__ import annotations
 
@@ -88,6 +91,18 @@ def _restart_run(sd):
                 seconds=round(time.time() - t, 1))
 
 
+def _uneven_run(args):
+    """The oracle's multistart run of problem i of the uneven-blocks batch."""
+    i, seed, S, max_sweeps, tol = args
+    from paper_2405_12866_gb300 import workloads as w
+    p = w.uneven_blocks(P=i + 1, seed=seed, S=S)[i]
+    r = o.instantiate(p.U, p.samples(), p.init_gates()[:S], p.pairs, p.n, tol, max_sweeps)
+    return dict(n=p.n, L=p.L, converged=r.converged, sweeps=r.sweeps, best_start=r.best_start, cost=r.cost)
+
+
+UNEVEN_SEED, UNEVEN_S, UNEVEN_MAX_SWEEPS, UNEVEN_TOL = 4, 8, 300, 1e-8
+
+
 RESTART_OTR = 0.1
 RESTART_MIN_SWEEPS = 6
 
@@ -96,6 +111,18 @@ def main(argv):
     from paper_2405_12866_gb300 import workloads as w
     kind = argv[0]
     seeds = [int(x) for x in argv[1:]] or [0]
+    if kind == "uneven_blocks":
+        # problems 0 .. P-1 of the batched workload (seed 4, 8 starts, 300 sweeps)
+        P = seeds[0]
+        out_path = os.path.join(ROOT, "tests", "golden", "uneven_blocks_oracle_runs.json")
+        jobs = [(i, UNEVEN_SEED, UNEVEN_S, UNEVEN_MAX_SWEEPS, UNEVEN_TOL) for i in range(P)]
+        t = time.time()
+        with mp.get_context("spawn").Pool(os.cpu_count()) as pool:
+            runs = pool.map(_uneven_run, jobs, chunksize=4)
+        json.dump(dict(seed=UNEVEN_SEED, starts=UNEVEN_S, max_sweeps=UNEVEN_MAX_SWEEPS, tol=UNEVEN_TOL,
+                       seconds=round(time.time() - t, 1), runs=runs), open(out_path, "w"), indent=0)
+        print(kind, P, sum(r["converged"] for r in runs), "converged", flush=True)
+        return
     if kind == "brick_n8_restart":
         out_path = os.path.join(ROOT, "tests", "golden", "brick_n8_restart_oracle_runs.json")
         runs = json.load(open(out_path)) if os.path.exists(out_path) else {}

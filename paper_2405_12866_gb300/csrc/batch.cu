@@ -1,21 +1,28 @@
 // Batched QFactor-Sample: many small instantiation problems (3-5 qubits,
 // 2-10 two-qubit gates each) and their multistarts in one persistent launch.
 //
-// Each warp runs whole instantiations of one (problem, start) pair taken from
-// an atomic work queue ordered largest problem first.  A warp keeps its
-// running state B and Phi (N x M complex, N <= 32, M <= 16) and its gates in
-// its own slice of shared memory and sweeps as in Section 3 of the paper;
-// the list of intermediate states is replaced by walking B back with the
-// old gate (B_{k-1} = g_k^dagger B_k), so nothing leaves the SM between
-// sweeps.  Environments are reduced with one warp reduce-scatter; the update
-// (Eq. 2) is the FP32 Jacobi polar factor with a Newton-Schulz step (FP64
-// Jacobi for ill-conditioned environments).  The run's stop rule is kept
-// without any waiting: a start stops when it converges or once its sweep
-// passes the earliest converged sweep of its problem (an atomicMin); the
-// lowest-cost start among those that converged at that sweep is the
-// problem's answer, which is what lock-step multistarts would return.
-// A finishing kernel then makes the selected gates unitary in FP64, checks
-// the cost in FP64 and, if needed, refines with FP64 sweeps.
+// Work is handed out in units: a unit is one problem and 32/G of its starts,
+// run by one warp with G lanes per start (G = 32: a warp per start; G = 16,
+// 8 or 4: two, four or eight starts share a warp).  Each start keeps its
+// running state B and Phi (N x M complex, N <= 32, M <= 16), its gates and
+// the right singular vectors of their last updates in its own slice of
+// shared memory and sweeps as in Section 3 of the paper; the list of
+// intermediate states is replaced by walking B back with the old gate
+// (B_{k-1} = g_k^dagger B_k), so nothing leaves the SM between sweeps.  The
+// starts' state arithmetic (gate applications, environment sums) runs side
+// by side in their lane groups; each group reduces its environment over its
+// own lanes, and the warp then updates the unit's gates one after another
+// (Eq. 2: the FP32 Jacobi polar factor with a Newton-Schulz step, FP64
+// Jacobi for ill-conditioned environments).  Units come from an atomic work
+// queue ordered largest problem first; the schedule G (and the warps per
+// block) of each class of problems (n, L, M) is chosen by the host's
+// autotuner.  The run's stop rule is kept without any waiting: a start stops
+// when it converges or once its sweep passes the earliest converged sweep of
+// its problem (an atomicMin); the lowest-cost start among those that
+// converged at that sweep is the problem's answer, which is what lock-step
+// multistarts would return.  A finishing kernel then makes the selected
+// gates unitary in FP64, checks the cost in FP64 and, if needed, refines
+// with FP64 sweeps.
 #include "polar4.cuh"
 #include "qfs_common.cuh"
 #include "qfs_kernels.h"
@@ -37,10 +44,10 @@ __device__ __forceinline__ uint32_t ins2(uint32_t r, int lo, int hi) {
 }
 
 // X <- g X (dag = false) or X <- g^dagger X (dag = true) on qubits (qa, qb),
-// X an N x M state in this warp's shared memory.
-template <typename T2>
-__device__ void warp_apply(T2* X, const T2* g, int n, int M, int qa, int qb, bool dag) {
-  const int lane = threadIdx.x & 31;
+// X an N x M state in shared memory, by the G lanes of one group (gl = lane
+// within the group).  The caller synchronises the warp.
+template <int G, typename T2>
+__device__ void group_apply(T2* X, const T2* g, int n, int M, int qa, int qb, bool dag, int gl) {
   const int pa = n - 1 - qa, pb = n - 1 - qb;
   const int lo = min(pa, pb), hi = max(pa, pb);
   const int groups = (1 << (n - 2)) * M;
@@ -51,8 +58,7 @@ __device__ void warp_apply(T2* X, const T2* g, int n, int M, int qa, int qb, boo
   for (int y = 0; y < 4; ++y)
 #pragma unroll
     for (int x = 0; x < 4; ++x) gg[4 * y + x] = dag ? T2{g[4 * x + y].x, -g[4 * x + y].y} : g[4 * y + x];
-  __syncwarp();
-  for (int w = lane; w < groups; w += 32) {
+  for (int w = gl; w < groups; w += G) {
     const int r = w / M, j = w - r * M;
     const uint32_t base = ins2((uint32_t)r, lo, hi);
     int off[4];
@@ -70,22 +76,40 @@ __device__ void warp_apply(T2* X, const T2* g, int n, int M, int qa, int qb, boo
       X[off[y]] = t;
     }
   }
-  __syncwarp();
 }
 
-// E[x][y] = sum B[x] conj(Phi[y]) over the groups of (qa, qb); on return
-// lane l16 < 16 holds the complex entry E[c][r] with l16 = 4c + r, the
-// layout the polar routines take (as A[r][c] after conjugation).
-template <typename T, typename T2>
-__device__ T2 warp_env(const T2* Bs, const T2* Ph, int n, int M, int qa, int qb) {
-  const int lane = threadIdx.x & 31;
+// Reduce-scatter of 32 per-lane values over the G lanes of a group: on
+// return lane gl holds, in v[0 .. 32/G - 1], the group's sums of the values
+// base .. base + 32/G - 1, base returned.
+template <int G, typename T>
+__device__ __forceinline__ int group_reduce_scatter(T (&v)[32], int gl) {
+  int base = 0;
+  int cnt = 32;
+#pragma unroll
+  for (int o = G / 2; o >= 1; o >>= 1) {
+    cnt >>= 1;
+    const bool upper = (gl & o) != 0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      if (i < cnt) {
+        const T send = upper ? v[i] : v[i + cnt];
+        const T keep = upper ? v[i + cnt] : v[i];
+        v[i] = keep + __shfl_xor_sync(FULL, send, o);
+      }
+    }
+    if (upper) base += cnt;
+  }
+  return base;
+}
+
+// Environment partial sums of one start over its group's lanes:
+// acc[2(4x+y)+{0,1}] += B[x] conj(Phi[y]) over the groups of (qa, qb).
+template <int G, typename T, typename T2>
+__device__ void group_env_acc(const T2* Bs, const T2* Ph, int n, int M, int qa, int qb, int gl, T (&acc)[32]) {
   const int pa = n - 1 - qa, pb = n - 1 - qb;
   const int lo = min(pa, pb), hi = max(pa, pb);
   const int groups = (1 << (n - 2)) * M;
-  T acc[32];
-#pragma unroll
-  for (int i = 0; i < 32; ++i) acc[i] = T(0);
-  for (int w = lane; w < groups; w += 32) {
+  for (int w = gl; w < groups; w += G) {
     const int r = w / M, j = w - r * M;
     const uint32_t base = ins2((uint32_t)r, lo, hi);
     T2 b[4], p[4];
@@ -102,9 +126,6 @@ __device__ T2 warp_env(const T2* Bs, const T2* Ph, int n, int M, int qa, int qb)
         cfma_conj(acc[2 * (4 * x + y)], acc[2 * (4 * x + y) + 1], b[x], p[y]);
       }
   }
-  const T v = warp_reduce_scatter32<T>(acc, lane);
-  const int l16 = lane & 15;
-  return T2{__shfl_sync(FULL, v, 2 * l16), __shfl_sync(FULL, v, 2 * l16 + 1)};
 }
 
 // New gate from E (E[c][r] in lane 4c + r): the polar factor of E^dagger.
@@ -132,62 +153,130 @@ __device__ void warp_update<float2>(float2 e, float2* g, double2* sm, float2* v)
 template <>
 __device__ void warp_update<double2>(double2 e, double2* g, double2* sm, float2* v) {
   (void)v;
-  const int lane = threadIdx.x & 31;
-  const int l16 = lane & 15, r = l16 & 3, c = l16 >> 2;
   double2 p;
   polar_update_warp<2>(e, nullptr, 0.0, sm, g, nullptr, &p, nullptr);
-  (void)r;
-  (void)c;
   __syncwarp();
 }
 
-// (1/M) sum |g_1^dagger Phi_1 - Psi|^2 after the sweep (Phi_1 in Ph, which
-// is overwritten).
-template <typename T, typename T2>
-__device__ T warp_residual(T2* Ph, const T2* g1, const T2* psi, int n, int M, int qa, int qb) {
-  warp_apply<T2>(Ph, g1, n, M, qa, qb, true);
-  const int lane = threadIdx.x & 31;
-  const int E = M << n;
-  // A sum of squares in the sweep's own precision: no cancellation, so its
-  // relative error stays ~1e-6 even for the largest states, far below what
-  // the FP64 check at dist_tol needs (FP64 on this GPU would cost a
-  // 64-cycle warp instruction per operation).
-  T acc = T(0);
-  for (int i = lane; i < E; i += 32) {
-    const T2 p = Ph[i], q = psi[i];
-    const T dx = p.x - q.x, dy = p.y - q.y;
-    acc = fmat(dx, dx, fmat(dy, dy, acc));
-  }
-#pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
-  if constexpr (sizeof(T) == 4) return acc * (1.f / (float)M);
-  else return acc / M;
+// Per-start smem slice (complex64): B (E_max), Phi (E_max), gates (16 L_max),
+// right singular vectors (16 L_max), environment (16).
+__host__ __device__ __forceinline__ int batch_slice_f2(int max_elems, int max_L) {
+  return 2 * max_elems + 32 * max_L + 16;
 }
 
-// One sweep of one start (Section 3): forward to B_{L-1} with the current
-// gates, then k = L..1: environment from (B_{k-1}, Phi_k), update gate k,
-// B_{k-2} = g_{k-1}^dagger B_{k-1} (old gate), Phi_{k-1} = g_k^dagger Phi_k
-// (new gate).  Returns the residual cost of the swept gates.
-template <typename T, typename T2>
-__device__ T warp_sweep(T2* Bs, T2* Ph, T2* G, const T2* psi, const T2* phil, const int* pairs,
-                             int n, int M, int L, double2* sm, float2* V = nullptr) {
+// One sweep (Section 3) of every active start of a unit: forward to B_{L-1}
+// with the current gates, then k = L..1: environment from (B_{k-1}, Phi_k),
+// update gate k, B_{k-2} = g_{k-1}^dagger B_{k-1} (old gate), Phi_{k-1} =
+// g_k^dagger Phi_k (new gate).  Returns, in every lane of a group, the
+// residual (1/M) sum |g_1^dagger Phi_1 - Psi|^2 of its start's swept gates,
+// as an FP32 sum of squares (no cancellation; relative error ~1e-6, far
+// below what the FP64 check at dist_tol needs).  `act` is this group's
+// start being active; `act_mask` has bit j set when group j is active.
+template <int G>
+__device__ float group_sweep(float2* slice, int slice_f2, int E_max, int L_max, const float2* psi,
+                             const float2* phil, const int* pairs, int n, int M, int L, double2* sm, bool act,
+                             unsigned act_mask) {
+  constexpr int NG = 32 / G;
   const int lane = threadIdx.x & 31;
+  const int gi = lane / G, gl = lane % G;
+  float2* Bs = slice + gi * slice_f2;
+  float2* Ph = Bs + E_max;
+  float2* Gt = Ph + E_max;
+  float2* V = Gt + 16 * L_max;
+  float* Env = reinterpret_cast<float*>(V + 16 * L_max);
   const int E = M << n;
-  for (int i = lane; i < E; i += 32) Bs[i] = psi[i];
-  __syncwarp();
-  for (int k = 1; k <= L - 1; ++k) warp_apply<T2>(Bs, G + 16 * (k - 1), n, M, pairs[2 * (k - 1)], pairs[2 * (k - 1) + 1], false);
-  for (int i = lane; i < E; i += 32) Ph[i] = phil[i];
-  __syncwarp();
-  for (int k = L; k >= 1; --k) {
-    const int qa = pairs[2 * (k - 1)], qb = pairs[2 * (k - 1) + 1];
-    const T2 e = warp_env<T, T2>(Bs, Ph, n, M, qa, qb);
-    warp_update<T2>(e, G + 16 * (k - 1), sm, V ? V + 16 * (k - 1) : nullptr);
-    if (k > 1) {
-      warp_apply<T2>(Bs, G + 16 * (k - 2), n, M, pairs[2 * (k - 2)], pairs[2 * (k - 2) + 1], true);
-      warp_apply<T2>(Ph, G + 16 * (k - 1), n, M, qa, qb, true);
+  if (act) {
+    for (int i = gl; i < E; i += G) {
+      Bs[i] = psi[i];
+      Ph[i] = phil[i];
     }
   }
-  return warp_residual<T, T2>(Ph, G, psi, n, M, pairs[0], pairs[1]);
+  __syncwarp();
+  for (int k = 1; k <= L - 1; ++k) {
+    if (act) group_apply<G, float2>(Bs, Gt + 16 * (k - 1), n, M, pairs[2 * (k - 1)], pairs[2 * (k - 1) + 1], false, gl);
+    __syncwarp();
+  }
+  for (int k = L; k >= 1; --k) {
+    const int qa = pairs[2 * (k - 1)], qb = pairs[2 * (k - 1) + 1];
+    float acc[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) acc[i] = 0.f;
+    if (act) group_env_acc<G, float, float2>(Bs, Ph, n, M, qa, qb, gl, acc);
+    if constexpr (G == 32) {
+      const float v = warp_reduce_scatter32<float>(acc, lane);
+      const int l16 = lane & 15;
+      const float2 e{__shfl_sync(FULL, v, 2 * l16), __shfl_sync(FULL, v, 2 * l16 + 1)};
+      if (act) warp_update<float2>(e, Gt + 16 * (k - 1), sm, V + 16 * (k - 1));
+    } else {
+      const int base = group_reduce_scatter<G, float>(acc, gl);
+#pragma unroll
+      for (int i = 0; i < 32 / G; ++i) Env[base + i] = acc[i];
+      __syncwarp();
+      // The warp updates the unit's gates one start after another.
+      const int l16 = lane & 15;
+#pragma unroll 1
+      for (int j = 0; j < NG; ++j) {
+        if (!((act_mask >> j) & 1u)) continue;
+        float2* sj = slice + j * slice_f2;
+        const float* envj = reinterpret_cast<const float*>(sj + 2 * E_max + 32 * L_max);
+        const float2 e{envj[2 * l16], envj[2 * l16 + 1]};
+        warp_update<float2>(e, sj + 2 * E_max + 16 * (k - 1), sm, sj + 2 * E_max + 16 * L_max + 16 * (k - 1));
+      }
+    }
+    __syncwarp();
+    if (k > 1 && act) {
+      group_apply<G, float2>(Bs, Gt + 16 * (k - 2), n, M, pairs[2 * (k - 2)], pairs[2 * (k - 2) + 1], true, gl);
+      group_apply<G, float2>(Ph, Gt + 16 * (k - 1), n, M, qa, qb, true, gl);
+    }
+    __syncwarp();
+  }
+  float r = 0.f;
+  if (act) group_apply<G, float2>(Ph, Gt, n, M, pairs[0], pairs[1], true, gl);
+  __syncwarp();
+  if (act) {
+    for (int i = gl; i < E; i += G) {
+      const float2 p = Ph[i], q = psi[i];
+      const float dx = p.x - q.x, dy = p.y - q.y;
+      r = fmaf(dx, dx, fmaf(dy, dy, r));
+    }
+  }
+#pragma unroll
+  for (int o = G / 2; o >= 1; o >>= 1) r += __shfl_xor_sync(FULL, r, o);
+  __syncwarp();
+  return r * (1.f / (float)M);
+}
+
+// One FP64 sweep of one start by a whole warp (the refinement sweeps of the
+// finishing kernel), as group_sweep with G = 32, B and Phi in Bs and Ph.
+__device__ void warp_sweep64(double2* Bs, double2* Ph, double2* G, const double2* psi, const double2* phil,
+                             const int* pairs, int n, int M, int L, double2* sm) {
+  const int lane = threadIdx.x & 31;
+  const int E = M << n;
+  for (int i = lane; i < E; i += 32) {
+    Bs[i] = psi[i];
+    Ph[i] = phil[i];
+  }
+  __syncwarp();
+  for (int k = 1; k <= L - 1; ++k) {
+    group_apply<32, double2>(Bs, G + 16 * (k - 1), n, M, pairs[2 * (k - 1)], pairs[2 * (k - 1) + 1], false, lane);
+    __syncwarp();
+  }
+  for (int k = L; k >= 1; --k) {
+    const int qa = pairs[2 * (k - 1)], qb = pairs[2 * (k - 1) + 1];
+    double acc[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) acc[i] = 0.0;
+    group_env_acc<32, double, double2>(Bs, Ph, n, M, qa, qb, lane, acc);
+    const double v = warp_reduce_scatter32<double>(acc, lane);
+    const int l16 = lane & 15;
+    const double2 e{__shfl_sync(FULL, v, 2 * l16), __shfl_sync(FULL, v, 2 * l16 + 1)};
+    warp_update<double2>(e, G + 16 * (k - 1), sm, nullptr);
+    if (k > 1) {
+      group_apply<32, double2>(Bs, G + 16 * (k - 2), n, M, pairs[2 * (k - 2)], pairs[2 * (k - 2) + 1], true, lane);
+      group_apply<32, double2>(Ph, G + 16 * (k - 1), n, M, qa, qb, true, lane);
+    }
+    __syncwarp();
+  }
 }
 
 }  // namespace
@@ -217,33 +306,41 @@ __global__ void k_batch_prep(BatchArgs a) {
   if (threadIdx.x == 0) a.s_star[p] = INT_MAX;
 }
 
-// Persistent sweep kernel: warps take (problem, start) items until the queue
-// is empty.
-__global__ void k_batch_sweep(BatchArgs a) {
+// Persistent sweep kernel with G lanes per start: warps take units (a
+// problem and 32/G of its starts) until the queue is empty.  slice_f2 is the
+// per-start shared-memory slice in float2 (batch_slice_f2 of the largest
+// problem this launch takes).
+template <int G>
+__global__ void k_batch_sweep(BatchArgs a, const BatchUnit* units, int nunits, int* queue, int slice_f2,
+                              int E_max, int L_max) {
+  constexpr int NG = 32 / G;
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ double2 sm_polar[kBatchMaxWarps][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int E = a.max_elems;
-  float2* base = reinterpret_cast<float2*>(dsm) + (size_t)warp * (2 * E + 32 * a.max_L);
-  float2* Bs = base;
-  float2* Ph = base + E;
-  float2* G = base + 2 * E;
-  float2* V = G + 16 * a.max_L;  // per gate: right singular vectors of its last update
-  const int total = a.P * a.S;
+  const int gi = lane / G, gl = lane % G;
+  float2* slice = reinterpret_cast<float2*>(dsm) + (size_t)warp * NG * slice_f2;
   while (true) {
     int item = 0;
-    if (lane == 0) item = atomicAdd(a.queue, 1);
+    if (lane == 0) item = atomicAdd(queue, 1);
     item = __shfl_sync(FULL, item, 0);
-    if (item >= total) break;
-    const int p = a.order[item / a.S], s = item % a.S;
+    if (item >= nunits) break;
+    const BatchUnit u = units[item];
+    const int p = u.p;
     const BatchProblem pr = a.probs[p];
     const int* pairs = a.pairs + pr.pair_off;
+    const int s = u.s0 + gi;
+    bool act = gi < u.ns;
+    float2* mine = slice + gi * slice_f2;
+    float2* Gt = mine + 2 * E_max;
+    float2* V = Gt + 16 * L_max;
     const size_t goff = pr.gate_off + (size_t)s * pr.L * 16;
-    for (int i = lane; i < 16 * pr.L; i += 32) {
-      const double2 g = a.init_gates[goff + i];
-      G[i] = float2{(float)g.x, (float)g.y};
-      const int e = i & 15;
-      V[i] = float2{(e & 3) == (e >> 2) ? 1.f : 0.f, 0.f};
+    if (act) {
+      for (int i = gl; i < 16 * pr.L; i += G) {
+        const double2 g = a.init_gates[goff + i];
+        Gt[i] = float2{(float)g.x, (float)g.y};
+        const int e = i & 15;
+        V[i] = float2{(e & 3) == (e >> 2) ? 1.f : 0.f, 0.f};
+      }
     }
     __syncwarp();
     const float2* psi = a.psi32 + pr.state_off;
@@ -256,29 +353,39 @@ __global__ void k_batch_sweep(BatchArgs a) {
     for (int sw = 1; sw <= a.max_sweeps; ++sw) {
       // A start that has not converged by its problem's earliest converged
       // sweep can no longer be selected.
-      if (sw > *(volatile int*)(a.s_star + p)) break;
-      cost = warp_sweep<float, float2>(Bs, Ph, G, psi, phil, pairs, pr.n, pr.M, pr.L, sm_polar[warp], V);
-      sweeps = sw;
-      if ((double)cost <= a.tol) {
-        conv = sw;
-        if (lane == 0) atomicMin(a.s_star + p, sw);
-        break;
+      if (sw > *(volatile int*)(a.s_star + p)) act = false;
+      const unsigned ballot = __ballot_sync(FULL, act && gl == 0);
+      unsigned mask = 0;
+#pragma unroll
+      for (int j = 0; j < NG; ++j) mask |= ((ballot >> (j * G)) & 1u) << j;
+      if (!mask) break;
+      const float c = group_sweep<G>(slice, slice_f2, E_max, L_max, psi, phil, pairs, pr.n, pr.M, pr.L,
+                                     sm_polar[warp], act, mask);
+      if (act) {
+        cost = c;
+        sweeps = sw;
+        if ((double)cost <= a.tol) {
+          conv = sw;
+          if (gl == 0) atomicMin(a.s_star + p, sw);
+          act = false;
+        } else if (a.plateau_window > 0 && prev >= 0.f) {
+          // Plateau (App. A): no relative improvement > diff_tol_r for
+          // plateau_window sweeps in a row stops this start.
+          stall = fabsf(prev) - fabsf(cost) > dtr * fabsf(cost) ? 0 : stall + 1;
+          if (stall >= a.plateau_window && sw >= a.min_sweeps) act = false;
+        }
+        prev = cost;
       }
-      // Plateau (App. A): no relative improvement > diff_tol_r for
-      // plateau_window sweeps in a row stops this start.
-      if (a.plateau_window > 0 && prev >= 0.f) {
-        stall = fabsf(prev) - fabsf(cost) > dtr * fabsf(cost) ? 0 : stall + 1;
-        if (stall >= a.plateau_window && sw >= a.min_sweeps) break;
+    }
+    if (gi < u.ns) {
+      const size_t ri = (size_t)p * a.S + s;
+      if (gl == 0) {
+        a.conv_sweep[ri] = conv;
+        a.final_cost[ri] = (double)cost;
+        a.sweeps_run[ri] = sweeps;
       }
-      prev = cost;
+      for (int i = gl; i < 16 * pr.L; i += G) a.gates32[goff + i] = Gt[i];
     }
-    const size_t ri = (size_t)p * a.S + s;
-    if (lane == 0) {
-      a.conv_sweep[ri] = conv;
-      a.final_cost[ri] = (double)cost;
-      a.sweeps_run[ri] = sweeps;
-    }
-    for (int i = lane; i < 16 * pr.L; i += 32) a.gates32[goff + i] = G[i];
     __syncwarp();
   }
 }
@@ -332,7 +439,11 @@ __global__ void k_batch_finalize(BatchArgs a) {
   auto cost64 = [&]() {
     for (int i = lane; i < E; i += 32) Bs[i] = psi[i];
     __syncwarp();
-    for (int k = 1; k <= pr.L; ++k) warp_apply<double2>(Bs, G + 16 * (k - 1), pr.n, pr.M, pairs[2 * (k - 1)], pairs[2 * (k - 1) + 1], false);
+    for (int k = 1; k <= pr.L; ++k) {
+      group_apply<32, double2>(Bs, G + 16 * (k - 1), pr.n, pr.M, pairs[2 * (k - 1)], pairs[2 * (k - 1) + 1], false,
+                               lane);
+      __syncwarp();
+    }
     double acc = 0.0;
     for (int i = lane; i < E; i += 32) {
       const double dx = phil[i].x - Bs[i].x, dy = phil[i].y - Bs[i].y;
@@ -345,7 +456,7 @@ __global__ void k_batch_finalize(BatchArgs a) {
   double c = cost64();
   int refine = 0;
   while (c > a.tol && refine < a.refine_max && (sst != INT_MAX || a.refine_unconverged)) {
-    warp_sweep<double, double2>(Bs, Ph, G, psi, phil, pairs, pr.n, pr.M, pr.L, sm_polar);
+    warp_sweep64(Bs, Ph, G, psi, phil, pairs, pr.n, pr.M, pr.L, sm_polar);
     ++refine;
     c = cost64();
   }
@@ -362,22 +473,47 @@ void launch_batch_prep(const BatchArgs& a, cudaStream_t st) {
   k_batch_prep<<<a.P, 128, 0, st>>>(a);
 }
 
-size_t batch_sweep_smem(int warps, int max_elems, int max_L) {
-  return (size_t)warps * (2 * max_elems + 32 * max_L) * sizeof(float2);
+size_t batch_sweep_smem(int G, int warps, int max_elems, int max_L) {
+  return (size_t)warps * (32 / G) * batch_slice_f2(max_elems, max_L) * sizeof(float2);
 }
 
-int batch_sweep_blocks_per_sm(int warps, size_t smem) {
-  cudaFuncSetAttribute(k_batch_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+namespace {
+template <int G>
+int blocks_per_sm_g(int warps, size_t smem) {
+  cudaFuncSetAttribute(k_batch_sweep<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_sweep, 32 * warps, smem) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_sweep<G>, 32 * warps, smem) != cudaSuccess) {
     cudaGetLastError();
-    b = 1;
+    b = 0;
   }
-  return b < 1 ? 1 : b;
+  return b;
+}
+}  // namespace
+
+int batch_sweep_blocks_per_sm(int G, int warps, size_t smem) {
+  switch (G) {
+    case 4: return blocks_per_sm_g<4>(warps, smem);
+    case 8: return blocks_per_sm_g<8>(warps, smem);
+    case 16: return blocks_per_sm_g<16>(warps, smem);
+    case 32: return blocks_per_sm_g<32>(warps, smem);
+    default: return 0;
+  }
 }
 
-void launch_batch_sweep(const BatchArgs& a, int blocks, int warps, size_t smem, cudaStream_t st) {
-  k_batch_sweep<<<blocks, 32 * warps, smem, st>>>(a);
+void launch_batch_sweep(int G, const BatchArgs& a, const BatchUnit* units, int nunits, int* queue, int blocks,
+                        int warps, int max_elems, int max_L, cudaStream_t st) {
+  const size_t smem = batch_sweep_smem(G, warps, max_elems, max_L);
+  const int sf = batch_slice_f2(max_elems, max_L);
+  switch (G) {
+    case 4: k_batch_sweep<4><<<blocks, 32 * warps, smem, st>>>(a, units, nunits, queue, sf, max_elems, max_L); break;
+    case 8: k_batch_sweep<8><<<blocks, 32 * warps, smem, st>>>(a, units, nunits, queue, sf, max_elems, max_L); break;
+    case 16:
+      k_batch_sweep<16><<<blocks, 32 * warps, smem, st>>>(a, units, nunits, queue, sf, max_elems, max_L);
+      break;
+    default:
+      k_batch_sweep<32><<<blocks, 32 * warps, smem, st>>>(a, units, nunits, queue, sf, max_elems, max_L);
+      break;
+  }
 }
 
 void launch_batch_finalize(const BatchArgs& a, cudaStream_t st) {

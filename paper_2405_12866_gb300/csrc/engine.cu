@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <functional>
 #include <cmath>
 #include <complex>
@@ -105,6 +106,20 @@ struct qfs_ctx {
   double df_items_per_cta = 1.5;           // work items per CTA and backward step (QFS_DF_ITEMS_PER_CTA)
   double df_items_per_cta_fwd = 1.0;       // ... and forward step (QFS_DF_ITEMS_PER_CTA_FWD)
   long long df_wait_limit = 1LL << 25;     // polls before a dataflow dependency wait gives up (QFS_OPT_WAIT_LIMIT)
+  // Batched form: the tuned launch shape per problem class (n, L, M) and the
+  // captured graphs of recent batch shapes (replayed when a call repeats one).
+  std::vector<std::pair<long long, std::pair<int, int>>> batch_tuned;  // class key -> (G, warps)
+  // Every autotuner trial: n, L, M, S, G, warps, and the measured time per
+  // start-sweep in ns (qfs_batch_schedules reads them back).
+  std::vector<std::array<int, 6>> batch_trial_shape;
+  std::vector<double> batch_trial_ns;
+  struct BatchGraph {
+    uint64_t key = 0;
+    cudaGraphExec_t exec = nullptr;
+    long long launches[QFS_PROF_KINDS] = {};
+  };
+  std::vector<BatchGraph> batch_graphs;
+  int batch_force_G = 0;                   // > 0: every class runs with G lanes per start (tests)
   size_t ws_cap = 0;                       // largest device workspace a call may use, 0 = no cap
   int coop = 0;             // device supports cooperative launches
   int device = 0;
@@ -1543,6 +1558,8 @@ void qfs_destroy(qfs_ctx* ctx) {
     if (ctx->gevent[g]) cudaEventDestroy(ctx->gevent[g]);
   }
   if (ctx->fork_event) cudaEventDestroy(ctx->fork_event);
+  for (auto& g : ctx->batch_graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
@@ -1919,67 +1936,164 @@ extern "C" int qfs_sweep_once_noalloc(void* cuda_stream, const qfs_circuit* circ
 }
 
 // ---------------------------------------------------------------------------
-// Batched instantiation of many small problems (one persistent launch).
+// Batched instantiation of many small problems (one persistent launch per
+// launch shape, all in one captured graph).
 
 namespace {
 
-struct BatchPlan {
-  int warps = 4;  // warps per block of the persistent sweep kernel
+// Where the arrays of a batched call live, and how drawn inputs are seeded.
+struct BatchInputs {
+  const double* targets = nullptr;
+  bool targets_dev = false;
+  const double* samples = nullptr;  // nullable: drawn
+  bool samples_dev = false;
+  const double* init_gates = nullptr;  // nullable: drawn
+  bool gates_dev = false;
+  double* gates_out = nullptr;  // nullable with sweep_once
+  bool out_dev = false;
+  const int32_t* draw_index = nullptr;  // nullable: problem i draws from seed + draw_index[i] (else seed + i)
+  // One complex64 sweep of every start, no selection or FP64 finish: the
+  // swept gates of every start (host, complex128) and their residual costs.
+  bool sweep_once = false;
+  double* start_gates_out = nullptr;
+  double* start_costs_out = nullptr;
 };
 
-// Calibrates the warps per block of the persistent kernel on this batch:
-// each candidate runs a few sweeps of every problem, the fastest wins.
-// Cached per (largest N*M, largest L) of the batch.
-int autotune_batch(qfs_ctx* ctx, BatchArgs a, int max_sweeps_run, int* warps_out) {
-  static std::mutex mu;
-  static std::vector<std::pair<long long, int>> cache;
-  const long long key = (long long)a.max_elems * 1000 + a.max_L;
-  {
-    std::lock_guard<std::mutex> lock(mu);
-    for (auto& kv : cache)
-      if (kv.first == key) {
-        *warps_out = kv.second;
-        return QFS_OK;
-      }
-  }
-  cudaStream_t st = ctx->stream;
-  a.max_sweeps = std::min(max_sweeps_run, 6);
-  float best_ms = 1e30f;
-  int best = 4;
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
-  for (int w : {2, 4, 8}) {
-    const size_t smem = batch_sweep_smem(w, a.max_elems, a.max_L);
-    if (smem > 200 * 1024) continue;
-    const int bps = batch_sweep_blocks_per_sm(w, smem);
-    launch_batch_prep(a, st);
-    CK(cudaMemsetAsync(a.queue, 0, sizeof(int), st));
-    CK(cudaEventRecord(e0, st));
-    launch_batch_sweep(a, ctx->num_sms * bps, w, smem, st);
-    CK(cudaEventRecord(e1, st));
-    CK(cudaEventSynchronize(e1));
-    CK(cudaGetLastError());
-    float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, e0, e1));
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = w;
+long long batch_class_key(int n, int L, int M, int S) { return (((long long)n * 64 + L) * 4096 + M) * 128 + S; }
+
+// Schedules worth trying for a class: G lanes per start no larger than the
+// state's 4-row groups (a lane with no group would idle in every state
+// step), at most S starts per warp (a unit holds starts of one problem), with
+// 2, 4 or 8 warps per block when the shared memory allows.
+std::vector<std::pair<int, int>> batch_candidates(int n, int M, int L, int S) {
+  std::vector<std::pair<int, int>> c;
+  const int groups = (1 << (n - 2)) * M;
+  for (int G : {4, 8, 16, 32}) {
+    if (32 / G > S) continue;
+    if (G > groups * 2 && G != 32) continue;
+    if (G < 32 && groups / G > 8) continue;  // many groups per lane: the warp-per-start form is as lane-efficient
+    for (int w : {2, 4, 8}) {
+      const size_t smem = batch_sweep_smem(G, w, M << n, L);
+      if (smem > 200 * 1024) continue;
+      if (batch_sweep_blocks_per_sm(G, w, smem) < 1) continue;
+      c.push_back({G, w});
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  {
-    std::lock_guard<std::mutex> lock(mu);
-    cache.push_back({key, best});
+  return c;
+}
+
+struct BatchClass {
+  int n, L, M;
+  std::vector<int> problems;  // indices into the batch
+  int G = 32, warps = 4;
+};
+
+// Units of the given problems (largest work first within the list, ties by
+// index): a problem's starts in runs of 32 / G.
+void batch_units(const std::vector<BatchProblem>& probs, std::vector<int> idx, int S, int G,
+                 std::vector<BatchUnit>& out) {
+  std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+    return ((long long)probs[x].L * probs[x].M << probs[x].n) > ((long long)probs[y].L * probs[y].M << probs[y].n);
+  });
+  const int per = 32 / G;
+  for (int i : idx)
+    for (int s0 = 0; s0 < S; s0 += per) out.push_back(BatchUnit{i, s0, std::min(per, S - s0)});
+}
+
+// The autotuner: for each class not yet tuned, time every candidate schedule
+// on that class's problems for a few sweeps with the tolerance out of reach
+// (every start runs them all) and keep the fastest per start-sweep.  The
+// choice is cached per (n, L, M) on the context.  `a` points at the batch's
+// prepared buffers; units and the queue go to the scratch at `scratch`.
+int autotune_batch(qfs_ctx* ctx, BatchArgs a, const std::vector<BatchProblem>& probs,
+                   std::vector<BatchClass>& classes, BatchUnit* units_dev, int* queue_dev) {
+  cudaStream_t st = ctx->stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  for (BatchClass& c : classes) {
+    const long long key = batch_class_key(c.n, c.L, c.M, a.S);
+    bool found = false;
+    for (auto& kv : ctx->batch_tuned)
+      if (kv.first == key) {
+        c.G = kv.second.first;
+        c.warps = kv.second.second;
+        found = true;
+      }
+    if (found) continue;
+    const auto cand = batch_candidates(c.n, c.M, c.L, a.S);
+    if (cand.empty()) return fail(QFS_EUNSUPPORTED, "no batched launch shape fits n = %d, L = %d, M = %d", c.n, c.L, c.M);
+    if (cand.size() == 1) {
+      c.G = cand[0].first;
+      c.warps = cand[0].second;
+      ctx->batch_tuned.push_back({key, cand[0]});
+      continue;
+    }
+    if (!e0) {
+      CK(cudaEventCreate(&e0));
+      CK(cudaEventCreate(&e1));
+    }
+    // A sample of the class: up to its first 512 problems, 4 sweeps of
+    // every start, timed twice after a warm-up run; the time per start-sweep
+    // decides.  The warp-per-start shape is kept unless another is at least
+    // 5% faster.
+    std::vector<int> sample(c.problems.begin(), c.problems.begin() + std::min<size_t>(c.problems.size(), 512));
+    BatchArgs t = a;
+    t.max_sweeps = 4;
+    t.tol = -1.0;
+    t.plateau_window = 0;
+    const double start_sweeps = (double)sample.size() * a.S * t.max_sweeps;
+    float best = 1e30f;
+    float best32 = 1e30f;
+    int w32 = 0;
+    for (auto [G, w] : cand) {
+      std::vector<BatchUnit> u;
+      batch_units(probs, sample, a.S, G, u);
+      CK(cudaMemcpyAsync(units_dev, u.data(), sizeof(BatchUnit) * u.size(), cudaMemcpyHostToDevice, st));
+      const size_t smem = batch_sweep_smem(G, w, c.M << c.n, c.L);
+      const int bps = batch_sweep_blocks_per_sm(G, w, smem);
+      const int blocks = std::max(1, std::min(ctx->num_sms * bps, (int)((u.size() + w - 1) / w)));
+      float ms = 1e30f;
+      for (int rep = 0; rep < 3; ++rep) {  // the first run warms up
+        CK(cudaMemsetAsync(queue_dev, 0, sizeof(int), st));
+        CK(cudaEventRecord(e0, st));
+        launch_batch_sweep(G, t, units_dev, (int)u.size(), queue_dev, blocks, w, c.M << c.n, c.L, st);
+        CK(cudaEventRecord(e1, st));
+        CK(cudaEventSynchronize(e1));
+        CK(cudaGetLastError());
+        float r = 0.f;
+        CK(cudaEventElapsedTime(&r, e0, e1));
+        if (rep) ms = std::min(ms, r);
+      }
+      ctx->batch_trial_shape.push_back({c.n, c.L, c.M, a.S, G, w});
+      ctx->batch_trial_ns.push_back(1e6 * ms / start_sweeps);
+      if (G == 32 && ms < best32) {
+        best32 = ms;
+        w32 = w;
+      }
+      if (ms < best) {
+        best = ms;
+        c.G = G;
+        c.warps = w;
+      }
+    }
+    if (w32 && c.G != 32 && best > 0.95f * best32) {
+      c.G = 32;
+      c.warps = w32;
+    }
+    ctx->batch_tuned.push_back({key, {c.G, c.warps}});
   }
-  *warps_out = best;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
   return QFS_OK;
 }
 
-}  // namespace
-
-namespace {
+uint64_t fnv1a(uint64_t h, const void* data, size_t n) {
+  const unsigned char* p = static_cast<const unsigned char*>(data);
+  for (size_t i = 0; i < n; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ULL;
+  }
+  return h;
+}
 
 // fn(0 .. n-1) over the host cores (at most 16 threads); the draws it runs
 // are pure functions of their index writing disjoint ranges.
@@ -1993,22 +2107,20 @@ void host_parallel_for(int n, F fn) {
   }
   std::vector<std::thread> th;
   for (int t = 0; t < T; ++t)
-    th.emplace_back([&, t]() {
-      for (int i = (int)((long long)n * t / T); i < (int)((long long)n * (t + 1) / T); ++i) fn(i);
+    th.emplace_back([&, t] {
+      for (int i = t; i < n; i += T) fn(i);
     });
   for (auto& x : th) x.join();
 }
 
 int batch_common(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls, const int32_t* pairs,
-                 const double* targets, const double* samples, const double* init_gates,
-                 const qfs_params* p, double* gates_out, qfs_result* results, bool dev) {
-  if (dev && (!samples || !init_gates))
-    return fail(QFS_EINVAL, "the device-pointer batch needs samples and init_gates");
-  const cudaMemcpyKind h2d = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  const cudaMemcpyKind d2h = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+                 const BatchInputs& in, const qfs_params* p, qfs_result* results) {
+  const bool any_dev = in.targets_dev || in.samples_dev || in.gates_dev || in.out_dev;
   if (P < 1) return fail(QFS_EINVAL, "P = %d: need >= 1", P);
-  if (!ns || !Ls || !pairs || !targets || !p || !gates_out || !results)
+  if (!ns || !Ls || !pairs || !in.targets || !p || (!in.sweep_once && (!in.gates_out || !results)))
     return fail(QFS_EINVAL, "ns, Ls, pairs, targets, params, gates_out and results must be given");
+  if (in.sweep_once && (!in.samples || !in.init_gates || !in.start_gates_out))
+    return fail(QFS_EINVAL, "one batched sweep needs samples, init_gates and gates_out");
   const int S = p->multistarts;
   if (S < 1 || S > 64) return fail(QFS_EUNSUPPORTED, "multistarts = %d: the batched form takes 1..64", S);
   if (p->max_sweeps < 1) return fail(QFS_EINVAL, "max_sweeps = %d: need >= 1", p->max_sweeps);
@@ -2040,12 +2152,23 @@ int batch_common(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls, 
   }
   TRY(ctx_check(ctx));
   TRY(set_device(ctx));
-  // Largest work first (L * N * M per sweep), ties by index.
-  std::vector<int> order(P);
-  for (int i = 0; i < P; ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-    return (long long)probs[x].L * probs[x].M << probs[x].n > (long long)probs[y].L * probs[y].M << probs[y].n;
-  });
+  // Problem classes (n, L, M) in order of first appearance.
+  std::vector<BatchClass> classes;
+  {
+    std::vector<std::pair<long long, int>> seen;
+    for (int i = 0; i < P; ++i) {
+      const long long key = batch_class_key(probs[i].n, probs[i].L, probs[i].M, S);
+      int ci = -1;
+      for (auto& kv : seen)
+        if (kv.first == key) ci = kv.second;
+      if (ci < 0) {
+        ci = (int)classes.size();
+        seen.push_back({key, ci});
+        classes.push_back(BatchClass{probs[i].n, probs[i].L, probs[i].M, {}});
+      }
+      classes[ci].problems.push_back(i);
+    }
+  }
   // Workspace.
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -2053,13 +2176,14 @@ int batch_common(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls, 
     off += align_up(bytes);
     return o;
   };
-  const size_t o_probs = take(sizeof(BatchProblem) * P), o_order = take(sizeof(int) * P),
+  const long long max_units = (long long)P * S;
+  const size_t o_probs = take(sizeof(BatchProblem) * P), o_units = take(sizeof(BatchUnit) * max_units),
                o_pairs = take(sizeof(int) * pair_off), o_tgt = take(sizeof(double2) * target_off),
                o_psi64 = take(sizeof(double2) * state_off), o_phil64 = take(sizeof(double2) * state_off),
                o_psi32 = take(sizeof(float2) * state_off), o_phil32 = take(sizeof(float2) * state_off),
                o_g0 = take(sizeof(double2) * gate_off), o_g32 = take(sizeof(float2) * gate_off),
                o_conv = take(sizeof(int) * P * S), o_cost = take(sizeof(double) * P * S),
-               o_swr = take(sizeof(int) * P * S), o_sstar = take(sizeof(int) * P), o_q = take(sizeof(int) * 4),
+               o_swr = take(sizeof(int) * P * S), o_sstar = take(sizeof(int) * P), o_q = take(sizeof(int) * 64),
                o_gout = take(sizeof(double2) * gout_off), o_rc = take(sizeof(double) * P),
                o_rs = take(sizeof(int) * P), o_rb = take(sizeof(int) * P), o_rr = take(sizeof(int) * P);
   TRY(ensure_ws(ctx, off));
@@ -2082,10 +2206,10 @@ int batch_common(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls, 
   a.sweeps_run = reinterpret_cast<int*>(w + o_swr);
   a.s_star = reinterpret_cast<int*>(w + o_sstar);
   a.queue = reinterpret_cast<int*>(w + o_q);
-  a.order = reinterpret_cast<int*>(w + o_order);
-  a.max_sweeps = p->max_sweeps;
-  a.tol = p->dist_tol;
-  a.plateau_window = p->plateau_window;
+  a.order = nullptr;
+  a.max_sweeps = in.sweep_once ? 1 : p->max_sweeps;
+  a.tol = in.sweep_once ? -1.0 : p->dist_tol;
+  a.plateau_window = in.sweep_once ? 0 : p->plateau_window;
   a.diff_tol_r = p->diff_tol_r;
   a.min_sweeps = p->min_sweeps;
   a.max_elems = max_elems;
@@ -2097,73 +2221,226 @@ int batch_common(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls, 
   a.res_refine = reinterpret_cast<int*>(w + o_rr);
   a.refine_max = std::max(0, p->refine_sweeps_max);
   a.refine_unconverged = 0;
+  BatchUnit* units_dev = reinterpret_cast<BatchUnit*>(w + o_units);
+  const cudaMemcpyKind t_kind = in.targets_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const cudaMemcpyKind s_kind = in.samples_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const cudaMemcpyKind g_kind = in.gates_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   CK(cudaMemcpyAsync(w + o_probs, probs.data(), sizeof(BatchProblem) * P, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(w + o_order, order.data(), sizeof(int) * P, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(w + o_pairs, pairs, sizeof(int) * pair_off, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(w + o_tgt, targets, sizeof(double2) * target_off, h2d, st));
+  CK(cudaMemcpyAsync(w + o_tgt, in.targets, sizeof(double2) * target_off, t_kind, st));
   // Training states and initial gates: given, or drawn per problem from
-  // seed + problem index (the library's Philox draws).
+  // seed + problem index (or seed + draw_index[i]; the library's Philox draws).
+  auto draw_seed = [&](int i) { return p->seed + (uint64_t)(in.draw_index ? in.draw_index[i] : i); };
   std::vector<std::complex<double>> hs, hg;
-  if (samples) {
-    CK(cudaMemcpyAsync(w + o_psi64, samples, sizeof(double2) * state_off, h2d, st));
+  if (in.samples) {
+    CK(cudaMemcpyAsync(w + o_psi64, in.samples, sizeof(double2) * state_off, s_kind, st));
   } else {
     hs.resize(state_off);
     host_parallel_for(P, [&](int i) {
-      draw_states(p->training_distribution, p->seed + (uint64_t)i, 1u, probs[i].n, probs[i].M,
-                  hs.data() + probs[i].state_off);
+      draw_states(p->training_distribution, draw_seed(i), 1u, probs[i].n, probs[i].M, hs.data() + probs[i].state_off);
     });
     CK(cudaMemcpyAsync(w + o_psi64, hs.data(), sizeof(double2) * state_off, cudaMemcpyHostToDevice, st));
   }
-  if (init_gates) {
-    CK(cudaMemcpyAsync(w + o_g0, init_gates, sizeof(double2) * gate_off, h2d, st));
+  if (in.init_gates) {
+    CK(cudaMemcpyAsync(w + o_g0, in.init_gates, sizeof(double2) * gate_off, g_kind, st));
   } else {
     hg.resize(gate_off);
-    host_parallel_for(P, [&](int i) {
-      generate_gates(p->seed + (uint64_t)i, S * probs[i].L, hg.data() + probs[i].gate_off);
-    });
+    host_parallel_for(P, [&](int i) { generate_gates(draw_seed(i), S * probs[i].L, hg.data() + probs[i].gate_off); });
     CK(cudaMemcpyAsync(w + o_g0, hg.data(), sizeof(double2) * gate_off, cudaMemcpyHostToDevice, st));
   }
-  int warps = 4;
-  TRY(autotune_batch(ctx, a, p->max_sweeps, &warps));
-  const size_t smem = batch_sweep_smem(warps, max_elems, max_L);
-  const int bps = batch_sweep_blocks_per_sm(warps, smem);
-  // Set-up, the persistent sweep and the finishing kernel as one graph.
-  if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed));
-  ctx->prof.capturing = true;
-  CK(cudaMemsetAsync(a.queue, 0, sizeof(int), ctx->cap_stream));
-  {
-    ProfScope ps(ctx, QFS_PROF_OTHER, 0.0, ctx->cap_stream);
-    launch_batch_prep(a, ctx->cap_stream);
+  (void)any_dev;
+  // Schedules: forced (tests) or tuned per class.
+  if (ctx->batch_force_G > 0) {
+    for (BatchClass& c : classes) {
+      c.G = ctx->batch_force_G;
+      c.warps = 0;
+      for (int wv : {4, 2, 8}) {
+        const size_t smem = batch_sweep_smem(c.G, wv, c.M << c.n, c.L);
+        if (smem <= 200 * 1024 && batch_sweep_blocks_per_sm(c.G, wv, smem) >= 1) {
+          c.warps = wv;
+          break;
+        }
+      }
+      if (!c.warps) return fail(QFS_EUNSUPPORTED, "G = %d does not fit n = %d, L = %d", c.G, c.n, c.L);
+    }
+  } else {
+    bool untuned = false;
+    for (const BatchClass& c : classes) {
+      bool f = false;
+      for (auto& kv : ctx->batch_tuned) f |= kv.first == batch_class_key(c.n, c.L, c.M, S);
+      untuned |= !f;
+    }
+    if (untuned) launch_batch_prep(a, st);
+    TRY(autotune_batch(ctx, a, probs, classes, units_dev, a.queue));
   }
+  // Launch groups: classes with the same (G, warps) share one persistent
+  // launch over their units, largest problems first.
+  struct Launch {
+    int G, warps, unit0, nunits, max_elems, max_L;
+  };
+  std::vector<Launch> launches;
+  std::vector<BatchUnit> units;
   {
-    ProfScope ps(ctx, QFS_PROF_BATCH, 0.0, ctx->cap_stream);
-    launch_batch_sweep(a, ctx->num_sms * bps, warps, smem, ctx->cap_stream);
+    std::vector<std::pair<int, int>> shapes;
+    for (const BatchClass& c : classes) {
+      bool have = false;
+      for (auto& sh : shapes) have |= sh.first == c.G && sh.second == c.warps;
+      if (!have) shapes.push_back({c.G, c.warps});
+    }
+    for (auto [G, wv] : shapes) {
+      std::vector<int> idx;
+      int me = 0, ml = 0;
+      for (const BatchClass& c : classes)
+        if (c.G == G && c.warps == wv) {
+          idx.insert(idx.end(), c.problems.begin(), c.problems.end());
+          me = std::max(me, c.M << c.n);
+          ml = std::max(ml, c.L);
+        }
+      const int u0 = (int)units.size();
+      batch_units(probs, idx, S, G, units);
+      launches.push_back(Launch{G, wv, u0, (int)units.size() - u0, me, ml});
+    }
   }
+  // Launches start in order of their largest problem, largest first (the
+  // persistent launches overlap; the largest units should not come last).
   {
-    ProfScope ps(ctx, QFS_PROF_CHECK, 0.0, ctx->cap_stream);
-    launch_batch_finalize(a, ctx->cap_stream);
+    std::vector<int> ord(launches.size());
+    for (size_t i = 0; i < ord.size(); ++i) ord[i] = (int)i;
+    auto work = [&](const Launch& L) {
+      const BatchProblem& b = probs[units[L.unit0].p];  // its first unit is its largest
+      return (long long)b.L * b.M << b.n;
+    };
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return work(launches[x]) > work(launches[y]); });
+    std::vector<Launch> sorted;
+    for (int i : ord) sorted.push_back(launches[i]);
+    launches.swap(sorted);
   }
-  ctx->prof.capturing = false;
-  CK(cudaStreamEndCapture(ctx->cap_stream, &graph));
-  cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
-  if (e == cudaSuccess) e = cudaGraphLaunch(exec, st);
-  if (exec) cudaGraphExecDestroy(exec);
-  cudaGraphDestroy(graph);
-  CK(e);
+  if ((int)launches.size() > 60) return fail(QFS_EUNSUPPORTED, "too many launch shapes (%d)", (int)launches.size());
+  CK(cudaMemcpyAsync(units_dev, units.data(), sizeof(BatchUnit) * units.size(), cudaMemcpyHostToDevice, st));
+  // The graph: queue reset, set-up, one persistent launch per shape (on
+  // parallel branches), the finishing kernel.  Replayed while the batch's
+  // shape, parameters and workspace stay the same.
+  uint64_t key = 1469598103934665603ULL;
+  {
+    const int sc[] = {P, S, a.max_sweeps, a.plateau_window, a.min_sweeps, a.refine_max, (int)in.sweep_once,
+                      (int)launches.size()};
+    key = fnv1a(key, sc, sizeof(sc));
+    const double sd[] = {a.tol, a.diff_tol_r};
+    key = fnv1a(key, sd, sizeof(sd));
+    key = fnv1a(key, &w, sizeof(w));
+    key = fnv1a(key, ns, sizeof(int32_t) * P);
+    key = fnv1a(key, Ls, sizeof(int32_t) * P);
+    key = fnv1a(key, launches.data(), sizeof(Launch) * launches.size());
+    const int mm[] = {p->M, max_elems, max_L};
+    key = fnv1a(key, mm, sizeof(mm));
+  }
+  // With per-launch timing on, the graph carries this call's event records:
+  // it is captured, replayed once, harvested and dropped.
+  const bool cache = !ctx->prof.on;
+  qfs_ctx::BatchGraph* bg = nullptr;
+  qfs_ctx::BatchGraph once;
+  if (cache)
+    for (auto& g : ctx->batch_graphs)
+      if (g.key == key && g.exec) bg = &g;
+  if (!bg) {
+    if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    TRY(ensure_group_streams(ctx, std::min<int>(kMaxGroups, (int)launches.size())));
+    long long before[QFS_PROF_KINDS];
+    for (int i = 0; i < QFS_PROF_KINDS; ++i) before[i] = ctx->prof.launches[i];
+    cudaStream_t cs = ctx->cap_stream;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+    ctx->prof.capturing = true;
+    cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(int) * 64, cs);
+    {
+      ProfScope ps(ctx, QFS_PROF_OTHER, 0.0, cs);
+      launch_batch_prep(a, cs);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->fork_event, cs);
+    for (size_t li = 0; li < launches.size() && e == cudaSuccess; ++li) {
+      const Launch& L = launches[li];
+      const size_t smem = batch_sweep_smem(L.G, L.warps, L.max_elems, L.max_L);
+      const int bps = std::max(1, batch_sweep_blocks_per_sm(L.G, L.warps, smem));
+      const int blocks = std::max(1, std::min(ctx->num_sms * bps, (L.nunits + L.warps - 1) / L.warps));
+      const int gs = (int)(li % kMaxGroups);
+      cudaStream_t ls = li == 0 ? cs : ctx->gstream[gs];
+      if (li > 0) e = cudaStreamWaitEvent(ls, ctx->fork_event, 0);
+      if (e != cudaSuccess) break;
+      {
+        ProfScope ps(ctx, QFS_PROF_BATCH, 0.0, ls);
+        launch_batch_sweep(L.G, a, units_dev + L.unit0, L.nunits, a.queue + li, blocks, L.warps, L.max_elems,
+                           L.max_L, ls);
+      }
+      if (li > 0) {
+        e = cudaEventRecord(ctx->gevent[gs], ls);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->gevent[gs], 0);
+      }
+    }
+    if (!in.sweep_once) {
+      ProfScope ps(ctx, QFS_PROF_CHECK, 0.0, cs);
+      launch_batch_finalize(a, cs);
+    }
+    ctx->prof.capturing = false;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    if (e == cudaSuccess) e = e2;
+    qfs_ctx::BatchGraph ng;
+    ng.key = key;
+    for (int i = 0; i < QFS_PROF_KINDS; ++i) {
+      ng.launches[i] = ctx->prof.launches[i] - before[i];
+      ctx->prof.launches[i] = before[i];
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ng.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      if (ng.exec) cudaGraphExecDestroy(ng.exec);
+      prof_release_graph(ctx);
+      CK(e);
+    }
+    if (cache) {
+      if (ctx->batch_graphs.size() >= 4) {
+        cudaGraphExecDestroy(ctx->batch_graphs.front().exec);
+        ctx->batch_graphs.erase(ctx->batch_graphs.begin());
+      }
+      ctx->batch_graphs.push_back(ng);
+      bg = &ctx->batch_graphs.back();
+    } else {
+      once = ng;
+      bg = &once;
+    }
+  }
+  const cudaError_t el = cudaGraphLaunch(bg->exec, st);
+  for (int i = 0; i < QFS_PROF_KINDS; ++i) ctx->prof.launches[i] += bg->launches[i];
+  if (!cache) {
+    const cudaError_t es = cudaStreamSynchronize(st);
+    if (el == cudaSuccess && es == cudaSuccess) prof_harvest_graph(ctx);
+    prof_release_graph(ctx);
+    cudaGraphExecDestroy(once.exec);
+    CK(el);
+    CK(es);
+  }
+  CK(el);
+  if (in.sweep_once) {
+    std::vector<float2> g32(gate_off);
+    std::vector<double> fc((size_t)P * S);
+    CK(cudaMemcpyAsync(g32.data(), a.gates32, sizeof(float2) * gate_off, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(fc.data(), a.final_cost, sizeof(double) * P * S, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (long long i = 0; i < gate_off; ++i) {
+      in.start_gates_out[2 * i] = g32[i].x;
+      in.start_gates_out[2 * i + 1] = g32[i].y;
+    }
+    if (in.start_costs_out) std::copy(fc.begin(), fc.end(), in.start_costs_out);
+    return QFS_OK;
+  }
   std::vector<double> rc(P);
   std::vector<int> rs(P), rb(P), rr(P);
-  CK(cudaMemcpyAsync(gates_out, a.gates_out, sizeof(double2) * gout_off, d2h, st));
+  CK(cudaMemcpyAsync(in.gates_out, a.gates_out, sizeof(double2) * gout_off,
+                     in.out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(rc.data(), a.res_cost, sizeof(double) * P, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(rs.data(), a.res_sweeps, sizeof(int) * P, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(rb.data(), a.res_best, sizeof(int) * P, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(rr.data(), a.res_refine, sizeof(int) * P, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  prof_harvest(ctx);
-  if (ctx->prof.on) prof_harvest_graph(ctx);
-  prof_release_graph(ctx);
   for (int i = 0; i < P; ++i) {
     results[i].cost = rc[i];
     results[i].sweeps = rs[i];
@@ -2182,7 +2459,12 @@ extern "C" int qfs_instantiate_batch(qfs_ctx* ctx, int32_t P, const int32_t* ns,
                                      const double* samples, const double* init_gates,
                                      const qfs_params* p, double* gates_out, qfs_result* results) {
   g_err.clear();
-  return batch_common(ctx, P, ns, Ls, pairs, targets, samples, init_gates, p, gates_out, results, false);
+  BatchInputs in;
+  in.targets = targets;
+  in.samples = samples;
+  in.init_gates = init_gates;
+  in.gates_out = gates_out;
+  return batch_common(ctx, P, ns, Ls, pairs, in, p, results);
 }
 
 extern "C" int qfs_instantiate_batch_dev(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls,
@@ -2190,8 +2472,65 @@ extern "C" int qfs_instantiate_batch_dev(qfs_ctx* ctx, int32_t P, const int32_t*
                                          const double* samples_dev, const double* init_gates_dev,
                                          const qfs_params* p, double* gates_out_dev, qfs_result* results) {
   g_err.clear();
-  return batch_common(ctx, P, ns, Ls, pairs, targets_dev, samples_dev, init_gates_dev, p, gates_out_dev,
-                      results, true);
+  if (!samples_dev || !init_gates_dev) return fail(QFS_EINVAL, "the device-pointer batch needs samples and init_gates");
+  BatchInputs in;
+  in.targets = targets_dev;
+  in.targets_dev = true;
+  in.samples = samples_dev;
+  in.samples_dev = true;
+  in.init_gates = init_gates_dev;
+  in.gates_dev = true;
+  in.gates_out = gates_out_dev;
+  in.out_dev = true;
+  return batch_common(ctx, P, ns, Ls, pairs, in, p, results);
+}
+
+extern "C" int qfs_batch_schedules(qfs_ctx* ctx, int32_t cap, int32_t* tuned, int32_t* n_tuned, int32_t* trials,
+                                   double* trial_ns, int32_t* n_trials) {
+  g_err.clear();
+  TRY(ctx_check(ctx));
+  if (n_tuned) *n_tuned = (int32_t)ctx->batch_tuned.size();
+  if (n_trials) *n_trials = (int32_t)ctx->batch_trial_ns.size();
+  for (int i = 0; tuned && i < cap && i < (int)ctx->batch_tuned.size(); ++i) {
+    const long long k = ctx->batch_tuned[i].first;
+    const int S = (int)(k % 128), M = (int)((k / 128) % 4096), L = (int)((k / 128 / 4096) % 64),
+              n = (int)(k / 128 / 4096 / 64);
+    const int v[6] = {n, L, M, S, ctx->batch_tuned[i].second.first, ctx->batch_tuned[i].second.second};
+    std::copy(v, v + 6, tuned + 6 * i);
+  }
+  for (int i = 0; trials && i < cap && i < (int)ctx->batch_trial_ns.size(); ++i) {
+    std::copy(ctx->batch_trial_shape[i].begin(), ctx->batch_trial_shape[i].end(), trials + 6 * i);
+    if (trial_ns) trial_ns[i] = ctx->batch_trial_ns[i];
+  }
+  return QFS_OK;
+}
+
+extern "C" int qfs_batch_sweep_once(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls,
+                                    const int32_t* pairs, const double* targets, const double* samples,
+                                    int32_t M, int32_t S, const double* gates_in, int32_t lanes_per_start,
+                                    double* gates_out, double* costs_out) {
+  g_err.clear();
+  TRY(ctx_check(ctx));
+  if (lanes_per_start != 0 && lanes_per_start != 4 && lanes_per_start != 8 && lanes_per_start != 16 &&
+      lanes_per_start != 32)
+    return fail(QFS_EINVAL, "lanes_per_start = %d: need 0, 4, 8, 16 or 32", lanes_per_start);
+  qfs_params prm;
+  qfs_default_params(&prm);
+  prm.M = M;
+  prm.multistarts = S;
+  prm.max_sweeps = 1;
+  BatchInputs in;
+  in.targets = targets;
+  in.samples = samples;
+  in.init_gates = gates_in;
+  in.sweep_once = true;
+  in.start_gates_out = gates_out;
+  in.start_costs_out = costs_out;
+  const int old = ctx->batch_force_G;
+  ctx->batch_force_G = lanes_per_start;
+  const int rc = batch_common(ctx, P, ns, Ls, pairs, in, &prm, nullptr);
+  ctx->batch_force_G = old;
+  return rc;
 }
 
 // ---------------------------------------------------------------------------
@@ -2275,6 +2614,8 @@ struct qfs_ws {
   double2* tgt = nullptr;        // B_cap x 256 complex (targets of a batch)
   double2* envs = nullptr;       // B_cap x 6 x 16 (projection scratch)
   int* err = nullptr;
+  double2* pred = nullptr;       // predicted gates of a policy call (grown on demand)
+  size_t pred_cap = 0;           // in problems
 };
 
 namespace {
@@ -2459,6 +2800,7 @@ extern "C" void qfs_ws_destroy(qfs_ws* m) {
   cudaSetDevice(m->ctx->device);
   cudaStreamSynchronize(m->ctx->stream);
   cudaFree(m->mem);
+  if (m->pred) cudaFree(m->pred);
   delete m;
 }
 
@@ -2638,4 +2980,104 @@ extern "C" int qfs_ws_predict(qfs_ws* m, int32_t count, const double* targets, d
   }
   CK(cudaStreamSynchronize(st));
   return check_err_word(m);
+}
+
+// ---------------------------------------------------------------------------
+// Learned warm start as a policy: the network's prediction is the only start
+// of a short first batched run; the targets it leaves unconverged fall back
+// to random multistarts.  The paper has no learned part; the sweep judges
+// every proposal, so a bad prediction costs sweeps, never correctness.
+
+extern "C" int qfs_ws_instantiate(qfs_ws* m, int32_t P, const double* targets, const double* first_gates,
+                                  const qfs_params* p, int32_t first_sweeps, double* gates_out,
+                                  qfs_result* results, int64_t* stats) {
+  g_err.clear();
+  if (!m || !targets || !p || !gates_out || !results)
+    return fail(QFS_EINVAL, "model, targets, params, gates_out and results must be given");
+  if (P < 1) return fail(QFS_EINVAL, "P = %d: need >= 1", P);
+  if (first_sweeps < 1) return fail(QFS_EINVAL, "first_sweeps = %d: need >= 1", first_sweeps);
+  TRY(set_device(m->ctx));
+  qfs_ctx* ctx = m->ctx;
+  cudaStream_t st = ctx->stream;
+  constexpr int kL = 6, kN = 4;
+  const int32_t pairs1[2 * kL] = {0, 1, 2, 3, 1, 2, 0, 1, 2, 3, 1, 2};
+  std::vector<int32_t> ns(P, kN), Ls(P, kL), pairs((size_t)P * 2 * kL);
+  for (int i = 0; i < P; ++i) std::copy(pairs1, pairs1 + 2 * kL, pairs.begin() + (size_t)i * 2 * kL);
+  // First start: the prediction (on the device) or the given gates.
+  BatchInputs in1;
+  in1.targets = targets;
+  in1.gates_out = gates_out;
+  if (first_gates) {
+    in1.init_gates = first_gates;
+  } else {
+    if (m->pred_cap < (size_t)P) {
+      if (m->pred) CK(cudaFree(m->pred));
+      m->pred = nullptr;
+      m->pred_cap = 0;
+      if (cudaMalloc(&m->pred, sizeof(double2) * 96 * (size_t)P) != cudaSuccess) {
+        cudaGetLastError();
+        m->pred = nullptr;
+        return fail(QFS_ENOMEM, "cannot allocate the predictions of %d targets", P);
+      }
+      m->pred_cap = (size_t)P;
+    }
+    for (int s0 = 0; s0 < P; s0 += m->B_cap) {
+      const int bv = std::min(m->B_cap, P - s0);
+      const int B = (bv + 127) / 128 * 128;
+      TRY(ws_load_features(m, targets + (size_t)s0 * 512, bv, B));
+      ws_forward(m, B);
+      // Output rows -> 6 gates each, projected onto U(4) by their polar
+      // factors (the update returns polar(E^dagger), so pass G^dagger).
+      double2* out = m->pred + (size_t)s0 * 96;
+      launch_ws_gates_adjoint(m->Z32[qfs_ws::kLayers - 1], m->dout[qfs_ws::kLayers - 1], bv, out, st);
+      launch_gate_update_batch(bv * 6, out, nullptr, 0.0, out, st);
+    }
+    TRY(check_err_word(m));
+    in1.init_gates = reinterpret_cast<const double*>(m->pred);
+    in1.gates_dev = true;
+  }
+  qfs_params p1 = *p;
+  p1.multistarts = 1;
+  p1.max_sweeps = first_sweeps;
+  TRY(batch_common(ctx, P, ns.data(), Ls.data(), pairs.data(), in1, &p1, results));
+  int64_t conv1 = 0, work1 = 0;
+  std::vector<int32_t> fail_idx;
+  for (int i = 0; i < P; ++i) {
+    conv1 += results[i].converged;
+    work1 += results[i].sweeps;
+    if (!results[i].converged) fail_idx.push_back(i);
+  }
+  int64_t work2 = 0;
+  if (!fail_idx.empty()) {
+    const int F = (int)fail_idx.size();
+    std::vector<double> tf((size_t)F * 512), gf((size_t)F * 192);
+    for (int j = 0; j < F; ++j)
+      std::copy(targets + (size_t)fail_idx[j] * 512, targets + (size_t)(fail_idx[j] + 1) * 512,
+                tf.begin() + (size_t)j * 512);
+    std::vector<qfs_result> rf(F);
+    BatchInputs in2;
+    in2.targets = tf.data();
+    in2.gates_out = gf.data();
+    in2.draw_index = fail_idx.data();
+    qfs_params p2 = *p;
+    p2.seed = p->seed + (1ULL << 30);
+    TRY(batch_common(ctx, F, ns.data(), Ls.data(), pairs.data(), in2, &p2, rf.data()));
+    for (int j = 0; j < F; ++j) {
+      const int i = fail_idx[j];
+      work2 += (int64_t)rf[j].sweeps * p->multistarts;
+      std::copy(gf.begin() + (size_t)j * 192, gf.begin() + (size_t)(j + 1) * 192, gates_out + (size_t)i * 192);
+      qfs_result r = rf[j];
+      r.sweeps += results[i].sweeps;
+      r.fp64_sweeps += results[i].fp64_sweeps;
+      r.best_start += 1;  // 0 is the first start; fallback start j is j + 1
+      results[i] = r;
+    }
+  }
+  if (stats) {
+    stats[0] = conv1;
+    stats[1] = work1;
+    stats[2] = work2;
+    stats[3] = (int64_t)fail_idx.size();
+  }
+  return QFS_OK;
 }

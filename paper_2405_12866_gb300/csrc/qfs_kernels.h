@@ -240,10 +240,21 @@ struct BatchArgs {
   int refine_unconverged;  // also refine problems whose starts never reached tol
 };
 
+// A unit of the batched sweep: problem p and its starts s0 .. s0 + ns - 1,
+// swept by one warp with G lanes per start (ns <= 32 / G).
+struct BatchUnit {
+  int p, s0, ns;
+};
+
 void launch_batch_prep(const BatchArgs& a, cudaStream_t st);
-size_t batch_sweep_smem(int warps, int max_elems, int max_L);
-int batch_sweep_blocks_per_sm(int warps, size_t smem);
-void launch_batch_sweep(const BatchArgs& a, int blocks, int warps, size_t smem, cudaStream_t st);
+// Shared memory of a block of `warps` warps with G lanes per start, for
+// problems of at most max_elems = N * M amplitudes and max_L gates.
+size_t batch_sweep_smem(int G, int warps, int max_elems, int max_L);
+// Resident blocks per SM of that launch shape (0: it does not fit).
+int batch_sweep_blocks_per_sm(int G, int warps, size_t smem);
+// The persistent sweep over `units` (queue: a zeroed counter), G in {4, 8, 16, 32}.
+void launch_batch_sweep(int G, const BatchArgs& a, const BatchUnit* units, int nunits, int* queue, int blocks,
+                        int warps, int max_elems, int max_L, cudaStream_t st);
 void launch_batch_finalize(const BatchArgs& a, cudaStream_t st);
 
 // ---------------------------------------------------------- learned part

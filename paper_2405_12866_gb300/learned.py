@@ -220,30 +220,20 @@ class PolicyStats:
 def two_stage(ctx: qfs.Context, targets: np.ndarray, first: np.ndarray | None, S_fallback: int = 8,
               first_sweeps: int = 100, max_sweeps: int = 300, tol: float = 1e-8, seed: int = 0,
               ws: "qfs.WarmStart | None" = None, name: str = "") -> PolicyStats:
-    """One start per target first (the model's prediction when ws is given,
-    else the given starts `first` (P, 6, 4, 4)), at most first_sweeps sweeps;
-    the targets it leaves unconverged fall back to S_fallback random starts
-    drawn by the library.  Prediction, both stages and all host<->device
-    copies are inside the timed region."""
-    P = len(targets)
+    """The library's two-stage policy (qfs_ws_instantiate): one start per
+    target first (the model's prediction when `first` is None, else the given
+    starts (P, 6, 4, 4)), at most first_sweeps sweeps; the targets it leaves
+    unconverged fall back to S_fallback random starts drawn by the library.
+    Prediction, both stages and all host<->device copies are inside the
+    timed region and inside the one call."""
+    if ws is None:
+        raise ValueError("the policy runs through a WarmStart model's entry point")
+    params = instantiate_params(S_fallback, tol, max_sweeps, seed)
     t0 = time.perf_counter()
-    tp = 0.0
-    if ws is not None:
-        first = ws.predict(targets)
-        tp = time.perf_counter() - t0
-    p1 = instantiate_params(1, tol, first_sweeps, seed)
-    _g, _c, sw, conv, _b = ctx.instantiate_batch_uniform(N_QUBITS, PAIRS, targets, p1, first[:, None])
-    work = int(sw.sum())
-    n1 = int(conv.sum())
-    fail = np.flatnonzero(~conv)
-    if len(fail):
-        p2 = instantiate_params(S_fallback, tol, max_sweeps, seed + (1 << 30))
-        _g2, _c2, sw2, conv2, _b2 = ctx.instantiate_batch_uniform(N_QUBITS, PAIRS, targets[fail], p2)
-        work += int(sw2.sum()) * S_fallback
-        conv = conv.copy()
-        conv[fail] = conv2
+    _g, r, st = ws.instantiate(targets, params, first_sweeps=first_sweeps, first_gates=first)
     secs = time.perf_counter() - t0
-    return PolicyStats(name, P, int(conv.sum()), secs, work, n1, tp)
+    work = st["first_start_sweeps"] + st["fallback_start_sweeps"]
+    return PolicyStats(name, len(targets), int(r["converged"].sum()), secs, work, st["first_converged"], 0.0)
 
 
 def multistart(ctx: qfs.Context, targets: np.ndarray, S: int = 8, max_sweeps: int = 300, tol: float = 1e-8,

@@ -47,7 +47,8 @@ EXPORTS = [
     "qfs_instantiate_batch_dev", "qfs_gemm_bf16_dev", "qfs_ws_create", "qfs_ws_destroy", "qfs_ws_params",
     "qfs_ws_loss_grad", "qfs_ws_train", "qfs_ws_predict",
     "qfs_dataflow_trace_enable", "qfs_dataflow_trace_read", "qfs_target_product_dev",
-    "qfs_set_option", "qfs_get_option",
+    "qfs_set_option", "qfs_get_option", "qfs_batch_sweep_once", "qfs_ws_instantiate",
+    "qfs_batch_schedules",
 ]
 (PROF_BACKWARD, PROF_FORWARD, PROF_UPDATE, PROF_GEMM, PROF_RESIDUAL, PROF_CHECK, PROF_OTHER, PROF_BATCH,
  PROF_MLP, PROF_DATAFLOW) = range(10)
@@ -134,6 +135,11 @@ def lib():
                                          C.c_double, _P, _P, _P, _P]
     L.qfs_profile_enable.argtypes = [_P, C.c_int]
     L.qfs_set_option.argtypes = [_P, C.c_int32, C.c_int64]
+    L.qfs_batch_schedules.argtypes = [_P, C.c_int32, _P, C.POINTER(C.c_int32), _P, _P, C.POINTER(C.c_int32)]
+    L.qfs_ws_instantiate.argtypes = [_P, C.c_int32, _P, _P, C.POINTER(Params), C.c_int32, _P, _P,
+                                     C.POINTER(C.c_int64)]
+    L.qfs_batch_sweep_once.argtypes = [_P, C.c_int32, _P, _P, _P, _P, _P, C.c_int32, C.c_int32, _P, C.c_int32,
+                                       _P, _P]
     L.qfs_get_option.argtypes = [_P, C.c_int32, C.POINTER(C.c_int64)]
     L.qfs_profile_reset.argtypes = [_P]
     L.qfs_profile_read.argtypes = [_P, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
@@ -390,6 +396,45 @@ class Context:
                      fp64_sweeps=r.fp64_sweeps, training_states=r.training_states) for r in res]
         return gates, info
 
+    def batch_schedules(self):
+        """The batched form's tuned shapes: (list of dicts per class, list of
+        dicts per timed trial)."""
+        nt, nr = C.c_int32(), C.c_int32()
+        _check(lib().qfs_batch_schedules(self._h, 0, None, C.byref(nt), None, None, C.byref(nr)))
+        cap = max(nt.value, nr.value, 1)
+        tuned = np.zeros((cap, 6), dtype=np.int32)
+        trials = np.zeros((cap, 6), dtype=np.int32)
+        tns = np.zeros(cap)
+        _check(lib().qfs_batch_schedules(self._h, cap, tuned.ctypes.data, C.byref(nt), trials.ctypes.data,
+                                         tns.ctypes.data, C.byref(nr)))
+        keys = ("n", "L", "M", "S", "G", "warps")
+        return ([dict(zip(keys, map(int, r))) for r in tuned[:nt.value]],
+                [dict(zip(keys, map(int, r)), ns_per_start_sweep=float(t)) for r, t in zip(trials[:nr.value],
+                                                                                             tns[:nr.value])])
+
+    def batch_sweep_once(self, problems, samples, init_gates, M: int = 0, lanes_per_start: int = 0):
+        """qfs_batch_sweep_once: one complex64 batched sweep of every start.
+        problems: list of (n, pairs, U); samples and init_gates (S, L, 4, 4)
+        lists per problem.  Returns (list of (S, L, 4, 4) swept gates, (P, S) costs)."""
+        P = len(problems)
+        ns = np.array([pr[0] for pr in problems], dtype=np.int32)
+        Ls = np.array([len(pr[1]) for pr in problems], dtype=np.int32)
+        S = int(np.asarray(init_gates[0]).shape[0])
+        pairs = np.ascontiguousarray(np.concatenate([np.asarray(pr[1], dtype=np.int32).reshape(-1)
+                                                     for pr in problems]))
+        targets = np.ascontiguousarray(np.concatenate([_host_c128(pr[2]).reshape(-1) for pr in problems]))
+        sm = np.ascontiguousarray(np.concatenate([_host_c128(x).reshape(-1) for x in samples]))
+        ig = np.ascontiguousarray(np.concatenate([_host_c128(x).reshape(-1) for x in init_gates]))
+        out = np.zeros_like(ig)
+        costs = np.zeros((P, S), dtype=np.float64)
+        _check(lib().qfs_batch_sweep_once(self._h, P, ns.ctypes.data, Ls.ctypes.data, pairs.ctypes.data,
+                                          targets.ctypes.data, sm.ctypes.data, M, S, ig.ctypes.data,
+                                          lanes_per_start, out.ctypes.data, costs.ctypes.data))
+        gates, offs = [], np.concatenate([[0], np.cumsum(S * Ls * 16)])
+        for i in range(P):
+            gates.append(out[offs[i]:offs[i + 1]].reshape(S, Ls[i], 4, 4))
+        return gates, costs
+
     def instantiate_batch_uniform(self, n, pairs, targets, params: Params, init_gates=None):
         """P problems of one structure: targets (P, N, N), init_gates (P, S, L, 4, 4)
         or None (drawn from params.seed + index), samples drawn from params.seed +
@@ -545,6 +590,24 @@ class WarmStart:
         _check(lib().qfs_ws_train(self._h, count, t.ctypes.data, lab.ctypes.data, epochs, batch, lr,
                                   lr if lr_final is None else lr_final, seed, losses.ctypes.data))
         return losses
+
+    def instantiate(self, targets, params: Params, first_sweeps: int = 100, first_gates=None):
+        """qfs_ws_instantiate: the two-stage policy (predicted first start,
+        random multistarts as the fallback) for targets (P, 16, 16).  Returns
+        (gates (P, 6, 4, 4), result records, stats dict)."""
+        t = _host_c128(targets)
+        P = t.size // 256
+        fg = None if first_gates is None else _host_c128(first_gates, (P, 6, 4, 4))
+        out = np.zeros((P, 6, 4, 4), dtype=np.complex128)
+        res = (Result * P)()
+        st = (C.c_int64 * 4)()
+        _check(lib().qfs_ws_instantiate(self._h, P, t.ctypes.data, fg.ctypes.data if fg is not None else None,
+                                        C.byref(params), first_sweeps, out.ctypes.data, res, st))
+        r = np.frombuffer(res, dtype=np.dtype([("cost", "f8"), ("sweeps", "i4"), ("converged", "i4"),
+                                                ("best_start", "i4"), ("fp64_sweeps", "i4"),
+                                                ("training_states", "i4")], align=True), count=P).copy()
+        return out, r, dict(first_converged=int(st[0]), first_start_sweeps=int(st[1]),
+                            fallback_start_sweeps=int(st[2]), fallback_targets=int(st[3]))
 
     def predict(self, targets):
         t = _host_c128(targets)

@@ -36,6 +36,59 @@ def _run(ctx, probs, S, max_sweeps, tol=1e-8):
     return samples, inits, gates, info
 
 
+@pytest.mark.parametrize("G", [4, 8, 16, 32])
+def test_one_batched_sweep_per_schedule_matches_oracle(ctx, G):
+    """One complex64 sweep of every start with G lanes per start against the
+    oracle's FP64 sweep from the same gates: gates within 1e-4 where the
+    update is unique (sigma_min(E) > 1e-3 sigma_max(E): a complex64
+    environment fixes the polar factor to ~1e-7 kappa), residual costs within
+    1e-5 (complex64 states)."""
+    probs = [p for p in w.uneven_blocks(P=96, seed=21, S=4) if (1 << (p.n - 2)) * p.M * 2 >= G or G == 32][:40]
+    S = 4
+    samples = [p.samples() for p in probs]
+    inits = [p.init_gates()[:S] for p in probs]
+    got, costs = ctx.batch_sweep_once([(p.n, p.pairs, p.U) for p in probs], samples, inits, lanes_per_start=G)
+    checked = 0
+    for p, Psi, G0, g, c in zip(probs, samples, inits, got, costs):
+        UPsi = p.U @ Psi
+        for s in range(S):
+            r = o.sweep(UPsi, Psi, G0[s], p.pairs, p.n)
+            sv = np.linalg.svd(r.envs, compute_uv=False)
+            if np.all(sv[:, -1] > 1e-3 * sv[:, 0]):
+                assert np.max(np.abs(g[s] - r.gates)) < 1e-4, (p.name, s)
+                checked += 1
+            assert abs(c[s] - r.cost) < 1e-5 * max(1.0, r.cost), (p.name, s, c[s], r.cost)
+    assert checked >= len(probs) * S // 2
+
+
+def test_batch_512_problems_match_oracle_runs(ctx):
+    """The first 512 problems of the batched workload against the oracle's
+    own multistart runs (tests/golden/uneven_blocks_oracle_runs.json, written
+    by oracle/make_golden.py): the same converged set, and every returned
+    solution's FP64 cost, recomputed by the oracle, <= tol when converged.
+    complex64 trajectories follow the FP64 ones to ~1e-6 per sweep; a
+    problem whose converging start first crosses the tolerance within a few
+    sweeps of max_sweeps can end on either side of it, so such a problem
+    (oracle stopping sweep > max_sweeps - 10) may differ."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "uneven_blocks_oracle_runs.json")))
+    runs = gold["runs"]
+    probs = w.uneven_blocks(P=len(runs), seed=gold["seed"], S=gold["starts"])
+    samples, inits, gates, info = _run(ctx, probs, gold["starts"], gold["max_sweeps"], gold["tol"])
+    differ = []
+    for i, (p, Psi, g, r, want) in enumerate(zip(probs, samples, gates, info, runs)):
+        assert (p.n, p.L) == (want["n"], want["L"])
+        if r["converged"] != want["converged"]:
+            differ.append((i, want["sweeps"]))
+        if r["converged"]:
+            c = o.sample_cost(p.U @ Psi, Psi, g, p.pairs, p.n)
+            assert c <= gold["tol"] and abs(c - r["cost"]) < 1e-12 + 1e-6 * c
+    late = [i for i, sw in differ if sw > gold["max_sweeps"] - 10 or not runs[i]["converged"]]
+    assert len(differ) == len(late), f"converged sets differ on problems {differ}"
+    assert len(differ) <= 2, differ
+
+
 def test_batch_matches_oracle_converged_set(ctx):
     probs = w.uneven_blocks(P=24, seed=4, S=8)
     S, max_sweeps = 8, 300

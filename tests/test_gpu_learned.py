@@ -44,7 +44,7 @@ def test_trained_warm_start_beats_random_first_starts(ctx):
     Tev = learned.make_targets(42, neval)
     first = learned.random_starts(4242, neval, 1)[:, 0]
     warm = learned.two_stage(ctx, Tev, None, ws=ws, first_sweeps=300)
-    rand = learned.two_stage(ctx, Tev, first, first_sweeps=300)
+    rand = learned.two_stage(ctx, Tev, first, ws=ws, first_sweeps=300)
     base = learned.multistart(ctx, Tev, S=8)
     print(f"\nfirst start converged: learned {warm.first_stage_converged}, random {rand.first_stage_converged}"
           f" of {neval}; sweep work: learned {warm.start_sweeps}, random {rand.start_sweeps},"
@@ -55,4 +55,39 @@ def test_trained_warm_start_beats_random_first_starts(ctx):
     assert warm.start_sweeps < rand.start_sweeps < base.start_sweeps
     # ... at the same accuracy (every answer is judged by the sweep).
     assert warm.converged >= base.converged - 0.005 * neval
+    ws.close()
+
+
+def test_policy_entry_point_equals_its_two_batched_stages(ctx):
+    """qfs_ws_instantiate with given first starts against the batched entry
+    point called for each stage by hand: stage 1 is every target with its
+    first start alone (training states from seed + i, first_sweeps sweeps);
+    stage 2 reruns the unconverged targets with multistarts random starts and
+    training states drawn from seed + 2^30 + i.  Same schedules, same
+    inputs: the answers agree bit for bit."""
+    from paper_2405_12866_gb300 import learned, qfs
+    from paper_2405_12866_gb300 import workloads as w
+    P, S2, seed, fs = 256, 4, 900, 20
+    T = learned.make_targets(77, P)
+    first = learned.random_starts(5151, P, 1)[:, 0]
+    ws = qfs.WarmStart(ctx, seed=1, batch_cap=256)
+    prm = learned.instantiate_params(S2, 1e-8, 200, seed)
+    gates, res, st = ws.instantiate(T, prm, first_sweeps=fs, first_gates=first)
+    p1 = learned.instantiate_params(1, 1e-8, fs, seed)
+    g1, _c1, sw1, conv1, _b1 = ctx.instantiate_batch_uniform(4, learned.PAIRS, T, p1, first[:, None])
+    assert st["first_converged"] == int(conv1.sum())
+    assert st["fallback_targets"] == int((~conv1).sum())
+    ok = np.flatnonzero(conv1)
+    assert np.array_equal(gates[ok], g1[ok]) and np.all(res["best_start"][ok] == 0)
+    bad = np.flatnonzero(~conv1)
+    if len(bad):
+        probs = [(4, learned.PAIRS, T[i]) for i in bad]
+        smp = [w.sample_states(seed + (1 << 30) + int(i), 4, 8) for i in bad]
+        ini = [w.initial_gates(seed + (1 << 30) + int(i), S2, 6) for i in bad]
+        g2, info2 = ctx.instantiate_batch(probs, prm, smp, ini)
+        for j, i in enumerate(bad):
+            assert np.array_equal(gates[i], g2[j])
+            assert res["converged"][i] == info2[j]["converged"]
+            assert res["best_start"][i] == info2[j]["best_start"] + 1
+            assert res["sweeps"][i] == info2[j]["sweeps"] + sw1[i]
     ws.close()

@@ -106,9 +106,9 @@ def test_warm_start_gradients_match_oracle(ctx):
             assert not np.any(bad), (f"layer {li} {name}: {int(bad.sum())} of {bad.size} entries outside the "
                                      f"bf16 rounding bound; worst excess "
                                      f"{float(np.max((np.abs(a - b) - bound) / np.maximum(m, 1e-30)))}")
-        # and most entries agree far more closely than the bound
+        # and most entries agree far more closely than the bound (2^-7 = 7.8e-3)
         rel = np.abs(gw - ww) / np.maximum(mw, 1e-30)
-        assert np.median(rel) < 1e-4, (li, float(np.median(rel)))
+        assert np.median(rel) < 1e-3, (li, float(np.median(rel)))
     model.close()
 
 

@@ -141,3 +141,27 @@ def test_workspace_cap_gives_enomem_before_allocating(qfs):
         c.set_option(qfs.QFS_OPT_WORKSPACE_CAP, 0)
         r = c.instantiate(p.n, p.pairs, p.U, prm, p.samples(), p.init_gates())
         assert r.sweeps == 2
+
+
+@pytest.mark.parametrize("win", [1, 3, 5])
+def test_plateau_window_length_on_the_gpu(qfs, win):
+    """One gate on three qubits with a target it cannot reach: the first
+    update is already optimal and the cost stays constant, so plateau
+    detection with a window of w sweeps ends every run at sweep w + 1 (the
+    oracle's pin of the same rule), in FP64, in the mixed path and in the
+    batched form."""
+    n, pairs = 3, [(0, 1)]
+    U = w.target_unitary(w.haar_gates(141, w.STREAM_TARGET_GATES, 2), [(0, 1), (1, 2)], n)
+    Psi, G0 = w.sample_states(142, n, 8), w.initial_gates(143, 2, 1)
+    want = o.instantiate(U, Psi, G0, pairs, n, 0.0, 100, plateau_window=win, diff_tol_r=1e-3, min_sweeps=0)
+    assert want.sweeps == win + 1
+    with _ctx(qfs) as c:
+        for prec in (qfs.QFS_FP64, qfs.QFS_MIXED):
+            prm = qfs.default_params(M=8, multistarts=2, max_sweeps=100, dist_tol=0.0, precision=prec,
+                                     plateau_window=win, diff_tol_r=1e-3, min_sweeps=0)
+            r = c.instantiate(n, pairs, U, prm, Psi, G0)
+            assert r.sweeps == win + 1, (prec, r.sweeps)
+        prm = qfs.default_params(M=8, multistarts=2, max_sweeps=100, dist_tol=0.0, plateau_window=win,
+                                 diff_tol_r=1e-3, min_sweeps=0, refine_sweeps_max=0)
+        _, info = c.instantiate_batch([(n, pairs, U)], prm, [Psi], [G0])
+        assert info[0]["sweeps"] == win + 1, info[0]
