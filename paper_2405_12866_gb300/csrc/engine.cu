@@ -1961,10 +1961,28 @@ struct BatchInputs {
 
 long long batch_class_key(int n, int L, int M, int S) { return (((long long)n * 64 + L) * 4096 + M) * 128 + S; }
 
+// Warps per block for G lanes per start and problems of at most max_elems
+// amplitudes and max_L gates: the choice (2, 4 or 8) with the most resident
+// warps per SM (the kernel has no block-wide barrier, so this only sets the
+// shared-memory granularity); 0 if none fits.
+int batch_warps_for(int G, int max_elems, int max_L) {
+  int best = 0, best_res = 0;
+  for (int w : {4, 2, 8}) {
+    const size_t smem = batch_sweep_smem(G, w, max_elems, max_L);
+    if (smem > 200 * 1024) continue;
+    const int res = w * batch_sweep_blocks_per_sm(G, w, smem);
+    if (res > best_res) {
+      best_res = res;
+      best = w;
+    }
+  }
+  return best;
+}
+
 // Schedules worth trying for a class: G lanes per start no larger than the
 // state's 4-row groups (a lane with no group would idle in every state
-// step), at most S starts per warp (a unit holds starts of one problem), with
-// 2, 4 or 8 warps per block when the shared memory allows.
+// step), at most S starts per warp (a unit holds starts of one problem), and
+// a block shape that fits.
 std::vector<std::pair<int, int>> batch_candidates(int n, int M, int L, int S) {
   std::vector<std::pair<int, int>> c;
   const int groups = (1 << (n - 2)) * M;
@@ -1972,12 +1990,8 @@ std::vector<std::pair<int, int>> batch_candidates(int n, int M, int L, int S) {
     if (32 / G > S) continue;
     if (G > groups * 2 && G != 32) continue;
     if (G < 32 && groups / G > 8) continue;  // many groups per lane: the warp-per-start form is as lane-efficient
-    for (int w : {2, 4, 8}) {
-      const size_t smem = batch_sweep_smem(G, w, M << n, L);
-      if (smem > 200 * 1024) continue;
-      if (batch_sweep_blocks_per_sm(G, w, smem) < 1) continue;
-      c.push_back({G, w});
-    }
+    const int w = batch_warps_for(G, M << n, L);
+    if (w) c.push_back({G, w});
   }
   return c;
 }
@@ -2006,7 +2020,7 @@ void batch_units(const std::vector<BatchProblem>& probs, std::vector<int> idx, i
 // choice is cached per (n, L, M) on the context.  `a` points at the batch's
 // prepared buffers; units and the queue go to the scratch at `scratch`.
 int autotune_batch(qfs_ctx* ctx, BatchArgs a, const std::vector<BatchProblem>& probs,
-                   std::vector<BatchClass>& classes, BatchUnit* units_dev, int* queue_dev) {
+                   std::vector<BatchClass>& classes, BatchUnit* units_dev, int* queue_dev, long long max_units_trial) {
   cudaStream_t st = ctx->stream;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   for (BatchClass& c : classes) {
@@ -2031,22 +2045,26 @@ int autotune_batch(qfs_ctx* ctx, BatchArgs a, const std::vector<BatchProblem>& p
       CK(cudaEventCreate(&e0));
       CK(cudaEventCreate(&e1));
     }
-    // A sample of the class: up to its first 512 problems, 4 sweeps of
-    // every start, timed twice after a warm-up run; the time per start-sweep
-    // decides.  The warp-per-start shape is kept unless another is at least
-    // 5% faster.
+    // A trial of the class at full occupancy: its problems (up to 512,
+    // repeated until the units fill every resident warp four times over),
+    // 4 sweeps of every start, timed twice after a warm-up run; the time per
+    // start-sweep decides.  The warp-per-start shape is kept unless another
+    // is at least 5% faster.
     std::vector<int> sample(c.problems.begin(), c.problems.begin() + std::min<size_t>(c.problems.size(), 512));
     BatchArgs t = a;
     t.max_sweeps = 4;
     t.tol = -1.0;
     t.plateau_window = 0;
-    const double start_sweeps = (double)sample.size() * a.S * t.max_sweeps;
     float best = 1e30f;
     float best32 = 1e30f;
     int w32 = 0;
     for (auto [G, w] : cand) {
       std::vector<BatchUnit> u;
-      batch_units(probs, sample, a.S, G, u);
+      const size_t smem0 = batch_sweep_smem(G, w, c.M << c.n, c.L);
+      const long long slots = 4LL * ctx->num_sms * w * std::max(1, batch_sweep_blocks_per_sm(G, w, smem0));
+      while ((long long)u.size() < slots && (long long)u.size() < max_units_trial) batch_units(probs, sample, a.S, G, u);
+      if ((long long)u.size() > max_units_trial) u.resize((size_t)max_units_trial);
+      const double start_sweeps = (double)u.size() * std::min(a.S, 32 / G) * t.max_sweeps;
       CK(cudaMemcpyAsync(units_dev, u.data(), sizeof(BatchUnit) * u.size(), cudaMemcpyHostToDevice, st));
       const size_t smem = batch_sweep_smem(G, w, c.M << c.n, c.L);
       const int bps = batch_sweep_blocks_per_sm(G, w, smem);
@@ -2176,7 +2194,8 @@ int batch_common(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls, 
     off += align_up(bytes);
     return o;
   };
-  const long long max_units = (long long)P * S;
+  // Unit lists: a batch needs at most P * S; the autotuner's trials up to 16384.
+  const long long max_units = std::max<long long>((long long)P * S, 16384);
   const size_t o_probs = take(sizeof(BatchProblem) * P), o_units = take(sizeof(BatchUnit) * max_units),
                o_pairs = take(sizeof(int) * pair_off), o_tgt = take(sizeof(double2) * target_off),
                o_psi64 = take(sizeof(double2) * state_off), o_phil64 = take(sizeof(double2) * state_off),
@@ -2271,7 +2290,7 @@ int batch_common(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls, 
       untuned |= !f;
     }
     if (untuned) launch_batch_prep(a, st);
-    TRY(autotune_batch(ctx, a, probs, classes, units_dev, a.queue));
+    TRY(autotune_batch(ctx, a, probs, classes, units_dev, a.queue, max_units));
   }
   // Launch groups: classes with the same (G, warps) share one persistent
   // launch over their units, largest problems first.
@@ -2281,21 +2300,20 @@ int batch_common(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls, 
   std::vector<Launch> launches;
   std::vector<BatchUnit> units;
   {
-    std::vector<std::pair<int, int>> shapes;
-    for (const BatchClass& c : classes) {
-      bool have = false;
-      for (auto& sh : shapes) have |= sh.first == c.G && sh.second == c.warps;
-      if (!have) shapes.push_back({c.G, c.warps});
-    }
-    for (auto [G, wv] : shapes) {
+    std::vector<int> shapes;
+    for (const BatchClass& c : classes)
+      if (std::find(shapes.begin(), shapes.end(), c.G) == shapes.end()) shapes.push_back(c.G);
+    for (int G : shapes) {
       std::vector<int> idx;
       int me = 0, ml = 0;
       for (const BatchClass& c : classes)
-        if (c.G == G && c.warps == wv) {
+        if (c.G == G) {
           idx.insert(idx.end(), c.problems.begin(), c.problems.end());
           me = std::max(me, c.M << c.n);
           ml = std::max(ml, c.L);
         }
+      const int wv = batch_warps_for(G, me, ml);
+      if (!wv) return fail(QFS_EUNSUPPORTED, "no block shape fits G = %d with N*M = %d, L = %d", G, me, ml);
       const int u0 = (int)units.size();
       batch_units(probs, idx, S, G, units);
       launches.push_back(Launch{G, wv, u0, (int)units.size() - u0, me, ml});
