@@ -155,6 +155,9 @@ int qfs_device_sms(const qfs_ctx* ctx);
  *     forward gates on four distinct qubits in one step (0: one per step).
  *   QFS_OPT_FP64_TARGET_PRODUCT [0]: QFS_MIXED runs form U Psi in FP64
  *     instead of FP32 pair arithmetic.
+ *   QFS_OPT_BATCH_LANES_PER_START [0 = tuned]: the batched form runs every
+ *     problem class with this many lanes per start (4, 8, 16 or 32) instead
+ *     of the autotuner's choice.
  * Every setting gives the same results up to the order of reduction sums.
  * QFS_EINVAL for an unknown option or a value out of range. */
 #define QFS_OPT_WAIT_LIMIT 0
@@ -163,6 +166,7 @@ int qfs_device_sms(const qfs_ctx* ctx);
 #define QFS_OPT_DATAFLOW 3
 #define QFS_OPT_TWO_GATE_FORWARD 4
 #define QFS_OPT_FP64_TARGET_PRODUCT 5
+#define QFS_OPT_BATCH_LANES_PER_START 6
 int qfs_set_option(qfs_ctx* ctx, int32_t option, int64_t value);
 int qfs_get_option(qfs_ctx* ctx, int32_t option, int64_t* value);
 
@@ -324,11 +328,15 @@ int qfs_target_product_dev(qfs_ctx* ctx, int32_t n, int32_t M, const double* tar
  * (host) one qfs_result per problem (fp64_sweeps = refinement sweeps).
  * Problems are grouped in classes (n, L, M); for each class an autotuner
  * times the launch shapes that fit (G = 4, 8, 16 or 32 lanes per start, i.e.
- * 8, 4, 2 or 1 starts of a problem per warp, and 2, 4 or 8 warps per block)
- * on a few sweeps of that class's problems the first time the context sees
- * the class, and keeps the fastest; the batch then runs as one captured
- * graph with one persistent launch per shape, replayed by later calls of the
- * same shape.  Results do not depend on the shapes chosen beyond the order of
+ * 8, 4, 2 or 1 starts of a problem per warp, the block shape with the most
+ * resident warps) on 4 sweeps of that class's problems at full occupancy the
+ * first time the context sees the class, and keeps the fastest per
+ * start-sweep (G = 32 unless another is 5% faster).  A unit of several
+ * starts lives longer than a warp-per-start unit, so the first call of a
+ * batch shape also times the whole batch with the per-class shapes and
+ * with one start per warp everywhere, and keeps the faster plan.  The batch
+ * runs as one captured graph with one persistent launch per shape,
+ * replayed by later calls of the same shape.  Results do not depend on the shapes chosen beyond the order of
  * FP32 sums.  beta must be 0; multistarts 1..64. */
 int qfs_instantiate_batch(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls,
                           const int32_t* pairs, const double* targets, const double* samples,
@@ -348,9 +356,14 @@ int qfs_instantiate_batch_dev(qfs_ctx* ctx, int32_t P, const int32_t* ns, const 
  * warps per block; *n_tuned: the classes tuned so far.  trials (cap x 6,
  * may be NULL) and trial_ns (cap doubles, may be NULL): every timed trial
  * (n, L, M, multistarts, G, warps) and its time per start-sweep in ns;
- * *n_trials: the trials so far.  At most cap rows are written. */
+ * *n_trials: the trials so far.  plan_choice (cap int32, may be NULL) and
+ * plan_ms (cap x 2 doubles, may be NULL): per batch shape whose per-class
+ * shapes were not all warp-per-start, the plan kept (0: per-class shapes,
+ * 1: one start per warp everywhere) and the timed ms of the two; *n_plans:
+ * their number.  At most cap rows are written. */
 int qfs_batch_schedules(qfs_ctx* ctx, int32_t cap, int32_t* tuned, int32_t* n_tuned, int32_t* trials,
-                        double* trial_ns, int32_t* n_trials);
+                        double* trial_ns, int32_t* n_trials, int32_t* plan_choice, double* plan_ms,
+                        int32_t* n_plans);
 
 /* Exactly one complex64 sweep of the batched form for every start of P
  * problems (parity checks): inputs as qfs_instantiate_batch (host; samples

@@ -113,6 +113,10 @@ struct qfs_ctx {
   // start-sweep in ns (qfs_batch_schedules reads them back).
   std::vector<std::array<int, 6>> batch_trial_shape;
   std::vector<double> batch_trial_ns;
+  // Whole-batch plan decisions: batch shape key -> 0 (per-class shapes) or
+  // 1 (one start per warp everywhere), with the two timings in ms.
+  std::vector<std::pair<uint64_t, int>> batch_plans;
+  std::vector<std::pair<float, float>> batch_plan_ms;
   struct BatchGraph {
     uint64_t key = 0;
     cudaGraphExec_t exec = nullptr;
@@ -1583,6 +1587,11 @@ int qfs_set_option(qfs_ctx* ctx, int32_t option, int64_t value) {
     case QFS_OPT_DATAFLOW: ctx->dataflow = value != 0; return QFS_OK;
     case QFS_OPT_TWO_GATE_FORWARD: ctx->df_fwd2 = value != 0; return QFS_OK;
     case QFS_OPT_FP64_TARGET_PRODUCT: ctx->upsi_fp64 = value != 0; return QFS_OK;
+    case QFS_OPT_BATCH_LANES_PER_START:
+      if (value != 0 && value != 4 && value != 8 && value != 16 && value != 32)
+        return fail(QFS_EINVAL, "lanes per start %lld: need 0, 4, 8, 16 or 32", (long long)value);
+      ctx->batch_force_G = (int)value;
+      return QFS_OK;
     default: return fail(QFS_EINVAL, "unknown option %d", option);
   }
 }
@@ -1597,6 +1606,7 @@ int qfs_get_option(qfs_ctx* ctx, int32_t option, int64_t* value) {
     case QFS_OPT_DATAFLOW: *value = ctx->dataflow; return QFS_OK;
     case QFS_OPT_TWO_GATE_FORWARD: *value = ctx->df_fwd2; return QFS_OK;
     case QFS_OPT_FP64_TARGET_PRODUCT: *value = ctx->upsi_fp64; return QFS_OK;
+    case QFS_OPT_BATCH_LANES_PER_START: *value = ctx->batch_force_G; return QFS_OK;
     default: return fail(QFS_EINVAL, "unknown option %d", option);
   }
 }
@@ -1959,7 +1969,9 @@ struct BatchInputs {
   double* start_costs_out = nullptr;
 };
 
-long long batch_class_key(int n, int L, int M, int S) { return (((long long)n * 64 + L) * 4096 + M) * 128 + S; }
+long long batch_class_key(int n, int L, int M, int S, bool lane_groups) {
+  return ((((long long)n * 64 + L) * 4096 + M) * 128 + S) * 2 + (lane_groups ? 1 : 0);
+}
 
 // Warps per block for G lanes per start and problems of at most max_elems
 // amplitudes and max_L gates: the choice (2, 4 or 8) with the most resident
@@ -1983,10 +1995,11 @@ int batch_warps_for(int G, int max_elems, int max_L) {
 // state's 4-row groups (a lane with no group would idle in every state
 // step), at most S starts per warp (a unit holds starts of one problem), and
 // a block shape that fits.
-std::vector<std::pair<int, int>> batch_candidates(int n, int M, int L, int S) {
+std::vector<std::pair<int, int>> batch_candidates(int n, int M, int L, int S, bool lane_groups) {
   std::vector<std::pair<int, int>> c;
   const int groups = (1 << (n - 2)) * M;
   for (int G : {4, 8, 16, 32}) {
+    if (G < 32 && !lane_groups) continue;
     if (32 / G > S) continue;
     if (G > groups * 2 && G != 32) continue;
     if (G < 32 && groups / G > 8) continue;  // many groups per lane: the warp-per-start form is as lane-efficient
@@ -2024,7 +2037,7 @@ int autotune_batch(qfs_ctx* ctx, BatchArgs a, const std::vector<BatchProblem>& p
   cudaStream_t st = ctx->stream;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   for (BatchClass& c : classes) {
-    const long long key = batch_class_key(c.n, c.L, c.M, a.S);
+    const long long key = batch_class_key(c.n, c.L, c.M, a.S, true);
     bool found = false;
     for (auto& kv : ctx->batch_tuned)
       if (kv.first == key) {
@@ -2033,7 +2046,7 @@ int autotune_batch(qfs_ctx* ctx, BatchArgs a, const std::vector<BatchProblem>& p
         found = true;
       }
     if (found) continue;
-    const auto cand = batch_candidates(c.n, c.M, c.L, a.S);
+    const auto cand = batch_candidates(c.n, c.M, c.L, a.S, true);
     if (cand.empty()) return fail(QFS_EUNSUPPORTED, "no batched launch shape fits n = %d, L = %d, M = %d", c.n, c.L, c.M);
     if (cand.size() == 1) {
       c.G = cand[0].first;
@@ -2081,14 +2094,15 @@ int autotune_batch(qfs_ctx* ctx, BatchArgs a, const std::vector<BatchProblem>& p
         CK(cudaEventElapsedTime(&r, e0, e1));
         if (rep) ms = std::min(ms, r);
       }
+      const float per = (float)(1e6 * ms / start_sweeps);  // ns per start-sweep
       ctx->batch_trial_shape.push_back({c.n, c.L, c.M, a.S, G, w});
-      ctx->batch_trial_ns.push_back(1e6 * ms / start_sweeps);
-      if (G == 32 && ms < best32) {
-        best32 = ms;
+      ctx->batch_trial_ns.push_back(per);
+      if (G == 32 && per < best32) {
+        best32 = per;
         w32 = w;
       }
-      if (ms < best) {
-        best = ms;
+      if (per < best) {
+        best = per;
         c.G = G;
         c.warps = w;
       }
@@ -2175,7 +2189,7 @@ int batch_common(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls, 
   {
     std::vector<std::pair<long long, int>> seen;
     for (int i = 0; i < P; ++i) {
-      const long long key = batch_class_key(probs[i].n, probs[i].L, probs[i].M, S);
+      const long long key = batch_class_key(probs[i].n, probs[i].L, probs[i].M, S, false);
       int ci = -1;
       for (auto& kv : seen)
         if (kv.first == key) ci = kv.second;
@@ -2286,157 +2300,213 @@ int batch_common(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls, 
     bool untuned = false;
     for (const BatchClass& c : classes) {
       bool f = false;
-      for (auto& kv : ctx->batch_tuned) f |= kv.first == batch_class_key(c.n, c.L, c.M, S);
+      for (auto& kv : ctx->batch_tuned) f |= kv.first == batch_class_key(c.n, c.L, c.M, S, true);
       untuned |= !f;
     }
     if (untuned) launch_batch_prep(a, st);
     TRY(autotune_batch(ctx, a, probs, classes, units_dev, a.queue, max_units));
   }
-  // Launch groups: classes with the same (G, warps) share one persistent
-  // launch over their units, largest problems first.
-  struct Launch {
-    int G, warps, unit0, nunits, max_elems, max_L;
-  };
-  std::vector<Launch> launches;
-  std::vector<BatchUnit> units;
-  {
-    std::vector<int> shapes;
-    for (const BatchClass& c : classes)
-      if (std::find(shapes.begin(), shapes.end(), c.G) == shapes.end()) shapes.push_back(c.G);
-    for (int G : shapes) {
-      std::vector<int> idx;
-      int me = 0, ml = 0;
-      for (const BatchClass& c : classes)
-        if (c.G == G) {
-          idx.insert(idx.end(), c.problems.begin(), c.problems.end());
-          me = std::max(me, c.M << c.n);
-          ml = std::max(ml, c.L);
-        }
-      const int wv = batch_warps_for(G, me, ml);
-      if (!wv) return fail(QFS_EUNSUPPORTED, "no block shape fits G = %d with N*M = %d, L = %d", G, me, ml);
-      const int u0 = (int)units.size();
-      batch_units(probs, idx, S, G, units);
-      launches.push_back(Launch{G, wv, u0, (int)units.size() - u0, me, ml});
-    }
-  }
-  // Launches start in order of their largest problem, largest first (the
-  // persistent launches overlap; the largest units should not come last).
-  {
-    std::vector<int> ord(launches.size());
-    for (size_t i = 0; i < ord.size(); ++i) ord[i] = (int)i;
-    auto work = [&](const Launch& L) {
-      const BatchProblem& b = probs[units[L.unit0].p];  // its first unit is its largest
-      return (long long)b.L * b.M << b.n;
+  // Builds (or finds in the cache) and launches the graph of one plan: the
+  // classes with the same G share one persistent launch over their units,
+  // largest problems first.
+  auto launch_plan = [&](const std::vector<BatchClass>& classes) -> int {
+    struct Launch {
+      int G, warps, unit0, nunits, max_elems, max_L;
     };
-    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return work(launches[x]) > work(launches[y]); });
-    std::vector<Launch> sorted;
-    for (int i : ord) sorted.push_back(launches[i]);
-    launches.swap(sorted);
-  }
-  if ((int)launches.size() > 60) return fail(QFS_EUNSUPPORTED, "too many launch shapes (%d)", (int)launches.size());
-  CK(cudaMemcpyAsync(units_dev, units.data(), sizeof(BatchUnit) * units.size(), cudaMemcpyHostToDevice, st));
-  // The graph: queue reset, set-up, one persistent launch per shape (on
-  // parallel branches), the finishing kernel.  Replayed while the batch's
-  // shape, parameters and workspace stay the same.
-  uint64_t key = 1469598103934665603ULL;
-  {
-    const int sc[] = {P, S, a.max_sweeps, a.plateau_window, a.min_sweeps, a.refine_max, (int)in.sweep_once,
-                      (int)launches.size()};
-    key = fnv1a(key, sc, sizeof(sc));
-    const double sd[] = {a.tol, a.diff_tol_r};
-    key = fnv1a(key, sd, sizeof(sd));
-    key = fnv1a(key, &w, sizeof(w));
-    key = fnv1a(key, ns, sizeof(int32_t) * P);
-    key = fnv1a(key, Ls, sizeof(int32_t) * P);
-    key = fnv1a(key, launches.data(), sizeof(Launch) * launches.size());
-    const int mm[] = {p->M, max_elems, max_L};
-    key = fnv1a(key, mm, sizeof(mm));
-  }
-  // With per-launch timing on, the graph carries this call's event records:
-  // it is captured, replayed once, harvested and dropped.
-  const bool cache = !ctx->prof.on;
-  qfs_ctx::BatchGraph* bg = nullptr;
-  qfs_ctx::BatchGraph once;
-  if (cache)
-    for (auto& g : ctx->batch_graphs)
-      if (g.key == key && g.exec) bg = &g;
-  if (!bg) {
-    if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
-    TRY(ensure_group_streams(ctx, std::min<int>(kMaxGroups, (int)launches.size())));
-    long long before[QFS_PROF_KINDS];
-    for (int i = 0; i < QFS_PROF_KINDS; ++i) before[i] = ctx->prof.launches[i];
-    cudaStream_t cs = ctx->cap_stream;
-    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
-    ctx->prof.capturing = true;
-    cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(int) * 64, cs);
+    std::vector<Launch> launches;
+    std::vector<BatchUnit> units;
     {
-      ProfScope ps(ctx, QFS_PROF_OTHER, 0.0, cs);
-      launch_batch_prep(a, cs);
+      std::vector<int> shapes;
+      for (const BatchClass& c : classes)
+        if (std::find(shapes.begin(), shapes.end(), c.G) == shapes.end()) shapes.push_back(c.G);
+      for (int G : shapes) {
+        std::vector<int> idx;
+        int me = 0, ml = 0;
+        for (const BatchClass& c : classes)
+          if (c.G == G) {
+            idx.insert(idx.end(), c.problems.begin(), c.problems.end());
+            me = std::max(me, c.M << c.n);
+            ml = std::max(ml, c.L);
+          }
+        const int wv = batch_warps_for(G, me, ml);
+        if (!wv) return fail(QFS_EUNSUPPORTED, "no block shape fits G = %d with N*M = %d, L = %d", G, me, ml);
+        const int u0 = (int)units.size();
+        batch_units(probs, idx, S, G, units);
+        launches.push_back(Launch{G, wv, u0, (int)units.size() - u0, me, ml});
+      }
     }
-    if (e == cudaSuccess) e = cudaEventRecord(ctx->fork_event, cs);
-    for (size_t li = 0; li < launches.size() && e == cudaSuccess; ++li) {
-      const Launch& L = launches[li];
-      const size_t smem = batch_sweep_smem(L.G, L.warps, L.max_elems, L.max_L);
-      const int bps = std::max(1, batch_sweep_blocks_per_sm(L.G, L.warps, smem));
-      const int blocks = std::max(1, std::min(ctx->num_sms * bps, (L.nunits + L.warps - 1) / L.warps));
-      const int gs = (int)(li % kMaxGroups);
-      cudaStream_t ls = li == 0 ? cs : ctx->gstream[gs];
-      if (li > 0) e = cudaStreamWaitEvent(ls, ctx->fork_event, 0);
-      if (e != cudaSuccess) break;
+    // Launches start in order of their largest problem, largest first (the
+    // persistent launches overlap; the largest units should not come last).
+    {
+      std::vector<int> ord(launches.size());
+      for (size_t i = 0; i < ord.size(); ++i) ord[i] = (int)i;
+      auto work = [&](const Launch& L) {
+        const BatchProblem& b = probs[units[L.unit0].p];  // its first unit is its largest
+        return (long long)b.L * b.M << b.n;
+      };
+      std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return work(launches[x]) > work(launches[y]); });
+      std::vector<Launch> sorted;
+      for (int i : ord) sorted.push_back(launches[i]);
+      launches.swap(sorted);
+    }
+    if ((int)launches.size() > 60) return fail(QFS_EUNSUPPORTED, "too many launch shapes (%d)", (int)launches.size());
+    CK(cudaMemcpyAsync(units_dev, units.data(), sizeof(BatchUnit) * units.size(), cudaMemcpyHostToDevice, st));
+    // The graph: queue reset, set-up, one persistent launch per shape (on
+    // parallel branches), the finishing kernel.  Replayed while the batch's
+    // shape, parameters and workspace stay the same.
+    uint64_t key = 1469598103934665603ULL;
+    {
+      const int sc[] = {P, S, a.max_sweeps, a.plateau_window, a.min_sweeps, a.refine_max, (int)in.sweep_once,
+                        (int)launches.size()};
+      key = fnv1a(key, sc, sizeof(sc));
+      const double sd[] = {a.tol, a.diff_tol_r};
+      key = fnv1a(key, sd, sizeof(sd));
+      key = fnv1a(key, &w, sizeof(w));
+      key = fnv1a(key, ns, sizeof(int32_t) * P);
+      key = fnv1a(key, Ls, sizeof(int32_t) * P);
+      key = fnv1a(key, launches.data(), sizeof(Launch) * launches.size());
+      const int mm[] = {p->M, max_elems, max_L};
+      key = fnv1a(key, mm, sizeof(mm));
+    }
+    // With per-launch timing on, the graph carries this call's event records:
+    // it is captured, replayed once, harvested and dropped.
+    const bool cache = !ctx->prof.on;
+    qfs_ctx::BatchGraph* bg = nullptr;
+    qfs_ctx::BatchGraph once;
+    if (cache)
+      for (auto& g : ctx->batch_graphs)
+        if (g.key == key && g.exec) bg = &g;
+    if (!bg) {
+      if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+      TRY(ensure_group_streams(ctx, std::min<int>(kMaxGroups, (int)launches.size())));
+      long long before[QFS_PROF_KINDS];
+      for (int i = 0; i < QFS_PROF_KINDS; ++i) before[i] = ctx->prof.launches[i];
+      cudaStream_t cs = ctx->cap_stream;
+      CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+      ctx->prof.capturing = true;
+      cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(int) * 64, cs);
       {
-        ProfScope ps(ctx, QFS_PROF_BATCH, 0.0, ls);
-        launch_batch_sweep(L.G, a, units_dev + L.unit0, L.nunits, a.queue + li, blocks, L.warps, L.max_elems,
-                           L.max_L, ls);
+        ProfScope ps(ctx, QFS_PROF_OTHER, 0.0, cs);
+        launch_batch_prep(a, cs);
       }
-      if (li > 0) {
-        e = cudaEventRecord(ctx->gevent[gs], ls);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->gevent[gs], 0);
+      if (e == cudaSuccess) e = cudaEventRecord(ctx->fork_event, cs);
+      for (size_t li = 0; li < launches.size() && e == cudaSuccess; ++li) {
+        const Launch& L = launches[li];
+        const size_t smem = batch_sweep_smem(L.G, L.warps, L.max_elems, L.max_L);
+        const int bps = std::max(1, batch_sweep_blocks_per_sm(L.G, L.warps, smem));
+        const int blocks = std::max(1, std::min(ctx->num_sms * bps, (L.nunits + L.warps - 1) / L.warps));
+        const int gs = (int)(li % kMaxGroups);
+        cudaStream_t ls = li == 0 ? cs : ctx->gstream[gs];
+        if (li > 0) e = cudaStreamWaitEvent(ls, ctx->fork_event, 0);
+        if (e != cudaSuccess) break;
+        {
+          ProfScope ps(ctx, QFS_PROF_BATCH, 0.0, ls);
+          launch_batch_sweep(L.G, a, units_dev + L.unit0, L.nunits, a.queue + li, blocks, L.warps, L.max_elems,
+                             L.max_L, ls);
+        }
+        if (li > 0) {
+          e = cudaEventRecord(ctx->gevent[gs], ls);
+          if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->gevent[gs], 0);
+        }
+      }
+      if (!in.sweep_once) {
+        ProfScope ps(ctx, QFS_PROF_CHECK, 0.0, cs);
+        launch_batch_finalize(a, cs);
+      }
+      ctx->prof.capturing = false;
+      cudaGraph_t graph = nullptr;
+      const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+      if (e == cudaSuccess) e = e2;
+      qfs_ctx::BatchGraph ng;
+      ng.key = key;
+      for (int i = 0; i < QFS_PROF_KINDS; ++i) {
+        ng.launches[i] = ctx->prof.launches[i] - before[i];
+        ctx->prof.launches[i] = before[i];
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&ng.exec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        if (ng.exec) cudaGraphExecDestroy(ng.exec);
+        prof_release_graph(ctx);
+        CK(e);
+      }
+      if (cache) {
+        if (ctx->batch_graphs.size() >= 4) {
+          cudaGraphExecDestroy(ctx->batch_graphs.front().exec);
+          ctx->batch_graphs.erase(ctx->batch_graphs.begin());
+        }
+        ctx->batch_graphs.push_back(ng);
+        bg = &ctx->batch_graphs.back();
+      } else {
+        once = ng;
+        bg = &once;
       }
     }
-    if (!in.sweep_once) {
-      ProfScope ps(ctx, QFS_PROF_CHECK, 0.0, cs);
-      launch_batch_finalize(a, cs);
-    }
-    ctx->prof.capturing = false;
-    cudaGraph_t graph = nullptr;
-    const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
-    if (e == cudaSuccess) e = e2;
-    qfs_ctx::BatchGraph ng;
-    ng.key = key;
-    for (int i = 0; i < QFS_PROF_KINDS; ++i) {
-      ng.launches[i] = ctx->prof.launches[i] - before[i];
-      ctx->prof.launches[i] = before[i];
-    }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&ng.exec, graph, 0);
-    if (graph) cudaGraphDestroy(graph);
-    if (e != cudaSuccess) {
-      if (ng.exec) cudaGraphExecDestroy(ng.exec);
+    const cudaError_t el = cudaGraphLaunch(bg->exec, st);
+    for (int i = 0; i < QFS_PROF_KINDS; ++i) ctx->prof.launches[i] += bg->launches[i];
+    if (!cache) {
+      const cudaError_t es = cudaStreamSynchronize(st);
+      if (el == cudaSuccess && es == cudaSuccess) prof_harvest_graph(ctx);
       prof_release_graph(ctx);
-      CK(e);
+      cudaGraphExecDestroy(once.exec);
+      CK(el);
+      CK(es);
     }
-    if (cache) {
-      if (ctx->batch_graphs.size() >= 4) {
-        cudaGraphExecDestroy(ctx->batch_graphs.front().exec);
-        ctx->batch_graphs.erase(ctx->batch_graphs.begin());
-      }
-      ctx->batch_graphs.push_back(ng);
-      bg = &ctx->batch_graphs.back();
-    } else {
-      once = ng;
-      bg = &once;
-    }
-  }
-  const cudaError_t el = cudaGraphLaunch(bg->exec, st);
-  for (int i = 0; i < QFS_PROF_KINDS; ++i) ctx->prof.launches[i] += bg->launches[i];
-  if (!cache) {
-    const cudaError_t es = cudaStreamSynchronize(st);
-    if (el == cudaSuccess && es == cudaSuccess) prof_harvest_graph(ctx);
-    prof_release_graph(ctx);
-    cudaGraphExecDestroy(once.exec);
     CK(el);
-    CK(es);
+    return QFS_OK;
+  };
+
+  // Plans: the per-class shapes, and (when they differ from it) every class
+  // with one start per warp.  The autotuner's per-class trials measure
+  // throughput at full occupancy, but a lane-group unit sweeps its starts
+  // one warp-update after another, so it lives 32 / G times longer than a
+  // warp-per-start unit; when the starts of a problem run long (a problem
+  // that does not converge runs all of them to max_sweeps) such units set
+  // the batch's makespan.  So the first call of a batch shape times both
+  // plans on the batch itself and keeps the faster (cached per shape).
+  bool mixed = false;
+  for (const BatchClass& c : classes) mixed |= c.G != 32;
+  if (mixed && ctx->batch_force_G == 0) {
+    std::vector<BatchClass> all32 = classes;
+    for (BatchClass& c : all32) c.G = 32;
+    uint64_t pk = 1469598103934665603ULL;
+    {
+      const int sc[] = {P, S, a.max_sweeps, a.plateau_window, a.min_sweeps};
+      pk = fnv1a(pk, sc, sizeof(sc));
+      pk = fnv1a(pk, ns, sizeof(int32_t) * P);
+      pk = fnv1a(pk, Ls, sizeof(int32_t) * P);
+      const double sd[] = {a.tol, a.diff_tol_r};
+      pk = fnv1a(pk, sd, sizeof(sd));
+    }
+    int choice = -1;
+    for (auto& kv : ctx->batch_plans)
+      if (kv.first == pk) choice = kv.second;
+    if (choice < 0) {
+      cudaEvent_t e0, e1;
+      CK(cudaEventCreate(&e0));
+      CK(cudaEventCreate(&e1));
+      float ms[2] = {0.f, 0.f};
+      for (int k = 0; k < 2; ++k) {
+        CK(cudaEventRecord(e0, st));
+        const int rc = launch_plan(k == 0 ? classes : all32);
+        if (rc != QFS_OK) {
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          return rc;
+        }
+        CK(cudaEventRecord(e1, st));
+        CK(cudaEventSynchronize(e1));
+        CK(cudaEventElapsedTime(&ms[k], e0, e1));
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      choice = ms[0] < ms[1] ? 0 : 1;
+      ctx->batch_plans.push_back({pk, choice});
+      ctx->batch_plan_ms.push_back({ms[0], ms[1]});
+    }
+    if (choice == 1) classes = all32;
   }
-  CK(el);
+  TRY(launch_plan(classes));
   if (in.sweep_once) {
     std::vector<float2> g32(gate_off);
     std::vector<double> fc((size_t)P * S);
@@ -2504,13 +2574,22 @@ extern "C" int qfs_instantiate_batch_dev(qfs_ctx* ctx, int32_t P, const int32_t*
 }
 
 extern "C" int qfs_batch_schedules(qfs_ctx* ctx, int32_t cap, int32_t* tuned, int32_t* n_tuned, int32_t* trials,
-                                   double* trial_ns, int32_t* n_trials) {
+                                   double* trial_ns, int32_t* n_trials, int32_t* plan_choice, double* plan_ms,
+                                   int32_t* n_plans) {
   g_err.clear();
   TRY(ctx_check(ctx));
+  if (n_plans) *n_plans = (int32_t)ctx->batch_plans.size();
+  for (int i = 0; i < cap && i < (int)ctx->batch_plans.size(); ++i) {
+    if (plan_choice) plan_choice[i] = ctx->batch_plans[i].second;
+    if (plan_ms) {
+      plan_ms[2 * i] = ctx->batch_plan_ms[i].first;
+      plan_ms[2 * i + 1] = ctx->batch_plan_ms[i].second;
+    }
+  }
   if (n_tuned) *n_tuned = (int32_t)ctx->batch_tuned.size();
   if (n_trials) *n_trials = (int32_t)ctx->batch_trial_ns.size();
   for (int i = 0; tuned && i < cap && i < (int)ctx->batch_tuned.size(); ++i) {
-    const long long k = ctx->batch_tuned[i].first;
+    const long long k = ctx->batch_tuned[i].first / 2;
     const int S = (int)(k % 128), M = (int)((k / 128) % 4096), L = (int)((k / 128 / 4096) % 64),
               n = (int)(k / 128 / 4096 / 64);
     const int v[6] = {n, L, M, S, ctx->batch_tuned[i].second.first, ctx->batch_tuned[i].second.second};

@@ -341,8 +341,12 @@ __device__ __forceinline__ float2 jacobi32_sweeps(float2 x, bool* rotated_out = 
       if (ag2 > 1e-13f * alpha * beta && ag2 > 1e-36f) {
         const float rg = rsqrtf(ag2);
         const float zeta = 0.5f * (beta - alpha) * rg;
-        const float t = fabsf(zeta) > 1e18f ? 0.5f / zeta
-                                             : copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+        // t = sign(zeta) / (|zeta| + sqrt(zeta^2 + 1)) with the hardware
+        // reciprocal and square root: the angle only has to shrink gamma,
+        // the convergence test below decides, and V is renormalised.
+        const float q = fmaf(zeta, zeta, 1.f);
+        const float t = fabsf(zeta) > 1e18f ? __fdividef(0.5f, zeta)
+                                             : copysignf(__fdividef(1.f, fabsf(zeta) + q * rsqrtf(q)), zeta);
         cs = rsqrtf(fmaf(t, t, 1.f));
         sn = t * cs;
         px = g.x * rg;
@@ -458,8 +462,8 @@ __device__ __forceinline__ bool warp_polar4_fast(double2 a, double2 v0, double2*
   smin = fminf(smin, __shfl_xor_sync(FULL, smin, 4));
   smin = fminf(smin, __shfl_xor_sync(FULL, smin, 8));
   if (!(smin > 1e-6f * smax)) return false;  // sigma_min < 1e-3 sigma_max
-  const float sig = sqrtf(nrm);               // sigma of column `col` (scaled)
-  const float inv = 1.f / sig;
+  const float inv = rsqrtf(nrm);
+  const float sig = nrm * inv;                // sigma of column `col` (scaled)
   w = float2{w.x * inv, w.y * inv};
   // Q0 = W V^H (FP32, unitary to ~1e-6), promoted; two Newton-Schulz steps
   // in FP64 make it unitary to rounding.

@@ -674,8 +674,8 @@ __device__ __forceinline__ bool df_polar_begin(double2 a, double2 v0, DfUpd& u) 
   smin = fminf(smin, __shfl_xor_sync(FULL, smin, 4));
   smin = fminf(smin, __shfl_xor_sync(FULL, smin, 8));
   if (!(smin > 1e-6f * smax)) return false;
-  const float sig = sqrtf(nrm);
-  const float inv = 1.f / sig;
+  const float inv = rsqrtf(nrm);
+  const float sig = nrm * inv;
   w = float2{w.x * inv, w.y * inv};
   const float2 q32 = mm_bh(w, v, row, col);
   if (!isV) {

@@ -32,6 +32,7 @@ QFS_OPT_FUSED_UPDATE = 2
 QFS_OPT_DATAFLOW = 3
 QFS_OPT_TWO_GATE_FORWARD = 4
 QFS_OPT_FP64_TARGET_PRODUCT = 5
+QFS_OPT_BATCH_LANES_PER_START = 6
 QFS_FP64 = 0
 QFS_MIXED = 1
 QFS_STATES_HAAR = 0
@@ -135,7 +136,8 @@ def lib():
                                          C.c_double, _P, _P, _P, _P]
     L.qfs_profile_enable.argtypes = [_P, C.c_int]
     L.qfs_set_option.argtypes = [_P, C.c_int32, C.c_int64]
-    L.qfs_batch_schedules.argtypes = [_P, C.c_int32, _P, C.POINTER(C.c_int32), _P, _P, C.POINTER(C.c_int32)]
+    L.qfs_batch_schedules.argtypes = [_P, C.c_int32, _P, C.POINTER(C.c_int32), _P, _P, C.POINTER(C.c_int32),
+                                      _P, _P, C.POINTER(C.c_int32)]
     L.qfs_ws_instantiate.argtypes = [_P, C.c_int32, _P, _P, C.POINTER(Params), C.c_int32, _P, _P,
                                      C.POINTER(C.c_int64)]
     L.qfs_batch_sweep_once.argtypes = [_P, C.c_int32, _P, _P, _P, _P, _P, C.c_int32, C.c_int32, _P, C.c_int32,
@@ -399,15 +401,21 @@ class Context:
     def batch_schedules(self):
         """The batched form's tuned shapes: (list of dicts per class, list of
         dicts per timed trial)."""
-        nt, nr = C.c_int32(), C.c_int32()
-        _check(lib().qfs_batch_schedules(self._h, 0, None, C.byref(nt), None, None, C.byref(nr)))
-        cap = max(nt.value, nr.value, 1)
+        nt, nr, npl = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(lib().qfs_batch_schedules(self._h, 0, None, C.byref(nt), None, None, C.byref(nr), None, None,
+                                         C.byref(npl)))
+        cap = max(nt.value, nr.value, npl.value, 1)
         tuned = np.zeros((cap, 6), dtype=np.int32)
         trials = np.zeros((cap, 6), dtype=np.int32)
         tns = np.zeros(cap)
+        pc = np.zeros(cap, dtype=np.int32)
+        pms = np.zeros((cap, 2))
         _check(lib().qfs_batch_schedules(self._h, cap, tuned.ctypes.data, C.byref(nt), trials.ctypes.data,
-                                         tns.ctypes.data, C.byref(nr)))
+                                         tns.ctypes.data, C.byref(nr), pc.ctypes.data, pms.ctypes.data,
+                                         C.byref(npl)))
         keys = ("n", "L", "M", "S", "G", "warps")
+        self.batch_plans = [dict(choice=int(c), ms_per_class=float(m[0]), ms_warp_per_start=float(m[1]))
+                            for c, m in zip(pc[:npl.value], pms[:npl.value])]
         return ([dict(zip(keys, map(int, r))) for r in tuned[:nt.value]],
                 [dict(zip(keys, map(int, r)), ns_per_start_sweep=float(t)) for r, t in zip(trials[:nr.value],
                                                                                              tns[:nr.value])])
