@@ -57,16 +57,21 @@ def _check_against_oracle_cost(p, Psi, got):
     assert abs(c - got.cost) < 1e-11, (c, got.cost)
 
 
-@pytest.mark.parametrize("sd", ["0", "1", "2", "3"])
+@pytest.mark.parametrize("sd", [str(i) for i in range(12)])
 def test_brick_n12_mixed_instantiation_matches_oracle_run(ctx, sd):
     from paper_2405_12866_gb300 import qfs
-    g = _golden("brick_n12_oracle_runs.json")[sd]
+    runs = _golden("brick_n12_oracle_runs.json")
+    if sd not in runs:
+        pytest.skip(f"no oracle run of target {sd} recorded")
+    g = runs[sd]
     p = w.brick_n12(target_seed=int(sd))
     assert g["run_seed"] == p.seed and g["tol"] == p.tol
     Psi, G0 = p.samples(), p.init_gates()
     prm = qfs.default_params(M=p.M, multistarts=p.S, max_sweeps=p.max_sweeps, dist_tol=p.tol,
                              precision=qfs.QFS_MIXED)
     got = ctx.instantiate(p.n, p.pairs, p.U, prm, Psi, G0)
+    print(f"\ntarget {sd}: sweeps {got.sweeps} (oracle {g['sweeps']}), start {got.best_start} "
+          f"(oracle {g['best_start']}), FP64 sweeps {got.fp64_sweeps}, cost {got.cost:.3e}")
     assert got.converged == g["converged"]
     assert got.best_start == g["best_start"]
     assert abs(got.sweeps - g["sweeps"]) <= K_MIXED, (got.sweeps, g["sweeps"])
@@ -82,6 +87,7 @@ def test_brick_n12_forced_fp64_refinement_matches_oracle_run(ctx, sd):
     prm = qfs.default_params(M=p.M, multistarts=p.S, max_sweeps=p.max_sweeps, dist_tol=p.tol,
                              precision=qfs.QFS_MIXED, refine_switch_tol=1e-5, refine_sweeps_max=50)
     got = ctx.instantiate(p.n, p.pairs, p.U, prm, Psi, G0)
+    print(f"\ntarget {sd}: complex64 sweeps {got.sweeps} + FP64 sweeps {got.fp64_sweeps} (oracle {g['sweeps']})")
     assert got.fp64_sweeps > 0
     assert got.converged == g["converged"]
     assert got.best_start == g["best_start"]
