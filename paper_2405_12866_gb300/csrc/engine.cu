@@ -2469,12 +2469,18 @@ int batch_common(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls, 
   if (mixed && ctx->batch_force_G == 0) {
     std::vector<BatchClass> all32 = classes;
     for (BatchClass& c : all32) c.G = 32;
+    // The decision is kept per class mix (the set of classes and their
+    // shares of the batch, in tenths) and run parameters, so batches of the
+    // same composition but another size reuse it.
     uint64_t pk = 1469598103934665603ULL;
     {
-      const int sc[] = {P, S, a.max_sweeps, a.plateau_window, a.min_sweeps};
+      const int sc[] = {S, a.max_sweeps, a.plateau_window, a.min_sweeps};
       pk = fnv1a(pk, sc, sizeof(sc));
-      pk = fnv1a(pk, ns, sizeof(int32_t) * P);
-      pk = fnv1a(pk, Ls, sizeof(int32_t) * P);
+      std::vector<std::pair<long long, int>> mix;
+      for (const BatchClass& c : classes)
+        mix.push_back({batch_class_key(c.n, c.L, c.M, S, true), (int)(10 * c.problems.size() / P)});
+      std::sort(mix.begin(), mix.end());
+      for (auto& m : mix) pk = fnv1a(pk, &m, sizeof(m));
       const double sd[] = {a.tol, a.diff_tol_r};
       pk = fnv1a(pk, sd, sizeof(sd));
     }
