@@ -467,7 +467,9 @@ int qfs_ws_instantiate(qfs_ws* ws, int32_t P, const double* targets, const doubl
  * in the same call, so nothing has to be cleared between calls, but calls
  * that overlap on the GPU (two streams, or two host threads) race on it.
  * The first call on each device looks up the array's device address with
- * cudaGetSymbolAddress (with that device current) and caches it; make that
+ * cudaGetSymbolAddress (with that device current) and caches it for the
+ * rest of the process, which assumes the device's primary context lives as
+ * long (after a cudaDeviceReset the cached address is stale); make that
  * first call before any stream capture. */
 #define QFS_NOALLOC_SCRATCH_BYTES (16u << 20)
 int qfs_sweep_once_noalloc(void* cuda_stream, const qfs_circuit* circuit, const double* target_dev,

@@ -276,10 +276,15 @@ struct GemmArgs {
   int M, N, K, M_valid;
   int* err;
   int splitk = 1;  // > 1: K split over grid z, partial tiles added into C32 (C32 only)
+  int sms = 0;     // SMs of the device (> 0: products with fewer 128 x 256 tiles than SMs take
+                   // 128 x 128 tiles, two CTAs per SM)
 };
 cudaError_t launch_gemm_bf16_tc(const GemmArgs& g, cudaStream_t st);
 // Split-K factor that fills the GPU for a C32-only product (1 otherwise).
 int gemm_splitk_for(const GemmArgs& g, int num_sms);
+// Tile width of a product: 256 when N allows it and the 128 x 256 tiles fill
+// every SM (or the SM count is unknown), else 128.
+int gemm_bn_for(const GemmArgs& g);
 
 void launch_ws_features(const double2* U, const double2* phif, int count, int rows, __nv_bfloat16* X,
                         cudaStream_t st);
