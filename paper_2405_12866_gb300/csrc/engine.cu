@@ -2662,7 +2662,6 @@ extern "C" int qfs_gemm_bf16_dev(qfs_ctx* ctx, int32_t M, int32_t N, int32_t K, 
              C32, reinterpret_cast<__nv_bfloat16*>(C16), ldc, bias, gelu, M, N, K,
              M_valid > 0 ? M_valid : M, err};
   g.splitk = gemm_splitk_for(g, ctx->num_sms > 0 ? ctx->num_sms : 148);
-  g.sms = ctx->num_sms;
   {
     ProfScope ps(ctx, QFS_PROF_MLP, 2.0 * M * N * K, st);
     CK(launch_gemm_bf16_tc(g, st));
@@ -2734,7 +2733,6 @@ int ws_gemm(qfs_ws* m, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, 
             float* C32, __nv_bfloat16* C16, int ldc, const float* bias, int gelu, int M_valid) {
   GemmArgs g{A, lda, B, ldb, C32, C16, ldc, bias, gelu, M, N, K, M_valid, m->err};
   g.splitk = gemm_splitk_for(g, m->ctx->num_sms > 0 ? m->ctx->num_sms : 148);
-  g.sms = m->ctx->num_sms;
   ProfScope ps(m->ctx, QFS_PROF_MLP, 2.0 * M * N * K);
   CK(launch_gemm_bf16_tc(g, m->ctx->stream));
   return QFS_OK;

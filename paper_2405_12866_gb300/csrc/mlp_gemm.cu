@@ -4,7 +4,7 @@
 // memory (TMEM).
 //
 // k_gemm_bf16_tma: a warp-specialised pipeline.  Warp 0
-// issues TMA tile loads (128-byte swizzle) into a ring of ST shared
+// issues TMA tile loads (128-byte swizzle) into a ring of kStages shared
 // stages, each tracked by a "full" mbarrier (transaction bytes) and an
 // "empty" mbarrier; warp 1 owns the TMEM accumulator (128 x BN fp32
 // columns) and one of its threads issues the tcgen05.mma chain, releasing
@@ -16,7 +16,6 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
-#include <algorithm>
 #include <cstdlib>
 
 #include "qfs_kernels.h"
@@ -53,13 +52,10 @@ __device__ __forceinline__ float gelu_tanh(float x) {
 
 namespace {
 
-constexpr int kBM = 128, kBK = 64, kTmaThreads = 192;
+constexpr int kBM = 128, kBK = 64, kStages = 4, kTmaThreads = 192;
 
-// BN = 256 with 4 stages (one CTA per SM), or BN = 128 with 3 stages (two
-// CTAs per SM, whose main loops and epilogues interleave).
-template <int BN, int ST>
+template <int BN>
 struct TmaCfg {
-  static constexpr int kStages = ST;
   static constexpr int kABytes = kBM * kBK * 2;
   static constexpr int kBBytes = BN * kBK * 2;
   static constexpr int kStageBytes = kABytes + kBBytes;
@@ -95,11 +91,10 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
 
 }  // namespace
 
-template <int BN, int ST>
-__global__ void __launch_bounds__(kTmaThreads, ST == 3 ? 2 : 1)
+template <int BN>
+__global__ void __launch_bounds__(kTmaThreads, 1)
     k_gemm_bf16_tma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, GemmArgs g) {
-  using Cfg = TmaCfg<BN, ST>;
-  constexpr int kStages = Cfg::kStages;
+  using Cfg = TmaCfg<BN>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const uint32_t raw = su32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -311,26 +306,20 @@ bool encode_kmajor(CUtensorMap* map, const void* ptr, int rows, int K, int ld, i
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN, int ST>
+template <int BN>
 cudaError_t launch_tma(const GemmArgs& g, int splitk, cudaStream_t st) {
-  static const cudaError_t attr = cudaFuncSetAttribute(
-      k_gemm_bf16_tma<BN, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, TmaCfg<BN, ST>::kSmem);
+  static const cudaError_t attr = cudaFuncSetAttribute(k_gemm_bf16_tma<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       TmaCfg<BN>::kSmem);
   if (attr != cudaSuccess) return attr;
   CUtensorMap ma, mb;
   if (!encode_kmajor(&ma, g.A, g.M, g.K, g.lda, kBM) || !encode_kmajor(&mb, g.B, g.N, g.K, g.ldb, BN))
     return cudaErrorInvalidValue;
   dim3 grid(g.N / BN, g.M / kBM, splitk);
-  k_gemm_bf16_tma<BN, ST><<<grid, kTmaThreads, TmaCfg<BN, ST>::kSmem, st>>>(ma, mb, g);
+  k_gemm_bf16_tma<BN><<<grid, kTmaThreads, TmaCfg<BN>::kSmem, st>>>(ma, mb, g);
   return cudaGetLastError();
 }
 
 }  // namespace
-
-int gemm_bn_for(const GemmArgs& g) {
-  if (g.N % 256 != 0) return 128;
-  if (g.sms > 0 && (g.N / 256) * (g.M / kBM) * std::max(g.splitk, 1) < g.sms) return 128;
-  return 256;
-}
 
 int gemm_splitk_for(const GemmArgs& g, int num_sms) {
   if (g.C16 || g.bias || g.gelu || !g.C32) return 1;
@@ -349,7 +338,7 @@ cudaError_t launch_gemm_bf16_tc(const GemmArgs& g, cudaStream_t st) {
     const cudaError_t e = cudaMemset2DAsync(g.C32, (size_t)g.ldc * 4, 0, (size_t)g.N * 4, g.M_valid, st);
     if (e != cudaSuccess) return e;
   }
-  return gemm_bn_for(g) == 256 ? launch_tma<256, 4>(g, splitk, st) : launch_tma<128, 3>(g, splitk, st);
+  return g.N % 256 == 0 ? launch_tma<256>(g, splitk, st) : launch_tma<128>(g, splitk, st);
 }
 
 }  // namespace qfs
