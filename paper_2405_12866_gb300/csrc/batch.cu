@@ -158,6 +158,177 @@ __device__ void warp_update<double2>(double2 e, double2* g, double2* sm, float2*
   __syncwarp();
 }
 
+// ---------------------------------------------------------------------------
+// Two updates side by side, one per 16-lane half of the warp (the schedule
+// with 16 lanes per start).  Each lane of a half holds one entry of X = A V
+// and the same entry of V (M[row][col] at lane 4 col + row of the half), so
+// a Jacobi round needs no exchange between an X lane and a V lane; every
+// shuffle stays inside its half (width 16).
+
+__device__ __forceinline__ float2 shfl16(float2 v, int src) {
+  return float2{__shfl_sync(FULL, v.x, src, 16), __shfl_sync(FULL, v.y, src, 16)};
+}
+__device__ __forceinline__ float2 mm16(float2 a, float2 b, int row, int col) {
+  float2 acc{0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) acc = cfma(shfl16(a, 4 * k + row), shfl16(b, 4 * col + k), acc);
+  return acc;
+}
+__device__ __forceinline__ float2 mm16_ah(float2 a, float2 b, int row, int col) {
+  float2 acc{0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float2 ak = shfl16(a, 4 * row + k), bk = shfl16(b, 4 * col + k);
+    acc = cfma(float2{ak.x, -ak.y}, bk, acc);
+  }
+  return acc;
+}
+__device__ __forceinline__ float2 mm16_bh(float2 a, float2 b, int row, int col) {
+  float2 acc{0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float2 ak = shfl16(a, 4 * k + row), bk = shfl16(b, 4 * k + col);
+    acc = cfma(ak, float2{bk.x, -bk.y}, acc);
+  }
+  return acc;
+}
+// Whether every column pair of this half's X has |gamma|^2 <= 1e-13 alpha
+// beta (the Gram-matrix test of jacobi32_converged), as a warp-uniform
+// two-bit mask (bit h: half h).
+__device__ __forceinline__ unsigned half_converged(float2 x, int row, int col) {
+  const float2 g = mm16_ah(x, x, row, col);
+  const float dr = __shfl_sync(FULL, g.x, 5 * row, 16), dc = __shfl_sync(FULL, g.x, 5 * col, 16);
+  const bool ok = row == col || (g.x * g.x + g.y * g.y) <= 1e-13f * dr * dc;
+  const unsigned b = __ballot_sync(FULL, ok);
+  return ((b & 0xffffu) == 0xffffu ? 1u : 0u) | ((b >> 16) == 0xffffu ? 2u : 0u);
+}
+
+// The polar factor of A (A[row][col] at lane 4 col + row of each half), the
+// Jacobi started from V0 = v_io (that half's gate's right singular vectors
+// from its previous update) and the new V written back, as
+// warp_polar4_f32_warm does for one matrix.  Returns, warp-uniformly, a
+// two-bit mask of the halves whose fast path succeeded; a half that failed
+// (zero or too ill-conditioned) has not written v_io and its *q_out is
+// undefined.  `act` (per half): whether this half's result is wanted.
+__device__ unsigned halfwarp_polar4_f32_warm(float2 a, float2* v_io, bool act, float2* q_out) {
+  const int lane = threadIdx.x & 31;
+  const int l16 = lane & 15, row = l16 & 3, col = l16 >> 2, h = lane >> 4;
+  const float2 v0 = act ? v_io[l16] : float2{row == col ? 1.f : 0.f, 0.f};
+  if (!act) a = float2{row == col ? 1.f : 0.f, 0.f};
+  float2 x = mm16(a, v0, row, col);
+  float2 v = v0;
+  unsigned done = half_converged(x, row, col);
+  bool rotated = false;
+  for (int sweep = 0; sweep < 12 && done != 3u; ++sweep) {
+    const bool mine_done = (done >> h) & 1u;
+    bool any = false;
+#pragma unroll
+    for (int m = 1; m <= 3; ++m) {
+      const float2 y = shfl16(x, l16 ^ (4 * m)), yv = shfl16(v, l16 ^ (4 * m));
+      const bool isP = col < (col ^ m);
+      float nown = x.x * x.x + x.y * x.y;
+      float npar = y.x * y.x + y.y * y.y;
+      float2 g = isP ? float2{x.x * y.x + x.y * y.y, x.x * y.y - x.y * y.x}
+                     : float2{y.x * x.x + y.y * x.y, y.x * x.y - y.y * x.x};
+#pragma unroll
+      for (int o = 1; o <= 2; o <<= 1) {
+        nown += __shfl_xor_sync(FULL, nown, o);
+        npar += __shfl_xor_sync(FULL, npar, o);
+        g.x += __shfl_xor_sync(FULL, g.x, o);
+        g.y += __shfl_xor_sync(FULL, g.y, o);
+      }
+      const float alpha = isP ? nown : npar, beta = isP ? npar : nown;
+      const float ag2 = g.x * g.x + g.y * g.y;
+      float cs = 1.f, sn = 0.f, px = 1.f, py = 0.f;
+      if (!mine_done && ag2 > 1e-13f * alpha * beta && ag2 > 1e-36f) {
+        const float rg = rsqrtf(ag2);
+        const float zeta = 0.5f * (beta - alpha) * rg;
+        const float q = fmaf(zeta, zeta, 1.f);
+        const float t = fabsf(zeta) > 1e18f ? __fdividef(0.5f, zeta)
+                                             : copysignf(__fdividef(1.f, fabsf(zeta) + q * rsqrtf(q)), zeta);
+        cs = rsqrtf(fmaf(t, t, 1.f));
+        sn = t * cs;
+        px = g.x * rg;
+        py = -g.y * rg;
+        any = true;
+      }
+      if (isP) {
+        const float tx = px * y.x - py * y.y, ty = px * y.y + py * y.x;
+        const float ux = px * yv.x - py * yv.y, uy = px * yv.y + py * yv.x;
+        x = float2{cs * x.x - sn * tx, cs * x.y - sn * ty};
+        v = float2{cs * v.x - sn * ux, cs * v.y - sn * uy};
+      } else {
+        const float tx = px * x.x - py * x.y, ty = px * x.y + py * x.x;
+        const float ux = px * v.x - py * v.y, uy = px * v.y + py * v.x;
+        x = float2{sn * y.x + cs * tx, sn * y.y + cs * ty};
+        v = float2{sn * yv.x + cs * ux, sn * yv.y + cs * uy};
+      }
+    }
+    // A half with no rotation in a whole sweep is done; else the Gram test.
+    const unsigned b = __ballot_sync(FULL, any);
+    rotated |= ((b >> (16 * h)) & 0xffffu) != 0u;
+    const unsigned none = ((b & 0xffffu) == 0u ? 1u : 0u) | ((b >> 16) == 0u ? 2u : 0u);
+    done |= none;
+    if (done != 3u) done |= half_converged(x, row, col);
+  }
+  float nrm = x.x * x.x + x.y * x.y;
+  nrm += __shfl_xor_sync(FULL, nrm, 1);
+  nrm += __shfl_xor_sync(FULL, nrm, 2);
+  float smax = nrm, smin = nrm;
+  smax = fmaxf(smax, __shfl_xor_sync(FULL, smax, 4));
+  smax = fmaxf(smax, __shfl_xor_sync(FULL, smax, 8));
+  smin = fminf(smin, __shfl_xor_sync(FULL, smin, 4));
+  smin = fminf(smin, __shfl_xor_sync(FULL, smin, 8));
+  const bool good = smin > 1e-6f * smax;
+  const unsigned gb = __ballot_sync(FULL, good);
+  const unsigned okmask = ((gb & 0xffffu) == 0xffffu ? 1u : 0u) | ((gb >> 16) == 0xffffu ? 2u : 0u);
+  const float inv = rsqrtf(good ? nrm : 1.f);
+  const float2 w{x.x * inv, x.y * inv};
+  float2 q = mm16_bh(w, v, row, col);
+  const float2 gq = mm16_ah(q, q, row, col);
+  const float2 tq{(row == col ? 1.5f : 0.f) - 0.5f * gq.x, -0.5f * gq.y};
+  *q_out = mm16(q, tq, row, col);
+  // Renormalise a rotated V (one Newton-Schulz step) so no drift
+  // accumulates over sweeps; an unrotated V is the stored one.
+  if (__any_sync(FULL, rotated)) {
+    const float2 gv = mm16_ah(v, v, row, col);
+    const float2 tv{(row == col ? 1.5f : 0.f) - 0.5f * gv.x, -0.5f * gv.y};
+    v = mm16(v, tv, row, col);
+    __syncwarp();
+    if (act && ((okmask >> h) & 1u) && rotated) v_io[l16] = v;
+  }
+  __syncwarp();
+  return okmask;
+}
+
+// The unit's two gate updates at once (16 lanes per start): half h updates
+// the gate of start h from its environment e (E[c][r] at lane 4c + r of the
+// half).  A half whose fast path fails takes the FP64 Jacobi (warp-wide, one
+// half after the other), as warp_update does.
+__device__ void halfwarp_update(float2 e, float2* g, double2* sm, float2* v, bool act) {
+  const int lane = threadIdx.x & 31;
+  const int l16 = lane & 15, r = l16 & 3, c = l16 >> 2, h = lane >> 4;
+  const float2 a32{e.x, -e.y};  // A[r][c] = conj(E[c][r])
+  float2 q;
+  const unsigned act_mask = __ballot_sync(FULL, act);
+  const unsigned acts = ((act_mask & 0xffffu) ? 1u : 0u) | ((act_mask >> 16) ? 2u : 0u);
+  const unsigned ok = halfwarp_polar4_f32_warm(a32, v, act, &q);
+  for (int hh = 0; hh < 2; ++hh) {
+    if (!((acts >> hh) & 1u) || ((ok >> hh) & 1u)) continue;
+    // The FP64 Jacobi of half hh's matrix on the whole warp: A in lanes 0..15.
+    const float2 ah{__shfl_sync(FULL, a32.x, 16 * hh + l16), __shfl_sync(FULL, a32.y, 16 * hh + l16)};
+    const double2 p = warp_polar4(double2{(double)ah.x, (double)ah.y}, double2{r == c ? 1.0 : 0.0, 0.0}, sm, nullptr);
+    const float2 pf{(float)p.x, (float)p.y};
+    const float2 pq{__shfl_sync(FULL, pf.x, l16), __shfl_sync(FULL, pf.y, l16)};
+    if (h == hh) {
+      q = pq;
+      v[l16] = float2{r == c ? 1.f : 0.f, 0.f};  // restart from the identity
+    }
+  }
+  if (act) g[4 * r + c] = q;
+  __syncwarp();
+}
+
 // Per-start smem slice (complex64): B (E_max), Phi (E_max), gates (16 L_max),
 // right singular vectors (16 L_max), environment (16).
 __host__ __device__ __forceinline__ int batch_slice_f2(int max_elems, int max_L) {
@@ -207,6 +378,16 @@ __device__ float group_sweep(float2* slice, int slice_f2, int E_max, int L_max, 
       const int l16 = lane & 15;
       const float2 e{__shfl_sync(FULL, v, 2 * l16), __shfl_sync(FULL, v, 2 * l16 + 1)};
       if (act) warp_update<float2>(e, Gt + 16 * (k - 1), sm, V + 16 * (k - 1));
+    } else if constexpr (G == 16) {
+      // After the reduce-scatter lane gl holds two of its start's 32
+      // environment floats; gather E[c][r] to lane 4c + r of each half
+      // through shared memory, then both starts' updates run side by side.
+      const int base = group_reduce_scatter<G, float>(acc, gl);
+      Env[base] = acc[0];
+      Env[base + 1] = acc[1];
+      __syncwarp();
+      const float2 e{Env[2 * gl], Env[2 * gl + 1]};
+      halfwarp_update(e, Gt + 16 * (k - 1), sm, V + 16 * (k - 1), act);
     } else {
       const int base = group_reduce_scatter<G, float>(acc, gl);
 #pragma unroll
@@ -306,87 +487,95 @@ __global__ void k_batch_prep(BatchArgs a) {
   if (threadIdx.x == 0) a.s_star[p] = INT_MAX;
 }
 
-// Persistent sweep kernel with G lanes per start: warps take units (a
-// problem and 32/G of its starts) until the queue is empty.  slice_f2 is the
-// per-start shared-memory slice in float2 (batch_slice_f2 of the largest
-// problem this launch takes).
+// One unit (a problem and up to 32/G of its starts) swept by the warp to
+// its end, in `region` (the warp's shared memory, laid out for this
+// problem: a slice of batch_slice_f2(N M, L) float2 per start).
 template <int G>
-__global__ void k_batch_sweep(BatchArgs a, const BatchUnit* units, int nunits, int* queue, int slice_f2,
-                              int E_max, int L_max) {
+__device__ __forceinline__ void batch_run_unit(const BatchArgs& a, const BatchUnit& u, float2* region,
+                                               double2* sm_polar) {
   constexpr int NG = 32 / G;
+  const int lane = threadIdx.x & 31;
+  const int gi = lane / G, gl = lane % G;
+  const int p = u.p;
+  const BatchProblem pr = a.probs[p];
+  const int* pairs = a.pairs + pr.pair_off;
+  const int E = pr.M << pr.n, L = pr.L;
+  const int sf = batch_slice_f2(E, L);
+  const int s = u.s0 + gi;
+  bool act = gi < u.ns;
+  float2* mine = region + gi * sf;
+  float2* Gt = mine + 2 * E;
+  float2* V = Gt + 16 * L;
+  const size_t goff = pr.gate_off + (size_t)s * L * 16;
+  if (act) {
+    for (int i = gl; i < 16 * L; i += G) {
+      const double2 g = a.init_gates[goff + i];
+      Gt[i] = float2{(float)g.x, (float)g.y};
+      const int e = i & 15;
+      V[i] = float2{(e & 3) == (e >> 2) ? 1.f : 0.f, 0.f};
+    }
+  }
+  __syncwarp();
+  const float2* psi = a.psi32 + pr.state_off;
+  const float2* phil = a.phil32 + pr.state_off;
+  int conv = INT_MAX, sweeps = 0, stall = 0;
+  // The sweep's cost and the plateau test stay in FP32 (the FP64 pipe
+  // costs 64 cycles per warp instruction); only the tolerance test is FP64.
+  float cost = 4.f, prev = -1.f;
+  const float dtr = (float)a.diff_tol_r;
+  for (int sw = 1; sw <= a.max_sweeps; ++sw) {
+    // A start that has not converged by its problem's earliest converged
+    // sweep can no longer be selected.
+    if (sw > *(volatile int*)(a.s_star + p)) act = false;
+    const unsigned ballot = __ballot_sync(FULL, act && gl == 0);
+    unsigned mask = 0;
+#pragma unroll
+    for (int j = 0; j < NG; ++j) mask |= ((ballot >> (j * G)) & 1u) << j;
+    if (!mask) break;
+    const float c = group_sweep<G>(region, sf, E, L, psi, phil, pairs, pr.n, pr.M, L, sm_polar, act, mask);
+    if (act) {
+      cost = c;
+      sweeps = sw;
+      if ((double)cost <= a.tol) {
+        conv = sw;
+        if (gl == 0) atomicMin(a.s_star + p, sw);
+        act = false;
+      } else if (a.plateau_window > 0 && prev >= 0.f) {
+        // Plateau (App. A): no relative improvement > diff_tol_r for
+        // plateau_window sweeps in a row stops this start.
+        stall = fabsf(prev) - fabsf(cost) > dtr * fabsf(cost) ? 0 : stall + 1;
+        if (stall >= a.plateau_window && sw >= a.min_sweeps) act = false;
+      }
+      prev = cost;
+    }
+  }
+  if (gi < u.ns) {
+    const size_t ri = (size_t)p * a.S + s;
+    if (gl == 0) {
+      a.conv_sweep[ri] = conv;
+      a.final_cost[ri] = (double)cost;
+      a.sweeps_run[ri] = sweeps;
+    }
+    for (int i = gl; i < 16 * L; i += G) a.gates32[goff + i] = Gt[i];
+  }
+  __syncwarp();
+}
+
+// Persistent sweep kernel with G lanes per start: warps take units until
+// the queue is empty.  region_f2: each warp's shared memory in float2 (at
+// least (32/G) batch_slice_f2(N M, L) for every unit it may take).
+template <int G>
+__global__ void k_batch_sweep(BatchArgs a, const BatchUnit* units, int nunits, int* queue, int region_f2) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ double2 sm_polar[kBatchMaxWarps][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int gi = lane / G, gl = lane % G;
-  float2* slice = reinterpret_cast<float2*>(dsm) + (size_t)warp * NG * slice_f2;
+  float2* region = reinterpret_cast<float2*>(dsm) + (size_t)warp * region_f2;
   while (true) {
     int item = 0;
     if (lane == 0) item = atomicAdd(queue, 1);
     item = __shfl_sync(FULL, item, 0);
     if (item >= nunits) break;
-    const BatchUnit u = units[item];
-    const int p = u.p;
-    const BatchProblem pr = a.probs[p];
-    const int* pairs = a.pairs + pr.pair_off;
-    const int s = u.s0 + gi;
-    bool act = gi < u.ns;
-    float2* mine = slice + gi * slice_f2;
-    float2* Gt = mine + 2 * E_max;
-    float2* V = Gt + 16 * L_max;
-    const size_t goff = pr.gate_off + (size_t)s * pr.L * 16;
-    if (act) {
-      for (int i = gl; i < 16 * pr.L; i += G) {
-        const double2 g = a.init_gates[goff + i];
-        Gt[i] = float2{(float)g.x, (float)g.y};
-        const int e = i & 15;
-        V[i] = float2{(e & 3) == (e >> 2) ? 1.f : 0.f, 0.f};
-      }
-    }
-    __syncwarp();
-    const float2* psi = a.psi32 + pr.state_off;
-    const float2* phil = a.phil32 + pr.state_off;
-    int conv = INT_MAX, sweeps = 0, stall = 0;
-    // The sweep's cost and the plateau test stay in FP32 (the FP64 pipe
-    // costs 64 cycles per warp instruction); only the tolerance test is FP64.
-    float cost = 4.f, prev = -1.f;
-    const float dtr = (float)a.diff_tol_r;
-    for (int sw = 1; sw <= a.max_sweeps; ++sw) {
-      // A start that has not converged by its problem's earliest converged
-      // sweep can no longer be selected.
-      if (sw > *(volatile int*)(a.s_star + p)) act = false;
-      const unsigned ballot = __ballot_sync(FULL, act && gl == 0);
-      unsigned mask = 0;
-#pragma unroll
-      for (int j = 0; j < NG; ++j) mask |= ((ballot >> (j * G)) & 1u) << j;
-      if (!mask) break;
-      const float c = group_sweep<G>(slice, slice_f2, E_max, L_max, psi, phil, pairs, pr.n, pr.M, pr.L,
-                                     sm_polar[warp], act, mask);
-      if (act) {
-        cost = c;
-        sweeps = sw;
-        if ((double)cost <= a.tol) {
-          conv = sw;
-          if (gl == 0) atomicMin(a.s_star + p, sw);
-          act = false;
-        } else if (a.plateau_window > 0 && prev >= 0.f) {
-          // Plateau (App. A): no relative improvement > diff_tol_r for
-          // plateau_window sweeps in a row stops this start.
-          stall = fabsf(prev) - fabsf(cost) > dtr * fabsf(cost) ? 0 : stall + 1;
-          if (stall >= a.plateau_window && sw >= a.min_sweeps) act = false;
-        }
-        prev = cost;
-      }
-    }
-    if (gi < u.ns) {
-      const size_t ri = (size_t)p * a.S + s;
-      if (gl == 0) {
-        a.conv_sweep[ri] = conv;
-        a.final_cost[ri] = (double)cost;
-        a.sweeps_run[ri] = sweeps;
-      }
-      for (int i = gl; i < 16 * pr.L; i += G) a.gates32[goff + i] = Gt[i];
-    }
-    __syncwarp();
+    batch_run_unit<G>(a, units[item], region, sm_polar[warp]);
   }
 }
 
@@ -473,8 +662,10 @@ void launch_batch_prep(const BatchArgs& a, cudaStream_t st) {
   k_batch_prep<<<a.P, 128, 0, st>>>(a);
 }
 
+int batch_region_f2(int G, int max_elems, int max_L) { return (32 / G) * batch_slice_f2(max_elems, max_L); }
+
 size_t batch_sweep_smem(int G, int warps, int max_elems, int max_L) {
-  return (size_t)warps * (32 / G) * batch_slice_f2(max_elems, max_L) * sizeof(float2);
+  return (size_t)warps * batch_region_f2(G, max_elems, max_L) * sizeof(float2);
 }
 
 namespace {
@@ -501,18 +692,13 @@ int batch_sweep_blocks_per_sm(int G, int warps, size_t smem) {
 }
 
 void launch_batch_sweep(int G, const BatchArgs& a, const BatchUnit* units, int nunits, int* queue, int blocks,
-                        int warps, int max_elems, int max_L, cudaStream_t st) {
-  const size_t smem = batch_sweep_smem(G, warps, max_elems, max_L);
-  const int sf = batch_slice_f2(max_elems, max_L);
+                        int warps, int region_f2, cudaStream_t st) {
+  const size_t smem = (size_t)warps * region_f2 * sizeof(float2);
   switch (G) {
-    case 4: k_batch_sweep<4><<<blocks, 32 * warps, smem, st>>>(a, units, nunits, queue, sf, max_elems, max_L); break;
-    case 8: k_batch_sweep<8><<<blocks, 32 * warps, smem, st>>>(a, units, nunits, queue, sf, max_elems, max_L); break;
-    case 16:
-      k_batch_sweep<16><<<blocks, 32 * warps, smem, st>>>(a, units, nunits, queue, sf, max_elems, max_L);
-      break;
-    default:
-      k_batch_sweep<32><<<blocks, 32 * warps, smem, st>>>(a, units, nunits, queue, sf, max_elems, max_L);
-      break;
+    case 4: k_batch_sweep<4><<<blocks, 32 * warps, smem, st>>>(a, units, nunits, queue, region_f2); break;
+    case 8: k_batch_sweep<8><<<blocks, 32 * warps, smem, st>>>(a, units, nunits, queue, region_f2); break;
+    case 16: k_batch_sweep<16><<<blocks, 32 * warps, smem, st>>>(a, units, nunits, queue, region_f2); break;
+    default: k_batch_sweep<32><<<blocks, 32 * warps, smem, st>>>(a, units, nunits, queue, region_f2); break;
   }
 }
 

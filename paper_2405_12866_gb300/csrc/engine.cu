@@ -116,7 +116,7 @@ struct qfs_ctx {
   // Whole-batch plan decisions: batch shape key -> 0 (per-class shapes) or
   // 1 (one start per warp everywhere), with the two timings in ms.
   std::vector<std::pair<uint64_t, int>> batch_plans;
-  std::vector<std::pair<float, float>> batch_plan_ms;
+  std::vector<std::array<float, 3>> batch_plan_ms;
   struct BatchGraph {
     uint64_t key = 0;
     cudaGraphExec_t exec = nullptr;
@@ -1977,10 +1977,12 @@ long long batch_class_key(int n, int L, int M, int S, bool lane_groups) {
 // amplitudes and max_L gates: the choice (2, 4 or 8) with the most resident
 // warps per SM (the kernel has no block-wide barrier, so this only sets the
 // shared-memory granularity); 0 if none fits.
-int batch_warps_for(int G, int max_elems, int max_L) {
+// Warps per block for a launch whose warps each take region_f2 float2 of
+// shared memory: the most resident warps per SM (4 on ties, then 2, then 8).
+int batch_warps_region(int G, int region_f2) {
   int best = 0, best_res = 0;
   for (int w : {4, 2, 8}) {
-    const size_t smem = batch_sweep_smem(G, w, max_elems, max_L);
+    const size_t smem = (size_t)w * region_f2 * sizeof(float2);
     if (smem > 200 * 1024) continue;
     const int res = w * batch_sweep_blocks_per_sm(G, w, smem);
     if (res > best_res) {
@@ -1989,6 +1991,10 @@ int batch_warps_for(int G, int max_elems, int max_L) {
     }
   }
   return best;
+}
+
+int batch_warps_for(int G, int max_elems, int max_L) {
+  return batch_warps_region(G, batch_region_f2(G, max_elems, max_L));
 }
 
 // Schedules worth trying for a class: G lanes per start no larger than the
@@ -2015,13 +2021,18 @@ struct BatchClass {
   int G = 32, warps = 4;
 };
 
-// Units of the given problems (largest work first within the list, ties by
-// index): a problem's starts in runs of 32 / G.
+// A unit's cost per sweep, for ordering the queue: per gate, a fixed update
+// cost (about that of one gate step on 1024 amplitudes) plus the state's
+// N M amplitudes.  Longer circuits also run more sweeps before they
+// converge or give up, so the queue starts with them.
+long long batch_unit_weight(const BatchProblem& b) { return (long long)b.L * (1024 + ((long long)b.M << b.n)); }
+
+// Units of the given problems, heaviest first (ties by position): a
+// problem's starts in runs of 32 / G.
 void batch_units(const std::vector<BatchProblem>& probs, std::vector<int> idx, int S, int G,
                  std::vector<BatchUnit>& out) {
-  std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
-    return ((long long)probs[x].L * probs[x].M << probs[x].n) > ((long long)probs[y].L * probs[y].M << probs[y].n);
-  });
+  std::stable_sort(idx.begin(), idx.end(),
+                   [&](int x, int y) { return batch_unit_weight(probs[x]) > batch_unit_weight(probs[y]); });
   const int per = 32 / G;
   for (int i : idx)
     for (int s0 = 0; s0 < S; s0 += per) out.push_back(BatchUnit{i, s0, std::min(per, S - s0)});
@@ -2086,7 +2097,8 @@ int autotune_batch(qfs_ctx* ctx, BatchArgs a, const std::vector<BatchProblem>& p
       for (int rep = 0; rep < 3; ++rep) {  // the first run warms up
         CK(cudaMemsetAsync(queue_dev, 0, sizeof(int), st));
         CK(cudaEventRecord(e0, st));
-        launch_batch_sweep(G, t, units_dev, (int)u.size(), queue_dev, blocks, w, c.M << c.n, c.L, st);
+        launch_batch_sweep(G, t, units_dev, (int)u.size(), queue_dev, blocks, w, batch_region_f2(G, c.M << c.n, c.L),
+                           st);
         CK(cudaEventRecord(e1, st));
         CK(cudaEventSynchronize(e1));
         CK(cudaGetLastError());
@@ -2308,10 +2320,10 @@ int batch_common(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls, 
   }
   // Builds (or finds in the cache) and launches the graph of one plan: the
   // classes with the same G share one persistent launch over their units,
-  // largest problems first.
+  // heaviest first.
   auto launch_plan = [&](const std::vector<BatchClass>& classes) -> int {
     struct Launch {
-      int G, warps, unit0, nunits, max_elems, max_L;
+      int G, warps, unit0, nunits, region;
     };
     std::vector<Launch> launches;
     std::vector<BatchUnit> units;
@@ -2321,29 +2333,25 @@ int batch_common(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls, 
         if (std::find(shapes.begin(), shapes.end(), c.G) == shapes.end()) shapes.push_back(c.G);
       for (int G : shapes) {
         std::vector<int> idx;
-        int me = 0, ml = 0;
+        int region = 0;
         for (const BatchClass& c : classes)
           if (c.G == G) {
             idx.insert(idx.end(), c.problems.begin(), c.problems.end());
-            me = std::max(me, c.M << c.n);
-            ml = std::max(ml, c.L);
+            region = std::max(region, batch_region_f2(G, c.M << c.n, c.L));
           }
-        const int wv = batch_warps_for(G, me, ml);
-        if (!wv) return fail(QFS_EUNSUPPORTED, "no block shape fits G = %d with N*M = %d, L = %d", G, me, ml);
+        const int wv = batch_warps_region(G, region);
+        if (!wv) return fail(QFS_EUNSUPPORTED, "no block shape fits G = %d with %d float2 per warp", G, region);
         const int u0 = (int)units.size();
         batch_units(probs, idx, S, G, units);
-        launches.push_back(Launch{G, wv, u0, (int)units.size() - u0, me, ml});
+        launches.push_back(Launch{G, wv, u0, (int)units.size() - u0, region});
       }
     }
-    // Launches start in order of their largest problem, largest first (the
-    // persistent launches overlap; the largest units should not come last).
+    // Launches start in order of their heaviest unit, heaviest first (the
+    // persistent launches overlap; the heaviest units should not come last).
     {
       std::vector<int> ord(launches.size());
       for (size_t i = 0; i < ord.size(); ++i) ord[i] = (int)i;
-      auto work = [&](const Launch& L) {
-        const BatchProblem& b = probs[units[L.unit0].p];  // its first unit is its largest
-        return (long long)b.L * b.M << b.n;
-      };
+      auto work = [&](const Launch& L) { return batch_unit_weight(probs[units[L.unit0].p]); };
       std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return work(launches[x]) > work(launches[y]); });
       std::vector<Launch> sorted;
       for (int i : ord) sorted.push_back(launches[i]);
@@ -2392,7 +2400,7 @@ int batch_common(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls, 
       if (e == cudaSuccess) e = cudaEventRecord(ctx->fork_event, cs);
       for (size_t li = 0; li < launches.size() && e == cudaSuccess; ++li) {
         const Launch& L = launches[li];
-        const size_t smem = batch_sweep_smem(L.G, L.warps, L.max_elems, L.max_L);
+        const size_t smem = (size_t)L.warps * L.region * sizeof(float2);
         const int bps = std::max(1, batch_sweep_blocks_per_sm(L.G, L.warps, smem));
         const int blocks = std::max(1, std::min(ctx->num_sms * bps, (L.nunits + L.warps - 1) / L.warps));
         const int gs = (int)(li % kMaxGroups);
@@ -2401,8 +2409,7 @@ int batch_common(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls, 
         if (e != cudaSuccess) break;
         {
           ProfScope ps(ctx, QFS_PROF_BATCH, 0.0, ls);
-          launch_batch_sweep(L.G, a, units_dev + L.unit0, L.nunits, a.queue + li, blocks, L.warps, L.max_elems,
-                             L.max_L, ls);
+          launch_batch_sweep(L.G, a, units_dev + L.unit0, L.nunits, a.queue + li, blocks, L.warps, L.region, ls);
         }
         if (li > 0) {
           e = cudaEventRecord(ctx->gevent[gs], ls);
@@ -2456,19 +2463,26 @@ int batch_common(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls, 
     return QFS_OK;
   };
 
-  // Plans: the per-class shapes, and (when they differ from it) every class
-  // with one start per warp.  The autotuner's per-class trials measure
-  // throughput at full occupancy, but a lane-group unit sweeps its starts
-  // one warp-update after another, so it lives 32 / G times longer than a
-  // warp-per-start unit; when the starts of a problem run long (a problem
-  // that does not converge runs all of them to max_sweeps) such units set
-  // the batch's makespan.  So the first call of a batch shape times both
-  // plans on the batch itself and keeps the faster (cached per shape).
+  // Plans: the per-class shapes; every class with one start per warp; every
+  // class that admits it with 16 lanes per start.  The autotuner's per-class
+  // trials measure throughput at full occupancy over a few sweeps, but a
+  // batch's makespan is set by the starts that run long (a problem that does
+  // not converge runs all of them to max_sweeps), and their latency per
+  // sweep depends on the schedule and on what shares the SM with them.  So
+  // the first call of a class mix times the plans on the batch itself and
+  // keeps the fastest (cached per class mix).
   bool mixed = false;
   for (const BatchClass& c : classes) mixed |= c.G != 32;
   if (mixed && ctx->batch_force_G == 0) {
-    std::vector<BatchClass> all32 = classes;
-    for (BatchClass& c : all32) c.G = 32;
+    std::vector<BatchClass> plans[3] = {classes, classes, classes};
+    for (BatchClass& c : plans[1]) c.G = 32;
+    bool all16_differs = false;
+    for (BatchClass& c : plans[2]) {
+      c.G = 32;
+      for (auto [G, wv] : batch_candidates(c.n, c.M, c.L, S, true))
+        if (G == 16) c.G = 16;
+    }
+    for (size_t i = 0; i < classes.size(); ++i) all16_differs |= plans[2][i].G != classes[i].G;
     // The decision is kept per class mix (the set of classes and their
     // shares of the batch, in tenths) and run parameters, so batches of the
     // same composition but another size reuse it.
@@ -2491,10 +2505,11 @@ int batch_common(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls, 
       cudaEvent_t e0, e1;
       CK(cudaEventCreate(&e0));
       CK(cudaEventCreate(&e1));
-      float ms[2] = {0.f, 0.f};
-      for (int k = 0; k < 2; ++k) {
+      std::array<float, 3> ms = {-1.f, -1.f, -1.f};
+      for (int k = 0; k < 3; ++k) {
+        if (k == 2 && !all16_differs) continue;
         CK(cudaEventRecord(e0, st));
-        const int rc = launch_plan(k == 0 ? classes : all32);
+        const int rc = launch_plan(plans[k]);
         if (rc != QFS_OK) {
           cudaEventDestroy(e0);
           cudaEventDestroy(e1);
@@ -2506,11 +2521,13 @@ int batch_common(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls, 
       }
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
-      choice = ms[0] < ms[1] ? 0 : 1;
+      choice = 0;
+      for (int k = 1; k < 3; ++k)
+        if (ms[k] >= 0.f && ms[k] < ms[choice]) choice = k;
       ctx->batch_plans.push_back({pk, choice});
-      ctx->batch_plan_ms.push_back({ms[0], ms[1]});
+      ctx->batch_plan_ms.push_back(ms);
     }
-    if (choice == 1) classes = all32;
+    classes = plans[choice];
   }
   TRY(launch_plan(classes));
   if (in.sweep_once) {
@@ -2587,10 +2604,8 @@ extern "C" int qfs_batch_schedules(qfs_ctx* ctx, int32_t cap, int32_t* tuned, in
   if (n_plans) *n_plans = (int32_t)ctx->batch_plans.size();
   for (int i = 0; i < cap && i < (int)ctx->batch_plans.size(); ++i) {
     if (plan_choice) plan_choice[i] = ctx->batch_plans[i].second;
-    if (plan_ms) {
-      plan_ms[2 * i] = ctx->batch_plan_ms[i].first;
-      plan_ms[2 * i + 1] = ctx->batch_plan_ms[i].second;
-    }
+    if (plan_ms)
+      for (int k = 0; k < 3; ++k) plan_ms[3 * i + k] = ctx->batch_plan_ms[i][k];
   }
   if (n_tuned) *n_tuned = (int32_t)ctx->batch_tuned.size();
   if (n_trials) *n_trials = (int32_t)ctx->batch_trial_ns.size();

@@ -247,14 +247,18 @@ struct BatchUnit {
 };
 
 void launch_batch_prep(const BatchArgs& a, cudaStream_t st);
-// Shared memory of a block of `warps` warps with G lanes per start, for
-// problems of at most max_elems = N * M amplitudes and max_L gates.
+// A warp's shared memory (float2) with G lanes per start, for problems of
+// at most max_elems = N * M amplitudes and max_L gates.
+int batch_region_f2(int G, int max_elems, int max_L);
+// Shared memory of a block of `warps` warps of that shape.
 size_t batch_sweep_smem(int G, int warps, int max_elems, int max_L);
-// Resident blocks per SM of that launch shape (0: it does not fit).
+// Resident blocks per SM of a launch of `warps` warps and `smem` bytes (0:
+// it does not fit).
 int batch_sweep_blocks_per_sm(int G, int warps, size_t smem);
-// The persistent sweep over `units` (queue: a zeroed counter), G in {4, 8, 16, 32}.
+// The persistent sweep over `units` (queue: a zeroed counter), G in
+// {4, 8, 16, 32}; region_f2: each warp's shared memory in float2.
 void launch_batch_sweep(int G, const BatchArgs& a, const BatchUnit* units, int nunits, int* queue, int blocks,
-                        int warps, int max_elems, int max_L, cudaStream_t st);
+                        int warps, int region_f2, cudaStream_t st);
 void launch_batch_finalize(const BatchArgs& a, cudaStream_t st);
 
 // ---------------------------------------------------------- learned part

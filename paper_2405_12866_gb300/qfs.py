@@ -409,12 +409,13 @@ class Context:
         trials = np.zeros((cap, 6), dtype=np.int32)
         tns = np.zeros(cap)
         pc = np.zeros(cap, dtype=np.int32)
-        pms = np.zeros((cap, 2))
+        pms = np.zeros((cap, 3))
         _check(lib().qfs_batch_schedules(self._h, cap, tuned.ctypes.data, C.byref(nt), trials.ctypes.data,
                                          tns.ctypes.data, C.byref(nr), pc.ctypes.data, pms.ctypes.data,
                                          C.byref(npl)))
         keys = ("n", "L", "M", "S", "G", "warps")
-        self.batch_plans = [dict(choice=int(c), ms_per_class=float(m[0]), ms_warp_per_start=float(m[1]))
+        self.batch_plans = [dict(choice=int(c), ms_per_class=float(m[0]), ms_warp_per_start=float(m[1]),
+                                 ms_16_lanes=float(m[2]))
                             for c, m in zip(pc[:npl.value], pms[:npl.value])]
         return ([dict(zip(keys, map(int, r))) for r in tuned[:nt.value]],
                 [dict(zip(keys, map(int, r)), ns_per_start_sweep=float(t)) for r, t in zip(trials[:nr.value],

@@ -61,6 +61,31 @@ def test_one_batched_sweep_per_schedule_matches_oracle(ctx, G):
     assert checked >= len(probs) * S // 2
 
 
+@pytest.mark.parametrize("G", [16, 32])
+@pytest.mark.parametrize("S", [2, 3])
+def test_one_batched_sweep_rank_deficient_environments(ctx, G, S):
+    """One training state (M = 1) and one gate on 2 or 3 qubits: every
+    environment has rank 1 or 2, so the FP32 polar update gives up and the
+    FP64 Jacobi takes over (with 16 lanes per start, for each half of the
+    warp in turn; with S = 3 one half of the second unit is idle).  The
+    polar factor is then not unique, but the swept cost is: with one gate
+    the updated gate attains Re tr(g E) = sum of E's singular values (von
+    Neumann), whichever maximiser is taken, so the costs must match the
+    oracle's to 1e-5 and every gate must be unitary."""
+    probs = []
+    for i, (n, pair) in enumerate([(2, (0, 1)), (2, (1, 0)), (3, (0, 1)), (3, (1, 2)), (3, (2, 1))]):
+        gt = w.haar_gates(900 + i, w.STREAM_TARGET_GATES, 2)
+        U = w.target_unitary(gt, [pair, pair], n)
+        probs.append((n, [pair], U, w.sample_states(950 + i, n, 1), w.initial_gates(990 + i, S, 1)))
+    got, costs = ctx.batch_sweep_once([(n, pr, U) for n, pr, U, _, _ in probs], [x[3] for x in probs],
+                                      [x[4] for x in probs], M=1, lanes_per_start=G)
+    for (n, pr, U, Psi, G0), g, c in zip(probs, got, costs):
+        for s in range(S):
+            r = o.sweep(U @ Psi, Psi, G0[s], pr, n)
+            assert abs(c[s] - r.cost) < 1e-5, (n, pr, s, c[s], r.cost)
+            assert np.max(np.abs(g[s][0].conj().T @ g[s][0] - np.eye(4))) < 1e-5
+
+
 def test_batch_512_problems_match_oracle_runs(ctx):
     """The first 512 problems of the batched workload against the oracle's
     own multistart runs (tests/golden/uneven_blocks_oracle_runs.json, written
