@@ -192,13 +192,13 @@ __device__ __forceinline__ float2 mm16_bh(float2 a, float2 b, int row, int col) 
   }
   return acc;
 }
-// Whether every column pair of this half's X has |gamma|^2 <= 1e-13 alpha
-// beta (the Gram-matrix test of jacobi32_converged), as a warp-uniform
-// two-bit mask (bit h: half h).
+// Whether every column pair of this half's X has |gamma|^2 <= kJac32Tol
+// alpha beta (the Gram-matrix test of jacobi32_converged), as a
+// warp-uniform two-bit mask (bit h: half h).
 __device__ __forceinline__ unsigned half_converged(float2 x, int row, int col) {
   const float2 g = mm16_ah(x, x, row, col);
   const float dr = __shfl_sync(FULL, g.x, 5 * row, 16), dc = __shfl_sync(FULL, g.x, 5 * col, 16);
-  const bool ok = row == col || (g.x * g.x + g.y * g.y) <= 1e-13f * dr * dc;
+  const bool ok = row == col || (g.x * g.x + g.y * g.y) <= kJac32Tol * dr * dc;
   const unsigned b = __ballot_sync(FULL, ok);
   return ((b & 0xffffu) == 0xffffu ? 1u : 0u) | ((b >> 16) == 0xffffu ? 2u : 0u);
 }
@@ -240,7 +240,7 @@ __device__ unsigned halfwarp_polar4_f32_warm(float2 a, float2* v_io, bool act, f
       const float alpha = isP ? nown : npar, beta = isP ? npar : nown;
       const float ag2 = g.x * g.x + g.y * g.y;
       float cs = 1.f, sn = 0.f, px = 1.f, py = 0.f;
-      if (!mine_done && ag2 > 1e-13f * alpha * beta && ag2 > 1e-36f) {
+      if (!mine_done && ag2 > kJac32Tol * alpha * beta && ag2 > 1e-36f) {
         const float rg = rsqrtf(ag2);
         const float zeta = 0.5f * (beta - alpha) * rg;
         const float q = fmaf(zeta, zeta, 1.f);

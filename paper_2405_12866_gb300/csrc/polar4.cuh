@@ -292,7 +292,17 @@ __device__ __forceinline__ float2 skew_correction(float2 k32, float2 v, float si
   return float2{0.5f * (om.x - omt.x), 0.5f * (om.y + omt.y)};  // exactly skew-Hermitian
 }
 
-// True when every column pair of X (lanes 0..15) has |gamma|^2 <= 1e-13
+// FP32 Jacobi tolerance: a column pair counts as orthogonal when |gamma|^2
+// <= kJac32Tol alpha beta, i.e. |gamma| <= 1e-6 sqrt(alpha beta).  The Gram
+// entries of X = A V0 carry FP32 rounding of 2-5e-7 of sqrt(alpha beta), so a
+// tighter test keeps rotating rounding noise.  Columns orthogonal to 1e-6
+// leave the polar factor within ~1e-6 of the exact one; the polar factor
+// maximises Re tr(g E) over unitary g, so that error changes the objective
+// only at second order (1e-12), and the Newton-Schulz steps that follow
+// make the factor unitary to their own precision.
+constexpr float kJac32Tol = 1e-12f;
+
+// True when every column pair of X (lanes 0..15) has |gamma|^2 <= kJac32Tol
 // alpha beta, from the Gram matrix X^H X in one product: cheaper than a
 // sweep that finds nothing to rotate.
 __device__ __forceinline__ bool jacobi32_converged(float2 x) {
@@ -300,13 +310,13 @@ __device__ __forceinline__ bool jacobi32_converged(float2 x) {
   const int l16 = lane & 15, row = l16 & 3, col = l16 >> 2;
   const float2 g = mm_ah(x, x, row, col);  // G[row][col] = <x_row, x_col>
   const float dr = __shfl_sync(FULL, g.x, 5 * row), dc = __shfl_sync(FULL, g.x, 5 * col);
-  const bool ok = row == col || (g.x * g.x + g.y * g.y) <= 1e-13f * dr * dc;
+  const bool ok = row == col || (g.x * g.x + g.y * g.y) <= kJac32Tol * dr * dc;
   return __all_sync(FULL, ok);
 }
 
 // FP32 one-sided Jacobi sweeps on X (lanes 0..15, X[r][c] at 4c + r) with
 // the accumulated right rotations V in lanes 16..31, until every column pair
-// has |gamma|^2 <= 1e-13 alpha beta (FP32 accuracy) or 12 sweeps.
+// has |gamma|^2 <= kJac32Tol alpha beta or 12 sweeps.
 // *rotated_out (optional): whether any rotation was applied.
 __device__ __forceinline__ float2 jacobi32_sweeps(float2 x, bool* rotated_out = nullptr) {
   const int lane = threadIdx.x & 31;
@@ -338,7 +348,7 @@ __device__ __forceinline__ float2 jacobi32_sweeps(float2 x, bool* rotated_out = 
       const float alpha = isP ? nown : npar, beta = isP ? npar : nown;
       const float ag2 = g.x * g.x + g.y * g.y;
       float cs = 1.f, sn = 0.f, px = 1.f, py = 0.f;
-      if (ag2 > 1e-13f * alpha * beta && ag2 > 1e-36f) {
+      if (ag2 > kJac32Tol * alpha * beta && ag2 > 1e-36f) {
         const float rg = rsqrtf(ag2);
         const float zeta = 0.5f * (beta - alpha) * rg;
         // t = sign(zeta) / (|zeta| + sqrt(zeta^2 + 1)) with the hardware

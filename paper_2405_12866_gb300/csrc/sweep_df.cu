@@ -690,9 +690,12 @@ __device__ __forceinline__ bool df_polar_begin(double2 a, double2 v0, DfUpd& u) 
 // polar_update_warp / update_from_sum (FP32 Jacobi, two FP64 Newton-Schulz
 // steps, POLISH skew-Hermitian corrections), with the FP64 products spread
 // over the four warps.  Warp 0 holds the summed environment value v (lane j
-// = value j of E).  All threads call it.
+// = value j of E) and, in lanes 16..31, the Jacobi start v0 (the gate's V
+// from its previous update, or the identity), loaded by the caller before
+// the partial sums so that its latency is off the chain.  All threads call
+// it.
 template <typename T, int POLISH>
-__device__ void df_update(const UpdateArgs& ua, int s, DfShared<T>& sh, double v) {
+__device__ void df_update(const UpdateArgs& ua, int s, DfShared<T>& sh, double v, double2 v0) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int l16 = lane & 15, row = l16 & 3, col = l16 >> 2;
   DfUpd& u = sh.u;
@@ -708,8 +711,6 @@ __device__ void df_update(const UpdateArgs& ua, int s, DfShared<T>& sh, double v
       m = double2{(1.0 - ua.beta) * m.x + ua.beta * go.x, (1.0 - ua.beta) * m.y - ua.beta * go.y};
     }
     a = double2{m.x, -m.y};
-    double2 v0{row == col ? 1.0 : 0.0, 0.0};
-    if (vio && lane >= 16) v0 = vio[l16];
     const bool ok = df_polar_begin(a, v0, u);
     if (lane == 0) u.ok = ok ? 1 : 0;
   }
@@ -888,8 +889,10 @@ __global__ void __launch_bounds__(df_threads<T>(), 1) k_sweep_df(DfArgs a) {
             }
           }
         } else {
-          // Sum the chunk partials with all warps (warp w takes chunks w,
-          // w + NW, ...; fixed order), then the update.
+          // The Jacobi start of the update, then the chunk partials summed
+          // by all warps (warp w takes chunks w, w + NW, ...; fixed order).
+          double2 v0{(lane & 3) == ((lane & 15) >> 2) ? 1.0 : 0.0, 0.0};
+          if (warp == 0 && lane >= 16 && st.upd.vprev) v0 = (st.upd.vprev + s * st.upd.g_stride)[lane & 15];
           const T* pp = reinterpret_cast<const T*>(a.partials) + (long long)s * a.part_stride * 32;
           T acc[4] = {T(0), T(0), T(0), T(0)};
           int b = warp;
@@ -909,7 +912,7 @@ __global__ void __launch_bounds__(df_threads<T>(), 1) k_sweep_df(DfArgs a) {
           // complex64 sweeps: the polar factor to FP32 accuracy, the
           // accuracy of their environments (no skew-Hermitian correction);
           // FP64 sweeps: polar to FP64 rounding (two corrections).
-          df_update<T, sizeof(T) == 4 ? 0 : 2>(st.upd, s, sh, v);
+          df_update<T, sizeof(T) == 4 ? 0 : 2>(st.upd, s, sh, v, v0);
           if (st.upd.cost_out != nullptr && threadIdx.x == 0) {
             const double cost = st.upd.cost_out[s];
             if (a.cost_row != nullptr) a.cost_row[s] = cost;
