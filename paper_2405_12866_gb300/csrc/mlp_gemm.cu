@@ -41,9 +41,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
   return false;
 }
 
+// The tanh form of GELU, 0.5 x (1 + tanh u) with u = sqrt(2/pi) (x +
+// 0.044715 x^3), evaluated as the equal x / (1 + exp(-2u)): one exponential
+// and one division instead of tanhf, ~1e-6 relative, far below the bf16
+// rounding of the result.  exp(-2u) = inf for u < -44 gives -0.
 __device__ __forceinline__ float gelu_tanh(float x) {
   const float k0 = 0.7978845608028654f, k1 = 0.044715f;
-  return 0.5f * x * (1.f + tanhf(k0 * (x + k1 * x * x * x)));
+  const float u = k0 * fmaf(k1 * x, x * x, x);
+  return __fdividef(x, 1.f + __expf(-2.f * u));
 }
 
 }  // namespace
@@ -52,14 +57,21 @@ __device__ __forceinline__ float gelu_tanh(float x) {
 
 namespace {
 
-constexpr int kBM = 128, kBK = 64, kStages = 4, kTmaThreads = 192;
+// Warp 0: TMA producer; warp 1: MMA issuer; warps 2-9: epilogue (two per
+// TMEM lane quadrant, each with half of the tile's columns).
+constexpr int kBM = 128, kBK = 64, kStages = 4, kTmaThreads = 320;
+// Row stride (floats) of an epilogue warp's 32 x 32 staging block: 16-byte
+// aligned rows whose float4 accesses by 8 lanes cover all 32 banks.
+constexpr int kTileStride = 36;
+static_assert(8 * 32 * kTileStride * 4 <= kStages * kBM * kBK * 2, "epilogue blocks fit the operand stages");
 
 template <int BN>
 struct TmaCfg {
   static constexpr int kABytes = kBM * kBK * 2;
   static constexpr int kBBytes = BN * kBK * 2;
   static constexpr int kStageBytes = kABytes + kBBytes;
-  static constexpr int kSmem = kStages * kStageBytes + 1024 + 256;
+  // stages, 1024-byte alignment slack, barriers (256 B), the tile's bias
+  static constexpr int kSmem = kStages * kStageBytes + 1024 + 256 + BN * 4;
   static constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                                      ((uint32_t)(kBM >> 4) << 24);
 };
@@ -191,73 +203,87 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     }
     __syncwarp();
   } else {
-    // Epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows of the tile).
-    const int q = warp & 3;
-    const int row = m0 + q * 32 + lane;
+    // Epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows of the
+    // tile) and columns half * BN/2 .. + BN/2 - 1.  The bias (added by the
+    // first K split only) is staged in shared memory while the MMAs run.
+    const int q = warp & 3, half = (warp - 2) >> 2;
+    float* stile = reinterpret_cast<float*>(sb) + (warp - 2) * 32 * kTileStride;
+    float* sbias = reinterpret_cast<float*>(sb + kStages * Cfg::kStageBytes + 256);
+    const bool add_bias = g.bias != nullptr && blockIdx.z == 0;
+    if (add_bias)
+      for (int j = threadIdx.x - 64; j < BN; j += kTmaThreads - 64) sbias[j] = g.bias[n0 + j];
+    asm volatile("bar.sync 1, %0;" ::"n"(kTmaThreads - 64) : "memory");
     const bool ok = mbar_wait_bounded(accf, 0) && !*abort_flag;
     if (!ok) {
       *abort_flag = 1;
     } else {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      for (int cb = 0; cb < BN; cb += 32) {
-        uint32_t v[32];
+      constexpr int HC = BN / 2;
+      for (int cb = half * HC; cb < (half + 1) * HC; cb += 64) {
+        uint32_t v[64];
         const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)cb;
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-            "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-              "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-              "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-              "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-            : "r"(taddr)
-            : "memory");
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          uint32_t* w = v + 32 * hh;
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+              "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+              "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+              : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7]),
+                "=r"(w[8]), "=r"(w[9]), "=r"(w[10]), "=r"(w[11]), "=r"(w[12]), "=r"(w[13]), "=r"(w[14]),
+                "=r"(w[15]), "=r"(w[16]), "=r"(w[17]), "=r"(w[18]), "=r"(w[19]), "=r"(w[20]), "=r"(w[21]),
+                "=r"(w[22]), "=r"(w[23]), "=r"(w[24]), "=r"(w[25]), "=r"(w[26]), "=r"(w[27]), "=r"(w[28]),
+                "=r"(w[29]), "=r"(w[30]), "=r"(w[31])
+              : "r"(taddr + 32u * hh)
+              : "memory");
+        }
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (row >= g.M_valid) continue;
-        float x[32];
+        // Each 32 x 32 block goes through this warp's slice of the (now idle)
+        // operand stages: lane l writes its row, then eight lanes cover one
+        // row's 128 bytes per store, so every store writes whole lines.
 #pragma unroll
-        for (int j = 0; j < 32; ++j) x[j] = __uint_as_float(v[j]);
-        const int col = n0 + cb;
-        if (splitk > 1) {
-          float4* dst = reinterpret_cast<float4*>(g.C32 + (size_t)row * g.ldc + col);
+        for (int hh = 0; hh < 2; ++hh) {
+          const int lc = cb + 32 * hh, col = n0 + lc;
 #pragma unroll
-          for (int j = 0; j < 8; ++j) atomicAdd(dst + j, make_float4(x[4 * j], x[4 * j + 1], x[4 * j + 2], x[4 * j + 3]));
-          continue;
-        }
-        if (g.bias) {
-          const float4* bp = reinterpret_cast<const float4*>(g.bias + col);
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const float4 b4 = bp[j];
-            x[4 * j] += b4.x;
-            x[4 * j + 1] += b4.y;
-            x[4 * j + 2] += b4.z;
-            x[4 * j + 3] += b4.w;
-          }
-        }
-        if (g.C32) {
-          float4* dst = reinterpret_cast<float4*>(g.C32 + (size_t)row * g.ldc + col);
-#pragma unroll
-          for (int j = 0; j < 8; ++j) dst[j] = make_float4(x[4 * j], x[4 * j + 1], x[4 * j + 2], x[4 * j + 3]);
-        }
-        if (g.C16) {
-          uint4* dst = reinterpret_cast<uint4*>(g.C16 + (size_t)row * g.ldc + col);
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            uint32_t w[4];
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-              float a = x[8 * j + 2 * h], b = x[8 * j + 2 * h + 1];
-              if (g.gelu) {
-                a = gelu_tanh(a);
-                b = gelu_tanh(b);
-              }
-              const __nv_bfloat162 p = __floats2bfloat162_rn(a, b);
-              w[h] = *reinterpret_cast<const uint32_t*>(&p);
+          for (int j4 = 0; j4 < 8; ++j4) {
+            float4 f = make_float4(__uint_as_float(v[32 * hh + 4 * j4]), __uint_as_float(v[32 * hh + 4 * j4 + 1]),
+                                   __uint_as_float(v[32 * hh + 4 * j4 + 2]), __uint_as_float(v[32 * hh + 4 * j4 + 3]));
+            if (add_bias) {
+              f.x += sbias[lc + 4 * j4];
+              f.y += sbias[lc + 4 * j4 + 1];
+              f.z += sbias[lc + 4 * j4 + 2];
+              f.w += sbias[lc + 4 * j4 + 3];
             }
-            dst[j] = make_uint4(w[0], w[1], w[2], w[3]);
+            *reinterpret_cast<float4*>(stile + lane * kTileStride + 4 * j4) = f;
           }
+          __syncwarp();
+#pragma unroll
+          for (int it = 0; it < 8; ++it) {
+            const int r = 4 * it + (lane >> 3), c4 = lane & 7;
+            const int grow = m0 + q * 32 + r;
+            const float4 f = *reinterpret_cast<const float4*>(stile + r * kTileStride + 4 * c4);
+            if (grow < g.M_valid) {
+              float* d32 = g.C32 ? g.C32 + (size_t)grow * g.ldc + col + 4 * c4 : nullptr;
+              if (splitk > 1) {
+                atomicAdd(reinterpret_cast<float4*>(d32), f);
+              } else {
+                if (d32) *reinterpret_cast<float4*>(d32) = f;
+                if (g.C16) {
+                  float a0 = f.x, a1 = f.y, a2 = f.z, a3 = f.w;
+                  if (g.gelu) {
+                    a0 = gelu_tanh(a0);
+                    a1 = gelu_tanh(a1);
+                    a2 = gelu_tanh(a2);
+                    a3 = gelu_tanh(a3);
+                  }
+                  const __nv_bfloat162 p0 = __floats2bfloat162_rn(a0, a1), p1 = __floats2bfloat162_rn(a2, a3);
+                  *reinterpret_cast<uint2*>(g.C16 + (size_t)grow * g.ldc + col + 4 * c4) =
+                      make_uint2(*reinterpret_cast<const uint32_t*>(&p0), *reinterpret_cast<const uint32_t*>(&p1));
+                }
+              }
+            }
+          }
+          __syncwarp();
         }
       }
     }
@@ -322,7 +348,7 @@ cudaError_t launch_tma(const GemmArgs& g, int splitk, cudaStream_t st) {
 }  // namespace
 
 int gemm_splitk_for(const GemmArgs& g, int num_sms) {
-  if (g.C16 || g.bias || g.gelu || !g.C32) return 1;
+  if (g.C16 || g.gelu || !g.C32) return 1;  // (the bias is added by the first split)
   const int BN = g.N % 256 == 0 ? 256 : 128;
   const int tiles = (g.N / BN) * (g.M / kBM);
   const int KT = g.K / kBK;
