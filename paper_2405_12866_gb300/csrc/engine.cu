@@ -2985,7 +2985,6 @@ extern "C" int qfs_ws_train(qfs_ws* m, int32_t count, const double* targets, con
   TRY(set_device(m->ctx));
   cudaStream_t st = m->ctx->stream;
   const long long steps_total = (long long)epochs * ((count + batch - 1) / batch);
-  long long step_i = 0;
   // The whole training set stays on the device: features (bf16, count x
   // 256) computed once, labels (fp32, count x 192), and the shuffled order.
   __nv_bfloat16* Xall = nullptr;
@@ -3021,6 +3020,89 @@ extern "C" int qfs_ws_train(qfs_ws* m, int32_t count, const double* targets, con
   }
   std::vector<int> idx(count);
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  // The step's Adam values (lr with cosine decay from lr to lr_final over
+  // this call's steps, bias corrections) for every step of the call, and two
+  // device counters (step within the epoch, step of the call): every
+  // full-batch step is then the same work, captured once as a graph and
+  // replayed (no host launch work per step).
+  float* sched = nullptr;
+  int* counters = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  long long graph_launches[QFS_PROF_KINDS] = {};
+  auto release_train = [&]() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (sched) cudaFree(sched);
+    if (counters) cudaFree(counters);
+    prof_release_graph(m->ctx);
+  };
+  if (rc == QFS_OK) {
+    std::vector<float> hs((size_t)steps_total * 3);
+    for (long long k = 0; k < steps_total; ++k) {
+      const float t = (float)(m->step + 1 + k);
+      const double frac = steps_total > 1 ? (double)k / (double)(steps_total - 1) : 0.0;
+      hs[3 * k] = (float)(lr_final + 0.5 * (lr - lr_final) * (1.0 + std::cos(3.141592653589793 * frac)));
+      hs[3 * k + 1] = 1.f - std::pow(b1, t);
+      hs[3 * k + 2] = 1.f - std::pow(b2, t);
+    }
+    if (cudaMalloc(&sched, sizeof(float) * hs.size()) != cudaSuccess ||
+        cudaMalloc(&counters, 2 * sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      rc = fail(QFS_ENOMEM, "training schedule does not fit on the device");
+    } else if (cudaMemcpyAsync(sched, hs.data(), sizeof(float) * hs.size(), cudaMemcpyHostToDevice, st) !=
+                   cudaSuccess ||
+               cudaMemsetAsync(counters, 0, 2 * sizeof(int), st) != cudaSuccess ||
+               cudaStreamSynchronize(st) != cudaSuccess) {
+      rc = fail(QFS_ECUDA, "upload of the training schedule failed");
+    }
+  }
+  int* jstep = counters;
+  int* gstep = counters ? counters + 1 : nullptr;
+  double* ep_acc = m->loss_part + 1032;  // the epoch's loss, summed on the device
+  // One training step on the context's stream: gather, forward, backward,
+  // Adam with the device schedule, refreshed bf16 weights, counters advanced.
+  auto run_step = [&](int bv, int B) -> int {
+    cudaStream_t s = m->ctx->stream;
+    launch_ws_gather(Xall, Tall, didx, bv, B, m->X16, m->Tlab, s, jstep, batch);
+    ws_forward(m, B);
+    TRY(ws_backward(m, B, bv, nullptr, ep_acc));
+    for (int k = 0; k < qfs_ws::kLayers; ++k) {
+      launch_adam(m->W[k], m->mW[k], m->vW[k], m->gW[k], (long long)m->dout[k] * m->din[k], 0.f, b1, b2, eps, 1.f,
+                  1.f, m->W16[k], s, sched, gstep);
+      launch_adam(m->b[k], m->mb[k], m->vb[k], m->gb[k], m->dout[k], 0.f, b1, b2, eps, 1.f, 1.f, nullptr, s, sched,
+                  gstep);
+      launch_transpose_bf16(m->W16[k], m->dout[k], m->din[k], m->WT16[k], s);
+    }
+    launch_ws_step_advance(jstep, gstep, s);
+    return QFS_OK;
+  };
+  // The captured full-batch step, made on first use.
+  auto capture_step = [&]() -> int {
+    qfs_ctx* c = m->ctx;
+    if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    long long before[QFS_PROF_KINDS];
+    for (int i = 0; i < QFS_PROF_KINDS; ++i) before[i] = c->prof.launches[i];
+    cudaStream_t saved = c->stream;
+    c->stream = c->cap_stream;
+    CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed));
+    c->prof.capturing = true;
+    const int r = run_step(batch, batch);
+    c->prof.capturing = false;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+    c->stream = saved;
+    for (int i = 0; i < QFS_PROF_KINDS; ++i) {
+      graph_launches[i] = c->prof.launches[i] - before[i];
+      c->prof.launches[i] = before[i];
+    }
+    if (r != QFS_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return r;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    CK(e);
+    return QFS_OK;
+  };
   for (int ep = 0; ep < epochs && rc == QFS_OK; ++ep) {
     for (int i = 0; i < count; ++i) idx[i] = i;
     // Fisher-Yates with Philox draws (deterministic per seed and epoch).
@@ -3030,37 +3112,38 @@ extern "C" int qfs_ws_train(qfs_ws* m, int32_t count, const double* targets, con
       if (j > i) j = i;
       std::swap(idx[i], idx[j]);
     }
-    if (cudaMemcpyAsync(didx, idx.data(), sizeof(int) * count, cudaMemcpyHostToDevice, st) != cudaSuccess) {
-      rc = fail(QFS_ECUDA, "copy of the sample order failed");
-      break;
-    }
-    // The epoch's loss is summed on the device (no per-step synchronisation).
-    double* ep_acc = m->loss_part + 1032;
-    if (cudaMemsetAsync(ep_acc, 0, sizeof(double), st) != cudaSuccess) {
-      rc = fail(QFS_ECUDA, "cudaMemsetAsync failed");
+    if (cudaMemcpyAsync(didx, idx.data(), sizeof(int) * count, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(ep_acc, 0, sizeof(double), st) != cudaSuccess ||
+        cudaMemsetAsync(jstep, 0, sizeof(int), st) != cudaSuccess) {
+      rc = fail(QFS_ECUDA, "epoch set-up failed");
       break;
     }
     int nb = 0;
     for (int s0 = 0; s0 < count; s0 += batch) {
       const int bv = std::min(batch, count - s0);
-      const int B = (bv + 127) / 128 * 128;
-      launch_ws_gather(Xall, Tall, didx + s0, bv, B, m->X16, m->Tlab, st);
-      ws_forward(m, B);
-      rc = ws_backward(m, B, bv, nullptr, ep_acc);
-      if (rc != QFS_OK) break;
+      if (bv == batch) {
+        if (!exec) {
+          rc = capture_step();
+          if (rc != QFS_OK) break;
+        }
+        if (cudaGraphLaunch(exec, st) != cudaSuccess) {
+          rc = fail(QFS_ECUDA, "training step launch failed");
+          break;
+        }
+        for (int i = 0; i < QFS_PROF_KINDS; ++i) m->ctx->prof.launches[i] += graph_launches[i];
+        if (m->ctx->prof.on) {  // per-launch timings: harvested after each replay
+          if (cudaStreamSynchronize(st) != cudaSuccess) {
+            rc = fail(QFS_ECUDA, "training step failed");
+            break;
+          }
+          prof_harvest_graph(m->ctx);
+        }
+      } else {
+        rc = run_step(bv, (bv + 127) / 128 * 128);
+        if (rc != QFS_OK) break;
+      }
       ++nb;
       ++m->step;
-      const float bc1 = 1.f - std::pow(b1, (float)m->step), bc2 = 1.f - std::pow(b2, (float)m->step);
-      // Cosine decay from lr to lr_final over this call's steps.
-      const double frac = steps_total > 1 ? (double)step_i / (double)(steps_total - 1) : 0.0;
-      const float lr_t = (float)(lr_final + 0.5 * (lr - lr_final) * (1.0 + std::cos(3.141592653589793 * frac)));
-      ++step_i;
-      for (int k = 0; k < qfs_ws::kLayers; ++k) {
-        launch_adam(m->W[k], m->mW[k], m->vW[k], m->gW[k], (long long)m->dout[k] * m->din[k], lr_t, b1, b2, eps,
-                    bc1, bc2, m->W16[k], st);
-        launch_adam(m->b[k], m->mb[k], m->vb[k], m->gb[k], m->dout[k], lr_t, b1, b2, eps, bc1, bc2, nullptr, st);
-        launch_transpose_bf16(m->W16[k], m->dout[k], m->din[k], m->WT16[k], st);
-      }
     }
     if (rc != QFS_OK) break;
     double ep_loss = 0.0;
@@ -3072,6 +3155,7 @@ extern "C" int qfs_ws_train(qfs_ws* m, int32_t count, const double* targets, con
     if (epoch_loss) epoch_loss[ep] = ep_loss / std::max(nb, 1);
   }
   cudaStreamSynchronize(st);
+  release_train();
   release();
   if (rc != QFS_OK) return rc;
   CK(cudaGetLastError());

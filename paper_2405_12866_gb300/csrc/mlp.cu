@@ -132,9 +132,19 @@ __global__ void k_loss_accumulate(const double* __restrict__ parts, int n, doubl
 }
 
 // Adam (Kingma & Ba 2015) on fp32 master parameters with a bf16 copy.
+// With `sched` (device, 3 floats per step: lr, bc1, bc2) the step's values
+// are read at index *sched_step, so that one captured graph serves every
+// step; otherwise the arguments are used.
 __global__ void k_adam(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
                        const float* __restrict__ g, long long n, float lr, float b1, float b2, float eps,
-                       float bc1, float bc2, __nv_bfloat16* __restrict__ w16) {
+                       float bc1, float bc2, __nv_bfloat16* __restrict__ w16, const float* __restrict__ sched,
+                       const int* __restrict__ sched_step) {
+  if (sched) {
+    const int s = *sched_step;
+    lr = sched[3 * s];
+    bc1 = sched[3 * s + 1];
+    bc2 = sched[3 * s + 2];
+  }
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const float gi = g[i];
     const float mi = b1 * m[i] + (1.f - b1) * gi;
@@ -161,9 +171,13 @@ __global__ void k_ws_gates_adjoint(const float* __restrict__ Y, int ldy, int cou
 
 // Mini-batch gather: rows idx[0..bv) of the device training set into the
 // batch buffers; rows bv..B-1 of X are zeroed.
+// Rows idx[0 .. bv) of the training set, after advancing idx by
+// *jstep * batch when jstep is given (the step within the epoch, read on the
+// device so that one captured graph serves every step).
 __global__ void k_ws_gather(const __nv_bfloat16* __restrict__ Xall, const float* __restrict__ Tall,
                             const int* __restrict__ idx, int bv, int B, __nv_bfloat16* __restrict__ X,
-                            float* __restrict__ T) {
+                            float* __restrict__ T, const int* __restrict__ jstep, int batch) {
+  if (jstep) idx += (long long)*jstep * batch;
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (e < (long long)B * 256) {
     const int r = (int)(e / 256), c = (int)(e % 256);
@@ -172,6 +186,15 @@ __global__ void k_ws_gather(const __nv_bfloat16* __restrict__ Xall, const float*
   if (e < (long long)bv * 192) {
     const int r = (int)(e / 192), c = (int)(e % 192);
     T[e] = Tall[(size_t)idx[r] * 192 + c];
+  }
+}
+
+// The end of a training step: the step within the epoch and the step of
+// the call advance.
+__global__ void k_ws_step_advance(int* jstep, int* gstep) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    *jstep += 1;
+    *gstep += 1;
   }
 }
 
@@ -190,10 +213,11 @@ void launch_ws_gates_adjoint(const float* Y, int ldy, int count, double2* E, cud
   k_ws_gates_adjoint<<<(int)((n + 255) / 256), 256, 0, st>>>(Y, ldy, count, E);
 }
 void launch_ws_gather(const __nv_bfloat16* Xall, const float* Tall, const int* idx, int bv, int B,
-                      __nv_bfloat16* X, float* T, cudaStream_t st) {
+                      __nv_bfloat16* X, float* T, cudaStream_t st, const int* jstep, int batch) {
   const long long n = (long long)B * 256;
-  k_ws_gather<<<(int)((n + 255) / 256), 256, 0, st>>>(Xall, Tall, idx, bv, B, X, T);
+  k_ws_gather<<<(int)((n + 255) / 256), 256, 0, st>>>(Xall, Tall, idx, bv, B, X, T, jstep, batch);
 }
+void launch_ws_step_advance(int* jstep, int* gstep, cudaStream_t st) { k_ws_step_advance<<<1, 32, 0, st>>>(jstep, gstep); }
 void launch_transpose_bf16(const __nv_bfloat16* src, int R, int C, __nv_bfloat16* dst, cudaStream_t st) {
   k_transpose_bf16<<<dim3(C / 32, R / 32), dim3(32, 8), 0, st>>>(src, R, C, dst);
 }
@@ -219,8 +243,9 @@ void launch_loss_accumulate(const double* parts, int n, double scale, double* ac
   k_loss_accumulate<<<1, 256, 0, st>>>(parts, n, scale, acc);
 }
 void launch_adam(float* w, float* m, float* v, const float* g, long long n, float lr, float b1, float b2, float eps,
-                 float bc1, float bc2, __nv_bfloat16* w16, cudaStream_t st) {
-  k_adam<<<blocks_for(n), 256, 0, st>>>(w, m, v, g, n, lr, b1, b2, eps, bc1, bc2, w16);
+                 float bc1, float bc2, __nv_bfloat16* w16, cudaStream_t st, const float* sched,
+                 const int* sched_step) {
+  k_adam<<<blocks_for(n), 256, 0, st>>>(w, m, v, g, n, lr, b1, b2, eps, bc1, bc2, w16, sched, sched_step);
 }
 
 }  // namespace qfs

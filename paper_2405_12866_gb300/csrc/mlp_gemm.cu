@@ -17,6 +17,7 @@
 #include <cuda_bf16.h>
 
 #include <cstdlib>
+#include <mutex>
 
 #include "qfs_kernels.h"
 
@@ -332,13 +333,46 @@ bool encode_kmajor(CUtensorMap* map, const void* ptr, int rows, int K, int ld, i
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Encoded maps of recent operands (the training loop reuses the same
+// buffers every step; encoding is host work on every launch otherwise).
+// Keyed by everything the encoding reads; small, round-robin replacement.
+struct MapKey {
+  const void* ptr;
+  int rows, K, ld, box_rows;
+  bool operator==(const MapKey& o) const {
+    return ptr == o.ptr && rows == o.rows && K == o.K && ld == o.ld && box_rows == o.box_rows;
+  }
+};
+bool cached_kmajor(CUtensorMap* map, const void* ptr, int rows, int K, int ld, int box_rows) {
+  constexpr int kSlots = 64;
+  static std::mutex mu;
+  static MapKey keys[kSlots];
+  static CUtensorMap maps[kSlots];
+  static int used = 0, next = 0;
+  const MapKey k{ptr, rows, K, ld, box_rows};
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    for (int i = 0; i < used; ++i)
+      if (keys[i] == k) {
+        *map = maps[i];
+        return true;
+      }
+  }
+  if (!encode_kmajor(map, ptr, rows, K, ld, box_rows)) return false;
+  std::lock_guard<std::mutex> lock(mu);
+  const int slot = used < kSlots ? used++ : (next++ % kSlots);
+  keys[slot] = k;
+  maps[slot] = *map;
+  return true;
+}
+
 template <int BN>
 cudaError_t launch_tma(const GemmArgs& g, int splitk, cudaStream_t st) {
   static const cudaError_t attr = cudaFuncSetAttribute(k_gemm_bf16_tma<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                        TmaCfg<BN>::kSmem);
   if (attr != cudaSuccess) return attr;
   CUtensorMap ma, mb;
-  if (!encode_kmajor(&ma, g.A, g.M, g.K, g.lda, kBM) || !encode_kmajor(&mb, g.B, g.N, g.K, g.ldb, BN))
+  if (!cached_kmajor(&ma, g.A, g.M, g.K, g.lda, kBM) || !cached_kmajor(&mb, g.B, g.N, g.K, g.ldb, BN))
     return cudaErrorInvalidValue;
   dim3 grid(g.N / BN, g.M / kBM, splitk);
   k_gemm_bf16_tma<BN><<<grid, kTmaThreads, TmaCfg<BN>::kSmem, st>>>(ma, mb, g);

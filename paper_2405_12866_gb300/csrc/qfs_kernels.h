@@ -295,8 +295,12 @@ void launch_ws_features(const double2* U, const double2* phif, int count, int ro
 void launch_transpose_bf16(const __nv_bfloat16* src, int R, int C, __nv_bfloat16* dst, cudaStream_t st);
 void launch_ws_gates_adjoint(const float* Y, int ldy, int count, double2* E, cudaStream_t st);
 void launch_loss_accumulate(const double* parts, int n, double scale, double* acc, cudaStream_t st);
+// jstep (nullable, device): the step within the epoch; the rows taken
+// start at idx + *jstep * batch.
 void launch_ws_gather(const __nv_bfloat16* Xall, const float* Tall, const int* idx, int bv, int B,
-                      __nv_bfloat16* X, float* T, cudaStream_t st);
+                      __nv_bfloat16* X, float* T, cudaStream_t st, const int* jstep = nullptr, int batch = 0);
+// *jstep += 1 and *gstep += 1 on the device (the end of a training step).
+void launch_ws_step_advance(int* jstep, int* gstep, cudaStream_t st);
 void launch_cast_f32_bf16(const float* a, __nv_bfloat16* b, long long n, cudaStream_t st);
 // Returns the number of loss partial sums written.
 int launch_ws_loss_grad(const float* Y, int ldy, const float* T, int n_out, int rows, int B_valid, float* dY32,
@@ -304,7 +308,10 @@ int launch_ws_loss_grad(const float* Y, int ldy, const float* T, int n_out, int 
 void launch_gelu_back(const float* dH, const float* Z, long long n, int ld, int B_valid, float* dZ32,
                       __nv_bfloat16* dZ16, cudaStream_t st);
 void launch_colsum(const float* G, int rows, int cols, float* db, cudaStream_t st);
+// sched (nullable, device): lr, bc1, bc2 of step *sched_step (3 floats per
+// step), in place of the lr, bc1, bc2 arguments.
 void launch_adam(float* w, float* m, float* v, const float* g, long long n, float lr, float b1, float b2, float eps,
-                 float bc1, float bc2, __nv_bfloat16* w16, cudaStream_t st);
+                 float bc1, float bc2, __nv_bfloat16* w16, cudaStream_t st, const float* sched = nullptr,
+                 const int* sched_step = nullptr);
 
 }  // namespace qfs
