@@ -8,9 +8,11 @@
 // stages, each tracked by a "full" mbarrier (transaction bytes) and an
 // "empty" mbarrier; warp 1 owns the TMEM accumulator (128 x BN fp32
 // columns) and one of its threads issues the tcgen05.mma chain, releasing
-// each stage with tcgen05.commit; warps 2-5 wait for the final commit and
-// run the epilogue (tcgen05.ld, bias, GELU, stores).  With split-K (grid z)
-// each CTA reduces a K range and adds its tile into C32 with vector atomics.
+// each stage with tcgen05.commit; warps 2-9 wait for the final commit and
+// run the epilogue (tcgen05.ld, bias, GELU, stores in whole 128-byte lines
+// through shared memory).  With split-K (grid z) each CTA reduces a K range
+// and adds its tile into C32 with vector atomics (the first split adds the
+// bias).
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
