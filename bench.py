@@ -460,8 +460,9 @@ def profile_case(args):
         dev = torch.device("cuda", 0)
         prm = qfs.default_params(M=0, multistarts=8, max_sweeps=500, dist_tol=1e-8, refine_sweeps_max=20)
         with qfs.Context(0) as ctx:
-            # the shape the tuner keeps for this batch, without its trial launches
-            ctx.set_option(qfs.QFS_OPT_BATCH_LANES_PER_START, 32)
+            # the shape the tuner keeps for this batch (16 lanes per start, two
+            # starts per warp), without its trial launches
+            ctx.set_option(qfs.QFS_OPT_BATCH_LANES_PER_START, 16)
             out = torch.zeros(int(Ls.sum()) * 16, dtype=torch.complex128, device=dev)
             info = ctx.instantiate_batch_dev(ns, Ls, pairs, torch.from_numpy(tg).to(dev), torch.from_numpy(sm).to(dev),
                                              torch.from_numpy(ig).to(dev), prm, out)

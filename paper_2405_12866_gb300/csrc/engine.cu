@@ -2494,7 +2494,10 @@ int batch_common(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls, 
       for (const BatchClass& c : classes)
         mix.push_back({batch_class_key(c.n, c.L, c.M, S, true), (int)(10 * c.problems.size() / P)});
       std::sort(mix.begin(), mix.end());
-      for (auto& m : mix) pk = fnv1a(pk, &m, sizeof(m));
+      for (auto& m : mix) {  // field by field: a pair's padding bytes are indeterminate
+        pk = fnv1a(pk, &m.first, sizeof(m.first));
+        pk = fnv1a(pk, &m.second, sizeof(m.second));
+      }
       const double sd[] = {a.tol, a.diff_tol_r};
       pk = fnv1a(pk, sd, sizeof(sd));
     }

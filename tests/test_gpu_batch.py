@@ -114,6 +114,29 @@ def test_batch_512_problems_match_oracle_runs(ctx):
     assert len(differ) <= 2, differ
 
 
+def test_plan_decision_is_reused_for_the_same_class_mix():
+    """The whole-batch plan check runs once per class mix: further calls with
+    the same problems (host or device inputs alike) find the kept decision
+    instead of timing the plans again, and give the same results."""
+    import torch
+    from paper_2405_12866_gb300 import qfs
+    probs = w.uneven_blocks(P=512, seed=6, S=8)
+    prm = qfs.default_params(M=0, multistarts=8, max_sweeps=40, dist_tol=1e-8, refine_sweeps_max=5)
+    args = ([(p.n, p.pairs, p.U) for p in probs], prm, [p.samples() for p in probs],
+            [p.init_gates()[:8] for p in probs])
+    with qfs.Context(0) as c:
+        _, first = c.instantiate_batch(*args)
+        c.batch_schedules()
+        n1 = len(c.batch_plans)
+        assert n1 <= 1
+        for _ in range(2):
+            _, again = c.instantiate_batch(*args)
+            c.batch_schedules()
+            assert len(c.batch_plans) == n1, c.batch_plans
+            assert [r["converged"] for r in again] == [r["converged"] for r in first]
+    torch.cuda.synchronize()
+
+
 def test_batch_matches_oracle_converged_set(ctx):
     probs = w.uneven_blocks(P=24, seed=4, S=8)
     S, max_sweeps = 8, 300
