@@ -18,16 +18,21 @@ def ctx():
     c.close()
 
 
-@pytest.mark.parametrize("M0,min_sweeps,dist", [(2, 0, 0), (2, 6, 0), (4, 0, 0)])
-def test_chain_n3_restart_matches_oracle(ctx, M0, min_sweeps, dist):
+@pytest.mark.parametrize("target,M0,min_sweeps,dist",
+                         [(1, 2, 0, 0), (0, 2, 0, 0), (0, 2, 6, 0), (4, 4, 0, 0), (7, 2, 0, 0), (3, 4, 0, 0)])
+def test_chain_n3_restart_matches_oracle(ctx, target, M0, min_sweeps, dist):
     """Haar training and validation states drawn by the library against the
-    oracle's outer loop on the generator's draws.  (Computational-basis
-    states make the first gate's environment rank-deficient at small M, where
-    the update is not unique; they are checked for validity below.)"""
+    oracle's outer loop on the generator's draws: target 1 stalls (cost
+    0.0555 on both starts, no M converges), the others converge.  Both sides
+    run the same FP64 updates and differ only in the order of rounded sums,
+    so the returned gates agree to ~3e-14 (measured); 1e-11 bounds that with
+    room for the amplification by ~200 sweeps.  (Computational-basis states
+    make the first gate's environment rank-deficient at small M, where the
+    update is not unique; they are checked for validity below.)"""
     from oracle import qfs_oracle as o
     from paper_2405_12866_gb300 import qfs
     from paper_2405_12866_gb300 import workloads as w
-    p = w.chain_n3(target_seed=1)
+    p = w.chain_n3(target_seed=target)
     seed, S, otr = 77, 2, 0.1
     tr = lambda M, a: w.training_states(dist, w.attempt_seed(seed, a), p.n, M)
     va = lambda M, a: w.training_states(dist, w.attempt_seed(seed, a), p.n, M, stream=w.STREAM_VALIDATION)
@@ -40,18 +45,20 @@ def test_chain_n3_restart_matches_oracle(ctx, M0, min_sweeps, dist):
     assert got.training_states == want.training_states
     assert got.converged == want.converged
     assert abs(got.sweeps - want.sweeps) <= 1
+    assert abs(got.cost - want.cost) < 1e-11
     if want.converged:
-        assert got.cost <= 1e-10 and abs(got.cost - want.cost) < 1e-11
+        assert got.cost <= 1e-10
         assert got.best_start == want.best_start
-        assert np.max(np.abs(got.gates - want.gates)) < 1e-6
+        assert np.max(np.abs(got.gates - want.gates)) < 1e-11
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_brick_n8_restart_reaches_a_generalising_solution(ctx, prec):
     """At its literal M = 16 this target stalls near cost 1.3 on every start;
     the outer loop doubles M until the validation cost agrees with the
-    training cost and returns gates whose full-unitary cost (Eq. 1) is
-    within the paper's bound dist_tol (1 + overtrain_ratio), up to a margin."""
+    training cost and returns gates whose full-unitary cost (Eq. 1) per
+    state is within the paper's bound dist_tol (1 + overtrain_ratio)
+    (measured: 7.8e-9 in FP64, 9.1e-9 in the mixed path, against 1.1e-8)."""
     from oracle import qfs_oracle as o
     from paper_2405_12866_gb300 import qfs
     from paper_2405_12866_gb300 import workloads as w
@@ -63,7 +70,7 @@ def test_brick_n8_restart_reaches_a_generalising_solution(ctx, prec):
     assert got.converged and got.cost <= p.tol
     assert got.training_states >= 32
     per_state = o.full_cost(p.U, got.gates, p.pairs, p.n) / (1 << p.n)
-    assert per_state <= 10 * p.tol * (1 + otr)
+    assert per_state <= p.tol * (1 + otr)
 
 
 @pytest.mark.parametrize("dist", [0, 1])
