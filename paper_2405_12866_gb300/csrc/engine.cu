@@ -157,9 +157,11 @@ struct ProfScope {
   double bytes;
   cudaStream_t st;
   cudaEvent_t a = nullptr;
-  ProfScope(qfs_ctx* c, int i, double b, cudaStream_t s = nullptr)
+  // n: the launches the scope brackets (consecutive launches of one kind
+  // can share one pair of events).
+  ProfScope(qfs_ctx* c, int i, double b, cudaStream_t s = nullptr, int n = 1)
       : ctx(c), id(i), bytes(b), st(s ? s : c->stream) {
-    ctx->prof.launches[id] += 1;
+    ctx->prof.launches[id] += n;
     if (ctx->prof.on) {
       a = prof_event(ctx);
       record(a);
@@ -2747,11 +2749,12 @@ long long ws_param_count(const qfs_ws* m) {
   return c;
 }
 
+// One GEMM launch; its timing (when profiling) comes from the ProfScope the
+// caller opens around the consecutive GEMMs of one pass or layer.
 int ws_gemm(qfs_ws* m, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K,
             float* C32, __nv_bfloat16* C16, int ldc, const float* bias, int gelu, int M_valid) {
   GemmArgs g{A, lda, B, ldb, C32, C16, ldc, bias, gelu, M, N, K, M_valid, m->err};
   g.splitk = gemm_splitk_for(g, m->ctx->num_sms > 0 ? m->ctx->num_sms : 148);
-  ProfScope ps(m->ctx, QFS_PROF_MLP, 2.0 * M * N * K);
   CK(launch_gemm_bf16_tc(g, m->ctx->stream));
   return QFS_OK;
 }
@@ -2759,6 +2762,9 @@ int ws_gemm(qfs_ws* m, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, 
 // Forward pass on B rows (multiple of 128) of m->X16: Z32[l], H16[l].
 void ws_forward(qfs_ws* m, int B) {
   const __nv_bfloat16* in = m->X16;
+  double flops = 0.0;
+  for (int l = 0; l < qfs_ws::kLayers; ++l) flops += 2.0 * B * m->dout[l] * m->din[l];
+  ProfScope ps(m->ctx, QFS_PROF_MLP, flops, nullptr, qfs_ws::kLayers);  // four GEMMs back to back
   for (int l = 0; l < qfs_ws::kLayers; ++l) {
     const bool last = l == qfs_ws::kLayers - 1;
     ws_gemm(m, in, m->din[l], m->W16[l], m->din[l], B, m->dout[l], m->din[l], m->Z32[l], last ? nullptr : m->H16[l],
@@ -2783,12 +2789,17 @@ int ws_backward(qfs_ws* m, int B, int B_valid, double* loss, double* loss_acc_de
     launch_transpose_bf16(g16, B, N, m->T1, st);  // N x B
     const __nv_bfloat16* hin = l == 0 ? m->X16 : m->H16[l - 1];
     launch_transpose_bf16(hin, B, K, m->T2, st);  // K x B
-    TRY(ws_gemm(m, m->T1, B, m->T2, B, N, K, B, m->gW[l], nullptr, K, nullptr, 0, N));
+    float* o32 = g32 == m->dA32 ? m->dB32 : m->dA32;
+    __nv_bfloat16* o16 = g16 == m->dA16 ? m->dB16 : m->dA16;
+    {
+      // The layer's weight gradient and (below the first layer) dH = g W
+      // (B x K), back to back under one pair of events.
+      ProfScope ps(m->ctx, QFS_PROF_MLP, (l > 0 ? 4.0 : 2.0) * N * K * B, nullptr, l > 0 ? 2 : 1);
+      TRY(ws_gemm(m, m->T1, B, m->T2, B, N, K, B, m->gW[l], nullptr, K, nullptr, 0, N));
+      if (l > 0) TRY(ws_gemm(m, g16, N, m->WT16[l], N, B, K, N, o32, nullptr, K, nullptr, 0, B));
+    }
     if (l > 0) {
-      float* o32 = g32 == m->dA32 ? m->dB32 : m->dA32;
-      __nv_bfloat16* o16 = g16 == m->dA16 ? m->dB16 : m->dA16;
-      // dH = g W (B x K), then dZ = dH * gelu'(Z_{l-1}).
-      TRY(ws_gemm(m, g16, N, m->WT16[l], N, B, K, N, o32, nullptr, K, nullptr, 0, B));
+      // dZ = dH * gelu'(Z_{l-1}).
       launch_gelu_back(o32, m->Z32[l - 1], (long long)B * K, K, B_valid, o32, o16, st);
       g32 = o32;
       g16 = o16;
