@@ -13,10 +13,15 @@
 namespace qfs {
 
 namespace {
+// Derivative of the tanh form of GELU, 0.5 x (1 + tanh u) with u =
+// k0 (x + k1 x^3): with s = 1 / (1 + exp(-2u)) = (1 + tanh u) / 2 it is
+// s + 2 x s (1 - s) k0 (1 + 3 k1 x^2) (1 - tanh^2 u = 4 s (1 - s), free of
+// the cancellation of 1 - t^2); ~1e-6 relative.  exp(-2u) = inf gives s = 0.
 __device__ __forceinline__ float gelu_grad_f(float x) {
   const float k0 = 0.7978845608028654f, k1 = 0.044715f;
-  const float t = tanhf(k0 * (x + k1 * x * x * x));
-  return 0.5f * (1.f + t) + 0.5f * x * (1.f - t * t) * k0 * (1.f + 3.f * k1 * x * x);
+  const float u = k0 * fmaf(k1 * x, x * x, x);
+  const float s = __fdividef(1.f, 1.f + __expf(-2.f * u));
+  return fmaf(2.f * x * s * (1.f - s), k0 * fmaf(3.f * k1, x * x, 1.f), s);
 }
 }  // namespace
 
@@ -44,6 +49,28 @@ __global__ void k_ws_features(const double2* __restrict__ U, const double2* __re
 }
 
 // dst[c][r] = src[r][c] (bf16), 32 x 32 tiles; R, C multiples of 32.
+// dst (C x R) = src (R x C)^T, both bf16 row-major, R and C multiples of 64:
+// 64 x 64 tiles, two elements per access (128-byte rows per warp on both
+// sides); the shared tile's rows are padded by one word.
+__global__ void k_transpose_bf16_64(const __nv_bfloat16* __restrict__ src, int R, int C,
+                                    __nv_bfloat16* __restrict__ dst) {
+  __shared__ __nv_bfloat16 tile[64][66];
+  const int c0 = blockIdx.x * 64, r0 = blockIdx.y * 64;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int y = ty; y < 64; y += 8) {
+    const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(src + (size_t)(r0 + y) * C + c0 + 2 * tx);
+    tile[y][2 * tx] = v.x;
+    tile[y][2 * tx + 1] = v.y;
+  }
+  __syncthreads();
+  for (int y = ty; y < 64; y += 8) {
+    __nv_bfloat162 v;
+    v.x = tile[2 * tx][y];
+    v.y = tile[2 * tx + 1][y];
+    *reinterpret_cast<__nv_bfloat162*>(dst + (size_t)(c0 + y) * R + r0 + 2 * tx) = v;
+  }
+}
+
 __global__ void k_transpose_bf16(const __nv_bfloat16* __restrict__ src, int R, int C,
                                  __nv_bfloat16* __restrict__ dst) {
   __shared__ __nv_bfloat16 tile[32][33];
@@ -67,9 +94,8 @@ __global__ void k_ws_loss_grad(const float* __restrict__ Y, int ldy, const float
   __shared__ double red[256];
   double acc = 0.0;
   const double scale = 2.0 / ((double)B_valid * n_out);
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)rows * ldy;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int r = (int)(e / ldy), c = (int)(e % ldy);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < rows * ldy; e += gridDim.x * blockDim.x) {
+    const int r = e / ldy, c = e - r * ldy;
     float g = 0.f;
     if (r < B_valid && c < n_out) {
       const double d = (double)Y[e] - (double)T[(size_t)r * n_out + c];
@@ -89,12 +115,23 @@ __global__ void k_ws_loss_grad(const float* __restrict__ Y, int ldy, const float
 }
 
 // dZ = dH * gelu'(Z) (fp32 and bf16), rows >= B_valid zeroed.
-__global__ void k_gelu_back(const float* __restrict__ dH, const float* __restrict__ Z, long long n, int ld,
-                            int B_valid, float* __restrict__ dZ32, __nv_bfloat16* __restrict__ dZ16) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const float g = (i / ld) < B_valid ? dH[i] * gelu_grad_f(Z[i]) : 0.f;
-    dZ32[i] = g;
-    dZ16[i] = __float2bfloat16(g);
+// Four elements per thread (n and ld multiples of 4); row-major, so the
+// first B_valid rows are exactly the elements below B_valid * ld.  dZ32 may
+// be dH (in place: each thread reads its four elements before writing them).
+__global__ void k_gelu_back(const float* dH, const float* __restrict__ Z, long long n, int ld, int B_valid,
+                            float* dZ32, __nv_bfloat16* __restrict__ dZ16) {
+  const long long nvalid = (long long)B_valid * ld;
+  for (long long i = 4 * (blockIdx.x * (long long)blockDim.x + threadIdx.x); i < n;
+       i += 4LL * gridDim.x * blockDim.x) {
+    float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i < nvalid) {
+      const float4 h = *reinterpret_cast<const float4*>(dH + i), z = *reinterpret_cast<const float4*>(Z + i);
+      g = make_float4(h.x * gelu_grad_f(z.x), h.y * gelu_grad_f(z.y), h.z * gelu_grad_f(z.z), h.w * gelu_grad_f(z.w));
+    }
+    *reinterpret_cast<float4*>(dZ32 + i) = g;
+    const __nv_bfloat162 a = __floats2bfloat162_rn(g.x, g.y), b = __floats2bfloat162_rn(g.z, g.w);
+    *reinterpret_cast<uint2*>(dZ16 + i) =
+        make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
   }
 }
 
@@ -219,7 +256,10 @@ void launch_ws_gather(const __nv_bfloat16* Xall, const float* Tall, const int* i
 }
 void launch_ws_step_advance(int* jstep, int* gstep, cudaStream_t st) { k_ws_step_advance<<<1, 32, 0, st>>>(jstep, gstep); }
 void launch_transpose_bf16(const __nv_bfloat16* src, int R, int C, __nv_bfloat16* dst, cudaStream_t st) {
-  k_transpose_bf16<<<dim3(C / 32, R / 32), dim3(32, 8), 0, st>>>(src, R, C, dst);
+  if (R % 64 == 0 && C % 64 == 0)
+    k_transpose_bf16_64<<<dim3(C / 64, R / 64), dim3(32, 8), 0, st>>>(src, R, C, dst);
+  else
+    k_transpose_bf16<<<dim3(C / 32, R / 32), dim3(32, 8), 0, st>>>(src, R, C, dst);
 }
 void launch_cast_f32_bf16(const float* a, __nv_bfloat16* b, long long n, cudaStream_t st) {
   k_cast_f32_bf16<<<blocks_for(n), 256, 0, st>>>(a, b, n);
@@ -232,7 +272,7 @@ int launch_ws_loss_grad(const float* Y, int ldy, const float* T, int n_out, int 
 }
 void launch_gelu_back(const float* dH, const float* Z, long long n, int ld, int B_valid, float* dZ32,
                       __nv_bfloat16* dZ16, cudaStream_t st) {
-  k_gelu_back<<<blocks_for(n), 256, 0, st>>>(dH, Z, n, ld, B_valid, dZ32, dZ16);
+  k_gelu_back<<<blocks_for(n / 4), 256, 0, st>>>(dH, Z, n, ld, B_valid, dZ32, dZ16);
 }
 void launch_colsum(const float* G, int rows, int cols, float* db, cudaStream_t st) {
   cudaMemsetAsync(db, 0, sizeof(float) * (size_t)cols, st);
