@@ -43,7 +43,10 @@ def build(verbose: bool = False, force: bool = False) -> str:
             and os.path.getmtime(LIB) > max(os.path.getmtime(d) for d in deps)):
         return LIB
     extra = shlex.split(os.environ.get("QFS_NVCC_FLAGS", ""))
-    common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O3,-pthread", "-I", INCLUDE] + extra
+    # Host code: no fused multiply-adds, so that it rounds alike on x86 and
+    # Arm (the library's seeded draws of training states and gates are then
+    # the same on both); device code keeps nvcc's FMAs.
+    common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O3,-pthread,-ffp-contract=off", "-I", INCLUDE] + extra
 
     def compile_one(src: str) -> str:
         obj = os.path.join(objdir, os.path.basename(src) + ".o")

@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <array>
+#include <future>
 #include <functional>
 #include <cmath>
 #include <complex>
@@ -3255,32 +3256,77 @@ extern "C" int qfs_ws_instantiate(qfs_ws* m, int32_t P, const double* targets, c
   qfs_params p1 = *p;
   p1.multistarts = 1;
   p1.max_sweeps = first_sweeps;
-  TRY(batch_common(ctx, P, ns.data(), Ls.data(), pairs.data(), in1, &p1, results));
-  int64_t conv1 = 0, work1 = 0;
-  std::vector<int32_t> fail_idx;
-  for (int i = 0; i < P; ++i) {
-    conv1 += results[i].converged;
-    work1 += results[i].sweeps;
-    if (!results[i].converged) fail_idx.push_back(i);
-  }
-  int64_t work2 = 0;
-  if (!fail_idx.empty()) {
-    const int F = (int)fail_idx.size();
+  qfs_params p2 = *p;
+  p2.seed = p->seed + (1ULL << 30);
+  const int S2 = p->multistarts;
+  const int M = p->M > 0 ? std::min(p->M, 1 << kN) : (1 << kN) / 2;
+  const size_t sN = (size_t)M << kN;
+  // Large calls run in two halves so that the host draws of one half's
+  // inputs (training states of stage 1; states and random starts of the
+  // unconverged targets for stage 2) overlap the other half's sweeps: the
+  // draws are those batch_common would make itself (state stream 1 from
+  // seed + i, gates from the same seed), so the answers do not change.
+  const int K = P >= 16384 ? 2 : 1;
+  auto lo = [&](int k) { return (int)((long long)P * k / K); };
+  using Cvec = std::vector<std::complex<double>>;
+  auto draw1 = [&](int k) {
+    const int c0 = lo(k), n = lo(k + 1) - c0;
+    Cvec st1((size_t)n * sN);
+    host_parallel_for(n, [&](int j) { draw_states(p->training_distribution, p1.seed + (uint64_t)(c0 + j), 1u, kN, M,
+                                                  st1.data() + (size_t)j * sN); });
+    return st1;
+  };
+  struct Draw2 {
+    Cvec states, gates;
+  };
+  auto draw2 = [&](const std::vector<int32_t>& idx) {
+    Draw2 d;
+    const int F = (int)idx.size();
+    d.states.resize((size_t)F * sN);
+    d.gates.resize((size_t)F * S2 * kL * 16);
+    host_parallel_for(F, [&](int j) {
+      const uint64_t sd = p2.seed + (uint64_t)idx[j];
+      draw_states(p->training_distribution, sd, 1u, kN, M, d.states.data() + (size_t)j * sN);
+      generate_gates(sd, S2 * kL, d.gates.data() + (size_t)j * S2 * kL * 16);
+    });
+    return d;
+  };
+  auto stage1 = [&](int k, const Cvec& st1) -> int {
+    const int c0 = lo(k), n = lo(k + 1) - c0;
+    BatchInputs in = in1;
+    in.targets = targets + (size_t)c0 * 512;
+    in.gates_out = gates_out + (size_t)c0 * 192;
+    in.init_gates = in1.init_gates + (size_t)c0 * 192;  // one start of six gates per target
+    in.samples = reinterpret_cast<const double*>(st1.data());
+    return batch_common(ctx, n, ns.data(), Ls.data(), pairs.data(), in, &p1, results + c0);
+  };
+  int64_t conv1 = 0, work1 = 0, work2 = 0, nfail = 0;
+  auto failures = [&](int k) {
+    std::vector<int32_t> f;
+    for (int i = lo(k); i < lo(k + 1); ++i) {
+      conv1 += results[i].converged;
+      work1 += results[i].sweeps;
+      if (!results[i].converged) f.push_back(i);
+    }
+    nfail += (int64_t)f.size();
+    return f;
+  };
+  auto stage2 = [&](const std::vector<int32_t>& idx, const Draw2& d) -> int {
+    const int F = (int)idx.size();
+    if (F == 0) return QFS_OK;
     std::vector<double> tf((size_t)F * 512), gf((size_t)F * 192);
     for (int j = 0; j < F; ++j)
-      std::copy(targets + (size_t)fail_idx[j] * 512, targets + (size_t)(fail_idx[j] + 1) * 512,
-                tf.begin() + (size_t)j * 512);
+      std::copy(targets + (size_t)idx[j] * 512, targets + (size_t)(idx[j] + 1) * 512, tf.begin() + (size_t)j * 512);
     std::vector<qfs_result> rf(F);
     BatchInputs in2;
     in2.targets = tf.data();
     in2.gates_out = gf.data();
-    in2.draw_index = fail_idx.data();
-    qfs_params p2 = *p;
-    p2.seed = p->seed + (1ULL << 30);
+    in2.samples = reinterpret_cast<const double*>(d.states.data());
+    in2.init_gates = reinterpret_cast<const double*>(d.gates.data());
     TRY(batch_common(ctx, F, ns.data(), Ls.data(), pairs.data(), in2, &p2, rf.data()));
     for (int j = 0; j < F; ++j) {
-      const int i = fail_idx[j];
-      work2 += (int64_t)rf[j].sweeps * p->multistarts;
+      const int i = idx[j];
+      work2 += (int64_t)rf[j].sweeps * S2;
       std::copy(gf.begin() + (size_t)j * 192, gf.begin() + (size_t)(j + 1) * 192, gates_out + (size_t)i * 192);
       qfs_result r = rf[j];
       r.sweeps += results[i].sweeps;
@@ -3288,12 +3334,40 @@ extern "C" int qfs_ws_instantiate(qfs_ws* m, int32_t P, const double* targets, c
       r.best_start += 1;  // 0 is the first start; fallback start j is j + 1
       results[i] = r;
     }
+    return QFS_OK;
+  };
+  if (K == 1) {
+    TRY(stage1(0, draw1(0)));
+    const std::vector<int32_t> f = failures(0);
+    TRY(stage2(f, draw2(f)));
+  } else try {
+    // draw1(1) || stage 1 of half 0; draw2(half 0) || stage 1 of half 1;
+    // draw2(half 1) || stage 2 of half 0.  Every future is joined before a
+    // return, so no helper outlives the inputs it reads.
+    const Cvec st0 = draw1(0);
+    std::future<Cvec> d1 = std::async(std::launch::async, draw1, 1);
+    const int r0 = stage1(0, st0);
+    const Cvec st1 = d1.get();
+    TRY(r0);
+    const std::vector<int32_t> f0 = failures(0);
+    std::future<Draw2> d20 = std::async(std::launch::async, draw2, std::cref(f0));
+    const int r1 = stage1(1, st1);
+    const Draw2 dr0 = d20.get();
+    TRY(r1);
+    const std::vector<int32_t> f1 = failures(1);
+    std::future<Draw2> d21 = std::async(std::launch::async, draw2, std::cref(f1));
+    const int r2 = stage2(f0, dr0);
+    const Draw2 dr1 = d21.get();
+    TRY(r2);
+    TRY(stage2(f1, dr1));
+  } catch (const std::exception& e) {
+    return fail(QFS_EINTERNAL, "host draw threads: %s", e.what());
   }
   if (stats) {
     stats[0] = conv1;
     stats[1] = work1;
     stats[2] = work2;
-    stats[3] = (int64_t)fail_idx.size();
+    stats[3] = nfail;
   }
   return QFS_OK;
 }
