@@ -177,6 +177,24 @@ def test_batch_seeded_draws(ctx):
         assert np.max(np.abs(a - b)) < 1e-12
 
 
+def test_large_seeded_batch_equals_its_explicit_draws(ctx):
+    """16384 problems with library-drawn inputs against the same problems
+    with the library's draws passed explicitly: problem i's states come from
+    seed + i (stream 1) and its starts from seed + i, so the answers agree
+    bit for bit."""
+    from paper_2405_12866_gb300 import learned, qfs
+    P, S, seed = 16384, 2, 4242
+    T = learned.make_targets(91, P)
+    prm = qfs.default_params(M=0, multistarts=S, max_sweeps=30, dist_tol=1e-8, seed=seed, refine_sweeps_max=5)
+    problems = [(4, learned.PAIRS, T[i]) for i in range(P)]
+    g_seed, i_seed = ctx.instantiate_batch(problems, prm)
+    drawn = [qfs.generate_inputs(seed + i, 4, 8, S, 6) for i in range(P)]
+    g_exp, i_exp = ctx.instantiate_batch(problems, prm, [d[0] for d in drawn], [d[1] for d in drawn])
+    assert all(np.array_equal(a, b) for a, b in zip(g_seed, g_exp))
+    assert [r["converged"] for r in i_seed] == [r["converged"] for r in i_exp]
+    assert [r["sweeps"] for r in i_seed] == [r["sweeps"] for r in i_exp]
+
+
 def test_batch_plateau_stops_stuck_starts_early():
     """With the paper's plateau detection (App. A) the starts of problems
     that do not converge stop early; converging problems still converge."""
