@@ -141,6 +141,7 @@ def bf16_peak(sustained=True):
 
 KERNEL_SOURCES = {
     "k_sweep_df": ("sweep_df.cu", "polar4.cuh", "qfs_common.cuh", "qfs_kernels.h"),
+    "k_batch_sweep": ("batch.cu", "polar4.cuh", "qfs_common.cuh", "qfs_kernels.h"),
     "k_backward_q4": ("kernels_sweep.cu", "polar4.cuh", "qfs_common.cuh", "qfs_kernels.h"),
 }
 
@@ -584,7 +585,8 @@ def run_ours_batch(args):
         "roofline": {"bound": "alu", "kernel": "k_batch_sweep (persistent)", "achieved": achieved,
                      "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                      "peak_source": "FP32 FMA peak measured on GB300 by an FMA-chain throughput kernel: 72.9 TFLOP/s",
-                     "traffic": None, "algorithmic_flops_per_step": flops / args.steps},
+                     "traffic": None if args.plateau else traffic_record("k_batch_sweep", "uneven_blocks"),
+                     "algorithmic_flops_per_step": flops / args.steps},
         "clocks": clk,
         "e2e": {"value": conv_e2e / t_e2e, "unit": UNIT, "note": "host API incl. host-side packing and copies",
                 "h2d_bytes_per_step": int(sum(x.nbytes for x in hin)), "d2h_bytes_per_step": int(b[1].sum()) * 256},
