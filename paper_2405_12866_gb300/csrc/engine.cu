@@ -2740,6 +2740,12 @@ struct qfs_ws {
   int* err = nullptr;
   double2* pred = nullptr;       // predicted gates of a policy call (grown on demand)
   size_t pred_cap = 0;           // in problems
+  // Pinned host buffers the policy draws its inputs into (grown on demand,
+  // reused by later calls): stage-1 states of each half, and states and
+  // random starts of each half's unconverged targets.
+  static constexpr int kPinSlots = 6;
+  std::complex<double>* pin[kPinSlots] = {};
+  size_t pin_cap[kPinSlots] = {};
 };
 
 namespace {
@@ -2934,6 +2940,8 @@ extern "C" void qfs_ws_destroy(qfs_ws* m) {
   cudaStreamSynchronize(m->ctx->stream);
   cudaFree(m->mem);
   if (m->pred) cudaFree(m->pred);
+  for (int i = 0; i < qfs_ws::kPinSlots; ++i)
+    if (m->pin[i]) cudaFreeHost(m->pin[i]);
   delete m;
 }
 
@@ -3268,36 +3276,56 @@ extern "C" int qfs_ws_instantiate(qfs_ws* m, int32_t P, const double* targets, c
   // seed + i, gates from the same seed), so the answers do not change.
   const int K = P >= 16384 ? 2 : 1;
   auto lo = [&](int k) { return (int)((long long)P * k / K); };
-  using Cvec = std::vector<std::complex<double>>;
+  // Pinned slot `slot` with room for n complex values (grown when needed;
+  // nullptr if the host allocation fails).
+  auto pinned = [&](int slot, size_t n) -> std::complex<double>* {
+    if (m->pin_cap[slot] < n) {
+      if (m->pin[slot]) cudaFreeHost(m->pin[slot]);
+      m->pin[slot] = nullptr;
+      m->pin_cap[slot] = 0;
+      void* ptr = nullptr;
+      if (cudaMallocHost(&ptr, std::max<size_t>(n, 1) * sizeof(std::complex<double>)) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+      }
+      m->pin[slot] = static_cast<std::complex<double>*>(ptr);
+      m->pin_cap[slot] = n;
+    }
+    return m->pin[slot];
+  };
+  for (int k = 0; k < K; ++k) {
+    if (!pinned(k, (size_t)(lo(k + 1) - lo(k)) * sN))
+      return fail(QFS_ENOMEM, "pinned host memory for the drawn training states");
+  }
+  // Stage-1 states of half k into slot k.
   auto draw1 = [&](int k) {
     const int c0 = lo(k), n = lo(k + 1) - c0;
-    Cvec st1((size_t)n * sN);
+    std::complex<double>* st1 = m->pin[k];
     host_parallel_for(n, [&](int j) { draw_states(p->training_distribution, p1.seed + (uint64_t)(c0 + j), 1u, kN, M,
-                                                  st1.data() + (size_t)j * sN); });
-    return st1;
+                                                  st1 + (size_t)j * sN); });
   };
-  struct Draw2 {
-    Cvec states, gates;
-  };
-  auto draw2 = [&](const std::vector<int32_t>& idx) {
-    Draw2 d;
+  // States and starts of the unconverged targets idx of half k into slots
+  // 2 + 2k and 3 + 2k (sized by the caller).
+  auto draw2 = [&](int k, const std::vector<int32_t>& idx) {
     const int F = (int)idx.size();
-    d.states.resize((size_t)F * sN);
-    d.gates.resize((size_t)F * S2 * kL * 16);
+    std::complex<double>* states = m->pin[2 + 2 * k];
+    std::complex<double>* gates = m->pin[3 + 2 * k];
     host_parallel_for(F, [&](int j) {
       const uint64_t sd = p2.seed + (uint64_t)idx[j];
-      draw_states(p->training_distribution, sd, 1u, kN, M, d.states.data() + (size_t)j * sN);
-      generate_gates(sd, S2 * kL, d.gates.data() + (size_t)j * S2 * kL * 16);
+      draw_states(p->training_distribution, sd, 1u, kN, M, states + (size_t)j * sN);
+      generate_gates(sd, S2 * kL, gates + (size_t)j * S2 * kL * 16);
     });
-    return d;
   };
-  auto stage1 = [&](int k, const Cvec& st1) -> int {
+  auto room2 = [&](int k, size_t F) {
+    return pinned(2 + 2 * k, F * sN) != nullptr && pinned(3 + 2 * k, F * S2 * kL * 16) != nullptr;
+  };
+  auto stage1 = [&](int k) -> int {
     const int c0 = lo(k), n = lo(k + 1) - c0;
     BatchInputs in = in1;
     in.targets = targets + (size_t)c0 * 512;
     in.gates_out = gates_out + (size_t)c0 * 192;
     in.init_gates = in1.init_gates + (size_t)c0 * 192;  // one start of six gates per target
-    in.samples = reinterpret_cast<const double*>(st1.data());
+    in.samples = reinterpret_cast<const double*>(m->pin[k]);
     return batch_common(ctx, n, ns.data(), Ls.data(), pairs.data(), in, &p1, results + c0);
   };
   int64_t conv1 = 0, work1 = 0, work2 = 0, nfail = 0;
@@ -3311,7 +3339,7 @@ extern "C" int qfs_ws_instantiate(qfs_ws* m, int32_t P, const double* targets, c
     nfail += (int64_t)f.size();
     return f;
   };
-  auto stage2 = [&](const std::vector<int32_t>& idx, const Draw2& d) -> int {
+  auto stage2 = [&](int k, const std::vector<int32_t>& idx) -> int {
     const int F = (int)idx.size();
     if (F == 0) return QFS_OK;
     std::vector<double> tf((size_t)F * 512), gf((size_t)F * 192);
@@ -3321,8 +3349,8 @@ extern "C" int qfs_ws_instantiate(qfs_ws* m, int32_t P, const double* targets, c
     BatchInputs in2;
     in2.targets = tf.data();
     in2.gates_out = gf.data();
-    in2.samples = reinterpret_cast<const double*>(d.states.data());
-    in2.init_gates = reinterpret_cast<const double*>(d.gates.data());
+    in2.samples = reinterpret_cast<const double*>(m->pin[2 + 2 * k]);
+    in2.init_gates = reinterpret_cast<const double*>(m->pin[3 + 2 * k]);
     TRY(batch_common(ctx, F, ns.data(), Ls.data(), pairs.data(), in2, &p2, rf.data()));
     for (int j = 0; j < F; ++j) {
       const int i = idx[j];
@@ -3337,29 +3365,34 @@ extern "C" int qfs_ws_instantiate(qfs_ws* m, int32_t P, const double* targets, c
     return QFS_OK;
   };
   if (K == 1) {
-    TRY(stage1(0, draw1(0)));
+    draw1(0);
+    TRY(stage1(0));
     const std::vector<int32_t> f = failures(0);
-    TRY(stage2(f, draw2(f)));
+    if (!room2(0, f.size())) return fail(QFS_ENOMEM, "pinned host memory for the fallback inputs");
+    draw2(0, f);
+    TRY(stage2(0, f));
   } else try {
     // draw1(1) || stage 1 of half 0; draw2(half 0) || stage 1 of half 1;
     // draw2(half 1) || stage 2 of half 0.  Every future is joined before a
-    // return, so no helper outlives the inputs it reads.
-    const Cvec st0 = draw1(0);
-    std::future<Cvec> d1 = std::async(std::launch::async, draw1, 1);
-    const int r0 = stage1(0, st0);
-    const Cvec st1 = d1.get();
+    // return, so no helper outlives the buffers it writes.
+    draw1(0);
+    std::future<void> d1 = std::async(std::launch::async, draw1, 1);
+    const int r0 = stage1(0);
+    d1.get();
     TRY(r0);
     const std::vector<int32_t> f0 = failures(0);
-    std::future<Draw2> d20 = std::async(std::launch::async, draw2, std::cref(f0));
-    const int r1 = stage1(1, st1);
-    const Draw2 dr0 = d20.get();
+    if (!room2(0, f0.size())) return fail(QFS_ENOMEM, "pinned host memory for the fallback inputs");
+    std::future<void> d20 = std::async(std::launch::async, draw2, 0, std::cref(f0));
+    const int r1 = stage1(1);
+    d20.get();
     TRY(r1);
     const std::vector<int32_t> f1 = failures(1);
-    std::future<Draw2> d21 = std::async(std::launch::async, draw2, std::cref(f1));
-    const int r2 = stage2(f0, dr0);
-    const Draw2 dr1 = d21.get();
+    if (!room2(1, f1.size())) return fail(QFS_ENOMEM, "pinned host memory for the fallback inputs");
+    std::future<void> d21 = std::async(std::launch::async, draw2, 1, std::cref(f1));
+    const int r2 = stage2(0, f0);
+    d21.get();
     TRY(r2);
-    TRY(stage2(f1, dr1));
+    TRY(stage2(1, f1));
   } catch (const std::exception& e) {
     return fail(QFS_EINTERNAL, "host draw threads: %s", e.what());
   }

@@ -55,6 +55,23 @@ def test_gemm_bf16_fp32_only_split_k(ctx, M, N, K):
     assert np.max(np.abs(got - ref)) < 2e-4 * max(1.0, np.max(np.abs(ref)))
 
 
+@pytest.mark.parametrize("M,N,K", [(4096, 256, 1024), (1024, 256, 2048)])
+def test_gemm_bf16_bias_only_split_k(ctx, M, N, K):
+    """A C32 output with a bias and no bf16 copy (the network's last layer)
+    also splits K; the first split adds the bias, the others only their
+    partial products."""
+    import torch
+    rng = np.random.default_rng(11 * M + N + K)
+    A = _bf16(rng.standard_normal((M, K)))
+    B = _bf16(rng.standard_normal((N, K)))
+    bias = torch.from_numpy(rng.standard_normal(N).astype(np.float32))
+    dev = torch.device("cuda:0")
+    C32, _ = ctx.gemm_bf16(A.to(dev), B.to(dev), bias=bias.to(dev))
+    ref = A.double().numpy() @ B.double().numpy().T + bias.double().numpy()[None, :]
+    got = C32.cpu().double().numpy()
+    assert np.max(np.abs(got - ref)) < 2e-4 * max(1.0, np.max(np.abs(ref)))
+
+
 def test_gemm_bf16_m_valid_rows(ctx):
     import torch
     rng = np.random.default_rng(11)
