@@ -134,6 +134,8 @@ struct qfs_ctx {
   size_t l2_bytes = 0;
   char* ws = nullptr;
   size_t ws_bytes = 0;
+  std::complex<double>* h_draw = nullptr;  // pinned: the batched form's host draws (grown on demand)
+  size_t h_draw_cap = 0;
   double* h_pinned = nullptr;  // cost read-back
   size_t h_pinned_n = 0;
 };
@@ -1558,6 +1560,7 @@ void qfs_destroy(qfs_ctx* ctx) {
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->df_trace) cudaFree(ctx->df_trace);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+  if (ctx->h_draw) cudaFreeHost(ctx->h_draw);
   prof_harvest(ctx);
   for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
   for (int g = 0; g < kMaxGroups; ++g) {
@@ -2279,22 +2282,41 @@ int batch_common(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls, 
   // Training states and initial gates: given, or drawn per problem from
   // seed + problem index (or seed + draw_index[i]; the library's Philox draws).
   auto draw_seed = [&](int i) { return p->seed + (uint64_t)(in.draw_index ? in.draw_index[i] : i); };
-  std::vector<std::complex<double>> hs, hg;
+  // Draws go into the context's pinned buffer (reused across calls; any
+  // copy still reading it has finished once the stream is idle).
+  const size_t need = (in.samples ? 0 : (size_t)state_off) + (in.init_gates ? 0 : (size_t)gate_off);
+  std::complex<double>* hbuf = nullptr;
+  if (need) {
+    CK(cudaStreamSynchronize(st));
+    if (ctx->h_draw_cap < need) {
+      if (ctx->h_draw) CK(cudaFreeHost(ctx->h_draw));
+      ctx->h_draw = nullptr;
+      ctx->h_draw_cap = 0;
+      void* ptr = nullptr;
+      if (cudaMallocHost(&ptr, need * sizeof(std::complex<double>)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(QFS_ENOMEM, "pinned host memory for %zu drawn complex values", need);
+      }
+      ctx->h_draw = static_cast<std::complex<double>*>(ptr);
+      ctx->h_draw_cap = need;
+    }
+    hbuf = ctx->h_draw;
+  }
   if (in.samples) {
     CK(cudaMemcpyAsync(w + o_psi64, in.samples, sizeof(double2) * state_off, s_kind, st));
   } else {
-    hs.resize(state_off);
+    std::complex<double>* hs = hbuf;
     host_parallel_for(P, [&](int i) {
-      draw_states(p->training_distribution, draw_seed(i), 1u, probs[i].n, probs[i].M, hs.data() + probs[i].state_off);
+      draw_states(p->training_distribution, draw_seed(i), 1u, probs[i].n, probs[i].M, hs + probs[i].state_off);
     });
-    CK(cudaMemcpyAsync(w + o_psi64, hs.data(), sizeof(double2) * state_off, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(w + o_psi64, hs, sizeof(double2) * state_off, cudaMemcpyHostToDevice, st));
   }
   if (in.init_gates) {
     CK(cudaMemcpyAsync(w + o_g0, in.init_gates, sizeof(double2) * gate_off, g_kind, st));
   } else {
-    hg.resize(gate_off);
-    host_parallel_for(P, [&](int i) { generate_gates(draw_seed(i), S * probs[i].L, hg.data() + probs[i].gate_off); });
-    CK(cudaMemcpyAsync(w + o_g0, hg.data(), sizeof(double2) * gate_off, cudaMemcpyHostToDevice, st));
+    std::complex<double>* hg = hbuf + (in.samples ? 0 : state_off);
+    host_parallel_for(P, [&](int i) { generate_gates(draw_seed(i), S * probs[i].L, hg + probs[i].gate_off); });
+    CK(cudaMemcpyAsync(w + o_g0, hg, sizeof(double2) * gate_off, cudaMemcpyHostToDevice, st));
   }
   (void)any_dev;
   // Schedules: forced (tests) or tuned per class.
