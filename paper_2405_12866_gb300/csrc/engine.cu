@@ -136,6 +136,8 @@ struct qfs_ctx {
   size_t ws_bytes = 0;
   std::complex<double>* h_draw = nullptr;  // pinned: the batched form's host draws (grown on demand)
   size_t h_draw_cap = 0;
+  std::complex<double>* h_half[2] = {};    // pinned: the draws of each half of a large seeded batch
+  size_t h_half_cap[2] = {};
   double* h_pinned = nullptr;  // cost read-back
   size_t h_pinned_n = 0;
 };
@@ -1561,6 +1563,8 @@ void qfs_destroy(qfs_ctx* ctx) {
   if (ctx->df_trace) cudaFree(ctx->df_trace);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
   if (ctx->h_draw) cudaFreeHost(ctx->h_draw);
+  for (int k = 0; k < 2; ++k)
+    if (ctx->h_half[k]) cudaFreeHost(ctx->h_half[k]);
   prof_harvest(ctx);
   for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
   for (int g = 0; g < kMaxGroups; ++g) {
@@ -2593,11 +2597,90 @@ int batch_common(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls, 
 
 }  // namespace
 
+// A large batch with library-drawn inputs in two halves: the host draws of
+// the second half (training states from seed + i, stream 1; initial gates
+// from seed + i, into pinned buffers of the context) run on a helper thread
+// while the first half sweeps.  The draws are those batch_common would make,
+// so each problem's inputs are unchanged.
+int batch_seeded_halves(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls, const int32_t* pairs,
+                        const double* targets, const qfs_params* p, double* gates_out, qfs_result* results) {
+  const int S = p->multistarts;
+  std::vector<long long> toff(P + 1, 0), poff(P + 1, 0), goff(P + 1, 0), soff(P + 1, 0), ioff(P + 1, 0);
+  for (int i = 0; i < P; ++i) {
+    const int n = ns[i], L = Ls[i];
+    const long long N = 1LL << n;
+    const long long M = p->M > 0 ? std::min<long long>(p->M, N) : N / 2;
+    toff[i + 1] = toff[i] + N * N;
+    poff[i + 1] = poff[i] + 2LL * L;
+    goff[i + 1] = goff[i] + 16LL * L;
+    soff[i + 1] = soff[i] + N * M;
+    ioff[i + 1] = ioff[i] + 16LL * S * L;
+  }
+  auto lo = [&](int k) { return k == 0 ? 0 : k == 1 ? P / 2 : P; };
+  TRY(ctx_check(ctx));
+  TRY(set_device(ctx));
+  CK(cudaStreamSynchronize(ctx->stream));  // no copy of an earlier call still reads the buffers
+  for (int k = 0; k < 2; ++k) {
+    const size_t need = (size_t)(soff[lo(k + 1)] - soff[lo(k)] + ioff[lo(k + 1)] - ioff[lo(k)]);
+    if (ctx->h_half_cap[k] < need) {
+      if (ctx->h_half[k]) CK(cudaFreeHost(ctx->h_half[k]));
+      ctx->h_half[k] = nullptr;
+      ctx->h_half_cap[k] = 0;
+      void* ptr = nullptr;
+      if (cudaMallocHost(&ptr, need * sizeof(std::complex<double>)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(QFS_ENOMEM, "pinned host memory for %zu drawn complex values", need);
+      }
+      ctx->h_half[k] = static_cast<std::complex<double>*>(ptr);
+      ctx->h_half_cap[k] = need;
+    }
+  }
+  // Half k's states, then its gates, in h_half[k].
+  auto draw = [&](int k) {
+    const int a = lo(k), b = lo(k + 1);
+    std::complex<double>* states = ctx->h_half[k];
+    std::complex<double>* gates = states + (soff[b] - soff[a]);
+    host_parallel_for(b - a, [&](int j) {
+      const int i = a + j;
+      const int n = ns[i];
+      const int N = 1 << n;
+      const int M = p->M > 0 ? std::min(p->M, N) : N / 2;
+      draw_states(p->training_distribution, p->seed + (uint64_t)i, 1u, n, M, states + (soff[i] - soff[a]));
+      generate_gates(p->seed + (uint64_t)i, S * Ls[i], gates + (ioff[i] - ioff[a]));
+    });
+  };
+  auto run = [&](int k) {
+    const int a = lo(k), b = lo(k + 1);
+    BatchInputs in;
+    in.targets = targets + 2 * toff[a];
+    in.samples = reinterpret_cast<const double*>(ctx->h_half[k]);
+    in.init_gates = reinterpret_cast<const double*>(ctx->h_half[k] + (soff[b] - soff[a]));
+    in.gates_out = gates_out + 2 * goff[a];
+    return batch_common(ctx, b - a, ns + a, Ls + a, pairs + poff[a], in, p, results + a);
+  };
+  try {
+    draw(0);
+    std::future<void> f1 = std::async(std::launch::async, draw, 1);
+    const int r0 = run(0);
+    f1.get();  // joined before any return
+    TRY(r0);
+    return run(1);
+  } catch (const std::exception& e) {
+    return fail(QFS_EINTERNAL, "host draw threads: %s", e.what());
+  }
+}
+
 extern "C" int qfs_instantiate_batch(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls,
                                      const int32_t* pairs, const double* targets,
                                      const double* samples, const double* init_gates,
                                      const qfs_params* p, double* gates_out, qfs_result* results) {
   g_err.clear();
+  if (!samples && !init_gates && P >= 16384 && ns && Ls && pairs && targets && p && gates_out && results) {
+    bool sized = p->multistarts >= 1 && p->multistarts <= 64 &&
+                 (p->training_distribution == QFS_STATES_HAAR || p->training_distribution == QFS_STATES_BASIS);
+    for (int i = 0; i < P && sized; ++i) sized = ns[i] >= 2 && ns[i] <= 6 && Ls[i] >= 1 && Ls[i] <= 32;
+    if (sized) return batch_seeded_halves(ctx, P, ns, Ls, pairs, targets, p, gates_out, results);
+  }
   BatchInputs in;
   in.targets = targets;
   in.samples = samples;
