@@ -148,6 +148,10 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
+  // Launched as a programmatic dependent of the previous kernel on the
+  // stream: the set-up above may overlap its tail; no global memory is read
+  // or written before that kernel has completed and its writes are visible.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
 
   if (warp == 0) {
     // Producer: one thread issues the TMA loads of both operands per stage.
@@ -203,6 +207,10 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
       // Arrives once every MMA issued above has completed.
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(accf))
                    : "memory");
+      // Every operand load of this CTA is issued: the next kernel on the
+      // stream may start its set-up (it waits for this grid to complete
+      // before touching memory).
+      asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     }
     __syncwarp();
   } else {
@@ -377,7 +385,21 @@ cudaError_t launch_tma(const GemmArgs& g, int splitk, cudaStream_t st) {
   if (!cached_kmajor(&ma, g.A, g.M, g.K, g.lda, kBM) || !cached_kmajor(&mb, g.B, g.N, g.K, g.ldb, BN))
     return cudaErrorInvalidValue;
   dim3 grid(g.N / BN, g.M / kBM, splitk);
-  k_gemm_bf16_tma<BN><<<grid, kTmaThreads, TmaCfg<BN>::kSmem, st>>>(ma, mb, g);
+  // Programmatic dependent launch: this GEMM's set-up may overlap the tail
+  // of the previous kernel on the stream (the kernel waits for it before
+  // any memory access).
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(kTmaThreads);
+  cfg.dynamicSmemBytes = TmaCfg<BN>::kSmem;
+  cfg.stream = st;
+  cudaLaunchAttribute pdl[1];
+  pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  pdl[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = pdl;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_gemm_bf16_tma<BN>, ma, mb, g);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
