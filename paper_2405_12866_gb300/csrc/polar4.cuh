@@ -570,10 +570,12 @@ __device__ __forceinline__ bool warp_polar4_f32_warm(float2 a, float2* v_io, flo
   if (!(smin > 1e-6f * smax)) return false;
   const float inv = rsqrtf(nrm);
   w = float2{w.x * inv, w.y * inv};
-  float2 q = mm_bh(w, v, row, col);
-  const float2 gq = mm_ah(q, q, row, col);
-  const float2 t{(row == col ? 1.5f : 0.f) - 0.5f * gq.x, -0.5f * gq.y};
-  *q_out = mm(q, t, row, col);
+  // Q = W V^H, unitary to the Jacobi tolerance (~1e-6), with no
+  // Newton-Schulz step: the batched sweeps (this routine's only user) see
+  // that deviation only quadratically in their residual cost, each update
+  // starts afresh, and their finishing kernel makes the answer unitary in
+  // FP64.  V carries over between sweeps, so it is renormalised.
+  *q_out = mm_bh(w, v, row, col);
   if (rotated) {  // an unrotated V is the stored one: nothing to renormalise
     const float2 gv = mm_ah(v, v, row, col);
     const float2 tv{(row == col ? 1.5f : 0.f) - 0.5f * gv.x, -0.5f * gv.y};
