@@ -33,6 +33,59 @@ namespace qfs {
 
 namespace {
 
+// As warp_polar4_f32 (polar4.cuh), but the Jacobi starts from the right singular vectors
+// V0 of the gate's previous update (16 complex at v_io, V[r][c] at 4c + r):
+// X = A V0, whose columns are already nearly orthogonal once the sweeps
+// settle, so fewer rotation sweeps are needed.  The new V, made unitary to
+// FP32 rounding by one Newton-Schulz step (so that no drift accumulates over
+// sweeps), is written back to v_io.
+__device__ __forceinline__ bool warp_polar4_f32_warm(float2 a, float2* v_io, float2* q_out) {
+  const int lane = threadIdx.x & 31;
+  const int l16 = lane & 15, row = l16 & 3, col = l16 >> 2;
+  const bool isV = lane >= 16;
+  const float2 v0 = v_io[l16];  // every lane: V0[row][col]
+  float2 x;
+  {
+    float2 acc{0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float2 ak = shfl_c(a, 4 * k + row), vk = shfl_c(v0, 4 * col + k);
+      acc = cfma(ak, vk, acc);
+    }
+    x = isV ? v0 : acc;
+  }
+  bool rotated = false;
+  x = jacobi32_sweeps(x, &rotated);
+  float2 w = shfl_c(x, l16);
+  float2 v = shfl_c(x, 16 + l16);
+  float nrm = w.x * w.x + w.y * w.y;
+  nrm += __shfl_xor_sync(FULL, nrm, 1);
+  nrm += __shfl_xor_sync(FULL, nrm, 2);
+  float smax = nrm, smin = nrm;
+  smax = fmaxf(smax, __shfl_xor_sync(FULL, smax, 4));
+  smax = fmaxf(smax, __shfl_xor_sync(FULL, smax, 8));
+  smin = fminf(smin, __shfl_xor_sync(FULL, smin, 4));
+  smin = fminf(smin, __shfl_xor_sync(FULL, smin, 8));
+  if (!(smin > 1e-6f * smax)) return false;
+  const float inv = rsqrtf(nrm);
+  w = float2{w.x * inv, w.y * inv};
+  // Q = W V^H, unitary to the Jacobi tolerance (~1e-6), with no
+  // Newton-Schulz step: the batched sweeps see that deviation only
+  // quadratically in their residual cost, each update starts afresh, and the
+  // finishing kernel makes the answer unitary in FP64.  V carries over
+  // between sweeps, so it is renormalised.
+  *q_out = mm_bh(w, v, row, col);
+  if (rotated) {  // an unrotated V is the stored one: nothing to renormalise
+    const float2 gv = mm_ah(v, v, row, col);
+    const float2 tv{(row == col ? 1.5f : 0.f) - 0.5f * gv.x, -0.5f * gv.y};
+    v = mm(v, tv, row, col);
+    __syncwarp();
+    if (lane < 16) v_io[l16] = v;
+  }
+  __syncwarp();
+  return true;
+}
+
 template <typename T> struct BT;
 template <> struct BT<float> { using t2 = float2; };
 template <> struct BT<double> { using t2 = double2; };
