@@ -12,8 +12,8 @@
 // starts' state arithmetic (gate applications, environment sums) runs side
 // by side in their lane groups; each group reduces its environment over its
 // own lanes, and the warp then updates the unit's gates one after another
-// (Eq. 2: the FP32 Jacobi polar factor with a Newton-Schulz step, FP64
-// Jacobi for ill-conditioned environments).  Units come from an atomic work
+// (Eq. 2: the FP32 Jacobi polar factor, FP64 Jacobi for ill-conditioned
+// environments).  Units come from an atomic work
 // queue ordered largest problem first; the schedule G (and the warps per
 // block) of each class of problems (n, L, M) is chosen by the host's
 // autotuner.  The run's stop rule is kept without any waiting: a start stops

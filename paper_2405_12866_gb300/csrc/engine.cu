@@ -114,8 +114,9 @@ struct qfs_ctx {
   // start-sweep in ns (qfs_batch_schedules reads them back).
   std::vector<std::array<int, 6>> batch_trial_shape;
   std::vector<double> batch_trial_ns;
-  // Whole-batch plan decisions: batch shape key -> 0 (per-class shapes) or
-  // 1 (one start per warp everywhere), with the two timings in ms.
+  // Whole-batch plan decisions: batch shape key -> 0 (per-class shapes), 1
+  // (one start per warp everywhere) or 2 (16 lanes per start wherever a class
+  // admits it), with the three timings in ms.
   std::vector<std::pair<uint64_t, int>> batch_plans;
   std::vector<std::array<float, 3>> batch_plan_ms;
   struct BatchGraph {
@@ -1983,12 +1984,10 @@ long long batch_class_key(int n, int L, int M, int S, bool lane_groups) {
   return ((((long long)n * 64 + L) * 4096 + M) * 128 + S) * 2 + (lane_groups ? 1 : 0);
 }
 
-// Warps per block for G lanes per start and problems of at most max_elems
-// amplitudes and max_L gates: the choice (2, 4 or 8) with the most resident
-// warps per SM (the kernel has no block-wide barrier, so this only sets the
+// Warps per block (2, 4 or 8) for a launch whose warps each take region_f2
+// float2 of shared memory: the most resident warps per SM (4 on ties, then
+// 2, then 8; the kernel has no block-wide barrier, so this only sets the
 // shared-memory granularity); 0 if none fits.
-// Warps per block for a launch whose warps each take region_f2 float2 of
-// shared memory: the most resident warps per SM (4 on ties, then 2, then 8).
 int batch_warps_region(int G, int region_f2) {
   int best = 0, best_res = 0;
   for (int w : {4, 2, 8}) {
@@ -2003,6 +2002,7 @@ int batch_warps_region(int G, int region_f2) {
   return best;
 }
 
+// The same for problems of at most max_elems amplitudes and max_L gates.
 int batch_warps_for(int G, int max_elems, int max_L) {
   return batch_warps_region(G, batch_region_f2(G, max_elems, max_L));
 }
