@@ -512,6 +512,31 @@ def _pack_batch(probs, S):
     return ns, Ls, pairs, tg, sm, ig
 
 
+def unit_trace_summary(tr, probs, info):
+    """Critical path of one traced batched run: how long the GPU stays full,
+    the tail after it, and the unit that ends the run (its problem's size,
+    sweeps, start and duration).  tr: Context.batch_trace_read()."""
+    if len(tr["t0"]) == 0:
+        return None
+    t0 = (tr["t0"] - tr["t0"].min()).astype(np.float64) / 1e6
+    t1 = (tr["t1"] - tr["t0"].min()).astype(np.float64) / 1e6
+    span = float(t1.max())
+    grid = np.linspace(0.0, span, 401)
+    active = np.array([int(((t0 <= t) & (t1 > t)).sum()) for t in grid])
+    peak = int(active.max())
+    full = grid[active >= 0.9 * peak]
+    full_until = float(full.max()) if len(full) else 0.0
+    last = int(np.argmax(t1))
+    p = int(tr["problem"][last])
+    sw = info[p]["sweeps"]
+    return {"units": int(len(t0)), "span_ms": span, "peak_concurrent_units": peak,
+            "full_until_ms": full_until, "tail_ms": span - full_until,
+            "last_unit": {"n": int(probs[p].n), "L": int(probs[p].L), "converged": bool(info[p]["converged"]),
+                          "sweeps": int(sw), "lanes_per_start": int(tr["G"][last]),
+                          "start_ms": float(t0[last]), "duration_ms": float(t1[last] - t0[last]),
+                          "us_per_sweep": float(1e3 * (t1[last] - t0[last]) / max(1, sw))}}
+
+
 def run_ours_batch(args):
     """The batched form: one step = one whole batch of problems."""
     import torch
@@ -592,6 +617,12 @@ def run_ours_batch(args):
                 "h2d_bytes_per_step": int(sum(x.nbytes for x in hin)), "d2h_bytes_per_step": int(b[1].sum()) * 256},
         "gpu_launches": int(launches),
     }
+    # One more step, untimed, with the unit trace on: where the makespan goes.
+    ctx.batch_trace(1 << 20)
+    tr_info = step(0)
+    torch.cuda.synchronize(dev)
+    line["unit_trace"] = unit_trace_summary(ctx.batch_trace_read(), batches[0][6], tr_info)
+    ctx.batch_trace(0)
     tuned, trials = ctx.batch_schedules()
     line["config"]["schedules"] = {f"n{t['n']}_L{t['L']}": f"G{t['G']}w{t['warps']}" for t in tuned}
     line["config"]["batch_plans"] = ctx.batch_plans

@@ -209,6 +209,22 @@ int qfs_dataflow_trace_enable(qfs_ctx* ctx, int64_t capacity);
 int qfs_dataflow_trace_read(qfs_ctx* ctx, uint64_t* out, int64_t capacity, int32_t* steps, int32_t* S,
                             int64_t* items);
 
+/* Unit time stamps of the batched form's persistent sweep (a measurement aid;
+ * the paper has no counterpart).  qfs_batch_trace_enable allocates room for
+ * `capacity` stamps on the device (0 frees it and turns tracing off); while
+ * enabled, every batched run whose units x 4 stamps fit records, per unit
+ * (one problem and the starts that one warp sweeps to the end), the device
+ * global timer (ns) when a warp took the unit and when it finished it, the
+ * problem index, and (SM << 32) | (first start << 16) | (starts << 8) |
+ * lanes per start.  Units are laid out launch by launch (one persistent
+ * launch per lanes-per-start shape), each launch's units largest problem
+ * first; the whole-batch plan check of a new class mix traces each plan it
+ * times, and the last run is the one kept.  qfs_batch_trace_read copies the
+ * stamps of the last traced run, [unit][4], to out (host, capacity entries;
+ * may be NULL to query *units only). */
+int qfs_batch_trace_enable(qfs_ctx* ctx, int64_t capacity);
+int qfs_batch_trace_read(qfs_ctx* ctx, uint64_t* out, int64_t capacity, int64_t* units);
+
 /* The method's own random draws (host only, no GPU): the M training states
  * (Section 3 and Appendix A: columns of a Haar-random unitary, here the Q
  * factor with positive R diagonal of a complex Gaussian N x M matrix) and

@@ -629,7 +629,18 @@ __global__ void k_batch_sweep(BatchArgs a, const BatchUnit* units, int nunits, i
     if (lane == 0) item = atomicAdd(queue, 1);
     item = __shfl_sync(FULL, item, 0);
     if (item >= nunits) break;
+    const unsigned long long t0 = a.unit_trace ? globaltimer_ns() : 0ull;
     batch_run_unit<G>(a, units[item], region, sm_polar[warp]);
+    if (a.unit_trace && lane == 0) {
+      const BatchUnit u = units[item];
+      unsigned sm;
+      asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+      unsigned long long* r = a.unit_trace + 4 * (size_t)item;
+      r[0] = t0;
+      r[1] = globaltimer_ns();
+      r[2] = (unsigned long long)u.p;
+      r[3] = ((unsigned long long)sm << 32) | ((unsigned long long)u.s0 << 16) | ((unsigned)u.ns << 8) | G;
+    }
   }
 }
 

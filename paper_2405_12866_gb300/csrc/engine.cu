@@ -103,6 +103,9 @@ struct qfs_ctx {
   size_t df_trace_n = 0;
   int df_trace_steps = 0, df_trace_S = 0;  // shape of the last traced sweep
   long long df_trace_items = 0;            // work items with stamps in that sweep (0: none)
+  unsigned long long* bt_trace = nullptr;  // device buffer for batched unit stamps (qfs_batch_trace_*)
+  size_t bt_trace_n = 0;
+  long long bt_units = 0;                  // units with stamps in the last traced batched run
   double df_item_bytes = 1024.0 * 1024.0;  // largest streaming bytes of one dataflow work item (QFS_DF_ITEM_KB)
   double df_items_per_cta = 1.5;           // work items per CTA and backward step (QFS_DF_ITEMS_PER_CTA)
   double df_items_per_cta_fwd = 1.0;       // ... and forward step (QFS_DF_ITEMS_PER_CTA_FWD)
@@ -1556,12 +1559,45 @@ int qfs_dataflow_trace_read(qfs_ctx* ctx, uint64_t* out, int64_t capacity, int32
   return QFS_OK;
 }
 
+int qfs_batch_trace_enable(qfs_ctx* ctx, int64_t capacity) {
+  g_err.clear();
+  TRY(ctx_check(ctx));
+  if (capacity < 0) return fail(QFS_EINVAL, "capacity = %lld", (long long)capacity);
+  TRY(set_device(ctx));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (ctx->bt_trace) CK(cudaFree(ctx->bt_trace));
+  ctx->bt_trace = nullptr;
+  ctx->bt_trace_n = 0;
+  ctx->bt_units = 0;
+  if (capacity > 0) {
+    CK(cudaMalloc(&ctx->bt_trace, sizeof(unsigned long long) * (size_t)capacity));
+    CK(cudaMemset(ctx->bt_trace, 0, sizeof(unsigned long long) * (size_t)capacity));
+    ctx->bt_trace_n = (size_t)capacity;
+  }
+  return QFS_OK;
+}
+
+int qfs_batch_trace_read(qfs_ctx* ctx, uint64_t* out, int64_t capacity, int64_t* units) {
+  g_err.clear();
+  TRY(ctx_check(ctx));
+  if (!units) return fail(QFS_EINVAL, "units must be given");
+  *units = ctx->bt_units;
+  const size_t n = (size_t)ctx->bt_units * 4;
+  if (!out || n == 0) return QFS_OK;
+  if ((size_t)capacity < n) return fail(QFS_EINVAL, "capacity %lld < %zu stamps", (long long)capacity, n);
+  TRY(set_device(ctx));
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaMemcpy(out, ctx->bt_trace, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost));
+  return QFS_OK;
+}
+
 void qfs_destroy(qfs_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->df_trace) cudaFree(ctx->df_trace);
+  if (ctx->bt_trace) cudaFree(ctx->bt_trace);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
   if (ctx->h_draw) cudaFreeHost(ctx->h_draw);
   for (int k = 0; k < 2; ++k)
@@ -2387,6 +2423,8 @@ int batch_common(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls, 
       launches.swap(sorted);
     }
     if ((int)launches.size() > 60) return fail(QFS_EUNSUPPORTED, "too many launch shapes (%d)", (int)launches.size());
+    unsigned long long* trace = ctx->bt_trace && ctx->bt_trace_n >= 4 * units.size() ? ctx->bt_trace : nullptr;
+    if (ctx->bt_trace) ctx->bt_units = trace ? (long long)units.size() : 0;
     CK(cudaMemcpyAsync(units_dev, units.data(), sizeof(BatchUnit) * units.size(), cudaMemcpyHostToDevice, st));
     // The graph: queue reset, set-up, one persistent launch per shape (on
     // parallel branches), the finishing kernel.  Replayed while the batch's
@@ -2404,6 +2442,7 @@ int batch_common(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls, 
       key = fnv1a(key, launches.data(), sizeof(Launch) * launches.size());
       const int mm[] = {p->M, max_elems, max_L};
       key = fnv1a(key, mm, sizeof(mm));
+      key = fnv1a(key, &trace, sizeof(trace));
     }
     // With per-launch timing on, the graph carries this call's event records:
     // it is captured, replayed once, harvested and dropped.
@@ -2438,7 +2477,9 @@ int batch_common(qfs_ctx* ctx, int32_t P, const int32_t* ns, const int32_t* Ls, 
         if (e != cudaSuccess) break;
         {
           ProfScope ps(ctx, QFS_PROF_BATCH, 0.0, ls);
-          launch_batch_sweep(L.G, a, units_dev + L.unit0, L.nunits, a.queue + li, blocks, L.warps, L.region, ls);
+          BatchArgs al = a;
+          al.unit_trace = trace ? trace + 4 * (size_t)L.unit0 : nullptr;
+          launch_batch_sweep(L.G, al, units_dev + L.unit0, L.nunits, a.queue + li, blocks, L.warps, L.region, ls);
         }
         if (li > 0) {
           e = cudaEventRecord(ctx->gevent[gs], ls);

@@ -17,6 +17,13 @@ template <typename T> struct C2;
 template <> struct C2<float>  { using t = float2;  };
 template <> struct C2<double> { using t = double2; };
 
+// The device's global timer (ns), for the trace stamps.
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 template <typename T2> __device__ __forceinline__ T2 cmul(T2 a, T2 b) {
   return T2{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }

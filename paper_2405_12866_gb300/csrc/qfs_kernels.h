@@ -238,6 +238,10 @@ struct BatchArgs {
   int* res_refine;
   int refine_max;
   int refine_unconverged;  // also refine problems whose starts never reached tol
+  // Non-null: 4 stamps per unit of this launch, indexed as its units are
+  // (taken, finished (global timer, ns), problem, (SM << 32) | (first start
+  // << 16) | (starts << 8) | lanes per start).
+  unsigned long long* unit_trace;
 };
 
 // A unit of the batched sweep: problem p and its starts s0 .. s0 + ns - 1,

@@ -49,7 +49,7 @@ EXPORTS = [
     "qfs_ws_loss_grad", "qfs_ws_train", "qfs_ws_predict",
     "qfs_dataflow_trace_enable", "qfs_dataflow_trace_read", "qfs_target_product_dev",
     "qfs_set_option", "qfs_get_option", "qfs_batch_sweep_once", "qfs_ws_instantiate",
-    "qfs_batch_schedules",
+    "qfs_batch_schedules", "qfs_batch_trace_enable", "qfs_batch_trace_read",
 ]
 (PROF_BACKWARD, PROF_FORWARD, PROF_UPDATE, PROF_GEMM, PROF_RESIDUAL, PROF_CHECK, PROF_OTHER, PROF_BATCH,
  PROF_MLP, PROF_DATAFLOW) = range(10)
@@ -132,6 +132,8 @@ def lib():
     L.qfs_dataflow_trace_enable.argtypes = [_P, C.c_int64]
     L.qfs_dataflow_trace_read.argtypes = [_P, _P, C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                           C.POINTER(C.c_int64)]
+    L.qfs_batch_trace_enable.argtypes = [_P, C.c_int64]
+    L.qfs_batch_trace_read.argtypes = [_P, _P, C.c_int64, C.POINTER(C.c_int64)]
     L.qfs_sweep_once_noalloc.argtypes = [_P, C.POINTER(Circuit), _P, _P, C.c_int32, C.c_int32,
                                          C.c_double, _P, _P, _P, _P]
     L.qfs_profile_enable.argtypes = [_P, C.c_int]
@@ -513,6 +515,26 @@ class Context:
         steps = out[:st.value * S.value * 4].reshape(st.value, S.value, 4)
         items = out[st.value * S.value * 4:].reshape(it.value, 4) if it.value else None
         return steps, items
+
+    def batch_trace(self, capacity: int):
+        """Record unit time stamps of batched runs (capacity stamps, 4 per unit; 0: off)."""
+        _check(lib().qfs_batch_trace_enable(self._h, capacity))
+
+    def batch_trace_read(self):
+        """Stamps of the last traced batched run as a dict of per-unit arrays:
+        t0, t1 (ns, unit taken and finished), problem, sm, s0 (first start),
+        starts, G (lanes per start)."""
+        nu = C.c_int64()
+        _check(lib().qfs_batch_trace_read(self._h, None, 0, C.byref(nu)))
+        out = np.zeros(4 * nu.value, dtype=np.uint64)
+        if nu.value:
+            _check(lib().qfs_batch_trace_read(self._h, out.ctypes.data, out.size, C.byref(nu)))
+        r = out.reshape(-1, 4)
+        return dict(t0=r[:, 0].copy(), t1=r[:, 1].copy(), problem=r[:, 2].astype(np.int64),
+                    sm=(r[:, 3] >> np.uint64(32)).astype(np.int64),
+                    s0=((r[:, 3] >> np.uint64(16)) & np.uint64(0xffff)).astype(np.int64),
+                    starts=((r[:, 3] >> np.uint64(8)) & np.uint64(0xff)).astype(np.int64),
+                    G=(r[:, 3] & np.uint64(0xff)).astype(np.int64))
 
     def profile(self, enable: bool):
         _check(lib().qfs_profile_enable(self._h, int(enable)))

@@ -222,3 +222,36 @@ def test_batch_plateau_stops_stuck_starts_early():
     if stuck0 and stuck1:
         assert np.mean(stuck1) < np.mean(stuck0)
     ctx.close()
+
+
+def test_batch_unit_trace_covers_every_start_once(ctx):
+    """The unit trace of a batched run: every (problem, start) is swept by
+    exactly one traced unit, each unit's stamps are ordered and its shape is
+    a valid schedule; tracing leaves the answers bit for bit unchanged."""
+    import torch
+    probs = w.uneven_blocks(P=64, seed=31, S=8)
+    S = 8
+    _, _, g_off, i_off = _run(ctx, probs, S, 60)
+    ctx.batch_trace(1 << 16)
+    try:
+        _, _, g_on, i_on = _run(ctx, probs, S, 60)
+        tr = ctx.batch_trace_read()
+    finally:
+        ctx.batch_trace(0)
+    assert all(np.array_equal(a, b) for a, b in zip(g_off, g_on))
+    assert i_off == i_on
+    nu = len(tr["t0"])
+    assert nu > 0
+    seen = np.zeros((len(probs), S), dtype=int)
+    for k in range(nu):
+        G, ns, s0, p = int(tr["G"][k]), int(tr["starts"][k]), int(tr["s0"][k]), int(tr["problem"][k])
+        assert G in (4, 8, 16, 32) and 1 <= ns <= 32 // G
+        assert 0 <= p < len(probs) and 0 <= s0 and s0 + ns <= S
+        seen[p, s0:s0 + ns] += 1
+    assert np.all(seen == 1)
+    assert np.all(tr["t0"] > 0) and np.all(tr["t1"] >= tr["t0"])
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert np.all(tr["sm"] < sms)
+    # off again: nothing recorded for the next run
+    _run(ctx, probs[:4], S, 10)
+    assert len(ctx.batch_trace_read()["t0"]) == 0
