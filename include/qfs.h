@@ -376,8 +376,9 @@ int qfs_instantiate_batch_dev(qfs_ctx* ctx, int32_t P, const int32_t* ns, const 
  * plan_ms (cap x 3 doubles, may be NULL): per class mix whose per-class
  * shapes were not all warp-per-start, the plan kept (0: per-class shapes,
  * 1: one start per warp everywhere, 2: 16 lanes per start wherever a class
- * admits it) and the timed ms of the three (-1: not timed, when plan 2 is
- * plan 0); *n_plans: their number.  At most cap rows are written. */
+ * admits it) and each plan's median ms over three interleaved timed runs
+ * (-1: not timed, when plan 2 is plan 0); *n_plans: their number.  At most
+ * cap rows are written. */
 int qfs_batch_schedules(qfs_ctx* ctx, int32_t cap, int32_t* tuned, int32_t* n_tuned, int32_t* trials,
                         double* trial_ns, int32_t* n_trials, int32_t* plan_choice, double* plan_ms,
                         int32_t* n_plans);
