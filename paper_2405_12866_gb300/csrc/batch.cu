@@ -33,12 +33,15 @@ namespace qfs {
 
 namespace {
 
-// As warp_polar4_f32 (polar4.cuh), but the Jacobi starts from the right singular vectors
-// V0 of the gate's previous update (16 complex at v_io, V[r][c] at 4c + r):
-// X = A V0, whose columns are already nearly orthogonal once the sweeps
-// settle, so fewer rotation sweeps are needed.  The new V, made unitary to
-// FP32 rounding by one Newton-Schulz step (so that no drift accumulates over
-// sweeps), is written back to v_io.
+// Polar factor in FP32 (batched complex64 sweeps) of A (lanes 0..15, A[r][c]
+// at 4c + r): one-sided Jacobi on X = A V0, V0 the right singular vectors of
+// the gate's previous update (16 complex at v_io, V[r][c] at 4c + r), whose
+// columns are already nearly orthogonal once the sweeps settle, so few
+// rotation sweeps are needed.  The new V, made unitary to FP32 rounding by
+// one Newton-Schulz step (so that no drift accumulates over sweeps), is
+// written back to v_io.  Returns false when sigma_min < 1e-3 sigma_max (the
+// caller then takes the FP64 Jacobi, which also completes rank-deficient
+// cases).
 __device__ __forceinline__ bool warp_polar4_f32_warm(float2 a, float2* v_io, float2* q_out) {
   const int lane = threadIdx.x & 31;
   const int l16 = lane & 15, row = l16 & 3, col = l16 >> 2;

@@ -298,8 +298,9 @@ __device__ __forceinline__ float2 skew_correction(float2 k32, float2 v, float si
 // tighter test keeps rotating rounding noise.  Columns orthogonal to 1e-6
 // leave the polar factor within ~1e-6 of the exact one; the polar factor
 // maximises Re tr(g E) over unitary g, so that error changes the objective
-// only at second order (1e-12), and the Newton-Schulz steps that follow
-// make the factor unitary to their own precision.
+// only at second order (1e-12).  The FP64 updates follow with Newton-Schulz
+// steps that make the factor unitary to FP64 precision; the batched form
+// keeps the FP32 factor and makes its answer unitary in FP64 at the end.
 constexpr float kJac32Tol = 1e-12f;
 
 // True when every column pair of X (lanes 0..15) has |gamma|^2 <= kJac32Tol
@@ -501,36 +502,6 @@ __device__ __forceinline__ bool warp_polar4_fast(double2 a, double2 v0, double2*
   }
   *p_out = q;
   if (v_out && lane < 16) v_out[l16] = double2{(double)v.x, (double)v.y};
-  return true;
-}
-
-// Polar factor in FP32 (batched complex64 sweeps): A (lanes 0..15, A[r][c]
-// at 4c + r, FP32), Jacobi from the identity, Q = W V^H, one Newton-Schulz
-// step.  Returns false when sigma_min < 1e-3 sigma_max (the caller then
-// takes the FP64 Jacobi, which also completes rank-deficient cases).
-__device__ __forceinline__ bool warp_polar4_f32(float2 a, float2* q_out) {
-  const int lane = threadIdx.x & 31;
-  const int l16 = lane & 15, row = l16 & 3, col = l16 >> 2;
-  const bool isV = lane >= 16;
-  float2 x = isV ? float2{row == col ? 1.f : 0.f, 0.f} : a;
-  x = jacobi32_sweeps(x);
-  float2 w = shfl_c(x, l16);
-  const float2 v = shfl_c(x, 16 + l16);
-  float nrm = w.x * w.x + w.y * w.y;
-  nrm += __shfl_xor_sync(FULL, nrm, 1);
-  nrm += __shfl_xor_sync(FULL, nrm, 2);
-  float smax = nrm, smin = nrm;
-  smax = fmaxf(smax, __shfl_xor_sync(FULL, smax, 4));
-  smax = fmaxf(smax, __shfl_xor_sync(FULL, smax, 8));
-  smin = fminf(smin, __shfl_xor_sync(FULL, smin, 4));
-  smin = fminf(smin, __shfl_xor_sync(FULL, smin, 8));
-  if (!(smin > 1e-6f * smax)) return false;
-  const float inv = rsqrtf(nrm);
-  w = float2{w.x * inv, w.y * inv};
-  float2 q = mm_bh(w, v, row, col);
-  const float2 gq = mm_ah(q, q, row, col);
-  const float2 t{(row == col ? 1.5f : 0.f) - 0.5f * gq.x, -0.5f * gq.y};
-  *q_out = mm(q, t, row, col);
   return true;
 }
 
