@@ -377,28 +377,43 @@ class Context:
     def instantiate_batch(self, problems, params: Params, samples=None, init_gates=None):
         """problems: list of (n, pairs, U).  samples/init_gates: lists per problem or None
         (drawn from params.seed + index).  Returns (list of (L,4,4) gates, list of dicts)."""
-        P = len(problems)
         ns = np.array([pr[0] for pr in problems], dtype=np.int32)
         Ls = np.array([len(pr[1]) for pr in problems], dtype=np.int32)
-        pairs = np.ascontiguousarray(np.concatenate([np.asarray(pr[1], dtype=np.int32).reshape(-1)
-                                                     for pr in problems]))
-        targets = np.ascontiguousarray(np.concatenate([_host_c128(pr[2]).reshape(-1) for pr in problems]))
-        sm = None if samples is None else np.ascontiguousarray(
-            np.concatenate([_host_c128(x).reshape(-1) for x in samples]))
-        ig = None if init_gates is None else np.ascontiguousarray(
-            np.concatenate([_host_c128(x).reshape(-1) for x in init_gates]))
-        out = np.zeros(int(Ls.sum()) * 16, dtype=np.complex128)
+        pairs = np.concatenate([np.asarray(pr[1], dtype=np.int32).reshape(-1) for pr in problems])
+        targets = np.concatenate([_host_c128(pr[2]).reshape(-1) for pr in problems])
+        sm = None if samples is None else np.concatenate([_host_c128(x).reshape(-1) for x in samples])
+        ig = None if init_gates is None else np.concatenate([_host_c128(x).reshape(-1) for x in init_gates])
+        out, info = self.instantiate_batch_packed(ns, Ls, pairs, targets, sm, ig, params)
+        offs = np.concatenate([[0], np.cumsum(Ls * 16)])
+        return [out[offs[i]:offs[i + 1]].reshape(Ls[i], 4, 4) for i in range(len(problems))], info
+
+    def instantiate_batch_packed(self, ns, Ls, pairs, targets, samples, init_gates, params: Params, out=None):
+        """qfs_instantiate_batch on packed host arrays, laid out as
+        instantiate_batch_dev takes them: ns, Ls, pairs int32; targets, samples,
+        init_gates complex128, problem after problem (samples and init_gates may
+        be None: drawn from params.seed + index).  The library copies straight
+        from these arrays (by DMA when they are pinned).  out: optional host
+        complex128 array of Ls.sum() * 16 for the gates.  Returns (out, list of
+        per-problem dicts)."""
+        ns = np.ascontiguousarray(ns, dtype=np.int32)
+        Ls = np.ascontiguousarray(Ls, dtype=np.int32)
+        pairs = np.ascontiguousarray(pairs, dtype=np.int32)
+        targets = np.ascontiguousarray(targets, dtype=np.complex128)
+        sm = None if samples is None else np.ascontiguousarray(samples, dtype=np.complex128)
+        ig = None if init_gates is None else np.ascontiguousarray(init_gates, dtype=np.complex128)
+        P = len(ns)
+        if out is None:
+            out = np.zeros(int(Ls.sum()) * 16, dtype=np.complex128)
+        elif out.dtype != np.complex128 or not out.flags.c_contiguous or out.size != int(Ls.sum()) * 16:
+            raise ValueError("out must be a contiguous complex128 array of Ls.sum() * 16 entries")
         res = (Result * P)()
         _check(lib().qfs_instantiate_batch(self._h, P, ns.ctypes.data, Ls.ctypes.data, pairs.ctypes.data,
                                            targets.ctypes.data, sm.ctypes.data if sm is not None else None,
                                            ig.ctypes.data if ig is not None else None, C.byref(params),
                                            out.ctypes.data, res))
-        gates, offs = [], np.concatenate([[0], np.cumsum(Ls * 16)])
-        for i in range(P):
-            gates.append(out[offs[i]:offs[i + 1]].reshape(Ls[i], 4, 4))
         info = [dict(cost=r.cost, sweeps=r.sweeps, converged=bool(r.converged), best_start=r.best_start,
                      fp64_sweeps=r.fp64_sweeps, training_states=r.training_states) for r in res]
-        return gates, info
+        return out, info
 
     def batch_schedules(self):
         """The batched form's tuned shapes: (list of dicts per class, list of

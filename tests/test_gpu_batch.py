@@ -255,3 +255,27 @@ def test_batch_unit_trace_covers_every_start_once(ctx):
     # off again: nothing recorded for the next run
     _run(ctx, probs[:4], S, 10)
     assert len(ctx.batch_trace_read()["t0"]) == 0
+
+
+def test_packed_host_entry_equals_list_entry(ctx):
+    """The packed host entry (flat arrays, here in pinned memory) returns the
+    list entry's answers bit for bit: both are the same C-ABI call."""
+    import torch
+    from paper_2405_12866_gb300 import qfs
+    probs = w.uneven_blocks(P=48, seed=17, S=4)
+    S = 4
+    _, _, g_list, i_list = _run(ctx, probs, S, 80)
+    ns = np.array([p.n for p in probs], dtype=np.int32)
+    Ls = np.array([p.L for p in probs], dtype=np.int32)
+    pairs = np.concatenate([np.asarray(p.pairs, dtype=np.int32).reshape(-1) for p in probs])
+    packed = [np.concatenate([np.asarray(x, dtype=np.complex128).reshape(-1) for x in xs])
+              for xs in ([p.U for p in probs], [p.samples() for p in probs], [p.init_gates()[:S] for p in probs])]
+    pinned = [torch.from_numpy(x).pin_memory().numpy() for x in packed]
+    prm = qfs.default_params(M=0, multistarts=S, max_sweeps=80, dist_tol=1e-8, refine_sweeps_max=20)
+    out, info = ctx.instantiate_batch_packed(ns, Ls, pairs, *pinned, prm)
+    assert info == i_list
+    offs = np.concatenate([[0], np.cumsum(Ls * 16)])
+    for i, g in enumerate(g_list):
+        assert np.array_equal(out[offs[i]:offs[i + 1]].reshape(-1, 4, 4), g)
+    with pytest.raises(ValueError):
+        ctx.instantiate_batch_packed(ns, Ls, pairs, *packed, prm, out=np.zeros(3, dtype=np.complex128))
