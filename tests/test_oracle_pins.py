@@ -544,3 +544,21 @@ def test_generalisation_error_against_the_full_cost():
     want = o.full_cost(p.U, G, p.pairs, p.n) / (1 << p.n) / c_train - 1.0
     got = o.generalisation_error(p.U @ Pv, Pv, G, p.pairs, p.n, c_train)
     assert abs(got - want) < 1e-12 * max(1.0, abs(want))
+
+
+@pytest.mark.parametrize("n,pair", [(2, (0, 1)), (2, (1, 0)), (3, (0, 2)), (4, (3, 1)), (5, (2, 4))])
+def test_pair_major_view_round_trip_and_row_order(n, pair):
+    """pair_major groups a state's rows by the two qubits' bits (row 2*bit_a +
+    bit_b, qubit q = bit n-1-q of the row index) and from_pair_major undoes
+    it; each entry is checked against that definition directly."""
+    M = 3
+    rng = np.random.default_rng(n)
+    X = rng.standard_normal((1 << n, M)) + 1j * rng.standard_normal((1 << n, M))
+    P = o.pair_major(X, n, pair)
+    assert P.shape == (4, (1 << n) // 4 * M)
+    assert np.array_equal(o.from_pair_major(P, n, pair, M), X)
+    a, b = pair
+    for r in range(1 << n):
+        loc = 2 * ((r >> (n - 1 - a)) & 1) + ((r >> (n - 1 - b)) & 1)
+        # the entries of row r land in row loc of the view, in the same sample order
+        assert any(np.array_equal(P[loc, k * M:(k + 1) * M], X[r]) for k in range((1 << n) // 4))
